@@ -1,0 +1,400 @@
+"""Throughput of the rational-program hot path on one GB300 (or N, weak scaling).
+
+A step is one pass of the whole path over the batched workload: fit all
+10,000 kernels x 8 metrics (80,000 rational fits, 50-2000 noisy samples each,
+about 82 M samples, 1.31 GB of FP32 samples in HBM), then evaluate the fitted
+rational program for 64 data sizes x 51 block shapes per kernel and choose the
+argmin (640,000 queries, 32.6 M evaluations).  The metric is argmin queries
+per second of whole steps.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl klr|reference]
+Under torchrun each rank runs its own seeded copy of the workload (weak
+scaling, no data-path collective) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(name="batched_fit_eval_fp32", kernels=10000, metrics=8, counts=(50, 2000),
+                noise=0.01, degree=2, n_vars=3, n_hi_log2=23, sizes_per_kernel=64, n_cfg=51)
+METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="klr", choices=["klr", "reference"])
+    ap.add_argument("--seed", type=int, default=2024)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-kernels", type=int, default=0,
+                    help="kernels in the bounded oracle sample (0: auto)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_inputs(seed):
+    import workloads as W
+    wl = WORKLOAD
+    fb = W.fit_batch(seed, wl["kernels"], wl["counts"], n_vars=wl["n_vars"], degree=wl["degree"],
+                     n_hi_log2=wl["n_hi_log2"], noise=wl["noise"], dtype=np.float32)
+    q = W.queries_per_kernel(wl["kernels"], W.log_spaced_sizes(wl["sizes_per_kernel"]))
+    return fb, q
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# oracle baseline (bounded sample, one host thread)
+# ---------------------------------------------------------------------------
+def oracle_worker(seed, groups):
+    """Time the oracle on groups of kernels (one group per step); prints JSON.
+    Runs in a child process with one BLAS/OpenMP thread."""
+    import workloads as W
+    from oracle import configs as ocfg
+    from oracle import program as oprog
+    from oracle import rational
+    wl = WORKLOAD
+    cfgs = ocfg.enumerate_configs(wl["n_vars"] - 1)
+    sizes = W.log_spaced_sizes(wl["sizes_per_kernel"])
+    out = []
+    for kernels in groups:
+        fb = W.fit_batch(seed, wl["kernels"], wl["counts"], n_vars=wl["n_vars"],
+                         degree=wl["degree"], n_hi_log2=wl["n_hi_log2"], noise=wl["noise"],
+                         dtype=np.float32, kernels=kernels)
+        t0 = time.perf_counter()
+        coef, _, _ = rational.fit_batch(fb.offsets, fb.x.astype(np.float64),
+                                        fb.y.astype(np.float64), wl["n_vars"], wl["degree"],
+                                        wl["n_hi_log2"], 10)
+        t1 = time.perf_counter()
+        q = W.queries_per_kernel(len(kernels), sizes)
+        prog = dict(coef=coef.reshape(len(kernels), 8, -1), regs=fb.truth.regs,
+                    smem=fb.truth.smem, n_vars=wl["n_vars"], degree=wl["degree"],
+                    n_scale_log2=wl["n_hi_log2"], b_scale_log2=10, metric_lo=W.METRIC_LO,
+                    metric_scale=W.METRIC_SCALE)
+        oprog.choose(prog, W.HARDWARE, cfgs, q.offsets, q.sizes)
+        t2 = time.perf_counter()
+        out.append(dict(fit_s=t1 - t0, eval_s=t2 - t1, kernels=len(kernels),
+                        samples=int(fb.offsets[-1]), n_queries=int(len(q.sizes))))
+    print(json.dumps(out))
+
+
+def oracle_steps(seed, n_groups, per_group):
+    """Run oracle_worker in a fresh single-threaded process; list of step records."""
+    import workloads as W
+    ids = W.subsample_kernels(seed + 7, WORKLOAD["kernels"], n_groups * per_group)
+    groups = [ids[i * per_group:(i + 1) * per_group].tolist() for i in range(n_groups)]
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
+            f"bench.oracle_worker({seed}, {groups!r})")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode:
+        raise RuntimeError("oracle worker failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def whole_step_seconds(rec):
+    """A whole step at the oracle's measured per-kernel cost (fits and queries
+    scale with the number of kernels)."""
+    return (rec["fit_s"] + rec["eval_s"]) * WORKLOAD["kernels"] / rec["kernels"]
+
+
+def oracle_baseline(seed, n_kernels_sample):
+    rec = oracle_steps(seed, 1, n_kernels_sample)[0]
+    n_q = WORKLOAD["kernels"] * WORKLOAD["sizes_per_kernel"]
+    step_s = whole_step_seconds(rec)
+    return dict(value=n_q / step_s, unit="queries/s", cores=1, kind="oracle",
+                sample=(f"{rec['kernels']} of {WORKLOAD['kernels']} kernels "
+                        f"({8 * rec['kernels']} fits, {rec['samples']} samples, "
+                        f"{rec['n_queries']} queries): fit {rec['fit_s']:.2f} s + evaluate "
+                        f"{rec['eval_s']:.2f} s on 1 host thread, scaled by kernel count"),
+                step_s=step_s)
+
+
+# ---------------------------------------------------------------------------
+# the library arm
+# ---------------------------------------------------------------------------
+def run_klr(args):
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1911_02373_gb300 as klr
+    import workloads as W
+
+    seed = args.seed + 1000 * rank
+    fb, q = make_inputs(seed)
+    wl = WORKLOAD
+    n_fits, n_q = fb.n_fits, len(q.sizes)
+    dev = torch.device("cuda", local)
+    ctx = klr.Context(local)
+    ctx.reserve(n_fits, n_q)
+    off_h = torch.from_numpy(fb.offsets).pin_memory()
+    x_h = torch.from_numpy(np.ascontiguousarray(fb.x)).pin_memory()
+    y_h = torch.from_numpy(fb.y).pin_memory()
+    qo_h = torch.from_numpy(q.offsets).pin_memory()
+    qn_h = torch.from_numpy(q.sizes).pin_memory()
+    off, x, y = off_h.to(dev), x_h.to(dev), y_h.to(dev)
+    qo, qn = qo_h.to(dev), qn_h.to(dev)
+    regs = torch.from_numpy(fb.truth.regs).to(dev)
+    smem = torch.from_numpy(fb.truth.smem).to(dev)
+    cfg = torch.from_numpy(klr.enumerate_configs(2)).to(dev)
+    hw = klr.make_hw(W.HARDWARE)
+    m = klr._n_monomials(3, 2)
+    coef = torch.empty((n_fits, 2 * m), device=dev, dtype=torch.float32)
+    fst = torch.empty(n_fits, device=dev, dtype=torch.int32)
+    fdg = torch.empty((n_fits, 4), device=dev, dtype=torch.float64)
+    best = torch.empty(n_q, device=dev, dtype=torch.int32)
+    cyc = torch.empty(n_q, device=dev, dtype=torch.float32)
+    mrg = torch.empty(n_q, device=dev, dtype=torch.float32)
+    qst = torch.empty(n_q, device=dev, dtype=torch.int32)
+    lp = torch.empty((n_q, 6), device=dev, dtype=torch.int32)
+    prog = klr.Context.program(coef.view(wl["kernels"], 8, 2 * m), regs, smem, n_vars=3,
+                               degree=2, n_scale_log2=23, b_scale_log2=10,
+                               metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+
+    def fit(xx, yy, oo):
+        ctx.fit(oo, xx, yy, n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10,
+                precision=klr.FIT_DF32, refine_iters=0, coef_dtype=klr.F32,
+                out=(coef, fst, fdg))
+
+    def choose(qoo, qnn):
+        ctx.argmin(prog, hw, cfg, qoo, qnn, out_dtype=klr.F32, out=(best, cyc, mrg, qst, lp))
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        fit(x, y, off)
+        choose(qo, qn)
+    torch.cuda.synchronize()
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(K):
+        ev[k][0].record(stream)
+        fit(x, y, off)
+        ev[k][1].record(stream)
+        choose(qo, qn)
+        ev[k][2].record(stream)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ck = clocks.stop()
+    total_ms = start.elapsed_time(stop)
+    fit_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
+    eval_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    ms_step = total_ms / K
+    if dist:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    fit_status = fst.cpu().numpy()
+    q_status = qst.cpu().numpy()
+
+    # end to end through the public API: pinned host inputs in, results out
+    E = args.e2e_steps
+    best_h = torch.empty(n_q, dtype=torch.int32).pin_memory()
+    cyc_h = torch.empty(n_q, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(E):
+        off.copy_(off_h, non_blocking=True)
+        x.copy_(x_h, non_blocking=True)
+        y.copy_(y_h, non_blocking=True)
+        qo.copy_(qo_h, non_blocking=True)
+        qn.copy_(qn_h, non_blocking=True)
+        fit(x, y, off)
+        choose(qo, qn)
+        best_h.copy_(best, non_blocking=True)
+        cyc_h.copy_(cyc, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / E
+    h2d = sum(t.numel() * t.element_size() for t in (off_h, x_h, y_h, qo_h, qn_h))
+    d2h = best_h.numel() * 4 + cyc_h.numel() * 4
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return None
+    n_samples = int(fb.offsets[-1])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    fit_bytes = n_samples * 16 + (n_fits + 1) * 8 + n_fits * (2 * m * 4 + 4 + 32)
+    sm_max = (ck or {}).get("sm_max_mhz") or 2070.0
+    # double-FP32 moment accumulation: per sample and moment, three error-free
+    # sums (6 FP32 ops + 1 compensation add each), two products and one FMA
+    n_mom = 35
+    fit_ops = n_samples * n_mom * (3 * 7 + 3)
+    alu_peak = 152 * 128 * sm_max * 1e6   # FP32 lanes x clock: lane-ops/s
+    out = {
+        "metric": METRIC,
+        "value": ws * n_q / (ms_step * 1e-3),
+        "unit": "queries/s",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded rational ground truth, 1% noise)",
+        "config": {"workload": WORKLOAD["name"], "kernels": wl["kernels"], "fits": n_fits,
+                   "samples": n_samples, "queries": n_q, "configs": wl["n_cfg"],
+                   "evals": n_q * wl["n_cfg"], "fit_precision": "df32", "refine_iters": 0,
+                   "l2": "inputs larger than L2 (1.31 GB of samples per step)",
+                   "parallelism": f"replicas x{ws}"},
+        "fits_per_s": ws * n_fits / (ms_step * 1e-3),
+        "config_evals_per_s": ws * n_q * wl["n_cfg"] / (ms_step * 1e-3),
+        "kernel_ms": {"fit": fit_ms, "argmin": eval_ms},
+        "roofline": {"bound": "alu", "achieved": fit_ops / (fit_ms * 1e-3) / 1e12,
+                     "peak": alu_peak / 1e12, "unit": "Tops/s (FP32 lane-ops)",
+                     "frac": fit_ops / (fit_ms * 1e-3) / alu_peak, "traffic": None,
+                     "kernel": "fit_kernel (double-FP32 moments)",
+                     "hbm_gbs": fit_bytes / (fit_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": fit_bytes / (fit_ms * 1e-3) / 1e9 / hbm_peak,
+                     "peak_source": "FP32 lanes x max SM clock (unit counts)"},
+        "e2e": {"value": ws * n_q / (e2e_ms * 1e-3), "unit": "queries/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": 3 * K,
+        "clocks": ck,
+        "fit_status_nonzero": int(np.count_nonzero(fit_status & ~8)),
+        "ties_resolved": int(np.count_nonzero(q_status & 4)),
+    }
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    per = args.cpu_sample_kernels or 1
+    recs = oracle_steps(args.seed, args.warmup + args.steps, per)[args.warmup:]
+    step_s = float(np.mean([whole_step_seconds(r) for r in recs]))
+    n_q = WORKLOAD["kernels"] * WORKLOAD["sizes_per_kernel"]
+    value = n_q / step_s
+    cb = dict(value=value, unit="queries/s", cores=1, kind="oracle",
+              sample=(f"{per} kernel(s) per step ({8 * per} fits and {64 * per} queries of "
+                      f"{WORKLOAD['kernels']} kernels), {len(recs)} timed steps on 1 host "
+                      f"thread, scaled by kernel count"))
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded rational ground truth, 1% noise)",
+        "config": {"workload": WORKLOAD["name"], "kernels": WORKLOAD["kernels"]},
+        "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out:
+            print(json.dumps(out))
+        return
+    ws, rank, _ = dist_env()
+    cb = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        # before the first CUDA call: the oracle runs in a fresh process
+        try:
+            cb = oracle_baseline(args.seed, args.cpu_sample_kernels or 1200)
+            cb.pop("step_s")
+        except Exception as e:  # report, do not hide
+            cb = {"error": str(e)[-300:]}
+    out = run_klr(args)
+    if out is not None:
+        out["cpu_baseline"] = cb
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,241 @@
+/*
+ * klr.h -- C ABI of the GB300 rational-program library.
+ *
+ * The library implements the data-parallel hot path of the rational-program
+ * method for choosing CUDA launch parameters (KLARAPTOR, arXiv 1911.02373):
+ *
+ *   1. fitting each low-level performance metric as a rational function
+ *      p(N, b) / q(N, b) of the data size N and the block shape b, posed as the
+ *      linearised least-squares problem [M_p | -y M_q] c = 0 over monomial
+ *      design matrices (Section V-E; Section IV, step 2);
+ *   2. evaluating the resulting rational program -- fitted metrics, integer
+ *      occupancy (Fig. 1, Eq. 1), the MWP-CWP cycle model (Example 2) -- over
+ *      every candidate block shape, and choosing the constrained argmin
+ *      (Section IV, steps 4 and 5), returned as the six launch integers of the
+ *      paper's IO function (Section V-C).
+ *
+ * Conventions for every entry point:
+ *   - Pointers documented as "device" must point to memory of the context's
+ *     device (cudaMalloc'd or a PyTorch CUDA tensor); "host" pointers to host
+ *     memory.  The caller owns every array; the library never frees them.
+ *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and the call returns without synchronising, except where noted.
+ *   - Argument errors are detected on the host before anything is enqueued
+ *     and return KLR_EINVAL; nothing is written then.  Per-item problems (a
+ *     degenerate fit, a query without a usable configuration) do not fail the
+ *     call: they are reported in the per-item status arrays.
+ *   - A context's scratch memory is allocated by klr_ctx_reserve() or, when the
+ *     stream is not capturing a CUDA graph, grown on demand by the first call
+ *     that needs more.  During graph capture a call that would need to grow it
+ *     returns KLR_ENOMEM instead, so reserve before capturing.
+ *   - A context is used by one host thread at a time; calls sharing a context
+ *     on different streams must not overlap (they share its scratch memory).
+ */
+#ifndef KLR_H
+#define KLR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KLR_VERSION_MAJOR 0
+#define KLR_VERSION_MINOR 1
+
+/* ---- status codes ------------------------------------------------------ */
+typedef int32_t klr_status;
+#define KLR_OK        0
+#define KLR_EINVAL    1   /* bad argument (NULL pointer, bad size, bad enum)   */
+#define KLR_ECUDA     2   /* a CUDA runtime call failed; see klr_last_error()   */
+#define KLR_ENOMEM    3   /* scratch memory could not be provided               */
+#define KLR_ENOTSUP   4   /* valid but unsupported combination of options       */
+
+/* ---- element types ----------------------------------------------------- */
+#define KLR_F32 0
+#define KLR_F64 1
+
+/* ---- fit precision modes (how the Gram matrix is accumulated) ------------
+ * The Gram matrix G = A^T A of the design matrix A = [Phi | -y Phi] is built
+ * from the moment sums  sum_s y_s^k x_s^mu  (k = 0, 1, 2; mu over monomials of
+ * degree <= 2d), which determine every entry of G.  The small null-vector
+ * solve and the optional refinement passes are FP64 in every mode.
+ *   KLR_FIT_FP64: moments accumulated in FP64.
+ *   KLR_FIT_DF32: moments accumulated in double-FP32 (error-free transforms on
+ *                 FP32 pipes, ~2^-44 relative); needs KLR_F32 samples.  Exact
+ *                 products need sample coordinates that are powers of two; a
+ *                 fit with other coordinates is flagged KLR_FIT_INEXACT.
+ *   KLR_FIT_FP32: moments accumulated in plain FP32 (fast, inaccurate).
+ *   KLR_FIT_TF32, KLR_FIT_BF16: Gram products on tensor cores with operands
+ *                 rounded to TF32 / BF16, FP32 accumulation.               */
+#define KLR_FIT_FP64 0
+#define KLR_FIT_DF32 1
+#define KLR_FIT_FP32 2
+#define KLR_FIT_TF32 3
+#define KLR_FIT_BF16 4
+
+/* ---- per-fit status bits ------------------------------------------------- */
+#define KLR_FIT_OK              0
+#define KLR_FIT_EMPTY           1  /* no samples: coefficients are zero        */
+#define KLR_FIT_NONFINITE       2  /* NaN/Inf in the samples: coefficients zero */
+#define KLR_FIT_RANK_DEFICIENT  4  /* null space of dimension > 1 (estimated)  */
+#define KLR_FIT_INEXACT         8  /* DF32 with non-power-of-two coordinates    */
+#define KLR_FIT_SOLVE_FAILED   16  /* the FP64 factorisation broke down         */
+
+/* ---- per-query status bits ----------------------------------------------- */
+#define KLR_Q_OK             0
+#define KLR_Q_BAD_METRIC     1  /* some meaningful config had q(x) = 0 or a
+                                   non-finite metric; it was skipped           */
+#define KLR_Q_NONE_FEASIBLE  2  /* no meaningful configuration: best = -1      */
+#define KLR_Q_TIE_RESOLVED   4  /* FP32 near-tie re-decided in FP64            */
+
+typedef struct klr_ctx klr_ctx;
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * *out receives the context.  Returns KLR_EINVAL for a bad device index. */
+klr_status klr_ctx_create(klr_ctx** out, int device);
+
+/* Destroy a context and free its scratch memory (synchronises the device). */
+klr_status klr_ctx_destroy(klr_ctx* ctx);
+
+/* Pre-allocate scratch memory for up to `max_fits` fits and `max_queries`
+ * queries, so that later calls of that size allocate nothing (required before
+ * capturing calls into a CUDA graph).  Synchronous. */
+klr_status klr_ctx_reserve(klr_ctx* ctx, int64_t max_fits, int64_t max_queries);
+
+/* Message of the last error on this thread (static storage, never NULL). */
+const char* klr_last_error(void);
+
+/* Library version as major * 100 + minor. */
+int klr_version(void);
+
+/* ---- E1: the configuration set F -----------------------------------------
+ * Section IV (step 4 and its footnote) and Section V: the candidate block
+ * shapes are tuples of powers of two (b0[, b1[, b2]]) whose thread count T is
+ * a multiple of 32 with min_threads <= T <= max_threads, ordered by T, then by
+ * decreasing b0, then decreasing b1.  dims in 1..3.
+ * cfg_out: host, capacity `capacity` rows of 3 int32 (unused dims = 1), may
+ * be NULL to query the count; *count receives |F|.  Returns KLR_EINVAL when
+ * capacity < |F| and cfg_out is not NULL. */
+klr_status klr_enumerate_configs(int dims, int min_threads, int max_threads,
+                                 int32_t* cfg_out, int capacity, int* count);
+
+/* ---- F1-F4: batched rational fits ----------------------------------------
+ * Section V-E and Section IV step 2.  Fit f owns samples
+ * s in [offsets[f], offsets[f+1]).  Sample s has raw coordinates
+ * x[v * x_stride + s] (v = 0: N, v = 1..n_vars-1: b0, b1[, b2]) and value y[s].
+ * The monomial basis is every monomial of total degree <= degree in the scaled
+ * variables (N 2^-n_scale_log2, b 2^-b_scale_log2, ...), ordered by degree,
+ * then by decreasing exponent tuple; m = C(n_vars + degree, degree) monomials.
+ * The fitted coefficients c = (alpha_1..alpha_m, beta_1..beta_m) of
+ * p = sum alpha Phi and q = sum beta Phi are the least-squares null vector of
+ * the column-equilibrated design matrix A D, A = [Phi | -y Phi]: D scales
+ * column j by 2^-floor(e_j / 2), e_j the binary exponent (frexp) of the
+ * column's squared 2-norm; c = D v, normalised to unit 2-norm, with the
+ * denominator's constant coefficient positive (if it is below 1e-12 in
+ * magnitude, the largest-magnitude denominator coefficient is positive). */
+typedef struct klr_fit_batch {
+    int32_t n_fits;        /* >= 0                                           */
+    int32_t n_vars;        /* 3 (N, b0, b1) or 4 (N, b0, b1, b2)             */
+    int32_t degree;        /* total degree, 1..3                             */
+    int32_t n_scale_log2;  /* N is scaled by 2^-n_scale_log2                  */
+    int32_t b_scale_log2;  /* block dimensions are scaled by 2^-b_scale_log2  */
+    int32_t sample_dtype;  /* KLR_F32 or KLR_F64: element type of x and y    */
+    const int64_t* offsets;/* device, n_fits + 1, non-decreasing, >= 0        */
+    const void* x;         /* device, n_vars rows, row stride x_stride        */
+    int64_t x_stride;      /* elements between rows of x, >= offsets[n_fits]  */
+    const void* y;         /* device, y[s]                                    */
+    int32_t precision;     /* KLR_FIT_*                                        */
+    int32_t refine_iters;  /* FP64 refinement passes over the samples, 0..8   */
+} klr_fit_batch;
+
+/* coef_out: device, n_fits x 2m elements of coef_dtype (row-major).
+ * fit_status: device, n_fits int32 (KLR_FIT_* bits).
+ * fit_diag: device, n_fits x 4 doubles or NULL: (lambda_min / lambda_max of
+ *   the equilibrated Gram matrix, an estimate of its next-smallest eigenvalue
+ *   over lambda_max, rms of A c over the samples, refinement passes run). */
+klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* batch, void* coef_out,
+                   int32_t coef_dtype, int32_t* fit_status, double* fit_diag,
+                   void* stream);
+
+/* ---- E2-E5: the rational program ----------------------------------------- */
+
+/* Hardware parameters H.  Integer limits per SM feed the occupancy program of
+ * Fig. 1 / Eq. 1; the rest feed MWP-CWP (Example 2). */
+typedef struct klr_hw {
+    int32_t n_sm;                  /* number of SMs                            */
+    int32_t max_warps_per_sm;      /* W_max                                    */
+    int32_t regs_per_sm;           /* R_max (per SM)                           */
+    int32_t smem_per_sm;           /* Z_max, bytes per SM                      */
+    int32_t max_blocks_per_sm;     /* B_max                                    */
+    int32_t max_threads_per_block; /* T_max                                    */
+    double mem_latency;            /* cycles (Mem_LD)                          */
+    double mem_bandwidth;          /* bytes / second                           */
+    double clock_hz;               /* SM clock                                 */
+    double departure_delay_coal;   /* cycles between coalesced transactions    */
+    double departure_delay_uncoal; /* cycles between uncoalesced transactions  */
+} klr_hw;
+
+/* A rational program per kernel: eight fitted metrics, in the order
+ * comp_insts, coal_mem_insts, uncoal_mem_insts, synch_insts, coal_per_mw,
+ * uncoal_per_mw, load_bytes_per_warp, issue_cycles.  Metric i of a kernel is
+ * L_i = metric_lo[i] + metric_scale[i] * |p_i(x) / q_i(x)|, x the scaled
+ * (N, b...) point, p_i and q_i in the basis documented for klr_fit.
+ * coef_lo + metric_scale must make coal + uncoal >= 1. */
+typedef struct klr_program {
+    int32_t n_kernels;
+    int32_t n_vars;        /* 3 (2D blocks) or 4 (3D blocks)                 */
+    int32_t degree;        /* 1..3                                           */
+    int32_t n_scale_log2;
+    int32_t b_scale_log2;
+    int32_t coef_dtype;    /* KLR_F32 or KLR_F64                              */
+    const void* coef;      /* device, n_kernels x 8 x 2m                      */
+    const int32_t* regs;   /* device, n_kernels: registers per thread R       */
+    const int32_t* smem;   /* device, n_kernels: shared memory bytes/block Z  */
+    double metric_lo[8];
+    double metric_scale[8];
+} klr_program;
+
+/* Queries, grouped by kernel: kernel k asks for data sizes
+ * q_N[q_offsets[k] .. q_offsets[k+1]) (device arrays; q_offsets has
+ * n_kernels + 1 entries, non-decreasing, q_offsets[0] = 0). */
+typedef struct klr_queries {
+    const int64_t* q_offsets;
+    const int64_t* q_N;    /* data sizes, >= 1                               */
+    int64_t n_queries;     /* = q_offsets[n_kernels]                         */
+} klr_queries;
+
+/* Table mode: cycles of every (query, configuration) pair.
+ * cfg: device, n_cfg x 3 int32 block shapes (unused dims 1), n_cfg <= 256,
+ *   e.g. from klr_enumerate_configs.  A configuration is meaningful for a
+ *   query when B_active > 0, T <= T_max and every block dimension <= N
+ *   (footnote to Section IV step 4).
+ * cycles_out: device, n_queries x n_cfg of out_dtype; +inf where the
+ *   configuration is not meaningful or a metric is invalid.
+ * out_dtype selects the arithmetic: KLR_F32 evaluates in FP32, KLR_F64 in FP64.
+ */
+klr_status klr_eval(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
+                    const int32_t* cfg, int n_cfg, const klr_queries* q,
+                    void* cycles_out, int32_t out_dtype, void* stream);
+
+/* Argmin mode (Section IV step 5): per query the meaningful configuration of
+ * least cycles (ties: lowest index; none: -1).
+ * best_idx: device int32[n_queries]; best_cycles: device [n_queries] of
+ * out_dtype (+inf when none); margin: device float[n_queries] or NULL,
+ * (runner-up - best) / best (+inf with one candidate, 0 with none);
+ * q_status: device int32[n_queries] or NULL (KLR_Q_* bits);
+ * launch_out: device int32[n_queries x 6] or NULL: (gx, gy, gz, bx, by, bz)
+ * with g_i = ceil(N / b_i) for the used dimensions (Section V-A, V-C).
+ * With out_dtype KLR_F32 the sweep runs in FP32 and every query whose FP32
+ * runner-up lies within the FP32 error bound of its best is re-decided by
+ * FP64 evaluation of the tied configurations (KLR_Q_TIE_RESOLVED). */
+klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
+                      const int32_t* cfg, int n_cfg, const klr_queries* q,
+                      int32_t* best_idx, void* best_cycles, int32_t out_dtype,
+                      float* margin, int32_t* q_status, int32_t* launch_out,
+                      void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KLR_H */

@@ -16,8 +16,10 @@ normalisation):
   then by decreasing exponent tuple (graded lexicographic);
 * the homogeneous least-squares solution is the right singular vector of the
   column-equilibrated matrix A D for its smallest singular value, where D scales
-  column j by the power of two 2^-e_j with max_s |A_sj| in [2^(e_j-1), 2^e_j)
-  (exact in binary); c = D v, normalised to unit 2-norm;
+  column j by the power of two 2^-floor(e_j / 2), e_j the binary exponent
+  (frexp: sum_s A_sj^2 = f 2^e_j, f in [0.5, 1)) of the squared column norm, so
+  the scaled squared norms lie in [0.5, 2) and the scaling is exact in binary;
+  c = D v, normalised to unit 2-norm;
 * sign: the denominator's constant coefficient is positive; if it is below
   1e-12 in magnitude, the largest-magnitude denominator coefficient (first on
   ties) is positive;
@@ -84,15 +86,14 @@ def design_matrix(xs: np.ndarray, y: np.ndarray, exps: list) -> np.ndarray:
 
 
 def equilibration(A: np.ndarray) -> np.ndarray:
-    """Power-of-two column scales d_j = 2^-e_j, max_s |A_sj| in [2^(e_j-1), 2^e_j)."""
+    """Power-of-two column scales d_j = 2^-floor(e_j / 2), e_j = frexp exponent
+    of sum_s A_sj^2 (1 for an all-zero column)."""
     d = np.ones(A.shape[1])
-    if A.shape[0] == 0:
-        return d
-    colmax = np.abs(A).max(axis=0)
-    for j, c in enumerate(colmax):
-        if c > 0:
-            _, e = math.frexp(c)
-            d[j] = math.ldexp(1.0, -e)
+    for j in range(A.shape[1]):
+        sq = float(np.sum(A[:, j] * A[:, j]))
+        if sq > 0:
+            _, e = math.frexp(sq)
+            d[j] = math.ldexp(1.0, -(e // 2))
     return d
 
 
@@ -128,7 +129,9 @@ def fit_one(x: np.ndarray, y: np.ndarray, n_vars: int, degree: int,
         return np.zeros(u), FIT_NONFINITE, np.zeros(3)
     A = design_matrix(scale_variables(xr, n_scale_log2, b_scale_log2), y, exps)
     d = equilibration(A)
-    _, s, vt = np.linalg.svd(A * d, full_matrices=True)
+    # right singular vectors of A D (U is not needed; with fewer samples than
+    # unknowns the full V supplies the null space)
+    _, s, vt = np.linalg.svd(A * d, full_matrices=S < u)
     sfull = np.zeros(u)
     sfull[:len(s)] = s
     c = normalise(d * vt[-1], m)

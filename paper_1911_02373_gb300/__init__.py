@@ -1,0 +1,235 @@
+"""Python binding of the GB300 rational-program library (``include/klr.h``).
+
+Argument marshalling only: every step of the fit and of the evaluation runs in
+the library's CUDA kernels.  PyTorch provides device memory and the current
+stream.  Importing this package loads ``_lib/libklr.so`` and raises if it is
+missing (build it with ``python paper_1911_02373_gb300/build.py`` or
+``__graft_entry__.build()``); there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libklr.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first "
+                      "(python paper_1911_02373_gb300/build.py)")
+_lib = ctypes.CDLL(LIB_PATH)
+
+# status codes and enums of klr.h
+OK, EINVAL, ECUDA, ENOMEM, ENOTSUP = 0, 1, 2, 3, 4
+F32, F64 = 0, 1
+FIT_FP64, FIT_DF32, FIT_FP32, FIT_TF32, FIT_BF16 = 0, 1, 2, 3, 4
+FIT_OK, FIT_EMPTY, FIT_NONFINITE, FIT_RANK_DEFICIENT, FIT_INEXACT, FIT_SOLVE_FAILED = 0, 1, 2, 4, 8, 16
+Q_OK, Q_BAD_METRIC, Q_NONE_FEASIBLE, Q_TIE_RESOLVED = 0, 1, 2, 4
+
+#: every entry point declared in include/klr.h
+ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last_error",
+               "klr_version", "klr_enumerate_configs", "klr_fit", "klr_eval", "klr_argmin")
+
+
+class KlrError(RuntimeError):
+    def __init__(self, fn, status):
+        msg = _lib.klr_last_error().decode()
+        super().__init__(f"{fn} returned {status}: {msg}")
+        self.status = status
+
+
+class FitBatch(ctypes.Structure):
+    _fields_ = [("n_fits", ctypes.c_int32), ("n_vars", ctypes.c_int32),
+                ("degree", ctypes.c_int32), ("n_scale_log2", ctypes.c_int32),
+                ("b_scale_log2", ctypes.c_int32), ("sample_dtype", ctypes.c_int32),
+                ("offsets", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("x_stride", ctypes.c_int64), ("y", ctypes.c_void_p),
+                ("precision", ctypes.c_int32), ("refine_iters", ctypes.c_int32)]
+
+
+class Hw(ctypes.Structure):
+    _fields_ = [("n_sm", ctypes.c_int32), ("max_warps_per_sm", ctypes.c_int32),
+                ("regs_per_sm", ctypes.c_int32), ("smem_per_sm", ctypes.c_int32),
+                ("max_blocks_per_sm", ctypes.c_int32), ("max_threads_per_block", ctypes.c_int32),
+                ("mem_latency", ctypes.c_double), ("mem_bandwidth", ctypes.c_double),
+                ("clock_hz", ctypes.c_double), ("departure_delay_coal", ctypes.c_double),
+                ("departure_delay_uncoal", ctypes.c_double)]
+
+
+class Program(ctypes.Structure):
+    _fields_ = [("n_kernels", ctypes.c_int32), ("n_vars", ctypes.c_int32),
+                ("degree", ctypes.c_int32), ("n_scale_log2", ctypes.c_int32),
+                ("b_scale_log2", ctypes.c_int32), ("coef_dtype", ctypes.c_int32),
+                ("coef", ctypes.c_void_p), ("regs", ctypes.c_void_p), ("smem", ctypes.c_void_p),
+                ("metric_lo", ctypes.c_double * 8), ("metric_scale", ctypes.c_double * 8)]
+
+
+class Queries(ctypes.Structure):
+    _fields_ = [("q_offsets", ctypes.c_void_p), ("q_N", ctypes.c_void_p),
+                ("n_queries", ctypes.c_int64)]
+
+
+_vp = ctypes.c_void_p
+_lib.klr_last_error.restype = ctypes.c_char_p
+_lib.klr_version.restype = ctypes.c_int
+for _name, _args in {
+    "klr_ctx_create": [ctypes.POINTER(_vp), ctypes.c_int],
+    "klr_ctx_destroy": [_vp],
+    "klr_ctx_reserve": [_vp, ctypes.c_int64, ctypes.c_int64],
+    "klr_enumerate_configs": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, ctypes.c_int,
+                              ctypes.POINTER(ctypes.c_int)],
+    "klr_fit": [_vp, ctypes.POINTER(FitBatch), _vp, ctypes.c_int32, _vp, _vp, _vp],
+    "klr_eval": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
+                 ctypes.POINTER(Queries), _vp, ctypes.c_int32, _vp],
+    "klr_argmin": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
+                   ctypes.POINTER(Queries), _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp],
+}.items():
+    getattr(_lib, _name).argtypes = _args
+    getattr(_lib, _name).restype = ctypes.c_int32
+
+
+def _check(fn, status):
+    if status != OK:
+        raise KlrError(fn, status)
+
+
+def version() -> int:
+    return _lib.klr_version()
+
+
+def enumerate_configs(dims: int, min_threads: int = 32, max_threads: int = 1024) -> np.ndarray:
+    """Configuration set F as an (|F|, 3) int32 array (unused dims are 1)."""
+    n = ctypes.c_int(0)
+    _check("klr_enumerate_configs",
+           _lib.klr_enumerate_configs(dims, min_threads, max_threads, None, 0, ctypes.byref(n)))
+    out = np.zeros((n.value, 3), dtype=np.int32)
+    _check("klr_enumerate_configs",
+           _lib.klr_enumerate_configs(dims, min_threads, max_threads,
+                                      out.ctypes.data_as(_vp), n.value, ctypes.byref(n)))
+    return out
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_hw(hw: dict) -> Hw:
+    return Hw(int(hw["n_sm"]), int(hw["max_warps_per_sm"]), int(hw["regs_per_sm"]),
+              int(hw["smem_per_sm"]), int(hw["max_blocks_per_sm"]),
+              int(hw["max_threads_per_block"]), float(hw["mem_latency"]),
+              float(hw["mem_bandwidth"]), float(hw["clock_hz"]),
+              float(hw["departure_delay_coal"]), float(hw["departure_delay_uncoal"]))
+
+
+class Context:
+    """A library context on one CUDA device (owns the scratch memory)."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        torch.cuda.init()
+        self.device = device
+        h = _vp()
+        _check("klr_ctx_create", _lib.klr_ctx_create(ctypes.byref(h), device))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.klr_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, max_fits: int, max_queries: int):
+        _check("klr_ctx_reserve", _lib.klr_ctx_reserve(self._h, max_fits, max_queries))
+
+    # -- F1-F4 ---------------------------------------------------------------
+    def fit(self, offsets, x, y, *, n_vars, degree, n_scale_log2, b_scale_log2,
+            precision=FIT_DF32, refine_iters=0, coef_dtype=None, out=None, stream=None):
+        """Fit every CSR fit.  offsets: int64 (F+1,); x: (n_vars, S) float32/64
+        rows (N, b0, b1[, b2]); y: (S,) same dtype.  Returns (coef, status, diag)
+        device tensors; ``out`` may pass preallocated (coef, status, diag)."""
+        import torch
+        sdt = F64 if x.dtype == torch.float64 else F32
+        cdt = sdt if coef_dtype is None else coef_dtype
+        n_fits = offsets.numel() - 1
+        m = _n_monomials(n_vars, degree)
+        if out is None:
+            coef = torch.empty((n_fits, 2 * m), device=x.device,
+                               dtype=torch.float64 if cdt == F64 else torch.float32)
+            status = torch.empty(n_fits, device=x.device, dtype=torch.int32)
+            diag = torch.empty((n_fits, 4), device=x.device, dtype=torch.float64)
+        else:
+            coef, status, diag = out
+        b = FitBatch(n_fits, n_vars, degree, n_scale_log2, b_scale_log2, sdt,
+                     offsets.data_ptr(), x.data_ptr(), x.stride(0), y.data_ptr(),
+                     precision, refine_iters)
+        _check("klr_fit", _lib.klr_fit(self._h, ctypes.byref(b), _ptr(coef), cdt, _ptr(status),
+                                       _ptr(diag), _stream(stream)))
+        return coef, status, diag
+
+    # -- E1-E5 ---------------------------------------------------------------
+    @staticmethod
+    def program(coef, regs, smem, *, n_vars, degree, n_scale_log2, b_scale_log2,
+                metric_lo, metric_scale) -> Program:
+        import torch
+        p = Program(regs.numel(), n_vars, degree, n_scale_log2, b_scale_log2,
+                    F64 if coef.dtype == torch.float64 else F32,
+                    coef.data_ptr(), regs.data_ptr(), smem.data_ptr())
+        for i in range(8):
+            p.metric_lo[i] = float(metric_lo[i])
+            p.metric_scale[i] = float(metric_scale[i])
+        p._keep = (coef, regs, smem)
+        return p
+
+    def eval(self, prog: Program, hw: Hw, cfg, q_offsets, q_N, out_dtype=F32, out=None,
+             stream=None):
+        """Cycles table (n_queries, n_cfg)."""
+        import torch
+        n_q = q_N.numel()
+        if out is None:
+            out = torch.empty((n_q, cfg.shape[0]), device=q_N.device,
+                              dtype=torch.float64 if out_dtype == F64 else torch.float32)
+        q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+        _check("klr_eval", _lib.klr_eval(self._h, ctypes.byref(prog), ctypes.byref(hw),
+                                         _ptr(cfg), cfg.shape[0], ctypes.byref(q), _ptr(out),
+                                         out_dtype, _stream(stream)))
+        return out
+
+    def argmin(self, prog: Program, hw: Hw, cfg, q_offsets, q_N, out_dtype=F32, out=None,
+               launch=True, stream=None):
+        """Per query: (best index, best cycles, margin, status, launch params)."""
+        import torch
+        n_q = q_N.numel()
+        dev = q_N.device
+        if out is None:
+            best = torch.empty(n_q, device=dev, dtype=torch.int32)
+            cyc = torch.empty(n_q, device=dev,
+                              dtype=torch.float64 if out_dtype == F64 else torch.float32)
+            margin = torch.empty(n_q, device=dev, dtype=torch.float32)
+            status = torch.empty(n_q, device=dev, dtype=torch.int32)
+            lp = torch.empty((n_q, 6), device=dev, dtype=torch.int32) if launch else None
+        else:
+            best, cyc, margin, status, lp = out
+        q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+        _check("klr_argmin", _lib.klr_argmin(self._h, ctypes.byref(prog), ctypes.byref(hw),
+                                             _ptr(cfg), cfg.shape[0], ctypes.byref(q),
+                                             _ptr(best), _ptr(cyc), out_dtype, _ptr(margin),
+                                             _ptr(status), _ptr(lp), _stream(stream)))
+        return best, cyc, margin, status, lp
+
+
+def _n_monomials(n_vars: int, degree: int) -> int:
+    from math import comb
+    return comb(n_vars + degree, degree)

@@ -1,0 +1,550 @@
+// E2-E5: evaluation of the rational program over every configuration and the
+// constrained argmin (Section IV, steps 4-5; Fig. 1 / Eq. 1; Example 2).
+//
+// Layout: a persistent grid walks the kernels of the program.  For its current
+// kernel a block
+//   1. stages the kernel's 8 x 2m coefficients in shared memory;
+//   2. specialises every metric to every configuration: with the block shape
+//      fixed, p(N, b) and q(N, b) become univariate polynomials in the scaled N
+//      (d + 1 coefficients each), folded once per (kernel, configuration);
+//   3. computes the occupancy cascade of Fig. 1 and Eq. 1 per configuration in
+//      integer arithmetic (B_active, W_active);
+// then each thread takes one query (data size N) and sweeps all
+// configurations: Horner evaluation of the 16 univariate polynomials, the
+// metric map L = lo + s |p/q|, the integer wave counts, MWP-CWP, and a running
+// top-4 of (cycles, index).  FP32 argmin queries whose runner-up lies within
+// the FP32 error window of the best are appended to a compact list and
+// re-decided by a second kernel in FP64 from the unspecialised program.
+#include <cfloat>
+#include <cmath>
+#include <type_traits>
+
+#include "klr_common.cuh"
+
+namespace klr {
+
+namespace {
+
+constexpr int kMaxCfg = 256;
+constexpr int kTopK = 4;
+// FP32 relative error window for the argmin decision (see the tie kernel).
+constexpr double kTieWindow = 5e-5;
+
+struct TieRecord {
+    int64_t q;
+    int32_t kernel;
+    int32_t n;                  // candidates, or -1 for a full FP64 sweep
+    int32_t cand[kTopK];
+};
+
+struct EvalParams {
+    int n_kernels, n_vars, dims, degree, m, u, n_scale_log2, b_scale_log2;
+    int coef_f64;
+    const void* coef;
+    const int32_t* regs;
+    const int32_t* smem;
+    double lo[8], sc[8];
+    int n_sm, W_max, R_max, Z_max, B_max, T_max;
+    double mem_ld, bw, freq, dep_c, dep_u;
+    int n_cfg;
+    const int32_t* cfg;
+    const int64_t* q_off;
+    const int64_t* q_N;
+    int64_t n_q;
+    int table;                  // 1: write cycles table, 0: argmin
+    void* cycles;               // table output
+    int32_t* best;
+    void* best_cycles;
+    float* margin;
+    int32_t* q_status;
+    int32_t* launch;
+    int* tie_count;
+    TieRecord* ties;
+    int64_t tie_cap;
+    uint8_t exps[kMaxBasis][kMaxVars];
+};
+
+// Fig. 1: B_active by the four tests in order; T > T_max fails to launch.
+__device__ __forceinline__ int active_blocks(long long T, long long R, long long Z,
+                                             const EvalParams& P) {
+    const long long Bm = P.B_max, Wm = P.W_max, Rm = P.R_max, Zm = P.Z_max;
+    if (T > P.T_max || T <= 0) return 0;
+    if (T * Bm <= 32 * Wm && R * T * Bm <= Rm && Z * Bm <= Zm) return (int)Bm;
+    if (32 * Wm <= T * Bm && 32 * Wm * R <= Rm && 32 * Wm * Z <= Zm * T) return (int)((32 * Wm) / T);
+    if (R > 0 && Rm <= R * T * Bm && Rm <= R * 32 * Wm && Rm * Z <= R * T * Zm)
+        return (int)(Rm / (R * T));
+    if (Z > 0 && Zm <= Bm * Z && Zm * T <= 32 * Wm * Z && Zm * R * T <= Z * Rm)
+        return (int)(Zm / Z);
+    return 0;
+}
+
+// MWP-CWP (Example 2; Hong and Kim's model) in precision T.
+template <typename T>
+__device__ __forceinline__ T mwpcwp(const T L[8], T Nw, T Bact, T active_sms, T rep,
+                                    const EvalParams& P) {
+    const T comp = L[0], coal = L[1], uncoal = L[2], synch = L[3];
+    const T coal_mw = L[4], uncoal_mw = L[5], load_bytes = L[6], issue = L[7];
+    const T mem_ld = (T)P.mem_ld, dep_c = (T)P.dep_c, dep_u = (T)P.dep_u;
+    const T one = T(1);
+    const T mem_l_uncoal = mem_ld + (uncoal_mw - one) * dep_u;
+    const T mem_l_coal = mem_ld + (coal_mw - one) * dep_c;
+    const T mem_insts = coal + uncoal;
+    const T w_u = uncoal / mem_insts;
+    const T w_c = coal / mem_insts;
+    const T mem_l = mem_l_uncoal * w_u + mem_l_coal * w_c;
+    const T departure = dep_u * uncoal_mw * w_u + dep_c * coal_mw * w_c;
+    const T mwp_nobw = mem_l / departure;
+    const T bw_per_warp = (T)P.freq * load_bytes / mem_l;
+    const T mwp_peakbw = (T)P.bw / (bw_per_warp * active_sms);
+    const T mwp = fmin(fmin(mwp_nobw, mwp_peakbw), Nw);
+    const T comp_cycles = issue * (comp + coal + uncoal);
+    const T mem_cycles = mem_l_uncoal * uncoal + mem_l_coal * coal;
+    const T cwp_full = (mem_cycles + comp_cycles) / comp_cycles;
+    const T cwp = fmin(cwp_full, Nw);
+    const T per_mem = comp_cycles / mem_insts * (mwp - one);
+    T e;
+    if (mwp == Nw && cwp == Nw) e = (mem_cycles + comp_cycles + per_mem) * rep;
+    else if (cwp >= mwp || comp_cycles > mem_cycles) e = (mem_cycles * Nw / mwp + per_mem) * rep;
+    else e = (mem_l + comp_cycles * Nw) * rep;
+    return e + departure * (mwp - one) * synch * Bact * rep;
+}
+
+__device__ __forceinline__ long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+// Full (unspecialised) FP64 evaluation of one (kernel, N, configuration):
+// the same algorithm as the oracle, used to re-decide FP32 near-ties.
+__device__ double eval_full_f64(const EvalParams& P, int k, long long N, int c, bool& usable) {
+    const int m = P.m, u = P.u, nv = P.n_vars;
+    const long long b0 = P.cfg[3 * c], b1 = P.cfg[3 * c + 1], b2 = P.cfg[3 * c + 2];
+    const long long T = b0 * b1 * b2;
+    const int B = active_blocks(T, P.regs[k], P.smem[k], P);
+    const int W = (int)min((long long)B * T / 32, (long long)P.W_max);
+    usable = B > 0 && T <= P.T_max && b0 <= N && (P.dims < 2 || b1 <= N) && (P.dims < 3 || b2 <= N);
+    if (!usable) return INFINITY;
+    double xs[kMaxVars];
+    xs[0] = ldexp((double)N, -P.n_scale_log2);
+    xs[1] = ldexp((double)b0, -P.b_scale_log2);
+    xs[2] = ldexp((double)b1, -P.b_scale_log2);
+    xs[3] = ldexp((double)b2, -P.b_scale_log2);
+    double L[8];
+    for (int i = 0; i < 8; ++i) {
+        double p = 0.0, q = 0.0;
+        for (int t = 0; t < m; ++t) {
+            double ph = 1.0;
+            for (int v = 0; v < nv; ++v)
+                for (int e = 0; e < P.exps[t][v]; ++e) ph *= xs[v];
+            double a, b;
+            if (P.coef_f64) {
+                const double* cf = reinterpret_cast<const double*>(P.coef) + ((int64_t)k * 8 + i) * u;
+                a = cf[t]; b = cf[m + t];
+            } else {
+                const float* cf = reinterpret_cast<const float*>(P.coef) + ((int64_t)k * 8 + i) * u;
+                a = cf[t]; b = cf[m + t];
+            }
+            p += a * ph;
+            q += b * ph;
+        }
+        double g = p / q;
+        if (q == 0.0 || !isfinite(g)) { usable = false; return INFINITY; }
+        L[i] = P.lo[i] + P.sc[i] * fabs(g);
+    }
+    const long long nb = ceil_div(N, T);
+    const long long asm_ = min((long long)P.n_sm, nb);
+    const long long rep = ceil_div(nb, max((long long)B * asm_, 1LL));
+    return mwpcwp<double>(L, (double)W, (double)B, (double)asm_, (double)rep, P);
+}
+
+__device__ void write_launch(const EvalParams& P, int64_t q, long long N, int c) {
+    if (!P.launch) return;
+    int32_t* o = P.launch + 6 * q;
+    if (c < 0) {
+        for (int i = 0; i < 6; ++i) o[i] = 0;
+        return;
+    }
+    const int b0 = P.cfg[3 * c], b1 = P.cfg[3 * c + 1], b2 = P.cfg[3 * c + 2];
+    o[0] = (int32_t)ceil_div(N, b0);
+    o[1] = P.dims >= 2 ? (int32_t)ceil_div(N, b1) : 1;
+    o[2] = P.dims >= 3 ? (int32_t)ceil_div(N, b2) : 1;
+    o[3] = b0;
+    o[4] = b1;
+    o[5] = b2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+eval_kernel(const __grid_constant__ EvalParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int d = P.degree, m = P.m, u = P.u, n_cfg = P.n_cfg;
+    const int NC = 2 * (d + 1);               // coefficients per (config, metric)
+    T* coef_s = reinterpret_cast<T*>(smem_raw);                 // 8 x u
+    T* spec = coef_s + 8 * u;                                   // n_cfg x 8 x NC
+    int* cinfo = reinterpret_cast<int*>(spec + (size_t)n_cfg * 8 * NC);  // n_cfg x 6
+    const T n_scale = (T)ldexp(1.0, -P.n_scale_log2);
+    T lo[8], sc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { lo[i] = (T)P.lo[i]; sc[i] = (T)P.sc[i]; }
+
+    for (int k = blockIdx.x; k < P.n_kernels; k += gridDim.x) {
+        const int64_t qa = P.q_off[k], qb = P.q_off[k + 1];
+        if (qa == qb) continue;
+        __syncthreads();   // previous kernel's tables no longer in use
+        for (int i = threadIdx.x; i < 8 * u; i += blockDim.x) {
+            if (P.coef_f64) coef_s[i] = (T)reinterpret_cast<const double*>(P.coef)[(int64_t)k * 8 * u + i];
+            else coef_s[i] = (T)reinterpret_cast<const float*>(P.coef)[(int64_t)k * 8 * u + i];
+        }
+        const int R = P.regs[k], Z = P.smem[k];
+        for (int c = threadIdx.x; c < n_cfg; c += blockDim.x) {
+            const long long b0 = P.cfg[3 * c], b1 = P.cfg[3 * c + 1], b2 = P.cfg[3 * c + 2];
+            const long long Tt = b0 * b1 * b2;
+            const int B = active_blocks(Tt, R, Z, P);
+            const int W = (int)min((long long)B * Tt / 32, (long long)P.W_max);
+            int* ci = cinfo + 6 * c;
+            ci[0] = (int)Tt;
+            ci[1] = (B > 0 && Tt <= P.T_max) ? B : 0;
+            ci[2] = W;
+            ci[3] = (int)b0;
+            ci[4] = P.dims >= 2 ? (int)b1 : 1;
+            ci[5] = P.dims >= 3 ? (int)b2 : 1;
+        }
+        __syncthreads();
+        // fold the block shape into univariate polynomials in the scaled N
+        for (int idx = threadIdx.x; idx < n_cfg * 8; idx += blockDim.x) {
+            const int c = idx >> 3, i = idx & 7;
+            T xb[3];
+            xb[0] = (T)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
+            xb[1] = (T)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
+            xb[2] = (T)ldexp((double)P.cfg[3 * c + 2], -P.b_scale_log2);
+            T acc[2][4];
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[s][j] = T(0);
+            for (int t = 0; t < m; ++t) {
+                T bm = T(1);
+                for (int v = 1; v < P.n_vars; ++v)
+                    for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
+                const int j = P.exps[t][0];
+                const T a = coef_s[i * u + t] * bm, b = coef_s[i * u + m + t] * bm;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if (jj == j) { acc[0][jj] += a; acc[1][jj] += b; }
+            }
+            T* sp = spec + (size_t)idx * NC;
+            for (int j = 0; j <= d; ++j) {
+                sp[j] = acc[0][j];
+                sp[d + 1 + j] = acc[1][j];
+            }
+        }
+        __syncthreads();
+
+        for (int64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) {
+            const long long N = P.q_N[q];
+            const T xN = (T)N * n_scale;
+            T topv[kTopK];
+            int topi[kTopK];
+#pragma unroll
+            for (int j = 0; j < kTopK; ++j) { topv[j] = (T)INFINITY; topi[j] = -1; }
+            int st = 0;
+            for (int c = 0; c < n_cfg; ++c) {
+                const int* ci = cinfo + 6 * c;
+                const int B = ci[1];
+                const bool meaningful = B > 0 && ci[3] <= N && ci[4] <= N && ci[5] <= N;
+                T e = (T)INFINITY;
+                if (meaningful) {
+                    const T* sp = spec + (size_t)c * 8 * NC;
+                    T L[8];
+                    bool valid = true;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const T* a = sp + i * NC;
+                        T p = a[d], qq = a[2 * d + 1];
+                        for (int j = d - 1; j >= 0; --j) {
+                            p = p * xN + a[j];
+                            qq = qq * xN + a[d + 1 + j];
+                        }
+                        const T g = p / qq;
+                        valid = valid && (qq != T(0)) && isfinite(g);
+                        L[i] = lo[i] + sc[i] * fabs(g);
+                    }
+                    if (valid) {
+                        const long long Tt = ci[0];
+                        const long long nb = ceil_div(N, Tt);
+                        const long long asm_ = min((long long)P.n_sm, nb);
+                        const long long rep = ceil_div(nb, (long long)B * asm_);
+                        e = mwpcwp<T>(L, (T)ci[2], (T)B, (T)asm_, (T)rep, P);
+                        if (!isfinite(e)) { e = (T)INFINITY; st |= KLR_Q_BAD_METRIC; }
+                    } else {
+                        st |= KLR_Q_BAD_METRIC;
+                    }
+                }
+                if (P.table) {
+                    reinterpret_cast<T*>(P.cycles)[q * n_cfg + c] = e;
+                } else if (e < topv[kTopK - 1]) {
+                    // insert into the sorted top-k; ties keep the lower index first
+                    T ve = e;
+                    int vi = c;
+#pragma unroll
+                    for (int j = 0; j < kTopK; ++j) {
+                        if (ve < topv[j]) {
+                            T tv = topv[j]; int ti = topi[j];
+                            topv[j] = ve; topi[j] = vi;
+                            ve = tv; vi = ti;
+                        }
+                    }
+                }
+            }
+            if (P.table) continue;
+            const int bi = topi[0];
+            if (bi < 0) st |= KLR_Q_NONE_FEASIBLE;
+            float mg = 0.f;
+            if (bi >= 0) mg = isfinite((float)topv[1]) ? (float)((topv[1] - topv[0]) / topv[0]) : INFINITY;
+            bool deferred = false;
+            if (std::is_same<T, float>::value && bi >= 0 && isfinite(topv[1]) &&
+                (double)topv[1] <= (double)topv[0] * (1.0 + kTieWindow)) {
+                // near-tie in FP32: hand the candidates to the FP64 re-decision
+                const int slot = atomicAdd(P.tie_count, 1);
+                if (slot < P.tie_cap) {
+                    TieRecord r;
+                    r.q = q;
+                    r.kernel = k;
+                    int n = 0;
+                    for (int j = 0; j < kTopK; ++j)
+                        if (topi[j] >= 0 && (double)topv[j] <= (double)topv[0] * (1.0 + kTieWindow))
+                            r.cand[n++] = topi[j];
+                    r.n = (n == kTopK) ? -1 : n;   // all top-k tied: re-sweep everything
+                    P.ties[slot] = r;
+                    deferred = true;
+                }
+                st |= KLR_Q_TIE_RESOLVED;
+                if (!deferred) {
+                    // scratch full: decide here in FP64 over every configuration
+                    double bv = INFINITY, sv = INFINITY;
+                    int bj = -1;
+                    for (int c = 0; c < n_cfg; ++c) {
+                        bool us;
+                        double v = eval_full_f64(P, k, N, c, us);
+                        if (v < bv) { sv = bv; bv = v; bj = c; }
+                        else if (v < sv) sv = v;
+                    }
+                    P.best[q] = bj;
+                    reinterpret_cast<float*>(P.best_cycles)[q] = (float)bv;
+                    if (P.margin) P.margin[q] = isfinite(sv) ? (float)((sv - bv) / bv) : INFINITY;
+                    if (P.q_status) P.q_status[q] = st;
+                    write_launch(P, q, N, bj);
+                    continue;
+                }
+            }
+            P.best[q] = bi;
+            reinterpret_cast<T*>(P.best_cycles)[q] = topv[0];
+            if (P.margin) P.margin[q] = mg;
+            if (P.q_status) P.q_status[q] = st;
+            write_launch(P, q, N, bi);
+        }
+    }
+}
+
+// Re-decide FP32 near-ties: FP64 evaluation of the tied candidates (or of
+// every configuration) with the unspecialised program, lowest index on ties.
+__global__ void __launch_bounds__(128)
+tie_kernel(const __grid_constant__ EvalParams P) {
+    const int64_t n = min((int64_t)*P.tie_count, P.tie_cap);
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const TieRecord rec = P.ties[r];
+        const long long N = P.q_N[rec.q];
+        double bv = INFINITY, sv = INFINITY;
+        int bj = -1;
+        const int cnt = rec.n < 0 ? P.n_cfg : rec.n;
+        // candidates are visited in increasing configuration index
+        int order[kTopK];
+        if (rec.n >= 0) {
+            for (int j = 0; j < cnt; ++j) order[j] = rec.cand[j];
+            for (int a = 1; a < cnt; ++a)
+                for (int b = a; b > 0 && order[b] < order[b - 1]; --b) {
+                    int t = order[b]; order[b] = order[b - 1]; order[b - 1] = t;
+                }
+        }
+        for (int j = 0; j < cnt; ++j) {
+            const int c = rec.n < 0 ? j : order[j];
+            bool us;
+            double v = eval_full_f64(P, rec.kernel, N, c, us);
+            if (v < bv) { sv = bv; bv = v; bj = c; }
+            else if (v < sv) sv = v;
+        }
+        P.best[rec.q] = bj;
+        reinterpret_cast<float*>(P.best_cycles)[rec.q] = (float)bv;
+        if (P.margin) P.margin[rec.q] = isfinite(sv) ? (float)((sv - bv) / bv) : INFINITY;
+        write_launch(P, rec.q, N, bj);
+    }
+}
+
+int64_t tie_capacity(int64_t n_q) {
+    return std::max<int64_t>(65536, std::min<int64_t>(n_q, 1 << 22) / 4);
+}
+
+klr_status prepare(Context* c, const klr_program* prog, const klr_hw* hw, const int32_t* cfg,
+                   int n_cfg, const klr_queries* q, int out_dtype, EvalParams& P) {
+    KLR_REQUIRE(prog && hw && q, "klr_eval/argmin: NULL program, hw or queries");
+    KLR_REQUIRE(prog->n_kernels >= 0, "n_kernels < 0");
+    KLR_REQUIRE(prog->n_vars == 3 || prog->n_vars == 4, "n_vars %d not 3 or 4", prog->n_vars);
+    KLR_REQUIRE(prog->degree >= 1 && prog->degree <= 3, "degree %d not in 1..3", prog->degree);
+    KLR_REQUIRE(prog->coef_dtype == KLR_F32 || prog->coef_dtype == KLR_F64, "bad coef_dtype");
+    KLR_REQUIRE(out_dtype == KLR_F32 || out_dtype == KLR_F64, "bad out_dtype");
+    KLR_REQUIRE(n_cfg >= 1 && n_cfg <= kMaxCfg, "n_cfg %d not in 1..%d", n_cfg, kMaxCfg);
+    KLR_REQUIRE(q->n_queries >= 0, "n_queries < 0");
+    KLR_REQUIRE(hw->n_sm > 0 && hw->max_warps_per_sm > 0 && hw->regs_per_sm > 0 &&
+                hw->smem_per_sm >= 0 && hw->max_blocks_per_sm > 0 && hw->max_threads_per_block > 0,
+                "bad hardware limits");
+    KLR_REQUIRE(hw->mem_latency > 0 && hw->mem_bandwidth > 0 && hw->clock_hz > 0 &&
+                hw->departure_delay_coal > 0 && hw->departure_delay_uncoal > 0,
+                "bad hardware timing parameters");
+    for (int i = 0; i < 8; ++i)
+        KLR_REQUIRE(std::isfinite(prog->metric_lo[i]) && std::isfinite(prog->metric_scale[i]),
+                    "non-finite metric map");
+    if (prog->n_kernels > 0 && q->n_queries > 0)
+        KLR_REQUIRE(prog->coef && prog->regs && prog->smem && cfg && q->q_offsets && q->q_N,
+                    "NULL device array");
+    Basis basis;
+    KLR_REQUIRE(make_basis(prog->n_vars, prog->degree, &basis), "no basis");
+    memset(&P, 0, sizeof(P));
+    P.n_kernels = prog->n_kernels;
+    P.n_vars = prog->n_vars;
+    P.dims = prog->n_vars - 1;
+    P.degree = prog->degree;
+    P.m = basis.m;
+    P.u = 2 * basis.m;
+    P.n_scale_log2 = prog->n_scale_log2;
+    P.b_scale_log2 = prog->b_scale_log2;
+    P.coef_f64 = prog->coef_dtype == KLR_F64;
+    P.coef = prog->coef;
+    P.regs = prog->regs;
+    P.smem = prog->smem;
+    for (int i = 0; i < 8; ++i) { P.lo[i] = prog->metric_lo[i]; P.sc[i] = prog->metric_scale[i]; }
+    P.n_sm = hw->n_sm;
+    P.W_max = hw->max_warps_per_sm;
+    P.R_max = hw->regs_per_sm;
+    P.Z_max = hw->smem_per_sm;
+    P.B_max = hw->max_blocks_per_sm;
+    P.T_max = hw->max_threads_per_block;
+    P.mem_ld = hw->mem_latency;
+    P.bw = hw->mem_bandwidth;
+    P.freq = hw->clock_hz;
+    P.dep_c = hw->departure_delay_coal;
+    P.dep_u = hw->departure_delay_uncoal;
+    P.n_cfg = n_cfg;
+    P.cfg = cfg;
+    P.q_off = q->q_offsets;
+    P.q_N = q->q_N;
+    P.n_q = q->n_queries;
+    for (int t = 0; t < basis.m; ++t)
+        for (int v = 0; v < kMaxVars; ++v) P.exps[t][v] = basis.exps[t][v];
+    (void)c;
+    return KLR_OK;
+}
+
+size_t eval_smem_bytes(const EvalParams& P, size_t tsz) {
+    const int NC = 2 * (P.degree + 1);
+    size_t b = tsz * (8 * (size_t)P.u + (size_t)P.n_cfg * 8 * NC);
+    b = (b + 15) & ~(size_t)15;
+    return b + sizeof(int) * 6 * (size_t)P.n_cfg;
+}
+
+klr_status launch_eval(Context* c, EvalParams& P, bool f64, cudaStream_t stream) {
+    const size_t smem = eval_smem_bytes(P, f64 ? 8 : 4);
+    if (smem > c->smem_optin) {
+        set_error("evaluator needs %zu bytes of shared memory", smem);
+        return KLR_ENOTSUP;
+    }
+    // threads: enough for the queries of a typical kernel, in whole warps
+    const int64_t per_kernel = P.n_kernels ? (P.n_q + P.n_kernels - 1) / P.n_kernels : 1;
+    int threads = 32;
+    while (threads < 256 && threads < per_kernel) threads <<= 1;
+    int per_sm = 0;
+    if (f64) {
+        auto k = eval_kernel<double>;
+        KLR_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+        const int grid = (int)std::min<int64_t>(P.n_kernels, (int64_t)c->n_sm * std::max(per_sm, 1));
+        k<<<grid, threads, smem, stream>>>(P);
+    } else {
+        auto k = eval_kernel<float>;
+        KLR_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+        const int grid = (int)std::min<int64_t>(P.n_kernels, (int64_t)c->n_sm * std::max(per_sm, 1));
+        k<<<grid, threads, smem, stream>>>(P);
+    }
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+}  // namespace
+
+size_t workspace_bytes(int64_t max_fits, int64_t max_queries) {
+    (void)max_fits;
+    return 256 + sizeof(TieRecord) * (size_t)tie_capacity(max_queries);
+}
+
+}  // namespace klr
+
+using namespace klr;
+
+extern "C" {
+
+size_t klr_workspace_bytes(int64_t max_fits, int64_t max_queries) {
+    return workspace_bytes(max_fits, max_queries);
+}
+
+klr_status klr_eval(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw, const int32_t* cfg,
+                    int n_cfg, const klr_queries* q, void* cycles_out, int32_t out_dtype,
+                    void* stream_) {
+    KLR_REQUIRE(ctx, "klr_eval: NULL context");
+    Context* c = reinterpret_cast<Context*>(ctx);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    EvalParams P;
+    klr_status st = prepare(c, prog, hw, cfg, n_cfg, q, out_dtype, P);
+    if (st != KLR_OK) return st;
+    if (P.n_q == 0 || P.n_kernels == 0) return KLR_OK;
+    KLR_REQUIRE(cycles_out, "klr_eval: NULL cycles_out");
+    KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    P.table = 1;
+    P.cycles = cycles_out;
+    return launch_eval(c, P, out_dtype == KLR_F64, stream);
+}
+
+klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
+                      const int32_t* cfg, int n_cfg, const klr_queries* q, int32_t* best_idx,
+                      void* best_cycles, int32_t out_dtype, float* margin, int32_t* q_status,
+                      int32_t* launch_out, void* stream_) {
+    KLR_REQUIRE(ctx, "klr_argmin: NULL context");
+    Context* c = reinterpret_cast<Context*>(ctx);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    EvalParams P;
+    klr_status st = prepare(c, prog, hw, cfg, n_cfg, q, out_dtype, P);
+    if (st != KLR_OK) return st;
+    if (P.n_q == 0 || P.n_kernels == 0) return KLR_OK;
+    KLR_REQUIRE(best_idx && best_cycles, "klr_argmin: NULL best_idx or best_cycles");
+    KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    P.table = 0;
+    P.best = best_idx;
+    P.best_cycles = best_cycles;
+    P.margin = margin;
+    P.q_status = q_status;
+    P.launch = launch_out;
+    const bool f64 = out_dtype == KLR_F64;
+    if (!f64) {
+        st = ensure_workspace(c, workspace_bytes(0, P.n_q), stream);
+        if (st != KLR_OK) return st;
+        P.tie_count = reinterpret_cast<int*>(c->ws);
+        P.ties = reinterpret_cast<TieRecord*>(reinterpret_cast<char*>(c->ws) + 256);
+        P.tie_cap = tie_capacity(P.n_q);
+        KLR_CHECK_CUDA(cudaMemsetAsync(P.tie_count, 0, sizeof(int), stream));
+    }
+    st = launch_eval(c, P, f64, stream);
+    if (st != KLR_OK || f64) return st;
+    const int grid = (int)std::min<int64_t>((P.tie_cap + 127) / 128, (int64_t)c->n_sm * 4);
+    tie_kernel<<<grid, 128, 0, stream>>>(P);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+"""GPU parity of the evaluator (E1-E5) against the FP64 oracle, through the C ABI.
+
+Tolerances (stated by the design): cycles within 1e-4 relative for the FP32
+evaluator and 1e-10 for the FP64 one, compared where the oracle's branch
+decisions are clear of their thresholds (a piecewise boundary can flip between
+precisions; those points are counted, not compared); the usable pattern
+(occupancy > 0, T <= T_max, b_i <= N, valid metrics) bit-exact; argmin indices
+bit-exact wherever the oracle's best-versus-runner-up margin exceeds 1e-6.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from tests import gpu_cases as G
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def klr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_02373_gb300 as k
+    return k
+
+
+@pytest.fixture(scope="module")
+def ctx(klr):
+    return klr.Context(0)
+
+
+def _run(klr, ctx, gt, coef, q_offsets, q_sizes, dtype, table):
+    ct = torch.tensor(coef).cuda()
+    prog = G.gpu_program(klr, ct, gt, torch)
+    hw = klr.make_hw(W.HARDWARE)
+    cfg = torch.tensor(klr.enumerate_configs(gt.n_vars - 1)).cuda()
+    qo = torch.tensor(q_offsets).cuda()
+    qn = torch.tensor(q_sizes).cuda()
+    if table:
+        out = ctx.eval(prog, hw, cfg, qo, qn, out_dtype=dtype)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+    res = ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=dtype)
+    torch.cuda.synchronize()
+    return [None if r is None else r.cpu().numpy() for r in res]
+
+
+CASES = [
+    # (name, seed, kernels, n_vars, sizes)
+    ("single_2d", 5, 1, 3, W.query_sizes("pow2", 16)),
+    ("batched_2d", 6, 48, 3, W.log_spaced_sizes(64)),
+    ("sweep_3d", 7, 6, 4, W.log_spaced_sizes(256)),
+    ("ragged_small_N", 8, 9, 3, np.array([1, 2, 17, 31, 32, 33, 100, 1000, 65537, 1 << 23])),
+]
+
+
+@pytest.mark.parametrize("name,seed,nk,nv,sizes", CASES)
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_table_matches_oracle(klr, ctx, name, seed, nk, nv, sizes, dtype):
+    gt = G.make_program(seed, nk, n_vars=nv)
+    coef = gt.coef.astype(np.float32 if dtype == "f32" else np.float64)
+    q = W.queries_per_kernel(nk, sizes)
+    got = _run(klr, ctx, gt, coef, q.offsets, q.sizes, klr.F32 if dtype == "f32" else klr.F64, True)
+    ref = G.oracle_choose(coef, gt, q.offsets, q.sizes)
+    want = np.stack(ref["cycles"]) if isinstance(ref["cycles"], list) else ref["cycles"]
+    ref = dict(ref, cycles=want.reshape(len(q.sizes), -1),
+               boundary=ref["boundary"].reshape(len(q.sizes), -1))
+    tol, btol = (1e-4, 1e-5) if dtype == "f32" else (1e-10, 1e-12)
+    n, excl, mx = G.compare_table(got, ref, tol, btol)
+    assert n > 0 and excl <= 0.01 * n + 5
+
+
+@pytest.mark.parametrize("name,seed,nk,nv,sizes", CASES)
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_argmin_matches_oracle(klr, ctx, name, seed, nk, nv, sizes, dtype):
+    gt = G.make_program(seed, nk, n_vars=nv)
+    coef = gt.coef.astype(np.float32 if dtype == "f32" else np.float64)
+    q = W.queries_per_kernel(nk, sizes)
+    best, cyc, margin, status, launch = _run(klr, ctx, gt, coef, q.offsets, q.sizes,
+                                             klr.F32 if dtype == "f32" else klr.F64, False)
+    ref = G.oracle_choose(coef, gt, q.offsets, q.sizes)
+    ref["cycles"] = ref["cycles"].reshape(len(q.sizes), -1)
+    ref["boundary"] = ref["boundary"].reshape(len(q.sizes), -1)
+    tol, btol = (1e-4, 1e-5) if dtype == "f32" else (1e-10, 0.0)
+    strict, loose = G.compare_argmin(best, cyc, ref, tol, 1e-6, btol)
+    assert strict > 0
+    # status: none-feasible exactly where the oracle has no candidate
+    assert np.array_equal((status & klr.Q_NONE_FEASIBLE) != 0, ref["best"] < 0)
+    # launch parameters: (ceil(N/b0), ceil(N/b1), 1, b0, b1, 1) or 3D
+    cfg = klr.enumerate_configs(nv - 1)
+    for r in range(0, len(best), max(1, len(best) // 50)):
+        if best[r] < 0:
+            assert np.all(launch[r] == 0)
+            continue
+        b = cfg[best[r]]
+        N = int(q.sizes[r])
+        g = [-(-N // int(b[i])) if i < nv - 1 else 1 for i in range(3)]
+        assert list(launch[r]) == g + [int(v) for v in b]
+
+
+def test_all_infeasible_and_empty_kernels(klr, ctx):
+    gt = G.make_program(9, 3)
+    gt.regs[:] = np.array([4096, 32, 64], dtype=np.int32)   # kernel 0: no block fits
+    coef = gt.coef.astype(np.float32)
+    # kernel 1 has no queries
+    q_offsets = np.array([0, 4, 4, 7], dtype=np.int64)
+    q_sizes = np.array([1024, 4096, 1 << 20, 64, 1 << 16, 300, 7], dtype=np.int64)
+    best, cyc, margin, status, launch = _run(klr, ctx, gt, coef, q_offsets, q_sizes, klr.F32, False)
+    assert np.all(best[:4] == -1) and np.all(np.isinf(cyc[:4]))
+    assert np.all(status[:4] & klr.Q_NONE_FEASIBLE)
+    ref = G.oracle_choose(coef, gt, q_offsets, q_sizes)
+    assert np.array_equal(best, ref["best"])
+
+
+def test_bad_arguments_return_einval(klr, ctx):
+    gt = G.make_program(3, 1)
+    ct = torch.tensor(gt.coef.astype(np.float32)).cuda()
+    prog = G.gpu_program(klr, ct, gt, torch)
+    hw = klr.make_hw(W.HARDWARE)
+    cfg = torch.tensor(klr.enumerate_configs(2)).cuda()
+    qo = torch.tensor([0, 2]).cuda()
+    qn = torch.tensor([256, 512]).cuda()
+    bad = klr.make_hw(dict(W.HARDWARE, n_sm=0))
+    with pytest.raises(klr.KlrError) as e:
+        ctx.argmin(prog, bad, cfg, qo, qn)
+    assert e.value.status == klr.EINVAL
+    with pytest.raises(klr.KlrError):
+        ctx.eval(prog, hw, torch.zeros((300, 3), dtype=torch.int32).cuda(), qo, qn)

@@ -1,0 +1,177 @@
+"""GPU parity of the batched rational fit (F1-F4) against the FP64 oracle,
+through the C ABI.
+
+Tolerance, derived from the arithmetic: the library solves the eigenproblem of
+the Gram matrix G of the equilibrated design matrix, accumulated with unit
+roundoff eps_acc (2^-53 for FP64, about 2^-44 for DF32 pairs, 2^-24 for FP32).
+A perturbation E of G moves the null vector by about |E| / gap, with
+|E| <= c u eps_acc |G| and gap = (sigma_{u-1}^2 - sigma_u^2) / sigma_1^2 the
+relative eigen-gap the oracle reports.  Each FP64 refinement pass over the
+samples multiplies the error by about eps_acc kappa^2 again, down to the
+FP64 floor of the SVD itself (eps_64 times kappa).  The coefficient bound used
+below is  64 u eps_acc / gap  (no refinement) or that bound squared with the
+floor, and predictions on the evaluation grid follow the coefficients.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import rational
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+EPS = {"fp64": 2.0 ** -53, "df32": 2.0 ** -44, "fp32": 2.0 ** -24}
+
+
+@pytest.fixture(scope="module")
+def klr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_02373_gb300 as k
+    return k
+
+
+@pytest.fixture(scope="module")
+def ctx(klr):
+    return klr.Context(0)
+
+
+def gpu_fit(klr, ctx, fb, precision, refine=0, coef_dtype=None):
+    off = torch.tensor(fb.offsets).cuda()
+    x = torch.tensor(np.ascontiguousarray(fb.x)).cuda()
+    y = torch.tensor(fb.y).cuda()
+    coef, status, diag = ctx.fit(off, x, y, n_vars=fb.n_vars, degree=fb.degree,
+                                 n_scale_log2=fb.n_scale_log2, b_scale_log2=fb.b_scale_log2,
+                                 precision=precision, refine_iters=refine,
+                                 coef_dtype=klr.F64 if coef_dtype is None else coef_dtype)
+    torch.cuda.synchronize()
+    return coef.cpu().numpy().astype(np.float64), status.cpu().numpy(), diag.cpu().numpy()
+
+
+def bound(mode, u, gap, refine):
+    b = 64.0 * u * EPS[mode] / gap
+    for _ in range(refine):
+        b = b * min(1.0, 64.0 * u * EPS[mode] / gap)
+    return max(b, 1e-11)
+
+
+def check(fb, coef, status, mode, refine, ref=None):
+    oc, ost, od = ref if ref is not None else rational.fit_batch(
+        fb.offsets, fb.x.astype(np.float64), fb.y.astype(np.float64), fb.n_vars, fb.degree,
+        fb.n_scale_log2, fb.b_scale_log2)
+    u = coef.shape[1]
+    errs = []
+    for f in range(len(oc)):
+        if ost[f] & rational.FIT_RANK_DEFICIENT:
+            continue
+        assert (int(status[f]) & ~8) == int(ost[f]), (f, status[f], ost[f])
+        gap = max(od[f][1] ** 2 - od[f][0] ** 2, 1e-300)
+        err = float(np.max(np.abs(coef[f] - oc[f])))
+        errs.append(err)
+        assert err <= bound(mode, u, gap, refine), (f, err, bound(mode, u, gap, refine), gap)
+    return max(errs) if errs else 0.0
+
+
+def test_single_kernel_fp64_exact_recovery(klr, ctx):
+    fb = W.fit_batch(21, 1, 200, dtype=np.float64)
+    for refine in (0, 1):
+        coef, st, diag = gpu_fit(klr, ctx, fb, klr.FIT_FP64, refine)
+        assert np.all(st == 0)
+        m = coef.shape[1] // 2
+        truth = fb.truth.coef[0] / np.linalg.norm(fb.truth.coef[0], axis=1, keepdims=True)
+        truth *= np.sign(truth[:, m:m + 1])
+        assert np.max(np.abs(coef - truth)) <= (1e-8 if refine == 0 else 1e-10)
+        check(fb, coef, st, "fp64", refine)
+        assert np.all(diag[:, 3] == refine)
+
+
+def test_df32_noiseless_float32_samples(klr, ctx):
+    fb = W.fit_batch(22, 4, 300, dtype=np.float32)
+    coef, st, _ = gpu_fit(klr, ctx, fb, klr.FIT_DF32, 0)
+    assert np.all(st == 0)
+    check(fb, coef, st, "df32", 0)
+    coef1, st1, _ = gpu_fit(klr, ctx, fb, klr.FIT_DF32, 1)
+    check(fb, coef1, st1, "df32", 1)
+
+
+@pytest.mark.parametrize("mode", ["df32", "fp64"])
+def test_batched_noisy_ragged(klr, ctx, mode):
+    fb = W.fit_batch(23, 24, (50, 2000), noise=0.01, dtype=np.float32)
+    prec = klr.FIT_DF32 if mode == "df32" else klr.FIT_FP64
+    coef, st, _ = gpu_fit(klr, ctx, fb, prec, 0, coef_dtype=klr.F32)
+    # coefficients are returned in FP32: add its rounding to the bound
+    ref = rational.fit_batch(fb.offsets, fb.x.astype(np.float64), fb.y.astype(np.float64),
+                             3, 2, 23, 10)
+    oc, ost, od = ref
+    for f in range(len(oc)):
+        gap = max(od[f][1] ** 2 - od[f][0] ** 2, 1e-300)
+        err = np.max(np.abs(coef[f] - oc[f]))
+        assert err <= bound(mode, 20, gap, 0) + 2.0 ** -24, (f, err, gap)
+
+
+def test_degree3_refinement(klr, ctx):
+    fb = W.fit_batch(24, 2, 1500, degree=3, n_hi_log2=30, dtype=np.float64)
+    ref = rational.fit_batch(fb.offsets, fb.x, fb.y, 3, 3, 30, 10)
+    errs = []
+    for refine in (0, 1, 2):
+        coef, st, _ = gpu_fit(klr, ctx, fb, klr.FIT_FP64, refine)
+        errs.append(check(fb, coef, st, "fp64", refine, ref))
+    assert errs[2] <= errs[0]
+
+
+def test_3d_blocks_degree2(klr, ctx):
+    fb = W.fit_batch(25, 3, 400, n_vars=4, noise=0.01, dtype=np.float32)
+    coef, st, _ = gpu_fit(klr, ctx, fb, klr.FIT_DF32, 1)
+    check(fb, coef, st, "df32", 1)
+
+
+def test_fp32_mode_runs_and_reports(klr, ctx):
+    fb = W.fit_batch(26, 2, 500, noise=0.01, dtype=np.float32)
+    coef, st, diag = gpu_fit(klr, ctx, fb, klr.FIT_FP32, 2)
+    assert np.all(np.isfinite(coef))
+    assert np.allclose(np.linalg.norm(coef, axis=1), 1.0, atol=1e-12)
+
+
+def test_edge_cases(klr, ctx):
+    # fit 0 empty, fit 1 has a NaN, fit 2 all samples at one point, fit 3 too few,
+    # fit 4 a regular noiseless fit
+    base = W.fit_batch(27, 1, 60, dtype=np.float64)
+    xs, ys, offs = [], [], [0]
+    xs.append(np.zeros((3, 0))); ys.append(np.zeros(0))
+    x1 = base.x[:, :30].copy(); y1 = base.y[:30].copy(); y1[7] = np.nan
+    xs.append(x1); ys.append(y1)
+    xs.append(np.tile(np.array([[4096.0], [32.0], [4.0]]), (1, 50))); ys.append(np.full(50, 1.5))
+    xs.append(base.x[:, :12]); ys.append(base.y[:12])
+    xs.append(base.x[:, :60]); ys.append(base.y[:60])
+    for a in ys:
+        offs.append(offs[-1] + len(a))
+    fb = W.FitBatch(3, 2, 23, 10, np.array(offs, dtype=np.int64), np.hstack(xs), np.hstack(ys),
+                    base.truth)
+    coef, st, _ = gpu_fit(klr, ctx, fb, klr.FIT_FP64, 0)
+    assert st[0] == klr.FIT_EMPTY and np.all(coef[0] == 0)
+    assert st[1] == klr.FIT_NONFINITE and np.all(coef[1] == 0)
+    assert st[2] & klr.FIT_RANK_DEFICIENT
+    assert st[3] & klr.FIT_RANK_DEFICIENT
+    assert st[4] == 0
+    oc, ost, _ = rational.fit_batch(fb.offsets, fb.x, fb.y, 3, 2, 23, 10)
+    assert ost[0] == rational.FIT_EMPTY and ost[1] == rational.FIT_NONFINITE
+    assert np.max(np.abs(coef[4] - oc[4])) < 1e-7
+    # zero fits is a no-op
+    z = W.FitBatch(3, 2, 23, 10, np.zeros(1, dtype=np.int64), np.zeros((3, 1)), np.zeros(1),
+                   base.truth)
+    c0, s0, _ = gpu_fit(klr, ctx, z, klr.FIT_FP64, 0)
+    assert c0.shape == (0, 20)
+
+
+def test_bad_arguments(klr, ctx):
+    fb = W.fit_batch(28, 1, 50, dtype=np.float64)
+    with pytest.raises(klr.KlrError) as e:
+        gpu_fit(klr, ctx, fb, klr.FIT_DF32, 0)        # DF32 needs FP32 samples
+    assert e.value.status == klr.EINVAL
+    with pytest.raises(klr.KlrError) as e:
+        gpu_fit(klr, ctx, fb, klr.FIT_FP64, 9)
+    assert e.value.status == klr.EINVAL

@@ -87,12 +87,18 @@ def test_equilibration_power_of_two_and_range():
     rng = np.random.default_rng(4)
     A = rng.standard_normal((50, 6)) * np.ldexp(1.0, rng.integers(-40, 40, 6))
     A[:, 2] = 0.5
+    A[:, 3] = 0.0
     d = rational.equilibration(A)
     for j in range(6):
         m_, e = math.frexp(d[j])
         assert m_ == 0.5
-        mx = np.abs(A[:, j] * d[j]).max()
-        assert 0.5 <= mx < 1.0
+        if j == 3:
+            assert d[j] == 1.0
+            continue
+        sq = np.sum((A[:, j] * d[j]) ** 2)
+        assert 0.5 <= sq < 2.0
+    # column of fifty 0.5s: sum of squares 12.5 = 0.78 * 2^4 -> scale 2^-2
+    assert d[2] == 0.25
 
 
 def test_degree_zero_closed_form():
@@ -106,7 +112,8 @@ def test_degree_zero_closed_form():
     y = np.array([1.0, 2.0, 3.0, 5.0])
     c, st, _ = rational.fit_one(np.ones((3, 4)), y, 3, 0, 0, 0)
     A = np.stack([np.ones(4), -y], 1)
-    d = np.array([0.5, 0.125])   # max|A_:,0| = 1 -> 2^-1; max|A_:,1| = 5 -> 2^-3
+    # squared norms 4 = 0.5*2^3 -> 2^-1, 39 = 0.61*2^6 -> 2^-3
+    d = np.array([0.5, 0.125])
     G = (A * d).T @ (A * d)
     # closed form of the smallest eigenvector of a symmetric 2x2 matrix
     a, b, cc = G[0, 0], G[0, 1], G[1, 1]

@@ -252,17 +252,20 @@ def scale_points(x: np.ndarray, n_scale_log2: int, b_scale_log2: int) -> np.ndar
 
 def ground_truth(seed: int, n_kernels: int, n_vars: int = 3, degree: int = 2,
                  n_lo_log2: int = 8, n_hi_log2: int = 23, b_scale_log2: int = 10,
-                 q_floor: float = 0.5, max_attempts: int = 64) -> GroundTruth:
+                 q_floor: float = 0.5, max_attempts: int = 64, kernels=None) -> GroundTruth:
     """Coefficients U(-1,1), +3 on the denominator's constant term, redrawn
     (next attempt id) until min q >= q_floor over every block shape and every
-    N in [2^n_lo_log2, 2^n_hi_log2]."""
+    N in [2^n_lo_log2, 2^n_hi_log2].  ``kernels`` selects a subset of the
+    n_kernels kernel ids (same values as in the full set)."""
     exps = term_exponents(n_vars, degree)
     m = len(exps)
     shapes = block_shape_exponents(n_vars - 1)
     xb = np.ldexp(1.0, shapes - b_scale_log2)
     xlo, xhi = np.ldexp(1.0, n_lo_log2 - n_hi_log2), 1.0
+    kid = np.arange(n_kernels) if kernels is None else np.asarray(kernels, dtype=np.int64)
+    n_kernels = len(kid)
     total = n_kernels * N_METRICS
-    ids = np.arange(total, dtype=np.uint64)
+    ids = (kid[:, None] * N_METRICS + np.arange(N_METRICS)[None, :]).reshape(-1).astype(np.uint64)
     coef = np.empty((total, 2 * m))
     attempts = np.zeros(total, dtype=np.int32)
     todo = np.arange(total)
@@ -279,7 +282,7 @@ def ground_truth(seed: int, n_kernels: int, n_vars: int = 3, degree: int = 2,
             break
     if todo.size:
         raise RuntimeError(f"{todo.size} ground-truth functions failed the q floor")
-    rk = stream_keys(seed, (_S_RES,), np.arange(n_kernels, dtype=np.uint64))
+    rk = stream_keys(seed, (_S_RES,), kid.astype(np.uint64))
     regs = REGS_CHOICES[(words(rk, 0) % np.uint64(3)).astype(np.int64)]
     smem = SMEM_CHOICES[(words(rk, 1) % np.uint64(3)).astype(np.int64)]
     return GroundTruth(n_vars, degree, n_hi_log2, b_scale_log2,
@@ -312,7 +315,7 @@ class FitBatch:
 def fit_batch(seed: int, n_kernels: int, counts, n_vars: int = 3, degree: int = 2,
               n_lo_log2: int = 8, n_hi_log2: int = 23, b_scale_log2: int = 10,
               noise: float = 0.0, dtype=np.float32, replace: bool | None = None,
-              truth: GroundTruth | None = None) -> FitBatch:
+              truth: GroundTruth | None = None, kernels=None) -> FitBatch:
     """Samples for every (kernel, metric) of a seeded ground truth.
 
     ``counts``: an int (same count for every fit) or a (lo, hi) pair, meaning a
@@ -323,9 +326,11 @@ def fit_batch(seed: int, n_kernels: int, counts, n_vars: int = 3, degree: int = 
     """
     if truth is None:
         truth = ground_truth(seed, n_kernels, n_vars, degree, n_lo_log2, n_hi_log2,
-                             b_scale_log2)
-    n_fits = n_kernels * N_METRICS
-    fid = np.arange(n_fits, dtype=np.uint64)
+                             b_scale_log2, kernels=kernels)
+    kid = np.arange(n_kernels) if kernels is None else np.asarray(kernels, dtype=np.int64)
+    n_fits = len(kid) * N_METRICS
+    # global fit ids: the streams of a fit do not depend on which others are drawn
+    fid = (kid[:, None] * N_METRICS + np.arange(N_METRICS)[None, :]).reshape(-1).astype(np.uint64)
     if isinstance(counts, (tuple, list)):
         lo, hi = counts
         ck = stream_keys(seed, (_S_COUNTS,), fid)
@@ -341,7 +346,7 @@ def fit_batch(seed: int, n_kernels: int, counts, n_vars: int = 3, degree: int = 
     # sample index within its fit
     fit_of = np.repeat(np.arange(n_fits, dtype=np.int64), cnt)
     local = np.arange(S, dtype=np.int64) - offsets[:-1][fit_of]
-    keys = stream_keys(seed, (_S_SAMPLES,), np.arange(n_fits, dtype=np.uint64))
+    keys = stream_keys(seed, (_S_SAMPLES,), fid)
     use_replace = (cnt.max(initial=0) > grid) if replace is None else replace
     if use_replace:
         pt = (words(keys[fit_of], local.astype(np.uint64)) % np.uint64(grid)).astype(np.int64)
@@ -379,7 +384,7 @@ def fit_batch(seed: int, n_kernels: int, counts, n_vars: int = 3, degree: int = 
         s0, s1 = offsets[f0], offsets[f1]
         y[s0:s1] = g[fit_of[s0:s1] - f0, pt[s0:s1]]
     if noise:
-        nk = stream_keys(seed, (_S_NOISE,), np.arange(n_fits, dtype=np.uint64))
+        nk = stream_keys(seed, (_S_NOISE,), fid)
         y = y * (1.0 + noise * normal(nk[fit_of], local.astype(np.uint64)))
     return FitBatch(n_vars, degree, n_hi_log2, b_scale_log2, offsets,
                     x.astype(dtype), y.astype(dtype), truth)
