@@ -235,6 +235,36 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
                       float* margin, int32_t* q_status, int32_t* launch_out,
                       void* stream);
 
+/* Argmin without allocation.  The paper has no counterpart: this entry point
+ * serves callers that cannot allocate device memory -- a launch hook that
+ * picks block shapes right before each kernel launch (a cudaMalloc there would
+ * synchronise the application), code that runs while a stream captures a CUDA
+ * graph, or a process whose device memory is owned by another allocator.
+ *
+ * Same computation and outputs as klr_argmin with out_dtype KLR_F32 (best_cycles
+ * is float[n_queries]), on the current CUDA device, without a context.  Its
+ * scratch (a tie counter and KLR_ARGMIN_NOALLOC_TIE_RECORDS tie records, about
+ * 512 KiB) is a static device array of the library, held by every GPU that loads
+ * the library until the process exits.  The call allocates nothing: it makes no
+ * cudaMalloc, cudaFree or allocating library call.
+ *
+ * Limits and caveats:
+ *   - n_queries must not exceed KLR_ARGMIN_NOALLOC_MAX_QUERIES; larger calls
+ *     return KLR_EINVAL and enqueue nothing.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) and caches it; make that first call before any
+ *     stream capture.
+ *   - Every call on a device shares the one array, which keeps the previous
+ *     call's contents (the call zeroes the counter it needs).  Calls that overlap
+ *     on the GPU -- on different streams, or from several host threads --
+ *     race on it; serialise them. */
+#define KLR_ARGMIN_NOALLOC_MAX_QUERIES 65536
+#define KLR_ARGMIN_NOALLOC_TIE_RECORDS 16384
+klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw,
+                              const int32_t* cfg, int n_cfg, const klr_queries* q,
+                              int32_t* best_idx, float* best_cycles, float* margin,
+                              int32_t* q_status, int32_t* launch_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,7 +30,10 @@ Q_OK, Q_BAD_METRIC, Q_NONE_FEASIBLE, Q_TIE_RESOLVED = 0, 1, 2, 4
 
 #: every entry point declared in include/klr.h
 ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last_error",
-               "klr_version", "klr_enumerate_configs", "klr_fit", "klr_eval", "klr_argmin")
+               "klr_version", "klr_enumerate_configs", "klr_fit", "klr_eval", "klr_argmin",
+               "klr_argmin_noalloc")
+#: largest query count klr_argmin_noalloc accepts
+ARGMIN_NOALLOC_MAX_QUERIES = 65536
 
 
 class KlrError(RuntimeError):
@@ -85,6 +88,8 @@ for _name, _args in {
                  ctypes.POINTER(Queries), _vp, ctypes.c_int32, _vp],
     "klr_argmin": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
                    ctypes.POINTER(Queries), _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp],
+    "klr_argmin_noalloc": [ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
+                           ctypes.POINTER(Queries), _vp, _vp, _vp, _vp, _vp, _vp],
 }.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = ctypes.c_int32
@@ -228,6 +233,20 @@ class Context:
                                              _ptr(best), _ptr(cyc), out_dtype, _ptr(margin),
                                              _ptr(status), _ptr(lp), _stream(stream)))
         return best, cyc, margin, status, lp
+
+
+def argmin_noalloc(prog: Program, hw: Hw, cfg, q_offsets, q_N, out, stream=None):
+    """klr_argmin_noalloc on the current device: FP32 argmin whose scratch is a
+    static device array of the library, for callers that cannot allocate device
+    memory.  ``out`` = (best int32, cycles float32, margin float32 or None,
+    status int32 or None, launch int32 (n, 6) or None), all preallocated."""
+    best, cyc, margin, status, lp = out
+    q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), q_N.numel())
+    _check("klr_argmin_noalloc",
+           _lib.klr_argmin_noalloc(ctypes.byref(prog), ctypes.byref(hw), _ptr(cfg), cfg.shape[0],
+                                   ctypes.byref(q), _ptr(best), _ptr(cyc), _ptr(margin),
+                                   _ptr(status), _ptr(lp), _stream(stream)))
+    return out
 
 
 def _n_monomials(n_vars: int, degree: int) -> int:

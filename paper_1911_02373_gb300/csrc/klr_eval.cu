@@ -17,6 +17,7 @@
 // re-decided by a second kernel in FP64 from the unspecialised program.
 #include <cfloat>
 #include <cmath>
+#include <mutex>
 #include <type_traits>
 
 #include "klr_common.cuh"
@@ -382,6 +383,38 @@ int64_t tie_capacity(int64_t n_q) {
     return std::max<int64_t>(65536, std::min<int64_t>(n_q, 1 << 22) / 4);
 }
 
+// Scratch of klr_argmin_noalloc: a tie counter (first 256 bytes) and
+// KLR_ARGMIN_NOALLOC_TIE_RECORDS tie records.  Every GPU that loads the
+// library holds it until the process exits.
+constexpr size_t kNoallocHeader = 256;
+constexpr size_t kNoallocBytes = kNoallocHeader + sizeof(TieRecord) * KLR_ARGMIN_NOALLOC_TIE_RECORDS;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device (the host
+// symbol is only a stand-in and must never be passed to a kernel).
+constexpr int kMaxDevices = 256;
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[kMaxDevices] = {};
+
+klr_status noalloc_scratch(int device, void** out) {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (device < 0 || device >= kMaxDevices) {
+        set_error("klr_argmin_noalloc: device %d out of range", device);
+        return KLR_EINVAL;
+    }
+    if (!g_noalloc_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error("klr_argmin_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return KLR_ECUDA;
+        }
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return KLR_OK;
+}
+
 klr_status prepare(Context* c, const klr_program* prog, const klr_hw* hw, const int32_t* cfg,
                    int n_cfg, const klr_queries* q, int out_dtype, EvalParams& P) {
     KLR_REQUIRE(prog && hw && q, "klr_eval/argmin: NULL program, hw or queries");
@@ -542,6 +575,49 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
     st = launch_eval(c, P, f64, stream);
     if (st != KLR_OK || f64) return st;
     const int grid = (int)std::min<int64_t>((P.tie_cap + 127) / 128, (int64_t)c->n_sm * 4);
+    tie_kernel<<<grid, 128, 0, stream>>>(P);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw, const int32_t* cfg,
+                              int n_cfg, const klr_queries* q, int32_t* best_idx,
+                              float* best_cycles, float* margin, int32_t* q_status,
+                              int32_t* launch_out, void* stream_) {
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    // a context on the stack: device facts only, no scratch
+    Context c;
+    KLR_CHECK_CUDA(cudaGetDevice(&c.device));
+    int v = 0;
+    KLR_CHECK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, c.device));
+    c.n_sm = v;
+    KLR_CHECK_CUDA(cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, c.device));
+    c.smem_optin = (size_t)v;
+    EvalParams P;
+    klr_status st = prepare(&c, prog, hw, cfg, n_cfg, q, KLR_F32, P);
+    if (st != KLR_OK) return st;
+    KLR_REQUIRE(P.n_q <= KLR_ARGMIN_NOALLOC_MAX_QUERIES,
+                "klr_argmin_noalloc: %lld queries exceed the maximum of %d",
+                (long long)P.n_q, KLR_ARGMIN_NOALLOC_MAX_QUERIES);
+    if (P.n_q == 0 || P.n_kernels == 0) return KLR_OK;
+    KLR_REQUIRE(best_idx && best_cycles, "klr_argmin_noalloc: NULL best_idx or best_cycles");
+    void* scratch = nullptr;
+    st = noalloc_scratch(c.device, &scratch);
+    if (st != KLR_OK) return st;
+    P.table = 0;
+    P.best = best_idx;
+    P.best_cycles = best_cycles;
+    P.margin = margin;
+    P.q_status = q_status;
+    P.launch = launch_out;
+    P.tie_count = reinterpret_cast<int*>(scratch);
+    P.ties = reinterpret_cast<TieRecord*>(reinterpret_cast<char*>(scratch) + kNoallocHeader);
+    P.tie_cap = KLR_ARGMIN_NOALLOC_TIE_RECORDS;
+    // the array keeps the previous call's contents: the tie counter starts at zero
+    KLR_CHECK_CUDA(cudaMemsetAsync(P.tie_count, 0, sizeof(int), stream));
+    st = launch_eval(&c, P, false, stream);
+    if (st != KLR_OK) return st;
+    const int grid = (int)std::min<int64_t>((P.tie_cap + 127) / 128, (int64_t)c.n_sm * 4);
     tie_kernel<<<grid, 128, 0, stream>>>(P);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
