@@ -74,11 +74,13 @@ int n_monomials(int n_vars, int degree);
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
-// Error-free sum (Knuth's TwoSum): a + b = s + e exactly.
+// Error-free sum (Knuth's TwoSum): a + b = s + e exactly.  The _rn
+// intrinsics keep the compiler from contracting a product into these sums,
+// which would break the error-free property.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-    s = a + b;
-    float bp = s - a;
-    e = (a - (s - bp)) + (b - bp);
+    s = __fadd_rn(a, b);
+    float bp = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
 // Double-FP32 accumulator (hi, lo) += t with an error-free TwoSum.
@@ -88,5 +90,103 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float t) {
     hi = s;
     lo += e;
 }
+
+// ---------------------------------------------------------------------------
+// Double-word (two FP32) arithmetic: the error-free transformations of
+// Knuth (TwoSum), Dekker (Fast2Sum) and FMA-based TwoProduct, and the
+// double-word algorithms of Joldes, Muller and Popescu (ACM TOMS 2017):
+// AccurateDWPlusDW, DWTimesDW, DWTimesFP.  A value is h + l with
+// |l| <= ulp(h) / 2; about 2^-44 relative accuracy per operation.
+// ---------------------------------------------------------------------------
+struct dw {
+    float h, l;
+};
+
+__device__ __forceinline__ dw dw_fast2sum(float a, float b) {  // needs |a| >= |b|
+    float s = __fadd_rn(a, b);
+    float t = __fsub_rn(b, __fsub_rn(s, a));
+    return {s, t};
+}
+__device__ __forceinline__ dw dw_2sum(float a, float b) {
+    float s, e;
+    two_sum(a, b, s, e);
+    return {s, e};
+}
+__device__ __forceinline__ dw dw_add(dw x, dw y) {
+    dw s = dw_2sum(x.h, y.h);
+    dw t = dw_2sum(x.l, y.l);
+    float c = __fadd_rn(s.l, t.h);
+    dw v = dw_fast2sum(s.h, c);
+    float w = __fadd_rn(t.l, v.l);
+    return dw_fast2sum(v.h, w);
+}
+__device__ __forceinline__ dw dw_neg(dw x) { return {-x.h, -x.l}; }
+__device__ __forceinline__ dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
+__device__ __forceinline__ dw dw_mul(dw x, dw y) {
+    float ch = __fmul_rn(x.h, y.h);
+    float cl1 = fmaf(x.h, y.h, -ch);
+    float tl0 = __fmul_rn(x.l, y.l);
+    float tl1 = fmaf(x.h, y.l, tl0);
+    float cl2 = fmaf(x.l, y.h, tl1);
+    return dw_fast2sum(ch, __fadd_rn(cl1, cl2));
+}
+__device__ __forceinline__ dw dw_mul_f(dw x, float y) {
+    float ch = __fmul_rn(x.h, y);
+    float cl1 = fmaf(x.h, y, -ch);
+    float cl3 = fmaf(x.l, y, cl1);
+    return dw_fast2sum(ch, cl3);
+}
+// x / y: an FP32 quotient, then one correction from the exact residual
+__device__ __forceinline__ dw dw_div(dw x, dw y) {
+    float q1 = __fdividef(x.h, y.h);
+    dw r = dw_sub(x, dw_mul_f(y, q1));
+    float q2 = __fdividef(r.h, y.h);
+    r = dw_sub(r, dw_mul_f(y, q2));
+    float q3 = __fdividef(r.h, y.h);
+    dw q = dw_fast2sum(q1, q2);
+    return dw_add(q, dw{q3, 0.f});
+}
+// sqrt(x), x > 0: FP32 root, then one Newton correction from the exact square
+__device__ __forceinline__ dw dw_sqrt(dw x) {
+    float s = sqrtf(x.h);
+    float p = __fmul_rn(s, s);
+    float pe = fmaf(s, s, -p);
+    float r = __fadd_rn(__fsub_rn(__fsub_rn(x.h, p), pe), x.l);
+    return dw_fast2sum(s, __fdividef(r, 2.0f * s));
+}
+__device__ __forceinline__ dw dw_from_double(double v) {
+    float h = (float)v;
+    return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ double dw_to_double(dw x) { return (double)x.h + (double)x.l; }
+// x > y, x and y normalised
+__device__ __forceinline__ bool dw_gt(dw x, dw y) { return x.h > y.h || (x.h == y.h && x.l > y.l); }
+
+// Compensated dot-product accumulator (Ogita, Rump and Oishi's Dot2 on the
+// high parts, plus the cross terms of the low parts): s + c tracks
+// target - sum a_k b_k.
+struct dw_acc {
+    float s, c;
+    __device__ __forceinline__ void init(dw t) { s = t.h; c = t.l; }
+    __device__ __forceinline__ void sub_prod(dw a, dw b) {
+        float ph = __fmul_rn(a.h, b.h);
+        float pe = fmaf(a.h, b.h, -ph);
+        float pl = fmaf(a.h, b.l, __fmul_rn(a.l, b.h));
+        float ns, e;
+        two_sum(s, -ph, ns, e);
+        s = ns;
+        c += e - pe - pl;
+    }
+    __device__ __forceinline__ void add_prod(dw a, dw b) {
+        float ph = __fmul_rn(a.h, b.h);
+        float pe = fmaf(a.h, b.h, -ph);
+        float pl = fmaf(a.h, b.l, __fmul_rn(a.l, b.h));
+        float ns, e;
+        two_sum(s, ph, ns, e);
+        s = ns;
+        c += e + pe + pl;
+    }
+    __device__ __forceinline__ dw value() const { return dw_2sum(s, c); }
+};
 
 }  // namespace klr

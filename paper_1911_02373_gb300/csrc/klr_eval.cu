@@ -512,9 +512,14 @@ klr_status launch_eval(Context* c, EvalParams& P, bool f64, cudaStream_t stream)
 
 }  // namespace
 
+size_t fit_workspace_bytes(int64_t n_fits, int n_mom);
+
+// A context's scratch serves one call at a time: the larger of the fit's
+// moment sums (sized here for fits of total degree <= 2 in up to four
+// variables) and the argmin's tie records.
 size_t workspace_bytes(int64_t max_fits, int64_t max_queries) {
-    (void)max_fits;
-    return 256 + sizeof(TieRecord) * (size_t)tie_capacity(max_queries);
+    const size_t ties = 256 + sizeof(TieRecord) * (size_t)tie_capacity(max_queries);
+    return std::max(ties, fit_workspace_bytes(max_fits, n_monomials(4, 4)));
 }
 
 }  // namespace klr

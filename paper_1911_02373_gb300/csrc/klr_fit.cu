@@ -1,24 +1,37 @@
 // F1-F4: batched rational fits (Section V-E; Section IV, step 2).
 //
-// One warp per fit.  The fit's samples are streamed once from HBM (coalesced,
-// 32 samples per step, staged as powers of the scaled coordinates in shared
-// memory) while the warp accumulates the moment sums
+// Three kernels.
+//
+// moments_kernel (F1 + F2), one warp per fit: the fit's samples are streamed
+// once from HBM (coalesced, 32 samples per step, staged as powers of the
+// scaled coordinates in shared memory) while the warp accumulates the moment
+// sums
 //     M_k[mu] = sum_s y_s^k x_s^mu,  k = 0, 1, 2,  deg(mu) <= 2d,
 // which determine every entry of the Gram matrix G = A^T A of
 // A = [Phi | -y Phi]:  G_pp[i][j] = M_0[mu_i + mu_j],
 // G_pq[i][j] = -M_1[mu_i + mu_j], G_qq[i][j] = M_2[mu_i + mu_j].
 // The moments are about half the multiply-adds of a direct Gram at degree 2
 // and a third at degree 3.  Lanes split the work as (sample group x moment
-// group) so each lane keeps only a few accumulators in registers.
+// group) so each lane keeps only a few accumulators in registers.  The
+// moments go to the context's scratch memory.
 //
-// The small solve is FP64: power-of-two column equilibration from the Gram
-// diagonal, shifted Cholesky factorisation and inverse iteration for the
-// smallest eigenpair (the smallest right singular vector of A D), a second
-// shift close below the Rayleigh quotient when the fit is noisy, deflated
-// inverse iteration for the next eigenvalue (rank test), and optional
-// refinement passes that recompute A^T A v from the samples in FP64 and take a
-// preconditioned inverse-iteration step (Knyazev-Neymeyr PINVIT) with the
-// Cholesky factor as preconditioner.
+// solve_lane_kernel (F3), one lane per fit: FP64 power-of-two column
+// equilibration from the Gram diagonal, then shifted Cholesky factorisation
+// and inverse iteration for the smallest eigenpair of the equilibrated Gram
+// matrix (the smallest right singular vector of A D).  GB300 issues FP64 at
+// 1/64 of the FP32 rate, so every lane works on its own fit and no FP64
+// instruction is spent on a uniform value; each lane's factor lives in
+// shared memory, interleaved across lanes.  A noisy fit re-factors at the
+// largest shift of a ladder below the Rayleigh quotient that keeps the matrix
+// positive definite, for a few rounds; deflated inverse iteration estimates
+// the next eigenvalue for the rank test.
+//
+// solve_warp_kernel (F3 + F4), one warp per fit: the same solve done
+// cooperatively by a warp, followed by optional refinement passes that
+// recompute A^T A v from the samples in FP64 and take a preconditioned
+// inverse-iteration step (Knyazev-Neymeyr PINVIT) with the Cholesky factor as
+// preconditioner.  Used when refinement is asked for or the problem is too
+// large for a lane's share of shared memory.
 #include <cfloat>
 #include <type_traits>
 
@@ -28,9 +41,8 @@ namespace klr {
 
 namespace {
 
-constexpr int kMG = 16;                 // lanes sharing one sample (moment groups)
-constexpr int kSG = 32 / kMG;           // sample groups per warp
 constexpr int kRefineMaxU = 40;         // unknowns supported by refinement passes
+constexpr int kLaneMaxU = 30;           // unknowns supported by the lane-per-fit solver
 
 enum { ACC_FP64 = 0, ACC_DF32 = 1, ACC_FP32 = 2 };
 
@@ -48,6 +60,10 @@ struct FitParams {
     int refine;
     int ld;        // leading dimension of the Gram matrix in shared memory
     int warp_smem; // bytes of shared memory per warp
+    double* mom;   // scratch: n_fits x 3 x n_mom moment sums (FP64, or
+                   // double-word float2 pairs when mom_dw)
+    int mom_dw;
+    int32_t* flags;// scratch: n_fits, bit 0 non-finite sample, bit 1 inexact DF32
     uint8_t exps[kMaxMoments][kMaxVars];
     uint8_t pair[kMaxBasis][kMaxBasis];
 };
@@ -154,9 +170,198 @@ __device__ void warp_copy(double* dst, const double* src, int u) {
     __syncwarp();
 }
 
-template <typename TS, int ACC, int MAXT>
-__global__ void __launch_bounds__(128)
-fit_kernel(const __grid_constant__ FitParams P) {
+// Compile-time list of the monomials of total degree <= D in NV variables,
+// graded, then decreasing exponent tuple (the same order as make_basis).
+template <int NV, int D>
+struct MonoTable {
+    __host__ __device__ static constexpr int count() {
+        int c = 1;
+        for (int i = 1; i <= D; ++i) c = c * (NV + i) / i;
+        return c;
+    }
+    int e[count()][4];
+    __host__ __device__ constexpr MonoTable() : e{} {
+        int idx = 0;
+        for (int d = 0; d <= D; ++d)
+            for (int a = d; a >= 0; --a)
+                for (int b = (NV > 1 ? d - a : 0); b >= 0; --b)
+                    for (int c = (NV > 2 ? d - a - b : 0); c >= 0; --c) {
+                        const int r = d - a - b - c;
+                        if (NV == 3 && r != 0) continue;
+                        if (NV == 4 || r == 0) {
+                            e[idx][0] = a;
+                            e[idx][1] = b;
+                            e[idx][2] = c;
+                            e[idx][3] = NV == 4 ? r : 0;
+                            ++idx;
+                        }
+                    }
+    }
+};
+
+// moments_kernel specialised on the basis: the staging lane computes all
+// n_mom monomials of its sample once (compile-time exponents, registers
+// only), and each accumulating lane reads its monomial with one load.
+template <typename TS, int ACC, int NV, int D2, int MG, int MAXT>
+__global__ void __launch_bounds__(128, 4)
+moments_fast_kernel(const __grid_constant__ FitParams P) {
+    constexpr MonoTable<NV, D2> tab{};
+    constexpr int NM = MonoTable<NV, D2>::count();
+    constexpr int REC = NM + 3 + ((NM + 3) % 2 == 0 ? 1 : 0);   // odd stride
+    constexpr int SG = 32 / MG;
+    static_assert(MG * MAXT >= NM, "too few lanes for the moments");
+    using TC = typename std::conditional<ACC == ACC_FP64, double, float>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = lane_id();
+    const int wib = threadIdx.x >> 5;
+    const int f = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (f >= P.n_fits) return;
+    TC* stage = reinterpret_cast<TC*>(smem_raw + (size_t)wib * P.warp_smem);
+    const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
+    const TS* X = reinterpret_cast<const TS*>(P.x);
+    const TS* Y = reinterpret_cast<const TS*>(P.y);
+    const TC sN = (TC)ldexpf(1.0f, -P.n_scale_log2), sB = (TC)ldexpf(1.0f, -P.b_scale_log2);
+    const int mg = lane % MG, sg = lane / MG;
+    TC a0[MAXT], a1[MAXT], a2[MAXT];
+    float c0[MAXT], c1[MAXT], c2[MAXT];
+#pragma unroll
+    for (int i = 0; i < MAXT; ++i) {
+        a0[i] = a1[i] = a2[i] = TC(0);
+        c0[i] = c1[i] = c2[i] = 0.f;
+    }
+    bool bad = false, inexact = false;
+    TS cx[NV], cy = TS(0), nx[NV], ny = TS(0);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) cx[v] = nx[v] = TS(1);
+    if (s0 + lane < s1) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) cx[v] = X[(int64_t)v * P.x_stride + s0 + lane];
+        cy = Y[s0 + lane];
+    }
+    for (int64_t base = s0; base < s1; base += 32) {
+        const int64_t s = base + lane;
+        const int64_t sn = s + 32;
+        if (sn < s1) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) nx[v] = X[(int64_t)v * P.x_stride + sn];
+            ny = Y[sn];
+        }
+        if (s < s1) {
+            TC pw[NV][D2 + 1];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const TS raw = cx[v];
+                bad |= !isfinite(raw);
+                if constexpr (ACC == ACC_DF32) inexact |= !is_pow2_positive(raw);
+                const TC xv = (TC)raw * (v == 0 ? sN : sB);
+                pw[v][0] = TC(1);
+#pragma unroll
+                for (int k = 1; k <= D2; ++k) pw[v][k] = pw[v][k - 1] * xv;
+            }
+            TC* r = stage + lane * REC;
+#pragma unroll
+            for (int t = 0; t < NM; ++t) {
+                TC x = pw[0][tab.e[t][0]] * pw[1][tab.e[t][1]];
+                if constexpr (NV > 2) x *= pw[2][tab.e[t][2]];
+                if constexpr (NV > 3) x *= pw[3][tab.e[t][3]];
+                r[t] = x;
+            }
+            bad |= !isfinite(cy);
+            const TC yv = (TC)cy;
+            const TC y2h = yv * yv;
+            TC y2l = TC(0);
+            if constexpr (ACC != ACC_FP64) y2l = fmaf(yv, yv, -y2h);
+            r[NM + 0] = yv;
+            r[NM + 1] = y2h;
+            r[NM + 2] = y2l;
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) cx[v] = nx[v];
+        cy = ny;
+        __syncwarp();
+        const int nvalid = (int)min((int64_t)32, s1 - base);
+        for (int ts = sg; ts < nvalid; ts += SG) {
+            const TC* r = stage + ts * REC;
+            const TC yv = r[NM + 0], y2h = r[NM + 1], y2l = r[NM + 2];
+#pragma unroll
+            for (int i = 0; i < MAXT; ++i) {
+                const int mu = mg + MG * i;
+                if (mu < NM) {
+                    const TC xm = r[mu];
+                    if constexpr (ACC == ACC_FP64) {
+                        a0[i] += xm;
+                        a1[i] = fma(yv, xm, a1[i]);
+                        a2[i] = fma(y2h, xm, a2[i]);
+                    } else if constexpr (ACC == ACC_DF32) {
+                        df_add(a0[i], c0[i], xm);
+                        df_add(a1[i], c1[i], __fmul_rn(yv, xm));
+                        df_add(a2[i], c2[i], __fmul_rn(y2h, xm));
+                        c2[i] = fmaf(y2l, xm, c2[i]);
+                    } else {
+                        a0[i] += xm;
+                        a1[i] = fmaf(yv, xm, a1[i]);
+                        a2[i] = fmaf(y2h, xm, a2[i]);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int i = 0; i < MAXT; ++i) {
+#pragma unroll
+        for (int o = MG; o < 32; o <<= 1) {
+            if constexpr (ACC == ACC_DF32) {
+                float h, e;
+                float oh0 = __shfl_xor_sync(0xffffffffu, a0[i], o);
+                float ol0 = __shfl_xor_sync(0xffffffffu, c0[i], o);
+                two_sum(a0[i], oh0, h, e);
+                a0[i] = h; c0[i] = c0[i] + ol0 + e;
+                float oh1 = __shfl_xor_sync(0xffffffffu, a1[i], o);
+                float ol1 = __shfl_xor_sync(0xffffffffu, c1[i], o);
+                two_sum(a1[i], oh1, h, e);
+                a1[i] = h; c1[i] = c1[i] + ol1 + e;
+                float oh2 = __shfl_xor_sync(0xffffffffu, a2[i], o);
+                float ol2 = __shfl_xor_sync(0xffffffffu, c2[i], o);
+                two_sum(a2[i], oh2, h, e);
+                a2[i] = h; c2[i] = c2[i] + ol2 + e;
+            } else {
+                a0[i] += __shfl_xor_sync(0xffffffffu, a0[i], o);
+                a1[i] += __shfl_xor_sync(0xffffffffu, a1[i], o);
+                a2[i] += __shfl_xor_sync(0xffffffffu, a2[i], o);
+            }
+        }
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    inexact = __any_sync(0xffffffffu, inexact);
+    if (sg == 0) {
+        double* mom = P.mom + (int64_t)f * 3 * NM;
+#pragma unroll
+        for (int i = 0; i < MAXT; ++i) {
+            const int mu = mg + MG * i;
+            if (mu < NM) {
+                if constexpr (ACC == ACC_FP64) {
+                    mom[mu] = a0[i];
+                    mom[NM + mu] = a1[i];
+                    mom[2 * NM + mu] = a2[i];
+                } else {
+                    float2* m2 = reinterpret_cast<float2*>(mom);
+                    const dw q0 = dw_2sum(a0[i], c0[i]), q1 = dw_2sum(a1[i], c1[i]),
+                             q2 = dw_2sum(a2[i], c2[i]);
+                    m2[mu] = make_float2(q0.h, q0.l);
+                    m2[NM + mu] = make_float2(q1.h, q1.l);
+                    m2[2 * NM + mu] = make_float2(q2.h, q2.l);
+                }
+            }
+        }
+    }
+    if (lane == 0) P.flags[f] = (bad ? 1 : 0) | (inexact ? 2 : 0);
+}
+
+template <typename TS, int ACC, int MG, int MAXT>
+__global__ void __launch_bounds__(128, 4)
+moments_kernel(const __grid_constant__ FitParams P) {
+    constexpr int SG = 32 / MG;
     using TC = typename std::conditional<ACC == ACC_FP64, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
@@ -165,17 +370,11 @@ fit_kernel(const __grid_constant__ FitParams P) {
     if (f >= P.n_fits) return;
     unsigned char* wsm = smem_raw + (size_t)wib * P.warp_smem;
 
-    const int nv = P.n_vars, d = P.degree, m = P.m, u = P.u, n_mom = P.n_mom, ld = P.ld;
+    const int nv = P.n_vars, d = P.degree, n_mom = P.n_mom;
     const int PW = 2 * d + 1;              // powers 0..2d per variable
     const int REC = nv * PW + 3;           // powers + (y, y^2 hi, y^2 lo)
     TC* stage = reinterpret_cast<TC*>(wsm);
-    double* mom = reinterpret_cast<double*>(wsm + ((32 * REC * sizeof(TC) + 15) & ~15));
-    double* G = mom + 3 * n_mom;
-    double* gdiag = G + u * ld;
-    double* D = gdiag + u;
-    double* v = D + u;
-    double* w = v + u;
-    double* t = w + u;
+    double* mom = P.mom + (int64_t)f * 3 * n_mom;
 
     const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
     const TS* X = reinterpret_cast<const TS*>(P.x);
@@ -184,16 +383,20 @@ fit_kernel(const __grid_constant__ FitParams P) {
     const double b_scale = ldexp(1.0, -P.b_scale_log2);
 
     // ---- F1 + F2: stream samples, accumulate moments ------------------------
-    const int mg = lane % kMG, sg = lane / kMG;
-    int off[MAXT][kMaxVars];
+    const int mg = lane % MG, sg = lane / MG;
+    // offsets into a staged record of the powers that make up each of this
+    // lane's moments, one byte per variable
+    unsigned off[MAXT];
     int my_n = 0;
 #pragma unroll
     for (int i = 0; i < MAXT; ++i) {
-        int mu = mg + kMG * i;
+        int mu = mg + MG * i;
         if (mu < n_mom) my_n = i + 1;
+        unsigned o = 0;
 #pragma unroll
         for (int vv = 0; vv < kMaxVars; ++vv)
-            off[i][vv] = (mu < n_mom && vv < nv) ? vv * PW + P.exps[mu][vv] : 0;
+            o |= (unsigned)((mu < n_mom && vv < nv) ? vv * PW + P.exps[mu][vv] : 0) << (8 * vv);
+        off[i] = o;
     }
     TC a0[MAXT], a1[MAXT], a2[MAXT];
     float c0[MAXT], c1[MAXT], c2[MAXT];
@@ -203,42 +406,66 @@ fit_kernel(const __grid_constant__ FitParams P) {
         c0[i] = c1[i] = c2[i] = 0.f;
     }
     bool bad = false, inexact = false;
+    // software pipeline: the next step's 32 samples are loaded into registers
+    // while the current step's are accumulated
+    const TC sN = (TC)n_scale, sB = (TC)b_scale;   // powers of two: exact scaling
+    TS cx[kMaxVars], cy = TS(0), nx[kMaxVars], ny = TS(0);
+#pragma unroll
+    for (int vv = 0; vv < kMaxVars; ++vv) cx[vv] = nx[vv] = TS(1);
+    if (s0 + lane < s1) {
+#pragma unroll
+        for (int vv = 0; vv < kMaxVars; ++vv)
+            if (vv < nv) cx[vv] = X[(int64_t)vv * P.x_stride + s0 + lane];
+        cy = Y[s0 + lane];
+    }
     for (int64_t base = s0; base < s1; base += 32) {
         const int64_t s = base + lane;
+        const int64_t sn = s + 32;
+        if (sn < s1) {
+#pragma unroll
+            for (int vv = 0; vv < kMaxVars; ++vv)
+                if (vv < nv) nx[vv] = X[(int64_t)vv * P.x_stride + sn];
+            ny = Y[sn];
+        }
         if (s < s1) {
             TC* r = stage + lane * REC;
-            for (int vv = 0; vv < nv; ++vv) {
-                TS raw = X[(int64_t)vv * P.x_stride + s];
-                bad |= !isfinite((double)raw);
-                if constexpr (ACC == ACC_DF32) inexact |= !is_pow2_positive(raw);
-                TC xv = (TC)((double)raw * (vv == 0 ? n_scale : b_scale));
-                TC p = TC(1);
-                for (int k = 0; k < PW; ++k) {
-                    r[vv * PW + k] = p;
-                    p *= xv;
+#pragma unroll
+            for (int vv = 0; vv < kMaxVars; ++vv) {
+                if (vv < nv) {
+                    const TS raw = cx[vv];
+                    bad |= !isfinite(raw);
+                    if constexpr (ACC == ACC_DF32) inexact |= !is_pow2_positive(raw);
+                    const TC xv = (TC)raw * (vv == 0 ? sN : sB);
+                    TC p = TC(1);
+                    for (int k = 0; k < PW; ++k) {
+                        r[vv * PW + k] = p;
+                        p *= xv;
+                    }
                 }
             }
-            TS yraw = Y[s];
-            bad |= !isfinite((double)yraw);
-            TC yv = (TC)yraw;
-            TC y2h = yv * yv;
+            bad |= !isfinite(cy);
+            const TC yv = (TC)cy;
+            const TC y2h = yv * yv;
             TC y2l = TC(0);
             if constexpr (ACC != ACC_FP64) y2l = fmaf(yv, yv, -y2h);
             r[nv * PW + 0] = yv;
             r[nv * PW + 1] = y2h;
             r[nv * PW + 2] = y2l;
         }
+#pragma unroll
+        for (int vv = 0; vv < kMaxVars; ++vv) cx[vv] = nx[vv];
+        cy = ny;
         __syncwarp();
         const int nvalid = (int)min((int64_t)32, s1 - base);
-        for (int ts = sg; ts < nvalid; ts += kSG) {
+        for (int ts = sg; ts < nvalid; ts += SG) {
             const TC* r = stage + ts * REC;
             const TC yv = r[nv * PW + 0], y2h = r[nv * PW + 1], y2l = r[nv * PW + 2];
 #pragma unroll
             for (int i = 0; i < MAXT; ++i) {
                 if (i < my_n) {
-                    TC xm = r[off[i][0]] * r[off[i][1]];
-                    if (nv > 2) xm *= r[off[i][2]];
-                    if (nv > 3) xm *= r[off[i][3]];
+                    TC xm = r[off[i] & 0xFF] * r[(off[i] >> 8) & 0xFF];
+                    if (nv > 2) xm *= r[(off[i] >> 16) & 0xFF];
+                    if (nv > 3) xm *= r[off[i] >> 24];
                     if constexpr (ACC == ACC_FP64) {
                         a0[i] += xm;
                         a1[i] = fma(yv, xm, a1[i]);
@@ -263,7 +490,7 @@ fit_kernel(const __grid_constant__ FitParams P) {
 #pragma unroll
     for (int i = 0; i < MAXT; ++i) {
 #pragma unroll
-        for (int o = kMG; o < 32; o <<= 1) {
+        for (int o = MG; o < 32; o <<= 1) {
             if constexpr (ACC == ACC_DF32) {
                 float h, e;
                 float oh0 = __shfl_xor_sync(0xffffffffu, a0[i], o);
@@ -291,13 +518,57 @@ fit_kernel(const __grid_constant__ FitParams P) {
 #pragma unroll
         for (int i = 0; i < MAXT; ++i) {
             if (i < my_n) {
-                int mu = mg + kMG * i;
-                mom[mu] = (double)a0[i] + (ACC == ACC_DF32 ? (double)c0[i] : 0.0);
-                mom[n_mom + mu] = (double)a1[i] + (ACC == ACC_DF32 ? (double)c1[i] : 0.0);
-                mom[2 * n_mom + mu] = (double)a2[i] + (ACC == ACC_DF32 ? (double)c2[i] : 0.0);
+                int mu = mg + MG * i;
+                if constexpr (ACC == ACC_FP64) {
+                    mom[mu] = a0[i];
+                    mom[n_mom + mu] = a1[i];
+                    mom[2 * n_mom + mu] = a2[i];
+                } else {
+                    // normalised double-word pairs (c is 0 in FP32 mode)
+                    float2* m2 = reinterpret_cast<float2*>(mom);
+                    const dw s0 = dw_2sum(a0[i], c0[i]), s1 = dw_2sum(a1[i], c1[i]),
+                             s2 = dw_2sum(a2[i], c2[i]);
+                    m2[mu] = make_float2(s0.h, s0.l);
+                    m2[n_mom + mu] = make_float2(s1.h, s1.l);
+                    m2[2 * n_mom + mu] = make_float2(s2.h, s2.l);
+                }
             }
         }
     }
+    if (lane == 0) P.flags[f] = (bad ? 1 : 0) | (inexact ? 2 : 0);
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(128)
+solve_warp_kernel(const __grid_constant__ FitParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = lane_id();
+    const int wib = threadIdx.x >> 5;
+    const int f = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (f >= P.n_fits) return;
+    const int nv = P.n_vars, m = P.m, u = P.u, n_mom = P.n_mom, ld = P.ld;
+    double* mom = reinterpret_cast<double*>(smem_raw + (size_t)wib * P.warp_smem);
+    double* G = mom + 3 * n_mom;
+    double* gdiag = G + u * ld;
+    double* D = gdiag + u;
+    double* v = D + u;
+    double* w = v + u;
+    double* t = w + u;
+    const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
+    const TS* X = reinterpret_cast<const TS*>(P.x);
+    const TS* Y = reinterpret_cast<const TS*>(P.y);
+    const double n_scale = ldexp(1.0, -P.n_scale_log2);
+    const double b_scale = ldexp(1.0, -P.b_scale_log2);
+    for (int i = lane; i < 3 * n_mom; i += 32) {
+        if (P.mom_dw) {
+            const float2 g = reinterpret_cast<const float2*>(P.mom)[(int64_t)f * 3 * n_mom + i];
+            mom[i] = (double)g.x + (double)g.y;
+        } else {
+            mom[i] = P.mom[(int64_t)f * 3 * n_mom + i];
+        }
+    }
+    const int32_t fl = P.flags[f];
+    const bool bad = fl & 1, inexact = fl & 2;
     __syncwarp();
 
     const int64_t S = s1 - s0;
@@ -513,26 +784,960 @@ fit_kernel(const __grid_constant__ FitParams P) {
     }
 }
 
-template <typename TS, int ACC>
-klr_status launch_fit(const FitParams& P, int maxt, size_t smem_block, int wpb,
-                      cudaStream_t stream) {
-    const int blocks = (P.n_fits + wpb - 1) / wpb;
-    if (maxt <= 6) {
-        auto k = fit_kernel<TS, ACC, 6>;
-        KLR_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem_block));
-        k<<<blocks, wpb * 32, smem_block, stream>>>(P);
-    } else {
-        auto k = fit_kernel<TS, ACC, 14>;
-        KLR_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem_block));
-        k<<<blocks, wpb * 32, smem_block, stream>>>(P);
+
+
+// One lane per fit.  Shared memory holds, per lane and interleaved across the
+// 32 lanes of the block (element e of lane l at [e * 32 + l]): the packed
+// lower Cholesky factor, the reciprocal diagonal, D, v and w.
+__global__ void __launch_bounds__(32)
+solve_lane_kernel(const __grid_constant__ FitParams P) {
+    extern __shared__ __align__(16) double lsm[];
+    const int lane = threadIdx.x;
+    const int f = blockIdx.x * 32 + lane;
+    if (f >= P.n_fits) return;
+    const int m = P.m, u = P.u, n_mom = P.n_mom;
+    const int nL = u * (u + 1) / 2;
+    double* Lf = lsm;                 // packed: (i, j), j <= i at i (i + 1) / 2 + j
+    double* rinv = Lf + nL * 32;
+    double* Dv = rinv + u * 32;
+    double* vv = Dv + u * 32;
+    double* wv = vv + u * 32;
+#define LF(i, j) Lf[((i) * ((i) + 1) / 2 + (j)) * 32 + lane]
+#define RI(i) rinv[(i) * 32 + lane]
+#define DD(i) Dv[(i) * 32 + lane]
+#define VV(i) vv[(i) * 32 + lane]
+#define WV(i) wv[(i) * 32 + lane]
+    const double* M = P.mom + (int64_t)f * 3 * n_mom;
+    const int64_t S = P.offsets[f + 1] - P.offsets[f];
+    const int32_t fl = P.flags[f];
+    int32_t status = 0;
+    if (S == 0) status = KLR_FIT_EMPTY;
+    else if (fl & 1) status = KLR_FIT_NONFINITE;
+    if (status) {
+        for (int j = 0; j < u; ++j) {
+            if (P.coef_f64) reinterpret_cast<double*>(P.coef)[(int64_t)f * u + j] = 0.0;
+            else reinterpret_cast<float*>(P.coef)[(int64_t)f * u + j] = 0.f;
+        }
+        P.status[f] = status;
+        if (P.diag) for (int k = 0; k < 4; ++k) P.diag[(int64_t)f * 4 + k] = 0.0;
+        return;
     }
+    if (fl & 2) status |= KLR_FIT_INEXACT;
+    // equilibration from the Gram diagonal (families 0 and 2 have sign +)
+    double trace = 0.0;
+    for (int j = 0; j < u; ++j) {
+        const int bj = j >= m, jj = j - bj * m;
+        const double g = __ldg(M + 2 * bj * n_mom + P.pair[jj][jj]);
+        double dj = 1.0;
+        if (g > 0.0) {
+            int e;
+            frexp(g, &e);
+            dj = ldexp(1.0, -(e >> 1));
+        }
+        DD(j) = dj;
+        trace += g * dj * dj;
+    }
+    // entry (i, j) of the equilibrated Gram matrix, assembled from the moments
+    auto gh = [&](int i, int j) -> double {
+        const int bi = i >= m, bj = j >= m;
+        double val = __ldg(M + (bi + bj) * n_mom + P.pair[i - bi * m][j - bj * m]);
+        if (bi != bj) val = -val;
+        return val * DD(i) * DD(j);
+    };
+    // Cholesky of (Ghat - shift I); false if a pivot is not positive
+    // (two partial sums in the inner products keep two FP64 chains in flight)
+    auto cholesky = [&](double shift) -> bool {
+        for (int j = 0; j < u; ++j) {
+            double s0 = gh(j, j) - shift, s1 = 0.0;
+            int k = 0;
+            for (; k + 1 < j; k += 2) {
+                s0 -= LF(j, k) * LF(j, k);
+                s1 -= LF(j, k + 1) * LF(j, k + 1);
+            }
+            if (k < j) s0 -= LF(j, k) * LF(j, k);
+            const double sjj = s0 + s1;
+            if (!(sjj > 0.0)) return false;
+            const double r = 1.0 / sqrt(sjj);
+            RI(j) = r;
+            for (int i = j + 1; i < u; ++i) {
+                double t0 = gh(i, j), t1 = 0.0;
+                int kk = 0;
+                for (; kk + 1 < j; kk += 2) {
+                    t0 -= LF(i, kk) * LF(j, kk);
+                    t1 -= LF(i, kk + 1) * LF(j, kk + 1);
+                }
+                if (kk < j) t0 -= LF(i, kk) * LF(j, kk);
+                LF(i, j) = (t0 + t1) * r;
+            }
+        }
+        return true;
+    };
+    // w <- (L L^T)^-1 w
+    auto solve = [&]() {
+        for (int i = 0; i < u; ++i) {
+            double t0 = WV(i), t1 = 0.0;
+            int k = 0;
+            for (; k + 1 < i; k += 2) {
+                t0 -= LF(i, k) * WV(k);
+                t1 -= LF(i, k + 1) * WV(k + 1);
+            }
+            if (k < i) t0 -= LF(i, k) * WV(k);
+            WV(i) = (t0 + t1) * RI(i);
+        }
+        for (int i = u - 1; i >= 0; --i) {
+            double t0 = WV(i), t1 = 0.0;
+            int k = i + 1;
+            for (; k + 1 < u; k += 2) {
+                t0 -= LF(k, i) * WV(k);
+                t1 -= LF(k + 1, i) * WV(k + 1);
+            }
+            if (k < u) t0 -= LF(k, i) * WV(k);
+            WV(i) = (t0 + t1) * RI(i);
+        }
+    };
+    // one inverse-iteration step v <- normalise((Ghat - shift)^-1 v); returns
+    // the Rayleigh quotient of the new v, shift + (v.w) / (w.w), and in dv2
+    // the squared change of v (no sign flips: the shifted matrix is positive
+    // definite, so v.w > 0)
+    auto step = [&](double shift, double& dv2) -> double {
+        for (int i = 0; i < u; ++i) WV(i) = VV(i);
+        solve();
+        double vw = 0.0, ww = 0.0;
+        for (int i = 0; i < u; ++i) {
+            vw += VV(i) * WV(i);
+            ww += WV(i) * WV(i);
+        }
+        const double inv = 1.0 / sqrt(ww);
+        dv2 = 0.0;
+        for (int i = 0; i < u; ++i) {
+            const double nv_ = WV(i) * inv;
+            const double dd = nv_ - VV(i);
+            dv2 += dd * dd;
+            VV(i) = nv_;
+        }
+        return shift + vw / ww;
+    };
+
+    const double eps = DBL_EPSILON;
+    const double jitter = 4.0 * u * eps * trace;
+    const double null_level = 64.0 * u * eps * trace;
+    double shift = -jitter;
+    bool ok = cholesky(shift);
+    if (!ok) {
+        shift = -1024.0 * jitter;
+        ok = cholesky(shift);
+    }
+    double theta = 0.0, theta2 = 0.0;
+    if (ok) {
+        double nn = 0.0;
+        for (int i = 0; i < u; ++i) {
+            const double x = 1.0 + 0.0625 * (double)((i * 7) % 11);
+            VV(i) = x;
+            nn += x * x;
+        }
+        nn = 1.0 / sqrt(nn);
+        for (int i = 0; i < u; ++i) VV(i) *= nn;
+        // stop when v moved by less than 1e-11, or stalls (rate above 1/2) at
+        // the rounding floor below 1e-8
+        auto converged = [](double dv2, double prev) {
+            return dv2 <= 1e-22 || (dv2 <= 1e-16 && dv2 >= 0.25 * prev);
+        };
+        double dv2 = 1.0, prev = 1.0;
+        for (int it = 0; it < 6; ++it) {
+            theta = step(shift, dv2);
+            if (converged(dv2, prev)) break;
+            prev = dv2;
+        }
+        if (theta > null_level) {
+            // A noisy fit: re-factor at the largest rung of a ladder below the
+            // Rayleigh quotient that keeps the matrix positive definite (so
+            // shift < lambda_min), iterate, and repeat with the better quotient.
+            const double ladder[7] = {1.0 - 1.0 / 64, 1.0 - 1.0 / 32, 1.0 - 1.0 / 16,
+                                      1.0 - 1.0 / 8, 1.0 - 1.0 / 4, 0.5, 0.25};
+            bool done = false;
+            for (int round = 0; round < 3 && !done; ++round) {
+                bool ok2 = false;
+                for (int k = 0; k < 8 && !ok2; ++k) {
+                    shift = k < 7 ? theta * ladder[k] : -jitter;
+                    ok2 = cholesky(shift);
+                }
+                if (!ok2) {
+                    status |= KLR_FIT_SOLVE_FAILED;
+                    ok = false;
+                    break;
+                }
+                prev = 1.0;
+                for (int it = 0; it < 8; ++it) {
+                    theta = step(shift, dv2);
+                    if (converged(dv2, prev)) { done = true; break; }
+                    prev = dv2;
+                }
+            }
+        }
+    } else {
+        status |= KLR_FIT_SOLVE_FAILED;
+    }
+    if (ok) {
+        // next eigenvalue: inverse iteration on the complement of v.  The
+        // diagonal slots of the packed factor are free (the factor keeps its
+        // reciprocal diagonal in rinv) and hold the previous iterate.
+        auto project_normalise = [&]() {
+            double c = 0.0;
+            for (int i = 0; i < u; ++i) c += WV(i) * VV(i);
+            double nn = 0.0;
+            for (int i = 0; i < u; ++i) {
+                WV(i) -= c * VV(i);
+                nn += WV(i) * WV(i);
+            }
+            nn = 1.0 / sqrt(nn);
+            for (int i = 0; i < u; ++i) WV(i) *= nn;
+        };
+        for (int i = 0; i < u; ++i) WV(i) = 1.0 + 0.03125 * (double)((i * 5) % 13) - 0.5 * (i & 1);
+        project_normalise();
+        for (int it = 0; it < 3; ++it) {
+            for (int i = 0; i < u; ++i) LF(i, i) = WV(i);
+            solve();
+            double zw = 0.0, zz = 0.0;
+            for (int i = 0; i < u; ++i) {
+                zw += WV(i) * LF(i, i);
+                zz += WV(i) * WV(i);
+            }
+            theta2 = shift + zw / zz;
+            project_normalise();
+        }
+        if (theta2 <= null_level) status |= KLR_FIT_RANK_DEFICIENT;
+    }
+    // c = D v, unit norm, sign rule
+    double nrm = 0.0;
+    for (int i = 0; i < u; ++i) {
+        const double ci = DD(i) * VV(i);
+        WV(i) = ci;
+        nrm += ci * ci;
+    }
+    nrm = sqrt(nrm);
+    double sgn = 1.0;
+    const double q0 = WV(m) / nrm;
+    if (fabs(q0) >= 1e-12) {
+        sgn = q0 > 0.0 ? 1.0 : -1.0;
+    } else {
+        double best = -1.0;
+        int bi = m;
+        for (int j = m; j < u; ++j)
+            if (fabs(WV(j)) > best) { best = fabs(WV(j)); bi = j; }
+        sgn = WV(bi) > 0.0 ? 1.0 : -1.0;
+    }
+    const double scale = ok ? sgn / nrm : 0.0;
+    for (int j = 0; j < u; ++j) {
+        const double cj = WV(j) * scale;
+        if (P.coef_f64) reinterpret_cast<double*>(P.coef)[(int64_t)f * u + j] = cj;
+        else reinterpret_cast<float*>(P.coef)[(int64_t)f * u + j] = (float)cj;
+    }
+    P.status[f] = status;
+    if (P.diag) {
+        double* dg = P.diag + (int64_t)f * 4;
+        dg[0] = trace > 0 ? theta / trace : 0.0;
+        dg[1] = trace > 0 ? theta2 / trace : 0.0;
+        dg[2] = sqrt(fmax(theta, 0.0) / (double)S) / nrm;
+        dg[3] = 0.0;
+    }
+#undef LF
+#undef RI
+#undef DD
+#undef VV
+#undef WV
+}
+
+// The lane-per-fit solver in double-word FP32 arithmetic (on the FP32 pipes).
+// Moments arrive as normalised double-word pairs; the factor, D, v and w live
+// in shared memory interleaved across the 32 lanes, 8 bytes per entry.
+__global__ void __launch_bounds__(32)
+solve_lane_dw_kernel(const __grid_constant__ FitParams P) {
+    extern __shared__ __align__(16) float2 lsm2[];
+    const int lane = threadIdx.x;
+    const int f = blockIdx.x * 32 + lane;
+    if (f >= P.n_fits) return;
+    const int m = P.m, u = P.u, n_mom = P.n_mom;
+    const int nL = u * (u + 1) / 2;
+    float2* Lf = lsm2;
+    float2* rinv = Lf + nL * 32;
+    float2* Dv = rinv + u * 32;
+    float2* vv = Dv + u * 32;
+    float2* wv = vv + u * 32;
+    auto ld2 = [](const float2 v) -> dw { return dw{v.x, v.y}; };
+    auto st2 = [](dw x) -> float2 { return make_float2(x.h, x.l); };
+#define LF(i, j) Lf[((i) * ((i) + 1) / 2 + (j)) * 32 + lane]
+#define RI(i) rinv[(i) * 32 + lane]
+#define DD(i) Dv[(i) * 32 + lane].x
+#define VV(i) vv[(i) * 32 + lane]
+#define WV(i) wv[(i) * 32 + lane]
+    const float2* M = reinterpret_cast<const float2*>(P.mom) + (int64_t)f * 3 * n_mom;
+    const int64_t S = P.offsets[f + 1] - P.offsets[f];
+    const int32_t fl = P.flags[f];
+    int32_t status = 0;
+    if (S == 0) status = KLR_FIT_EMPTY;
+    else if (fl & 1) status = KLR_FIT_NONFINITE;
+    if (status) {
+        for (int j = 0; j < u; ++j) {
+            if (P.coef_f64) reinterpret_cast<double*>(P.coef)[(int64_t)f * u + j] = 0.0;
+            else reinterpret_cast<float*>(P.coef)[(int64_t)f * u + j] = 0.f;
+        }
+        P.status[f] = status;
+        if (P.diag) for (int k = 0; k < 4; ++k) P.diag[(int64_t)f * 4 + k] = 0.0;
+        return;
+    }
+    if (fl & 2) status |= KLR_FIT_INEXACT;
+    // equilibration: 2^-floor(e/2), e the frexp exponent of the (exact)
+    // double-word diagonal entry
+    dw trace{0.f, 0.f};
+    for (int j = 0; j < u; ++j) {
+        const int bj = j >= m, jj = j - bj * m;
+        const float2 g2 = M[2 * bj * n_mom + P.pair[jj][jj]];
+        float dj = 1.0f;
+        if (g2.x > 0.f) {
+            int e;
+            const float mant = frexpf(g2.x, &e);
+            if (mant == 0.5f && g2.y < 0.f) e -= 1;   // h rounded up to a power of two
+            dj = ldexpf(1.0f, -(e >> 1));
+        }
+        Dv[j * 32 + lane] = make_float2(dj, 0.f);
+        trace = dw_add(trace, dw{g2.x * dj * dj, g2.y * dj * dj});
+    }
+    auto gh = [&](int i, int j) -> dw {
+        const int bi = i >= m, bj = j >= m;
+        const float2 g = M[(bi + bj) * n_mom + P.pair[i - bi * m][j - bj * m]];
+        const float sc = ((bi != bj) ? -1.f : 1.f) * DD(i) * DD(j);   // exact
+        return dw{g.x * sc, g.y * sc};
+    };
+    auto cholesky = [&](dw shift) -> bool {
+        for (int j = 0; j < u; ++j) {
+            dw_acc a0, a1;
+            a0.init(dw_sub(gh(j, j), shift));
+            a1.init(dw{0.f, 0.f});
+            int k = 0;
+            for (; k + 1 < j; k += 2) {
+                const dw x0 = ld2(LF(j, k)), x1 = ld2(LF(j, k + 1));
+                a0.sub_prod(x0, x0);
+                a1.sub_prod(x1, x1);
+            }
+            if (k < j) {
+                const dw x0 = ld2(LF(j, k));
+                a0.sub_prod(x0, x0);
+            }
+            const dw sjj = dw_add(a0.value(), a1.value());
+            if (!(sjj.h > 0.f)) return false;
+            const dw r = dw_div(dw{1.f, 0.f}, dw_sqrt(sjj));
+            RI(j) = st2(r);
+            for (int i = j + 1; i < u; ++i) {
+                dw_acc t0, t1;
+                t0.init(gh(i, j));
+                t1.init(dw{0.f, 0.f});
+                int kk = 0;
+                for (; kk + 1 < j; kk += 2) {
+                    t0.sub_prod(ld2(LF(i, kk)), ld2(LF(j, kk)));
+                    t1.sub_prod(ld2(LF(i, kk + 1)), ld2(LF(j, kk + 1)));
+                }
+                if (kk < j) t0.sub_prod(ld2(LF(i, kk)), ld2(LF(j, kk)));
+                LF(i, j) = st2(dw_mul(dw_add(t0.value(), t1.value()), r));
+            }
+        }
+        return true;
+    };
+    auto solve = [&]() {
+        for (int i = 0; i < u; ++i) {
+            dw_acc t0, t1;
+            t0.init(ld2(WV(i)));
+            t1.init(dw{0.f, 0.f});
+            int k = 0;
+            for (; k + 1 < i; k += 2) {
+                t0.sub_prod(ld2(LF(i, k)), ld2(WV(k)));
+                t1.sub_prod(ld2(LF(i, k + 1)), ld2(WV(k + 1)));
+            }
+            if (k < i) t0.sub_prod(ld2(LF(i, k)), ld2(WV(k)));
+            WV(i) = st2(dw_mul(dw_add(t0.value(), t1.value()), ld2(RI(i))));
+        }
+        for (int i = u - 1; i >= 0; --i) {
+            dw_acc t0, t1;
+            t0.init(ld2(WV(i)));
+            t1.init(dw{0.f, 0.f});
+            int k = i + 1;
+            for (; k + 1 < u; k += 2) {
+                t0.sub_prod(ld2(LF(k, i)), ld2(WV(k)));
+                t1.sub_prod(ld2(LF(k + 1, i)), ld2(WV(k + 1)));
+            }
+            if (k < u) t0.sub_prod(ld2(LF(k, i)), ld2(WV(k)));
+            WV(i) = st2(dw_mul(dw_add(t0.value(), t1.value()), ld2(RI(i))));
+        }
+    };
+    // inverse-iteration step; returns the Rayleigh quotient shift + (v.w)/(w.w)
+    // and the squared change of v (double-word norms, FP32 change)
+    auto step = [&](dw shift, float& dv2) -> dw {
+        for (int i = 0; i < u; ++i) WV(i) = VV(i);
+        solve();
+        dw_acc vw, ww;
+        vw.init(dw{0.f, 0.f});
+        ww.init(dw{0.f, 0.f});
+        for (int i = 0; i < u; ++i) {
+            const dw wi = ld2(WV(i));
+            vw.add_prod(ld2(VV(i)), wi);
+            ww.add_prod(wi, wi);
+        }
+        const dw wwv = ww.value();
+        const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(wwv));
+        dv2 = 0.f;
+        for (int i = 0; i < u; ++i) {
+            const dw nvi = dw_mul(ld2(WV(i)), inv);
+            const dw d = dw_sub(nvi, ld2(VV(i)));
+            dv2 += d.h * d.h;
+            VV(i) = st2(nvi);
+        }
+        return dw_add(shift, dw_div(vw.value(), wwv));
+    };
+    // stop when v moved by less than 1e-10, or stalls (rate above 1/2) below 1e-7
+    auto converged = [](float dv2, float prev) {
+        return dv2 <= 1e-20f || (dv2 <= 1e-14f && dv2 >= 0.25f * prev);
+    };
+
+    const float eps = ldexpf(1.0f, -44);   // double-word unit roundoff (approx.)
+    const dw jitter = dw_mul_f(trace, 4.0f * u * eps);
+    const dw null_level = dw_mul_f(trace, 64.0f * u * eps);
+    dw shift = dw_neg(jitter);
+    bool ok = cholesky(shift);
+    if (!ok) {
+        shift = dw_mul_f(shift, 1024.f);
+        ok = cholesky(shift);
+    }
+    dw theta{0.f, 0.f}, theta2{0.f, 0.f};
+    if (ok) {
+        dw_acc nn;
+        nn.init(dw{0.f, 0.f});
+        for (int i = 0; i < u; ++i) {
+            const float x = 1.0f + 0.0625f * (float)((i * 7) % 11);
+            VV(i) = make_float2(x, 0.f);
+            nn.add_prod(dw{x, 0.f}, dw{x, 0.f});
+        }
+        const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(nn.value()));
+        for (int i = 0; i < u; ++i) VV(i) = st2(dw_mul(ld2(VV(i)), inv));
+        float dv2 = 1.f, prev = 1.f;
+        for (int it = 0; it < 6; ++it) {
+            theta = step(shift, dv2);
+            if (converged(dv2, prev)) break;
+            prev = dv2;
+        }
+        if (dw_gt(theta, null_level)) {
+            const float ladder[7] = {1.0f - 1.0f / 64, 1.0f - 1.0f / 32, 1.0f - 1.0f / 16,
+                                     1.0f - 1.0f / 8, 1.0f - 1.0f / 4, 0.5f, 0.25f};
+            bool done = false;
+            for (int round = 0; round < 3 && !done; ++round) {
+                bool ok2 = false;
+                for (int k = 0; k < 8 && !ok2; ++k) {
+                    shift = k < 7 ? dw_mul_f(theta, ladder[k]) : dw_neg(jitter);
+                    ok2 = cholesky(shift);
+                }
+                if (!ok2) {
+                    status |= KLR_FIT_SOLVE_FAILED;
+                    ok = false;
+                    break;
+                }
+                prev = 1.f;
+                for (int it = 0; it < 8; ++it) {
+                    theta = step(shift, dv2);
+                    if (converged(dv2, prev)) { done = true; break; }
+                    prev = dv2;
+                }
+            }
+        }
+    } else {
+        status |= KLR_FIT_SOLVE_FAILED;
+    }
+    if (ok) {
+        // next eigenvalue: inverse iteration on the complement of v; the
+        // diagonal slots of the packed factor are free and hold the iterate
+        auto project_normalise = [&]() {
+            dw_acc c;
+            c.init(dw{0.f, 0.f});
+            for (int i = 0; i < u; ++i) c.add_prod(ld2(WV(i)), ld2(VV(i)));
+            const dw cv = c.value();
+            dw_acc nn;
+            nn.init(dw{0.f, 0.f});
+            for (int i = 0; i < u; ++i) {
+                const dw wi = dw_sub(ld2(WV(i)), dw_mul(cv, ld2(VV(i))));
+                WV(i) = st2(wi);
+                nn.add_prod(wi, wi);
+            }
+            const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(nn.value()));
+            for (int i = 0; i < u; ++i) WV(i) = st2(dw_mul(ld2(WV(i)), inv));
+        };
+        for (int i = 0; i < u; ++i)
+            WV(i) = make_float2(1.0f + 0.03125f * (float)((i * 5) % 13) - 0.5f * (float)(i & 1), 0.f);
+        project_normalise();
+        for (int it = 0; it < 3; ++it) {
+            for (int i = 0; i < u; ++i) LF(i, i) = WV(i);
+            solve();
+            dw_acc zw, zz;
+            zw.init(dw{0.f, 0.f});
+            zz.init(dw{0.f, 0.f});
+            for (int i = 0; i < u; ++i) {
+                const dw wi = ld2(WV(i));
+                zw.add_prod(wi, ld2(LF(i, i)));
+                zz.add_prod(wi, wi);
+            }
+            theta2 = dw_add(shift, dw_div(zw.value(), zz.value()));
+            project_normalise();
+        }
+        if (!dw_gt(theta2, null_level)) status |= KLR_FIT_RANK_DEFICIENT;
+    }
+    // c = D v, unit norm, sign rule
+    dw_acc nrm2;
+    nrm2.init(dw{0.f, 0.f});
+    for (int i = 0; i < u; ++i) {
+        const dw ci = dw_mul_f(ld2(VV(i)), DD(i));
+        WV(i) = st2(ci);
+        nrm2.add_prod(ci, ci);
+    }
+    const dw nrm = dw_sqrt(nrm2.value());
+    const double nrm_d = dw_to_double(nrm);
+    float sgn = 1.f;
+    const float q0 = WV(m).x / nrm.h;
+    if (fabsf(q0) >= 1e-12f) {
+        sgn = q0 > 0.f ? 1.f : -1.f;
+    } else {
+        float best = -1.f;
+        int bi = m;
+        for (int j = m; j < u; ++j)
+            if (fabsf(WV(j).x) > best) { best = fabsf(WV(j).x); bi = j; }
+        sgn = WV(bi).x > 0.f ? 1.f : -1.f;
+    }
+    const dw scale = ok ? dw_div(dw{sgn, 0.f}, nrm) : dw{0.f, 0.f};
+    for (int j = 0; j < u; ++j) {
+        const dw cj = dw_mul(ld2(WV(j)), scale);
+        if (P.coef_f64) reinterpret_cast<double*>(P.coef)[(int64_t)f * u + j] = dw_to_double(cj);
+        else reinterpret_cast<float*>(P.coef)[(int64_t)f * u + j] = cj.h + cj.l;
+    }
+    P.status[f] = status;
+    if (P.diag) {
+        double* dg = P.diag + (int64_t)f * 4;
+        const double tr = dw_to_double(trace), th = dw_to_double(theta);
+        dg[0] = tr > 0 ? th / tr : 0.0;
+        dg[1] = tr > 0 ? dw_to_double(theta2) / tr : 0.0;
+        dg[2] = sqrt(fmax(th, 0.0) / (double)S) / nrm_d;
+        dg[3] = 0.0;
+    }
+#undef LF
+#undef RI
+#undef DD
+#undef VV
+#undef WV
+}
+
+// The double-word solver with Q lanes per fit (32 / Q fits per warp).  Each
+// fit's factor lives in shared memory (packed lower triangle, 8-byte pairs);
+// row i of the factor is computed by lane i % Q of the fit's group, so a fit's
+// dependency chains are Q times shorter than with one lane per fit and four
+// times as many fits fit in an SM's shared memory per warp.  The triangular
+// solves are column-oriented (each lane updates the rows it owns), so they
+// need no reductions.  Control flow is uniform across the warp: every group
+// runs the same schedule and a group that has finished (or failed) keeps
+// running it with its writes switched off.
+template <int Q>
+__global__ void __launch_bounds__(32)
+solve_group_dw_kernel(const __grid_constant__ FitParams P) {
+    constexpr int GPW = 32 / Q;
+    extern __shared__ __align__(16) float2 gsm[];
+    const int lane = threadIdx.x;
+    const int q = lane % Q, g = lane / Q;
+    const int f_raw = blockIdx.x * GPW + g;
+    const bool live = f_raw < P.n_fits;
+    const int f = live ? f_raw : P.n_fits - 1;   // clamp reads for the spare groups
+    const int m = P.m, u = P.u, n_mom = P.n_mom;
+    const int nL = u * (u + 1) / 2;
+    const int stride = P.ld;                      // float2 per fit (padded)
+    float2* base = gsm + g * stride;
+    float2* Lf = base;
+    float2* rinv = Lf + nL;
+    float2* vv = rinv + u;
+    float2* wv = vv + u;
+    float2* av = wv + u;                          // Dot2 accumulators of the solves
+    float2* Dv = av + u;
+    auto ld2 = [](const float2 v) -> dw { return dw{v.x, v.y}; };
+    auto st2 = [](dw x) -> float2 { return make_float2(x.h, x.l); };
+    const unsigned full = 0xffffffffu;
+    // sum over the Q lanes of a group of a double-word value
+    auto gsum = [&](dw x) -> dw {
+#pragma unroll
+        for (int o = 1; o < Q; o <<= 1) {
+            dw y{__shfl_xor_sync(full, x.h, o), __shfl_xor_sync(full, x.l, o)};
+            x = dw_add(x, y);
+        }
+        return x;
+    };
+#define LF(i, j) Lf[(i) * ((i) + 1) / 2 + (j)]
+    const float2* M = reinterpret_cast<const float2*>(P.mom) + (int64_t)f * 3 * n_mom;
+    const int64_t S = P.offsets[f + 1] - P.offsets[f];
+    const int32_t fl = P.flags[f];
+    int32_t status = 0;
+    if (S == 0) status = KLR_FIT_EMPTY;
+    else if (fl & 1) status = KLR_FIT_NONFINITE;
+    bool ok = (status == 0);
+    if (fl & 2) status |= KLR_FIT_INEXACT;
+    // equilibration (every lane of the group computes all of D; lane 0 stores)
+    dw trace{0.f, 0.f};
+    for (int j = 0; j < u; ++j) {
+        const int bj = j >= m, jj = j - bj * m;
+        const float2 g2 = M[2 * bj * n_mom + P.pair[jj][jj]];
+        float dj = 1.0f;
+        if (g2.x > 0.f) {
+            int e;
+            const float mant = frexpf(g2.x, &e);
+            if (mant == 0.5f && g2.y < 0.f) e -= 1;
+            dj = ldexpf(1.0f, -(e >> 1));
+        }
+        if (q == 0) Dv[j] = make_float2(dj, 0.f);
+        trace = dw_add(trace, dw{g2.x * dj * dj, g2.y * dj * dj});
+    }
+    __syncwarp();
+    auto gh = [&](int i, int j) -> dw {
+        const int bi = i >= m, bj = j >= m;
+        const float2 gg = M[(bi + bj) * n_mom + P.pair[i - bi * m][j - bj * m]];
+        const float sc = ((bi != bj) ? -1.f : 1.f) * Dv[i].x * Dv[j].x;
+        return dw{gg.x * sc, gg.y * sc};
+    };
+    // Cholesky of (Ghat - shift I) for groups with `write`; returns the
+    // group's success (false also for groups not writing)
+    auto cholesky = [&](dw shift, bool write) -> bool {
+        bool good = write;
+        for (int j = 0; j < u; ++j) {
+            dw_acc a;
+            a.init(dw{0.f, 0.f});
+            for (int k = q; k < j; k += Q) {
+                const dw x = ld2(LF(j, k));
+                a.add_prod(x, x);
+            }
+            const dw sjj = dw_sub(dw_sub(gh(j, j), shift), gsum(a.value()));
+            good = good && (sjj.h > 0.f);
+            const dw r = good ? dw_div(dw{1.f, 0.f}, dw_sqrt(sjj)) : dw{1.f, 0.f};
+            if (good && q == 0) rinv[j] = st2(r);
+            for (int i = j + 1 + ((q - (j + 1) % Q) + Q) % Q; i < u; i += Q) {
+                dw_acc t0, t1;
+                t0.init(gh(i, j));
+                t1.init(dw{0.f, 0.f});
+                int k = 0;
+                for (; k + 1 < j; k += 2) {
+                    t0.sub_prod(ld2(LF(i, k)), ld2(LF(j, k)));
+                    t1.sub_prod(ld2(LF(i, k + 1)), ld2(LF(j, k + 1)));
+                }
+                if (k < j) t0.sub_prod(ld2(LF(i, k)), ld2(LF(j, k)));
+                if (good) LF(i, j) = st2(dw_mul(dw_add(t0.value(), t1.value()), r));
+            }
+            __syncwarp();
+        }
+        return good;
+    };
+    // w <- (L L^T)^-1 w, column-oriented; av holds per-row Dot2 accumulators
+    auto solve = [&](bool write) {
+        for (int i = q; i < u; i += Q) av[i] = wv[i];
+        __syncwarp();
+        for (int j = 0; j < u; ++j) {
+            const dw xj = dw_mul(ld2(av[j]), ld2(rinv[j]));   // final y_j (av[j] complete)
+            for (int i = j + 1 + ((q - (j + 1) % Q) + Q) % Q; i < u; i += Q) {
+                dw_acc a;
+                a.init(ld2(av[i]));
+                a.sub_prod(ld2(LF(i, j)), xj);
+                if (write) av[i] = st2(a.value());
+            }
+            if (write && q == j % Q) wv[j] = st2(xj);
+            __syncwarp();
+        }
+        for (int i = q; i < u; i += Q) av[i] = wv[i];
+        __syncwarp();
+        for (int j = u - 1; j >= 0; --j) {
+            const dw xj = dw_mul(ld2(av[j]), ld2(rinv[j]));
+            for (int i = q; i < j; i += Q) {
+                dw_acc a;
+                a.init(ld2(av[i]));
+                a.sub_prod(ld2(LF(j, i)), xj);
+                if (write) av[i] = st2(a.value());
+            }
+            if (write && q == j % Q) wv[j] = st2(xj);
+            __syncwarp();
+        }
+    };
+    auto gdot = [&](const float2* a, const float2* b) -> dw {
+        dw_acc s;
+        s.init(dw{0.f, 0.f});
+        for (int i = q; i < u; i += Q) s.add_prod(ld2(a[i]), ld2(b[i]));
+        return gsum(s.value());
+    };
+    // inverse-iteration step for groups with `write`
+    auto step = [&](dw shift, bool write, float& dv2) -> dw {
+        for (int i = q; i < u; i += Q) wv[i] = vv[i];
+        __syncwarp();
+        solve(write);
+        const dw vw = gdot(vv, wv), ww = gdot(wv, wv);
+        const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(ww));
+        float part = 0.f;
+        for (int i = q; i < u; i += Q) {
+            const dw nvi = dw_mul(ld2(wv[i]), inv);
+            const dw dd = dw_sub(nvi, ld2(vv[i]));
+            part += dd.h * dd.h;
+            if (write) vv[i] = st2(nvi);
+        }
+#pragma unroll
+        for (int o = 1; o < Q; o <<= 1) part += __shfl_xor_sync(full, part, o);
+        dv2 = part;
+        __syncwarp();
+        return dw_add(shift, dw_div(vw, ww));
+    };
+    auto converged = [](float dv2, float prev) {
+        return dv2 <= 1e-20f || (dv2 <= 1e-14f && dv2 >= 0.25f * prev);
+    };
+
+    const float eps = ldexpf(1.0f, -44);
+    const dw jitter = dw_mul_f(trace, 4.0f * u * eps);
+    const dw null_level = dw_mul_f(trace, 64.0f * u * eps);
+    dw shift = dw_neg(jitter);
+    bool fact = cholesky(shift, ok);
+    if (ok && !fact) {
+        shift = dw_mul_f(shift, 1024.f);
+    }
+    {
+        const bool retry = ok && !fact;
+        if (__any_sync(full, retry)) {
+            const bool f2 = cholesky(shift, retry);
+            if (retry) fact = f2;
+        }
+    }
+    if (ok && !fact) {
+        ok = false;
+        status |= KLR_FIT_SOLVE_FAILED;
+    }
+    dw theta{0.f, 0.f}, theta2{0.f, 0.f};
+    for (int i = q; i < u; i += Q) vv[i] = make_float2(1.0f + 0.0625f * (float)((i * 7) % 11), 0.f);
+    __syncwarp();
+    {
+        const dw nn = gdot(vv, vv);
+        const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(nn));
+        for (int i = q; i < u; i += Q) vv[i] = st2(dw_mul(ld2(vv[i]), inv));
+        __syncwarp();
+    }
+    bool active = ok;
+    float dv2 = 1.f, prev = 1.f;
+    for (int it = 0; it < 6 && __any_sync(full, active); ++it) {
+        const dw th = step(shift, active, dv2);
+        if (active) {
+            theta = th;
+            if (converged(dv2, prev)) active = false;
+            prev = dv2;
+        }
+    }
+    // noisy fits: rounds of re-factoring on a ladder of shifts below theta
+    bool noisy = ok && dw_gt(theta, null_level);
+    bool done = !noisy;
+    const float ladder[7] = {1.0f - 1.0f / 64, 1.0f - 1.0f / 32, 1.0f - 1.0f / 16,
+                             1.0f - 1.0f / 8, 1.0f - 1.0f / 4, 0.5f, 0.25f};
+    for (int round = 0; round < 3 && __any_sync(full, !done); ++round) {
+        bool need = !done;      // this group still needs a factor this round
+        bool have = false;
+        for (int k = 0; k < 8 && __any_sync(full, need && !have); ++k) {
+            const bool try_ = need && !have;
+            const dw sh = k < 7 ? dw_mul_f(theta, ladder[k]) : dw_neg(jitter);
+            const bool good = cholesky(sh, try_);
+            if (try_ && good) {
+                have = true;
+                shift = sh;
+            }
+        }
+        if (need && !have) {
+            status |= KLR_FIT_SOLVE_FAILED;
+            ok = false;
+            done = true;
+        }
+        bool act = need && have;
+        prev = 1.f;
+        for (int it = 0; it < 8 && __any_sync(full, act); ++it) {
+            const dw th = step(shift, act, dv2);
+            if (act) {
+                theta = th;
+                if (converged(dv2, prev)) { act = false; done = true; }
+                prev = dv2;
+            }
+        }
+    }
+    // next eigenvalue on the complement of v (rank test); w holds the iterate,
+    // the diagonal slots of the packed factor hold the previous one
+    {
+        auto project_normalise = [&](bool write) {
+            const dw c = gdot(wv, vv);
+            dw_acc nn;
+            nn.init(dw{0.f, 0.f});
+            for (int i = q; i < u; i += Q) {
+                const dw wi = dw_sub(ld2(wv[i]), dw_mul(c, ld2(vv[i])));
+                if (write) wv[i] = st2(wi);
+                nn.add_prod(wi, wi);
+            }
+            __syncwarp();
+            const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(gsum(nn.value())));
+            for (int i = q; i < u; i += Q)
+                if (write) wv[i] = st2(dw_mul(ld2(wv[i]), inv));
+            __syncwarp();
+        };
+        for (int i = q; i < u; i += Q)
+            wv[i] = make_float2(1.0f + 0.03125f * (float)((i * 5) % 13) - 0.5f * (float)(i & 1), 0.f);
+        __syncwarp();
+        project_normalise(ok);
+        for (int it = 0; it < 3; ++it) {
+            for (int i = q; i < u; i += Q) LF(i, i) = wv[i];
+            __syncwarp();
+            solve(ok);
+            dw_acc zw, zz;
+            zw.init(dw{0.f, 0.f});
+            zz.init(dw{0.f, 0.f});
+            for (int i = q; i < u; i += Q) {
+                const dw wi = ld2(wv[i]);
+                zw.add_prod(wi, ld2(LF(i, i)));
+                zz.add_prod(wi, wi);
+            }
+            const dw zwv = gsum(zw.value()), zzv = gsum(zz.value());
+            if (ok) theta2 = dw_add(shift, dw_div(zwv, zzv));
+            project_normalise(ok);
+        }
+        if (ok && !dw_gt(theta2, null_level)) status |= KLR_FIT_RANK_DEFICIENT;
+    }
+    // c = D v, unit norm, sign rule; lane q writes coefficients i = q mod Q
+    for (int i = q; i < u; i += Q) wv[i] = st2(dw_mul_f(ld2(vv[i]), Dv[i].x));
+    __syncwarp();
+    const dw nrm = dw_sqrt(gdot(wv, wv));
+    float sgn = 1.f;
+    {
+        const float q0 = wv[m].x / nrm.h;
+        if (fabsf(q0) >= 1e-12f) {
+            sgn = q0 > 0.f ? 1.f : -1.f;
+        } else {
+            float best = -1.f;
+            int bi = m;
+            for (int j = m; j < u; ++j)
+                if (fabsf(wv[j].x) > best) { best = fabsf(wv[j].x); bi = j; }
+            sgn = wv[bi].x > 0.f ? 1.f : -1.f;
+        }
+    }
+    if (live) {
+        const dw scale = ok ? dw_div(dw{sgn, 0.f}, nrm) : dw{0.f, 0.f};
+        for (int j = q; j < u; j += Q) {
+            const dw cj = ok ? dw_mul(ld2(wv[j]), scale) : dw{0.f, 0.f};
+            if (P.coef_f64) reinterpret_cast<double*>(P.coef)[(int64_t)f * u + j] = dw_to_double(cj);
+            else reinterpret_cast<float*>(P.coef)[(int64_t)f * u + j] = cj.h + cj.l;
+        }
+        if (q == 0) {
+            P.status[f] = status;
+            if (P.diag) {
+                double* dg = P.diag + (int64_t)f * 4;
+                const double tr = dw_to_double(trace), th = dw_to_double(theta);
+                dg[0] = (ok && tr > 0) ? th / tr : 0.0;
+                dg[1] = (ok && tr > 0) ? dw_to_double(theta2) / tr : 0.0;
+                dg[2] = ok ? sqrt(fmax(th, 0.0) / (double)S) / dw_to_double(nrm) : 0.0;
+                dg[3] = 0.0;
+            }
+        }
+    }
+#undef LF
+}
+
+template <typename TS, int ACC>
+klr_status launch_moments(const FitParams& P, int n_mom, int rec, cudaStream_t stream) {
+    // lanes per sample (moment groups) so that a lane holds at most MAXT moments
+    const size_t tc = ACC == ACC_FP64 ? 8 : 4;
+    FitParams Q = P;
+    Q.warp_smem = (int)((32 * rec * tc + 15) & ~(size_t)15);
+    const int wpb = 4;
+    const int blocks = (P.n_fits + wpb - 1) / wpb;
+    // specialised kernels for the common bases (degree 2 in 3 or 4 variables,
+    // degree 3 in 3 variables)
+    auto fast = [&](auto kern, int nm) -> klr_status {
+        FitParams R = P;
+        const int rec_ = nm + 3 + ((nm + 3) % 2 == 0 ? 1 : 0);
+        R.warp_smem = (int)((32 * rec_ * tc + 15) & ~(size_t)15);
+        KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            R.warp_smem * wpb));
+        kern<<<blocks, wpb * 32, (size_t)R.warp_smem * wpb, stream>>>(R);
+        KLR_CHECK_CUDA(cudaGetLastError());
+        return KLR_OK;
+    };
+    if (P.n_vars == 3 && P.degree == 2) return fast(moments_fast_kernel<TS, ACC, 3, 4, 4, 9>, 35);
+    if (P.n_vars == 4 && P.degree == 2) return fast(moments_fast_kernel<TS, ACC, 4, 4, 8, 9>, 70);
+    if (P.n_vars == 3 && P.degree == 3) return fast(moments_fast_kernel<TS, ACC, 3, 6, 8, 11>, 84);
+    const size_t smem = (size_t)Q.warp_smem * wpb;
+    auto generic = [&](auto kern) -> klr_status {
+        KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        kern<<<blocks, wpb * 32, smem, stream>>>(Q);
+        return KLR_OK;
+    };
+    klr_status st;
+    if (n_mom <= 4 * 9) st = generic(moments_kernel<TS, ACC, 4, 9>);
+    else if (n_mom <= 8 * 11) st = generic(moments_kernel<TS, ACC, 8, 11>);
+    else st = generic(moments_kernel<TS, ACC, 16, 14>);
+    if (st != KLR_OK) return st;
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+template <typename TS>
+klr_status launch_solve_warp(const FitParams& P, size_t smem_optin, cudaStream_t stream) {
+    size_t per_warp = sizeof(double) * (3 * (size_t)P.n_mom + (size_t)P.u * P.ld + 6 * (size_t)P.u);
+    per_warp = (per_warp + 15) & ~(size_t)15;
+    int wpb = 4;
+    while (wpb > 1 && per_warp * wpb > 96 * 1024) wpb >>= 1;
+    if (per_warp * wpb > smem_optin) {
+        set_error("klr_fit: %zu bytes of shared memory per fit exceed the device limit", per_warp);
+        return KLR_ENOTSUP;
+    }
+    FitParams Q = P;
+    Q.warp_smem = (int)per_warp;
+    const size_t smem = per_warp * wpb;
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(solve_warp_kernel<TS>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    solve_warp_kernel<TS><<<(P.n_fits + wpb - 1) / wpb, wpb * 32, smem, stream>>>(Q);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+klr_status launch_solve_lane_dw(const FitParams& P, cudaStream_t stream) {
+    const size_t smem = sizeof(float2) * 32 * ((size_t)P.u * (P.u + 1) / 2 + 4 * (size_t)P.u);
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(solve_lane_dw_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    solve_lane_dw_kernel<<<(P.n_fits + 31) / 32, 32, smem, stream>>>(P);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+klr_status launch_solve_group_dw(const FitParams& P, cudaStream_t stream) {
+    constexpr int Q = 4, GPW = 32 / Q;
+    FitParams Q_ = P;
+    int stride = P.u * (P.u + 1) / 2 + 5 * P.u;
+    if (stride % 2 == 0) ++stride;          // spread the groups over the banks
+    Q_.ld = stride;
+    const size_t smem = sizeof(float2) * (size_t)stride * GPW;
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(solve_group_dw_kernel<Q>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    solve_group_dw_kernel<Q><<<(P.n_fits + GPW - 1) / GPW, 32, smem, stream>>>(Q_);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+klr_status launch_solve_lane(const FitParams& P, cudaStream_t stream) {
+    const size_t smem = sizeof(double) * 32 * ((size_t)P.u * (P.u + 1) / 2 + 4 * (size_t)P.u);
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(solve_lane_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    solve_lane_kernel<<<(P.n_fits + 31) / 32, 32, smem, stream>>>(P);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
 }
 
 }  // namespace
+
+size_t fit_workspace_bytes(int64_t n_fits, int n_mom) {
+    return 256 + (size_t)n_fits * (3 * (size_t)n_mom * sizeof(double) + sizeof(int32_t));
+}
+
 }  // namespace klr
 
 using namespace klr;
@@ -595,34 +1800,32 @@ extern "C" klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_o
     memcpy(P.exps, basis.exps, sizeof(P.exps));
     memcpy(P.pair, basis.pair, sizeof(P.pair));
 
-    const bool acc64 = b->precision == KLR_FIT_FP64;
-    const size_t tc = acc64 ? 8 : 4;
-    const int REC = b->n_vars * (2 * b->degree + 1) + 3;
-    size_t per_warp = ((32 * REC * tc + 15) & ~(size_t)15) +
-                      sizeof(double) * (3 * basis.n_mom + (size_t)u * P.ld + 6 * u);
-    per_warp = (per_warp + 15) & ~(size_t)15;
-    P.warp_smem = (int)per_warp;
-    int wpb = 4;
-    while (wpb > 1 && per_warp * wpb > 96 * 1024) wpb >>= 1;
-    if (per_warp * wpb > c->smem_optin) {
-        set_error("klr_fit: %zu bytes of shared memory per warp exceed the device limit",
-                  per_warp);
-        return KLR_ENOTSUP;
-    }
-    const int maxt = (basis.n_mom + kMG - 1) / kMG;
-    const size_t smem_block = per_warp * wpb;
+    klr_status st = ensure_workspace(c, fit_workspace_bytes(b->n_fits, basis.n_mom), stream);
+    if (st != KLR_OK) return st;
+    P.mom = reinterpret_cast<double*>(reinterpret_cast<char*>(c->ws) + 256);
+    P.flags = reinterpret_cast<int32_t*>(P.mom + (size_t)b->n_fits * 3 * basis.n_mom);
+    P.mom_dw = b->precision != KLR_FIT_FP64;
+    const int rec = b->n_vars * (2 * b->degree + 1) + 3;
     const bool s64 = b->sample_dtype == KLR_F64;
     switch (b->precision) {
         case KLR_FIT_FP64:
-            return s64 ? launch_fit<double, ACC_FP64>(P, maxt, smem_block, wpb, stream)
-                       : launch_fit<float, ACC_FP64>(P, maxt, smem_block, wpb, stream);
+            st = s64 ? launch_moments<double, ACC_FP64>(P, basis.n_mom, rec, stream)
+                     : launch_moments<float, ACC_FP64>(P, basis.n_mom, rec, stream);
+            break;
         case KLR_FIT_DF32:
-            return launch_fit<float, ACC_DF32>(P, maxt, smem_block, wpb, stream);
+            st = launch_moments<float, ACC_DF32>(P, basis.n_mom, rec, stream);
+            break;
         case KLR_FIT_FP32:
-            return s64 ? launch_fit<double, ACC_FP32>(P, maxt, smem_block, wpb, stream)
-                       : launch_fit<float, ACC_FP32>(P, maxt, smem_block, wpb, stream);
+            st = s64 ? launch_moments<double, ACC_FP32>(P, basis.n_mom, rec, stream)
+                     : launch_moments<float, ACC_FP32>(P, basis.n_mom, rec, stream);
+            break;
         default:
             set_error("klr_fit: unsupported precision");
             return KLR_ENOTSUP;
     }
+    if (st != KLR_OK) return st;
+    if (b->refine_iters == 0 && u <= kLaneMaxU)
+        return P.mom_dw ? launch_solve_group_dw(P, stream) : launch_solve_lane(P, stream);
+    return s64 ? launch_solve_warp<double>(P, c->smem_optin, stream)
+               : launch_solve_warp<float>(P, c->smem_optin, stream);
 }

@@ -123,10 +123,12 @@ def test_degree3_refinement(klr, ctx):
     assert errs[2] <= errs[0]
 
 
-def test_3d_blocks_degree2(klr, ctx):
+@pytest.mark.parametrize("refine", [0, 1])
+def test_3d_blocks_degree2(klr, ctx, refine):
+    # refine 0 runs the lane-per-fit solver, refine 1 the warp solver + passes
     fb = W.fit_batch(25, 3, 400, n_vars=4, noise=0.01, dtype=np.float32)
-    coef, st, _ = gpu_fit(klr, ctx, fb, klr.FIT_DF32, 1)
-    check(fb, coef, st, "df32", 1)
+    coef, st, _ = gpu_fit(klr, ctx, fb, klr.FIT_DF32, refine)
+    check(fb, coef, st, "df32", refine)
 
 
 def test_fp32_mode_runs_and_reports(klr, ctx):
