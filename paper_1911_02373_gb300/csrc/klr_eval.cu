@@ -79,6 +79,10 @@ __device__ __forceinline__ int active_blocks(long long T, long long R, long long
     return 0;
 }
 
+// a / b: the fast approximate quotient in FP32 (2 ulp), IEEE in FP64
+template <typename T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float qdiv<float>(float a, float b) { return __fdividef(a, b); }
+
 // MWP-CWP (Example 2; Hong and Kim's model) in precision T.
 template <typename T>
 __device__ __forceinline__ T mwpcwp(const T L[8], T Nw, T Bact, T active_sms, T rep,
@@ -90,22 +94,23 @@ __device__ __forceinline__ T mwpcwp(const T L[8], T Nw, T Bact, T active_sms, T 
     const T mem_l_uncoal = mem_ld + (uncoal_mw - one) * dep_u;
     const T mem_l_coal = mem_ld + (coal_mw - one) * dep_c;
     const T mem_insts = coal + uncoal;
-    const T w_u = uncoal / mem_insts;
-    const T w_c = coal / mem_insts;
+    const T inv_mi = qdiv<T>(T(1), mem_insts);
+    const T w_u = uncoal * inv_mi;
+    const T w_c = coal * inv_mi;
     const T mem_l = mem_l_uncoal * w_u + mem_l_coal * w_c;
     const T departure = dep_u * uncoal_mw * w_u + dep_c * coal_mw * w_c;
-    const T mwp_nobw = mem_l / departure;
-    const T bw_per_warp = (T)P.freq * load_bytes / mem_l;
-    const T mwp_peakbw = (T)P.bw / (bw_per_warp * active_sms);
+    const T mwp_nobw = qdiv<T>(mem_l, departure);
+    const T bw_per_warp = qdiv<T>((T)P.freq * load_bytes, mem_l);
+    const T mwp_peakbw = qdiv<T>((T)P.bw, bw_per_warp * active_sms);
     const T mwp = fmin(fmin(mwp_nobw, mwp_peakbw), Nw);
     const T comp_cycles = issue * (comp + coal + uncoal);
     const T mem_cycles = mem_l_uncoal * uncoal + mem_l_coal * coal;
-    const T cwp_full = (mem_cycles + comp_cycles) / comp_cycles;
+    const T cwp_full = qdiv<T>(mem_cycles + comp_cycles, comp_cycles);
     const T cwp = fmin(cwp_full, Nw);
-    const T per_mem = comp_cycles / mem_insts * (mwp - one);
+    const T per_mem = comp_cycles * inv_mi * (mwp - one);
     T e;
     if (mwp == Nw && cwp == Nw) e = (mem_cycles + comp_cycles + per_mem) * rep;
-    else if (cwp >= mwp || comp_cycles > mem_cycles) e = (mem_cycles * Nw / mwp + per_mem) * rep;
+    else if (cwp >= mwp || comp_cycles > mem_cycles) e = (qdiv<T>(mem_cycles * Nw, mwp) + per_mem) * rep;
     else e = (mem_l + comp_cycles * Nw) * rep;
     return e + departure * (mwp - one) * synch * Bact * rep;
 }
@@ -171,19 +176,56 @@ __device__ void write_launch(const EvalParams& P, int64_t q, long long N, int c)
     o[5] = b2;
 }
 
-template <typename T>
+// floor(n / d) for n < 2^24 from an FP32 reciprocal, corrected to exact
+__device__ __forceinline__ unsigned udiv_small(unsigned n, unsigned d, float rd) {
+    unsigned q = (unsigned)((float)n * rd);
+    int r = (int)(n - q * d);
+    while (r < 0) { --q; r += (int)d; }
+    while (r >= (int)d) { ++q; r -= (int)d; }
+    return q;
+}
+
+// The rare in-place FP64 re-decision when the tie list is full (kept out of
+// line so the sweep's register allocation does not carry it).
+__device__ __noinline__ void decide_f64_inplace(const EvalParams& P, int k, int64_t q,
+                                                long long N, int st) {
+    double bv = INFINITY, sv = INFINITY;
+    int bj = -1;
+    for (int c = 0; c < P.n_cfg; ++c) {
+        bool us;
+        double v = eval_full_f64(P, k, N, c, us);
+        if (v < bv) { sv = bv; bv = v; bj = c; }
+        else if (v < sv) sv = v;
+    }
+    P.best[q] = bj;
+    reinterpret_cast<float*>(P.best_cycles)[q] = (float)bv;
+    if (P.margin) P.margin[q] = isfinite(sv) ? (float)((sv - bv) / bv) : INFINITY;
+    if (P.q_status) P.q_status[q] = st;
+    write_launch(P, q, N, bj);
+}
+
+// Per-configuration integer facts staged in shared memory.
+struct CfgInfo {
+    int T, B, W, b0, b1, b2;
+    int t_shift;      // log2 T when T is a power of two, else -1
+    unsigned wave;    // B_active * #SMs: blocks per full wave
+};
+
+template <typename T, int D>
 __global__ void __launch_bounds__(256)
 eval_kernel(const __grid_constant__ EvalParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int d = P.degree, m = P.m, u = P.u, n_cfg = P.n_cfg;
-    const int NC = 2 * (d + 1);               // coefficients per (config, metric)
+    constexpr int NC = 2 * (D + 1);           // coefficients per (config, metric)
+    const int m = P.m, u = P.u, n_cfg = P.n_cfg;
     T* coef_s = reinterpret_cast<T*>(smem_raw);                 // 8 x u
     T* spec = coef_s + 8 * u;                                   // n_cfg x 8 x NC
-    int* cinfo = reinterpret_cast<int*>(spec + (size_t)n_cfg * 8 * NC);  // n_cfg x 6
+    CfgInfo* cinfo = reinterpret_cast<CfgInfo*>(spec + (size_t)n_cfg * 8 * NC);
+    float* wave_rcp = reinterpret_cast<float*>(cinfo + n_cfg);
     const T n_scale = (T)ldexp(1.0, -P.n_scale_log2);
     T lo[8], sc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) { lo[i] = (T)P.lo[i]; sc[i] = (T)P.sc[i]; }
+    const unsigned n_sm = (unsigned)P.n_sm;
 
     for (int k = blockIdx.x; k < P.n_kernels; k += gridDim.x) {
         const int64_t qa = P.q_off[k], qb = P.q_off[k + 1];
@@ -197,15 +239,20 @@ eval_kernel(const __grid_constant__ EvalParams P) {
         for (int c = threadIdx.x; c < n_cfg; c += blockDim.x) {
             const long long b0 = P.cfg[3 * c], b1 = P.cfg[3 * c + 1], b2 = P.cfg[3 * c + 2];
             const long long Tt = b0 * b1 * b2;
-            const int B = active_blocks(Tt, R, Z, P);
+            int B = active_blocks(Tt, R, Z, P);
+            if (Tt > P.T_max) B = 0;
             const int W = (int)min((long long)B * Tt / 32, (long long)P.W_max);
-            int* ci = cinfo + 6 * c;
-            ci[0] = (int)Tt;
-            ci[1] = (B > 0 && Tt <= P.T_max) ? B : 0;
-            ci[2] = W;
-            ci[3] = (int)b0;
-            ci[4] = P.dims >= 2 ? (int)b1 : 1;
-            ci[5] = P.dims >= 3 ? (int)b2 : 1;
+            CfgInfo ci;
+            ci.T = (int)Tt;
+            ci.B = B;
+            ci.W = W;
+            ci.b0 = (int)b0;
+            ci.b1 = P.dims >= 2 ? (int)b1 : 1;
+            ci.b2 = P.dims >= 3 ? (int)b2 : 1;
+            ci.t_shift = (Tt > 0 && (Tt & (Tt - 1)) == 0) ? __ffsll(Tt) - 1 : -1;
+            ci.wave = (unsigned)max(B, 1) * n_sm;
+            cinfo[c] = ci;
+            wave_rcp[c] = 1.0f / (float)ci.wave;
         }
         __syncthreads();
         // fold the block shape into univariate polynomials in the scaled N
@@ -215,11 +262,11 @@ eval_kernel(const __grid_constant__ EvalParams P) {
             xb[0] = (T)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
             xb[1] = (T)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
             xb[2] = (T)ldexp((double)P.cfg[3 * c + 2], -P.b_scale_log2);
-            T acc[2][4];
+            T acc[2][D + 1];
 #pragma unroll
             for (int s = 0; s < 2; ++s)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[s][j] = T(0);
+                for (int j = 0; j <= D; ++j) acc[s][j] = T(0);
             for (int t = 0; t < m; ++t) {
                 T bm = T(1);
                 for (int v = 1; v < P.n_vars; ++v)
@@ -227,52 +274,84 @@ eval_kernel(const __grid_constant__ EvalParams P) {
                 const int j = P.exps[t][0];
                 const T a = coef_s[i * u + t] * bm, b = coef_s[i * u + m + t] * bm;
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
+                for (int jj = 0; jj <= D; ++jj)
                     if (jj == j) { acc[0][jj] += a; acc[1][jj] += b; }
             }
             T* sp = spec + (size_t)idx * NC;
-            for (int j = 0; j <= d; ++j) {
+#pragma unroll
+            for (int j = 0; j <= D; ++j) {
                 sp[j] = acc[0][j];
-                sp[d + 1 + j] = acc[1][j];
+                sp[D + 1 + j] = acc[1][j];
             }
         }
         __syncthreads();
 
         for (int64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) {
             const long long N = P.q_N[q];
+            const bool small = N < (1LL << 24);   // 32-bit wave counts exact
             const T xN = (T)N * n_scale;
             T topv[kTopK];
             int topi[kTopK];
 #pragma unroll
             for (int j = 0; j < kTopK; ++j) { topv[j] = (T)INFINITY; topi[j] = -1; }
             int st = 0;
+#pragma unroll 1
             for (int c = 0; c < n_cfg; ++c) {
-                const int* ci = cinfo + 6 * c;
-                const int B = ci[1];
-                const bool meaningful = B > 0 && ci[3] <= N && ci[4] <= N && ci[5] <= N;
+                const CfgInfo ci = cinfo[c];
+                const int B = ci.B;
+                const bool meaningful = B > 0 && ci.b0 <= N && ci.b1 <= N && ci.b2 <= N;
                 T e = (T)INFINITY;
                 if (meaningful) {
+                    T a[8 * NC];
                     const T* sp = spec + (size_t)c * 8 * NC;
+                    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                        for (int t = 0; t < 2 * NC; ++t) {
+                            const float4 f4 = reinterpret_cast<const float4*>(sp)[t];
+                            a[4 * t] = f4.x; a[4 * t + 1] = f4.y; a[4 * t + 2] = f4.z; a[4 * t + 3] = f4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < 4 * NC; ++t) {
+                            const double2 d2 = reinterpret_cast<const double2*>(sp)[t];
+                            a[2 * t] = d2.x; a[2 * t + 1] = d2.y;
+                        }
+                    }
                     T L[8];
                     bool valid = true;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const T* a = sp + i * NC;
-                        T p = a[d], qq = a[2 * d + 1];
-                        for (int j = d - 1; j >= 0; --j) {
-                            p = p * xN + a[j];
-                            qq = qq * xN + a[d + 1 + j];
+                        const T* ai = a + i * NC;
+                        T p = ai[D], qq = ai[2 * D + 1];
+#pragma unroll
+                        for (int j = D - 1; j >= 0; --j) {
+                            p = p * xN + ai[j];
+                            qq = qq * xN + ai[D + 1 + j];
                         }
-                        const T g = p / qq;
+                        const T g = qdiv<T>(p, qq);
                         valid = valid && (qq != T(0)) && isfinite(g);
                         L[i] = lo[i] + sc[i] * fabs(g);
                     }
                     if (valid) {
-                        const long long Tt = ci[0];
-                        const long long nb = ceil_div(N, Tt);
-                        const long long asm_ = min((long long)P.n_sm, nb);
-                        const long long rep = ceil_div(nb, (long long)B * asm_);
-                        e = mwpcwp<T>(L, (T)ci[2], (T)B, (T)asm_, (T)rep, P);
+                        long long nb, asm_, rep;
+                        if (small) {
+                            const unsigned n32 = (unsigned)N, t32 = (unsigned)ci.T;
+                            const unsigned nb32 = ci.t_shift >= 0 ? (n32 + t32 - 1) >> ci.t_shift
+                                                                  : (n32 + t32 - 1) / t32;
+                            nb = nb32;
+                            if (nb32 <= n_sm) {
+                                asm_ = nb32;
+                                rep = 1;   // ceil(nb / (B nb)) with B >= 1
+                            } else {
+                                asm_ = n_sm;
+                                rep = udiv_small(nb32 + ci.wave - 1, ci.wave, wave_rcp[c]);
+                            }
+                        } else {
+                            nb = ceil_div(N, (long long)ci.T);
+                            asm_ = min((long long)n_sm, nb);
+                            rep = ceil_div(nb, (long long)B * asm_);
+                        }
+                        e = mwpcwp<T>(L, (T)ci.W, (T)B, (T)asm_, (T)rep, P);
                         if (!isfinite(e)) { e = (T)INFINITY; st |= KLR_Q_BAD_METRIC; }
                     } else {
                         st |= KLR_Q_BAD_METRIC;
@@ -299,10 +378,10 @@ eval_kernel(const __grid_constant__ EvalParams P) {
             if (bi < 0) st |= KLR_Q_NONE_FEASIBLE;
             float mg = 0.f;
             if (bi >= 0) mg = isfinite((float)topv[1]) ? (float)((topv[1] - topv[0]) / topv[0]) : INFINITY;
-            bool deferred = false;
             if (std::is_same<T, float>::value && bi >= 0 && isfinite(topv[1]) &&
                 (double)topv[1] <= (double)topv[0] * (1.0 + kTieWindow)) {
                 // near-tie in FP32: hand the candidates to the FP64 re-decision
+                st |= KLR_Q_TIE_RESOLVED;
                 const int slot = atomicAdd(P.tie_count, 1);
                 if (slot < P.tie_cap) {
                     TieRecord r;
@@ -314,24 +393,8 @@ eval_kernel(const __grid_constant__ EvalParams P) {
                             r.cand[n++] = topi[j];
                     r.n = (n == kTopK) ? -1 : n;   // all top-k tied: re-sweep everything
                     P.ties[slot] = r;
-                    deferred = true;
-                }
-                st |= KLR_Q_TIE_RESOLVED;
-                if (!deferred) {
-                    // scratch full: decide here in FP64 over every configuration
-                    double bv = INFINITY, sv = INFINITY;
-                    int bj = -1;
-                    for (int c = 0; c < n_cfg; ++c) {
-                        bool us;
-                        double v = eval_full_f64(P, k, N, c, us);
-                        if (v < bv) { sv = bv; bv = v; bj = c; }
-                        else if (v < sv) sv = v;
-                    }
-                    P.best[q] = bj;
-                    reinterpret_cast<float*>(P.best_cycles)[q] = (float)bv;
-                    if (P.margin) P.margin[q] = isfinite(sv) ? (float)((sv - bv) / bv) : INFINITY;
-                    if (P.q_status) P.q_status[q] = st;
-                    write_launch(P, q, N, bj);
+                } else {
+                    decide_f64_inplace(P, k, q, N, st);   // scratch full
                     continue;
                 }
             }
@@ -479,7 +542,19 @@ size_t eval_smem_bytes(const EvalParams& P, size_t tsz) {
     const int NC = 2 * (P.degree + 1);
     size_t b = tsz * (8 * (size_t)P.u + (size_t)P.n_cfg * 8 * NC);
     b = (b + 15) & ~(size_t)15;
-    return b + sizeof(int) * 6 * (size_t)P.n_cfg;
+    return b + (sizeof(CfgInfo) + sizeof(float)) * (size_t)P.n_cfg;
+}
+
+template <typename T, int D>
+klr_status launch_eval_t(Context* c, EvalParams& P, size_t smem, int threads, cudaStream_t stream) {
+    auto k = eval_kernel<T, D>;
+    int per_sm = 0;
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
+    const int grid = (int)std::min<int64_t>(P.n_kernels, (int64_t)c->n_sm * std::max(per_sm, 1));
+    k<<<grid, threads, smem, stream>>>(P);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
 }
 
 klr_status launch_eval(Context* c, EvalParams& P, bool f64, cudaStream_t stream) {
@@ -492,22 +567,14 @@ klr_status launch_eval(Context* c, EvalParams& P, bool f64, cudaStream_t stream)
     const int64_t per_kernel = P.n_kernels ? (P.n_q + P.n_kernels - 1) / P.n_kernels : 1;
     int threads = 32;
     while (threads < 256 && threads < per_kernel) threads <<= 1;
-    int per_sm = 0;
-    if (f64) {
-        auto k = eval_kernel<double>;
-        KLR_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
-        const int grid = (int)std::min<int64_t>(P.n_kernels, (int64_t)c->n_sm * std::max(per_sm, 1));
-        k<<<grid, threads, smem, stream>>>(P);
-    } else {
-        auto k = eval_kernel<float>;
-        KLR_CHECK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem));
-        const int grid = (int)std::min<int64_t>(P.n_kernels, (int64_t)c->n_sm * std::max(per_sm, 1));
-        k<<<grid, threads, smem, stream>>>(P);
+    switch (P.degree * 2 + (f64 ? 1 : 0)) {
+        case 2: return launch_eval_t<float, 1>(c, P, smem, threads, stream);
+        case 3: return launch_eval_t<double, 1>(c, P, smem, threads, stream);
+        case 4: return launch_eval_t<float, 2>(c, P, smem, threads, stream);
+        case 5: return launch_eval_t<double, 2>(c, P, smem, threads, stream);
+        case 6: return launch_eval_t<float, 3>(c, P, smem, threads, stream);
+        default: return launch_eval_t<double, 3>(c, P, smem, threads, stream);
     }
-    KLR_CHECK_CUDA(cudaGetLastError());
-    return KLR_OK;
 }
 
 }  // namespace
