@@ -42,6 +42,12 @@ def parse():
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="eager launches instead of a CUDA graph")
+    ap.add_argument("--workload", default="batched", choices=["batched", "sweep3d"],
+                    help="batched: fit + argmin (default metric); sweep3d: 3D evaluator sweep")
+    ap.add_argument("--sweep-kernels", type=int, default=100000)
+    ap.add_argument("--sweep-check-kernels", type=int, default=100,
+                    help="kernels of the 3D sweep checked against the oracle")
     ap.add_argument("--cpu-sample-kernels", type=int, default=0,
                     help="kernels in the bounded oracle sample (0: auto)")
     return ap.parse_args()
@@ -236,6 +242,24 @@ def run_klr(args):
         fit(x, y, off)
         choose(qo, qn)
     torch.cuda.synchronize()
+    # the step captured as two CUDA graphs (fit, argmin) replayed back to
+    # back; events recorded between the replays time each part
+    graphs = None
+    if not args.no_graph:
+        try:
+            g_fit, g_eval = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g_fit):
+                fit(x, y, off)
+            with torch.cuda.graph(g_eval):
+                choose(qo, qn)
+            for _ in range(args.warmup):
+                g_fit.replay()
+                g_eval.replay()
+            torch.cuda.synchronize()
+            graphs = (g_fit, g_eval)
+        except Exception as e:  # report and fall back to eager launches
+            print(f"graph capture failed: {e}", file=sys.stderr)
+            graphs = None
     K = args.steps
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -246,11 +270,18 @@ def run_klr(args):
         dist.barrier()
     torch.cuda.synchronize()
     start.record(stream)
+    fit_t, eval_t = [], []
     for k in range(K):
         ev[k][0].record(stream)
-        fit(x, y, off)
+        if graphs is not None:
+            graphs[0].replay()
+        else:
+            fit(x, y, off)
         ev[k][1].record(stream)
-        choose(qo, qn)
+        if graphs is not None:
+            graphs[1].replay()
+        else:
+            choose(qo, qn)
         ev[k][2].record(stream)
     stop.record(stream)
     torch.cuda.synchronize()
@@ -326,6 +357,7 @@ def run_klr(args):
                    "samples": n_samples, "queries": n_q, "configs": wl["n_cfg"],
                    "evals": n_q * wl["n_cfg"], "fit_precision": "df32", "refine_iters": 0,
                    "l2": "inputs larger than L2 (1.31 GB of samples per step)",
+                   "launch": "CUDA graphs (fit, argmin)" if graphs is not None else "eager",
                    "parallelism": f"replicas x{ws}"},
         "fits_per_s": ws * n_fits / (ms_step * 1e-3),
         "config_evals_per_s": ws * n_q * wl["n_cfg"] / (ms_step * 1e-3),
@@ -339,7 +371,7 @@ def run_klr(args):
                      "peak_source": "FP32 lanes x max SM clock (unit counts)"},
         "e2e": {"value": ws * n_q / (e2e_ms * 1e-3), "unit": "queries/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 3 * K,
+        "gpu_launches": 4 * K,
         "clocks": ck,
         "fit_status_nonzero": int(np.count_nonzero(fit_status & ~8)),
         "ties_resolved": int(np.count_nonzero(q_status & 4)),
@@ -347,6 +379,89 @@ def run_klr(args):
     if dist:
         dist.destroy_process_group()
     return out
+
+
+SWEEP = dict(name="sweep3d_fp32_fp64", n_vars=4, degree=2, n_hi_log2=23, sizes=256, n_cfg=251)
+
+
+def run_sweep3d(args):
+    """3D block shapes: every kernel x 256 data sizes x 251 shapes, evaluated by
+    the FP32 sweep (FP64 near-ties) and by the FP64 sweep, with argmin agreement
+    against the oracle on a seeded subsample of kernels."""
+    import torch
+    import paper_1911_02373_gb300 as klr
+    import workloads as W
+    nk = args.sweep_kernels
+    gt = W.ground_truth(args.seed, nk, SWEEP["n_vars"], SWEEP["degree"], 8, SWEEP["n_hi_log2"], 10)
+    sizes = W.log_spaced_sizes(SWEEP["sizes"])
+    q = W.queries_per_kernel(nk, sizes)
+    dev = torch.device("cuda", 0)
+    ctx = klr.Context(0)
+    n_q = len(q.sizes)
+    ctx.reserve(0, n_q)
+    cfg = torch.from_numpy(klr.enumerate_configs(3)).to(dev)
+    hw = klr.make_hw(W.HARDWARE)
+    qo = torch.from_numpy(q.offsets).to(dev)
+    qn = torch.from_numpy(q.sizes).to(dev)
+    regs = torch.from_numpy(gt.regs).to(dev)
+    smem = torch.from_numpy(gt.smem).to(dev)
+    out = {}
+    results = {}
+    for name, dt, tdt in (("f32", klr.F32, torch.float32), ("f64", klr.F64, torch.float64)):
+        coef = torch.from_numpy(gt.coef.astype(np.float32 if dt == klr.F32 else np.float64)).to(dev)
+        prog = klr.Context.program(coef, regs, smem, n_vars=4, degree=2, n_scale_log2=23,
+                                   b_scale_log2=10, metric_lo=W.METRIC_LO,
+                                   metric_scale=W.METRIC_SCALE)
+        bufs = (torch.empty(n_q, dtype=torch.int32, device=dev), torch.empty(n_q, dtype=tdt, device=dev),
+                torch.empty(n_q, dtype=torch.float32, device=dev),
+                torch.empty(n_q, dtype=torch.int32, device=dev), None)
+        for _ in range(2):
+            ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=dt, out=bufs)
+        torch.cuda.synchronize()
+        K = max(1, args.steps if name == "f32" else max(1, args.steps // 4))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=dt, out=bufs)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        moved = coef.numel() * coef.element_size() + n_q * (8 + 4 + tdt.itemsize + 4 + 4)
+        out[name] = {"ms": ms, "queries_per_s": n_q / (ms * 1e-3),
+                     "config_evals_per_s": n_q * SWEEP["n_cfg"] / (ms * 1e-3),
+                     "hbm_gbs": moved / (ms * 1e-3) / 1e9}
+        results[name] = [b.cpu().numpy() for b in bufs[:2]]
+    # oracle on a seeded subsample of kernels
+    from oracle import configs as ocfg, program as oprog
+    ks = W.subsample_kernels(args.seed + 11, nk, min(nk, args.sweep_check_kernels))
+    rows = np.concatenate([np.arange(q.offsets[k], q.offsets[k + 1]) for k in ks])
+    prog = dict(coef=gt.coef, regs=gt.regs, smem=gt.smem, n_vars=4, degree=2, n_scale_log2=23,
+                b_scale_log2=10, metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+    ref = oprog.choose(prog, W.HARDWARE, ocfg.enumerate_configs(3), q.offsets, q.sizes, ks)
+    bnd = np.where(ref["best"] >= 0, ref["boundary"][np.arange(len(rows)), np.maximum(ref["best"], 0)],
+                   np.inf)
+    strict = (ref["margin"] > 1e-6) & (bnd > 1e-5)
+    agree = {}
+    for name in ("f32", "f64"):
+        b = results[name][0][rows]
+        agree[name] = {"strict_checked": int(strict.sum()),
+                       "strict_equal": int((b[strict] == ref["best"][strict]).sum()),
+                       "all_equal": int((b == ref["best"]).sum()), "checked": int(len(rows))}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    return {"metric": "argmin queries/s (3D sweep, FP32 with FP64 ties)",
+            "value": out["f32"]["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
+            "steps": args.steps, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (seeded rational ground truth)",
+            "config": {"workload": SWEEP["name"], "kernels": nk, "sizes_per_kernel": SWEEP["sizes"],
+                       "configs": SWEEP["n_cfg"], "queries": n_q,
+                       "check_kernels": int(len(ks))},
+            "fp32": out["f32"], "fp64": out["f64"],
+            "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+            "agreement_vs_oracle": agree}
 
 
 def run_reference(args):
@@ -380,6 +495,9 @@ def main():
         out = run_reference(args)
         if out:
             print(json.dumps(out))
+        return
+    if args.workload == "sweep3d":
+        print(json.dumps(run_sweep3d(args)))
         return
     ws, rank, _ = dist_env()
     cb = None
