@@ -18,10 +18,12 @@ Modules, each citing the paper passage it follows:
 * ``mwpcwp``    -- the MWP-CWP execution-time model cited by Example 2.
 * ``program``   -- the whole rational program: fitted metrics -> occupancy ->
   MWP-CWP -> constrained argmin (Section IV, steps 4 and 5).
+* ``mlp``       -- the learned proposer's network, loss, gradients and AdamW
+  (this project's addition; the paper has no learned component).
 
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` against
 closed forms, brute force, hand-worked cases or library routines, except
 the fidelity of the MWP-CWP formula to the paper's own generated code, which the
 paper does not print (parity unpinned; see ``mwpcwp``).
 """
-from . import configs, rational, occupancy, mwpcwp, program  # noqa: F401
+from . import configs, rational, occupancy, mwpcwp, program, mlp  # noqa: F401
