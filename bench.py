@@ -43,11 +43,16 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of a CUDA graph")
-    ap.add_argument("--workload", default="batched", choices=["batched", "sweep3d"],
+    ap.add_argument("--workload", default="batched", choices=["batched", "sweep3d", "surrogate"],
                     help="batched: fit + argmin (default metric); sweep3d: 3D evaluator sweep")
     ap.add_argument("--sweep-kernels", type=int, default=100000)
     ap.add_argument("--sweep-check-kernels", type=int, default=100,
                     help="kernels of the 3D sweep checked against the oracle")
+    ap.add_argument("--sur-kernels", type=int, default=50000)
+    ap.add_argument("--sur-rows-per-kernel", type=int, default=400)
+    ap.add_argument("--sur-epochs", type=int, default=2)
+    ap.add_argument("--sur-queries-per-kernel", type=int, default=20)
+    ap.add_argument("--sur-k", type=int, default=8)
     ap.add_argument("--cpu-sample-kernels", type=int, default=0,
                     help="kernels in the bounded oracle sample (0: auto)")
     return ap.parse_args()
@@ -464,6 +469,118 @@ def run_sweep3d(args):
             "agreement_vs_oracle": agree}
 
 
+def run_surrogate(args):
+    """Learned proposer at scale: train the surrogate on rows labelled by the
+    rational program, then resolve argmin queries by top-k proposal + exact
+    re-ranking and compare with the plain sweep (time and top-1 regret)."""
+    import torch
+    import paper_1911_02373_gb300 as klr
+    from paper_1911_02373_gb300 import proposer
+    import workloads as W
+    nk, seed = args.sur_kernels, args.seed
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    t0 = time.time()
+    gt = W.ground_truth(seed, nk, 3, 3, 8, 23, 10)
+    n_coef = 8 * gt.coef.shape[-1]
+    coef3 = t(gt.coef.astype(np.float32))
+    coef = coef3.reshape(nk, n_coef)
+    regs, smem = t(gt.regs), t(gt.smem)
+    ctx = klr.Context(0)
+    cfg = t(klr.enumerate_configs(2))
+    hw = klr.make_hw(W.HARDWARE)
+    prog = klr.Context.program(coef3, regs, smem, n_vars=3, degree=3, n_scale_log2=23,
+                               b_scale_log2=10, metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+    # training rows: (size, shape) pairs drawn per kernel over 64 log-spaced sizes
+    sizes = W.log_spaced_sizes(64)
+    q = W.queries_per_kernel(nk, sizes)
+    R = args.sur_rows_per_kernel
+    keys = W.stream_keys(seed, (90,), np.arange(nk, dtype=np.uint64))
+    draw = W.words(keys[:, None], np.arange(R, dtype=np.uint64)[None, :]) % np.uint64(64 * 51)
+    draw = draw.astype(np.int64)
+    row_q = (np.arange(nk)[:, None] * 64 + draw // 51).reshape(-1)
+    row_c = (draw % 51).reshape(-1)
+    y = proposer.table_targets(ctx, prog, hw, cfg, t(q.offsets), t(q.sizes), t(row_q), t(row_c))
+    keep = torch.isfinite(y)
+    rq, rc, y = t(row_q)[keep], t(row_c)[keep], y[keep]
+    mu, sd = float(y.mean()), float(y.std())
+    target = ((y - mu) / sd).float().contiguous()
+    kern = (rq // 64).int().contiguous()
+    N = t(q.sizes)[rq].contiguous()
+    ci = rc.int().contiguous()
+    n_rows = kern.numel()
+    z = W.normal(W.stream_key(seed, 91), np.arange(klr.mlp_param_count(n_coef), dtype=np.uint64))
+    sur = klr.Surrogate(ctx, n_coef, proposer.init_params(n_coef, z), np.ones(7))
+    okeys = W.stream_keys(seed, (92,), np.arange(args.sur_epochs, dtype=np.uint64))
+    order = lambda ep: torch.argsort(t(W.words(okeys[ep], np.arange(n_rows, dtype=np.uint64))
+                                       .view(np.int64)))
+    prep_s = time.time() - t0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = proposer.train(sur, coef, cfg, kern, N, ci, target, batch=65536,
+                            epochs=args.sur_epochs, lr=2e-3, order=order, log_every=50)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    steps = args.sur_epochs * ((n_rows + 65535) // 65536)
+    # evaluation queries: sizes off the training grid
+    qk = args.sur_queries_per_kernel
+    ek = W.stream_keys(seed, (93,), np.arange(nk, dtype=np.uint64))
+    u = (W.words(ek[:, None], np.arange(qk, dtype=np.uint64)[None, :]) >> np.uint64(11)).astype(
+        np.float64) * 2.0 ** -53
+    ev_sizes = np.floor(np.exp2(8 + 15 * u)).astype(np.int64).reshape(-1)
+    qo = t(np.arange(nk + 1, dtype=np.int64) * qk)
+    qn = t(ev_sizes)
+    n_q = qn.numel()
+    ctx.reserve(0, n_q)
+    K = max(1, args.steps // 10)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            r = fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / K, r
+    plain_ms, plain = timed(lambda: ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=klr.F32))
+    sur_ms, surr = timed(lambda: proposer.propose_and_rerank(ctx, sur, prog, hw, coef, regs, smem,
+                                                             cfg, qo, qn, args.sur_k))
+    prop_ms, _ = timed(lambda: sur.propose(coef, regs, smem, hw, cfg, qo, qn, args.sur_k))
+    c_best = plain[1].cpu().numpy().astype(np.float64)
+    c_sur = surr[1].cpu().numpy().astype(np.float64)
+    ok = np.isfinite(c_best)
+    reg = c_sur[ok] / c_best[ok] - 1.0
+    reg = np.where(np.isfinite(reg), reg, np.inf)
+    rk = W.stream_keys(seed, (94,), np.arange(n_q, dtype=np.uint64))
+    rnd = (W.words(rk[:, None], np.arange(args.sur_k, dtype=np.uint64)[None, :]) % np.uint64(51))
+    rb = klr.argmin_candidates(ctx, prog, hw, cfg, qo, qn, t(rnd.astype(np.int32)))
+    rreg = rb[1].cpu().numpy()[ok] / c_best[ok] - 1.0
+    rreg = np.where(np.isfinite(rreg), rreg, np.inf)
+    pct = lambda a, p: float(np.percentile(a, p))
+    return {"metric": "argmin queries/s (surrogate top-k proposal + exact re-rank)",
+            "value": n_q / (sur_ms * 1e-3), "unit": "queries/s", "n_gpus": 1, "steps": K,
+            "higher_is_better": True, "dtype": "bf16 (network), f32 (re-rank)",
+            "data": "synthetic (seeded rational ground truth)",
+            "config": {"workload": "learned_proposer", "kernels": nk, "degree": 3,
+                       "train_rows": n_rows, "epochs": args.sur_epochs, "batch": 65536,
+                       "train_steps": steps, "queries": n_q, "k": args.sur_k, "configs": 51},
+            "plain_sweep": {"ms": plain_ms, "queries_per_s": n_q / (plain_ms * 1e-3)},
+            "surrogate_path": {"ms": sur_ms, "propose_ms": prop_ms,
+                               "speedup_vs_plain": plain_ms / sur_ms},
+            "train": {"ms": train_ms, "rows_per_s": n_rows * args.sur_epochs / (train_ms * 1e-3),
+                      "loss_first": losses[0], "loss_last": losses[-1], "prep_s": prep_s},
+            "regret_top1": {"mean": float(np.mean(np.minimum(reg, 10))),
+                            "median": pct(reg, 50), "p90": pct(reg, 90), "p99": pct(reg, 99),
+                            "exact_fraction": float(np.mean(reg <= 1e-6)),
+                            "within_1pct": float(np.mean(reg <= 0.01))},
+            "random_k_regret": {"mean": float(np.mean(np.minimum(rreg, 10))),
+                                "median": pct(rreg, 50),
+                                "within_1pct": float(np.mean(rreg <= 0.01))}}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -498,6 +615,9 @@ def main():
         return
     if args.workload == "sweep3d":
         print(json.dumps(run_sweep3d(args)))
+        return
+    if args.workload == "surrogate":
+        print(json.dumps(run_surrogate(args)))
         return
     ws, rank, _ = dist_env()
     cb = None

@@ -235,6 +235,82 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
                       float* margin, int32_t* q_status, int32_t* launch_out,
                       void* stream);
 
+/* ---- learned proposer ------------------------------------------------------
+ * The paper has no learned component; these calls add a surrogate of the
+ * rational program that proposes candidate block shapes, which the exact
+ * program then re-ranks (klr_argmin_candidates), so the rational program is
+ * both the fallback and the judge of the surrogate.
+ *
+ * Network (FP32 master parameters, BF16 operands, FP32 accumulation; every
+ * dense layer y = x W^T + b with W stored out x in, row-major):
+ *   emb  = coef E^T,  E: 64 x n_coef        coef: a kernel's 8 x 2m fitted
+ *                                           coefficients (n_coef = 16 m)
+ *   x0   = [features(16) | emb(64)]         features: log2 N / 23, log2 b0 / 10,
+ *          log2 b1 / 10, log2 b2 / 10 (0 for 2D shapes), the 7 hardware
+ *          features hw_feat[7], then zeros
+ *   a1 = gelu(x0 W1^T + b1)  W1: 256 x 80;  a2 = gelu(a1 W2^T + b2)  W2: 256 x 256
+ *   a3 = gelu(a2 W3^T + b3)  W3: 256 x 256; pred = a3 W4^T + b4      W4: 1 x 256
+ *   gelu(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
+ * The parameter vector holds E, W1, b1, W2, b2, W3, b3, W4, b4 in that order;
+ * klr_mlp_param_count(n_coef) floats.  pred is trained against a target the
+ * caller chooses (normalised log2 cycles). */
+typedef struct klr_mlp {
+    int32_t n_coef;        /* coefficients per kernel, a multiple of 8        */
+    float* params;         /* device, param_count floats (FP32 master copy)   */
+    float* adam_m;         /* device, param_count floats (training only)      */
+    float* adam_v;         /* device, param_count floats (training only)      */
+    int64_t step;          /* AdamW steps taken; klr_mlp_train_step adds one  */
+    float hw_feat[7];      /* hardware features fed to every row              */
+} klr_mlp;
+
+/* Rows for the network: row r is (kernel[r], N[r], block shape cfg[cfg_idx[r]]). */
+typedef struct klr_mlp_rows {
+    int64_t n;
+    const int32_t* kernel;   /* device [n], indexes coef rows                 */
+    const int64_t* N;        /* device [n], >= 1                              */
+    const int32_t* cfg_idx;  /* device [n], rows of the cfg table             */
+    const float* target;     /* device [n] (training only)                    */
+} klr_mlp_rows;
+
+/* Number of parameters for n_coef coefficients per kernel. */
+int64_t klr_mlp_param_count(int32_t n_coef);
+
+/* One training step on a batch (n <= 262144): forward, mean-squared-error
+ * loss, backward, and (if apply_update) one AdamW step with bias correction,
+ * betas (0.9, 0.999), eps 1e-8, decoupled weight decay on every parameter.
+ * coef: device, n_kernels x n_coef FP32.  cfg: device n_cfg x 3 int32.
+ * loss_out: device float or NULL.  grads_out: device, param_count floats or
+ * NULL (the batch gradient, before the update). */
+klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef,
+                              const int32_t* cfg, int n_cfg, const klr_mlp_rows* rows,
+                              float lr, float weight_decay, int apply_update,
+                              float* loss_out, float* grads_out, void* stream);
+
+/* Forward pass for a batch of rows (n <= 262144): pred_out device [n] FP32. */
+klr_status klr_mlp_predict(klr_ctx* ctx, const klr_mlp* net, const float* coef,
+                           const int32_t* cfg, int n_cfg, const klr_mlp_rows* rows,
+                           float* pred_out, void* stream);
+
+/* Proposal: for every query of q (CSR by kernel) predict all n_cfg shapes and
+ * keep the k (1..16) of least predicted value among the meaningful ones
+ * (B_active > 0, T <= T_max, every b_i <= N; integer occupancy as in
+ * klr_argmin).  cand_out: device int32 [n_queries x k], -1 past the number of
+ * meaningful shapes.  regs, smem: device int32 [n_kernels]. */
+klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float* coef,
+                       const int32_t* regs, const int32_t* smem, int32_t n_kernels,
+                       const klr_hw* hw, const int32_t* cfg, int n_cfg,
+                       const klr_queries* q, int k, int32_t* cand_out, void* stream);
+
+/* Exact re-ranking (Section IV, step 5, restricted to candidates): per query,
+ * the candidate of least cycles by FP32 evaluation of the rational program
+ * (ties: lowest shape index; none usable: -1).  cand: device int32
+ * [n_queries x k] shape indices (-1 entries skipped).  best_cycles: device
+ * float [n_queries]; q_status: device int32 [n_queries] or NULL. */
+klr_status klr_argmin_candidates(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
+                                 const int32_t* cfg, int n_cfg, const klr_queries* q,
+                                 const int32_t* cand, int k, int32_t* best_idx,
+                                 float* best_cycles, int32_t* q_status, void* stream);
+
 /* Argmin without allocation.  The paper has no counterpart: this entry point
  * serves callers that cannot allocate device memory -- a launch hook that
  * picks block shapes right before each kernel launch (a cudaMalloc there would

@@ -31,7 +31,8 @@ Q_OK, Q_BAD_METRIC, Q_NONE_FEASIBLE, Q_TIE_RESOLVED = 0, 1, 2, 4
 #: every entry point declared in include/klr.h
 ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last_error",
                "klr_version", "klr_enumerate_configs", "klr_fit", "klr_eval", "klr_argmin",
-               "klr_argmin_noalloc")
+               "klr_argmin_noalloc", "klr_mlp_param_count", "klr_mlp_train_step",
+               "klr_mlp_predict", "klr_propose", "klr_argmin_candidates")
 #: largest query count klr_argmin_noalloc accepts
 ARGMIN_NOALLOC_MAX_QUERIES = 65536
 
@@ -74,8 +75,21 @@ class Queries(ctypes.Structure):
                 ("n_queries", ctypes.c_int64)]
 
 
+class MlpNet(ctypes.Structure):
+    _fields_ = [("n_coef", ctypes.c_int32), ("params", ctypes.c_void_p),
+                ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
+                ("step", ctypes.c_int64), ("hw_feat", ctypes.c_float * 7)]
+
+
+class MlpRows(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("kernel", ctypes.c_void_p), ("N", ctypes.c_void_p),
+                ("cfg_idx", ctypes.c_void_p), ("target", ctypes.c_void_p)]
+
+
 _vp = ctypes.c_void_p
 _lib.klr_last_error.restype = ctypes.c_char_p
+_lib.klr_mlp_param_count.restype = ctypes.c_int64
+_lib.klr_mlp_param_count.argtypes = [ctypes.c_int32]
 _lib.klr_version.restype = ctypes.c_int
 for _name, _args in {
     "klr_ctx_create": [ctypes.POINTER(_vp), ctypes.c_int],
@@ -90,6 +104,16 @@ for _name, _args in {
                    ctypes.POINTER(Queries), _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp],
     "klr_argmin_noalloc": [ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
                            ctypes.POINTER(Queries), _vp, _vp, _vp, _vp, _vp, _vp],
+    "klr_mlp_train_step": [_vp, ctypes.POINTER(MlpNet), _vp, _vp, ctypes.c_int,
+                           ctypes.POINTER(MlpRows), ctypes.c_float, ctypes.c_float, ctypes.c_int,
+                           _vp, _vp, _vp],
+    "klr_mlp_predict": [_vp, ctypes.POINTER(MlpNet), _vp, _vp, ctypes.c_int,
+                        ctypes.POINTER(MlpRows), _vp, _vp],
+    "klr_propose": [_vp, ctypes.POINTER(MlpNet), _vp, _vp, _vp, ctypes.c_int32,
+                    ctypes.POINTER(Hw), _vp, ctypes.c_int, ctypes.POINTER(Queries), ctypes.c_int,
+                    _vp, _vp],
+    "klr_argmin_candidates": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
+                              ctypes.POINTER(Queries), _vp, ctypes.c_int, _vp, _vp, _vp, _vp],
 }.items():
     getattr(_lib, _name).argtypes = _args
     getattr(_lib, _name).restype = ctypes.c_int32
@@ -233,6 +257,88 @@ class Context:
                                              _ptr(best), _ptr(cyc), out_dtype, _ptr(margin),
                                              _ptr(status), _ptr(lp), _stream(stream)))
         return best, cyc, margin, status, lp
+
+
+def mlp_param_count(n_coef: int) -> int:
+    return int(_lib.klr_mlp_param_count(n_coef))
+
+
+class Surrogate:
+    """The learned proposer's parameters and optimiser state (device tensors)
+    and the calls that train and use it.  ``init`` is the initial FP32
+    parameter vector (drawn by the caller's seeded generator)."""
+
+    def __init__(self, ctx: "Context", n_coef: int, init, hw_feat):
+        import torch
+        self.ctx = ctx
+        self.n_coef = n_coef
+        n = mlp_param_count(n_coef)
+        init = torch.as_tensor(init, dtype=torch.float32)
+        if init.numel() != n:
+            raise ValueError(f"init has {init.numel()} values, the network {n}")
+        self.params = init.cuda().contiguous()
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.net = MlpNet(n_coef, self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), 0)
+        for i in range(7):
+            self.net.hw_feat[i] = float(hw_feat[i])
+
+    @staticmethod
+    def _rows(kernel, N, cfg_idx, target=None):
+        return MlpRows(kernel.numel(), kernel.data_ptr(), N.data_ptr(), cfg_idx.data_ptr(),
+                       None if target is None else target.data_ptr())
+
+    def train_step(self, coef, cfg, kernel, N, cfg_idx, target, lr, weight_decay=0.0,
+                   apply_update=True, loss=None, grads=None, stream=None):
+        import torch
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device=coef.device)
+        rows = self._rows(kernel, N, cfg_idx, target)
+        _check("klr_mlp_train_step",
+               _lib.klr_mlp_train_step(self.ctx._h, ctypes.byref(self.net), _ptr(coef), _ptr(cfg),
+                                       cfg.shape[0], ctypes.byref(rows), lr, weight_decay,
+                                       int(apply_update), _ptr(loss), _ptr(grads),
+                                       _stream(stream)))
+        return loss
+
+    def predict(self, coef, cfg, kernel, N, cfg_idx, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(kernel.numel(), dtype=torch.float32, device=coef.device)
+        rows = self._rows(kernel, N, cfg_idx)
+        _check("klr_mlp_predict",
+               _lib.klr_mlp_predict(self.ctx._h, ctypes.byref(self.net), _ptr(coef), _ptr(cfg),
+                                    cfg.shape[0], ctypes.byref(rows), _ptr(out), _stream(stream)))
+        return out
+
+    def propose(self, coef, regs, smem, hw: Hw, cfg, q_offsets, q_N, k, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((q_N.numel(), k), dtype=torch.int32, device=coef.device)
+        q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), q_N.numel())
+        _check("klr_propose",
+               _lib.klr_propose(self.ctx._h, ctypes.byref(self.net), _ptr(coef), _ptr(regs),
+                                _ptr(smem), regs.numel(), ctypes.byref(hw), _ptr(cfg),
+                                cfg.shape[0], ctypes.byref(q), k, _ptr(out), _stream(stream)))
+        return out
+
+
+def argmin_candidates(ctx: "Context", prog: Program, hw: Hw, cfg, q_offsets, q_N, cand,
+                      out=None, stream=None):
+    """Exact re-ranking of candidate shapes (klr_argmin_candidates)."""
+    import torch
+    n_q = q_N.numel()
+    if out is None:
+        out = (torch.empty(n_q, dtype=torch.int32, device=q_N.device),
+               torch.empty(n_q, dtype=torch.float32, device=q_N.device),
+               torch.empty(n_q, dtype=torch.int32, device=q_N.device))
+    best, cyc, st = out
+    q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+    _check("klr_argmin_candidates",
+           _lib.klr_argmin_candidates(ctx._h, ctypes.byref(prog), ctypes.byref(hw), _ptr(cfg),
+                                      cfg.shape[0], ctypes.byref(q), _ptr(cand), cand.shape[1],
+                                      _ptr(best), _ptr(cyc), _ptr(st), _stream(stream)))
+    return out
 
 
 def argmin_noalloc(prog: Program, hw: Hw, cfg, q_offsets, q_N, out, stream=None):

@@ -74,6 +74,21 @@ int n_monomials(int n_vars, int degree);
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// Occupancy rational program of Fig. 1: B_active by the four tests in order
+// (blocks, warps, registers, shared memory per SM); T > T_max fails to launch.
+__device__ __forceinline__ int occupancy_blocks(long long T, long long R, long long Z,
+                                                long long Bm, long long Wm, long long Rm,
+                                                long long Zm, long long Tmax) {
+    if (T > Tmax || T <= 0) return 0;
+    if (T * Bm <= 32 * Wm && R * T * Bm <= Rm && Z * Bm <= Zm) return (int)Bm;
+    if (32 * Wm <= T * Bm && 32 * Wm * R <= Rm && 32 * Wm * Z <= Zm * T) return (int)((32 * Wm) / T);
+    if (R > 0 && Rm <= R * T * Bm && Rm <= R * 32 * Wm && Rm * Z <= R * T * Zm)
+        return (int)(Rm / (R * T));
+    if (Z > 0 && Zm <= Bm * Z && Zm * T <= 32 * Wm * Z && Zm * R * T <= Z * Rm)
+        return (int)(Zm / Z);
+    return 0;
+}
+
 // Error-free sum (Knuth's TwoSum): a + b = s + e exactly.  The _rn
 // intrinsics keep the compiler from contracting a product into these sums,
 // which would break the error-free property.

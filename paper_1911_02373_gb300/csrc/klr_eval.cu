@@ -65,18 +65,10 @@ struct EvalParams {
     uint8_t exps[kMaxBasis][kMaxVars];
 };
 
-// Fig. 1: B_active by the four tests in order; T > T_max fails to launch.
+// Fig. 1 with the program's hardware limits.
 __device__ __forceinline__ int active_blocks(long long T, long long R, long long Z,
                                              const EvalParams& P) {
-    const long long Bm = P.B_max, Wm = P.W_max, Rm = P.R_max, Zm = P.Z_max;
-    if (T > P.T_max || T <= 0) return 0;
-    if (T * Bm <= 32 * Wm && R * T * Bm <= Rm && Z * Bm <= Zm) return (int)Bm;
-    if (32 * Wm <= T * Bm && 32 * Wm * R <= Rm && 32 * Wm * Z <= Zm * T) return (int)((32 * Wm) / T);
-    if (R > 0 && Rm <= R * T * Bm && Rm <= R * 32 * Wm && Rm * Z <= R * T * Zm)
-        return (int)(Rm / (R * T));
-    if (Z > 0 && Zm <= Bm * Z && Zm * T <= 32 * Wm * Z && Zm * R * T <= Z * Rm)
-        return (int)(Zm / Z);
-    return 0;
+    return occupancy_blocks(T, R, Z, P.B_max, P.W_max, P.R_max, P.Z_max, P.T_max);
 }
 
 // a / b: the fast approximate quotient in FP32 (2 ulp), IEEE in FP64
@@ -117,47 +109,53 @@ __device__ __forceinline__ T mwpcwp(const T L[8], T Nw, T Bact, T active_sms, T 
 
 __device__ __forceinline__ long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
-// Full (unspecialised) FP64 evaluation of one (kernel, N, configuration):
-// the same algorithm as the oracle, used to re-decide FP32 near-ties.
-__device__ double eval_full_f64(const EvalParams& P, int k, long long N, int c, bool& usable) {
+// Full (unspecialised) evaluation of one (kernel, N, configuration) in
+// precision T: the same algorithm as the oracle.  FP64 re-decides FP32
+// near-ties; FP32 re-ranks proposed candidates.
+template <typename T>
+__device__ T eval_full(const EvalParams& P, int k, long long N, int c, bool& usable) {
     const int m = P.m, u = P.u, nv = P.n_vars;
     const long long b0 = P.cfg[3 * c], b1 = P.cfg[3 * c + 1], b2 = P.cfg[3 * c + 2];
-    const long long T = b0 * b1 * b2;
-    const int B = active_blocks(T, P.regs[k], P.smem[k], P);
-    const int W = (int)min((long long)B * T / 32, (long long)P.W_max);
-    usable = B > 0 && T <= P.T_max && b0 <= N && (P.dims < 2 || b1 <= N) && (P.dims < 3 || b2 <= N);
-    if (!usable) return INFINITY;
-    double xs[kMaxVars];
-    xs[0] = ldexp((double)N, -P.n_scale_log2);
-    xs[1] = ldexp((double)b0, -P.b_scale_log2);
-    xs[2] = ldexp((double)b1, -P.b_scale_log2);
-    xs[3] = ldexp((double)b2, -P.b_scale_log2);
-    double L[8];
+    const long long Tt = b0 * b1 * b2;
+    const int B = active_blocks(Tt, P.regs[k], P.smem[k], P);
+    const int W = (int)min((long long)B * Tt / 32, (long long)P.W_max);
+    usable = B > 0 && Tt <= P.T_max && b0 <= N && (P.dims < 2 || b1 <= N) && (P.dims < 3 || b2 <= N);
+    if (!usable) return (T)INFINITY;
+    T xs[kMaxVars];
+    xs[0] = (T)ldexp((double)N, -P.n_scale_log2);
+    xs[1] = (T)ldexp((double)b0, -P.b_scale_log2);
+    xs[2] = (T)ldexp((double)b1, -P.b_scale_log2);
+    xs[3] = (T)ldexp((double)b2, -P.b_scale_log2);
+    T L[8];
     for (int i = 0; i < 8; ++i) {
-        double p = 0.0, q = 0.0;
+        T p = 0, q = 0;
         for (int t = 0; t < m; ++t) {
-            double ph = 1.0;
+            T ph = 1;
             for (int v = 0; v < nv; ++v)
                 for (int e = 0; e < P.exps[t][v]; ++e) ph *= xs[v];
-            double a, b;
+            T a, b;
             if (P.coef_f64) {
                 const double* cf = reinterpret_cast<const double*>(P.coef) + ((int64_t)k * 8 + i) * u;
-                a = cf[t]; b = cf[m + t];
+                a = (T)cf[t]; b = (T)cf[m + t];
             } else {
                 const float* cf = reinterpret_cast<const float*>(P.coef) + ((int64_t)k * 8 + i) * u;
-                a = cf[t]; b = cf[m + t];
+                a = (T)cf[t]; b = (T)cf[m + t];
             }
             p += a * ph;
             q += b * ph;
         }
-        double g = p / q;
-        if (q == 0.0 || !isfinite(g)) { usable = false; return INFINITY; }
-        L[i] = P.lo[i] + P.sc[i] * fabs(g);
+        const T g = p / q;
+        if (q == T(0) || !isfinite(g)) { usable = false; return (T)INFINITY; }
+        L[i] = (T)P.lo[i] + (T)P.sc[i] * fabs(g);
     }
-    const long long nb = ceil_div(N, T);
+    const long long nb = ceil_div(N, Tt);
     const long long asm_ = min((long long)P.n_sm, nb);
     const long long rep = ceil_div(nb, max((long long)B * asm_, 1LL));
-    return mwpcwp<double>(L, (double)W, (double)B, (double)asm_, (double)rep, P);
+    return mwpcwp<T>(L, (T)W, (T)B, (T)asm_, (T)rep, P);
+}
+
+__device__ double eval_full_f64(const EvalParams& P, int k, long long N, int c, bool& usable) {
+    return eval_full<double>(P, k, N, c, usable);
 }
 
 __device__ void write_launch(const EvalParams& P, int64_t q, long long N, int c) {
@@ -442,6 +440,35 @@ tie_kernel(const __grid_constant__ EvalParams P) {
     }
 }
 
+// Exact re-ranking of proposed candidates: one thread per query.
+__global__ void __launch_bounds__(128)
+candidates_kernel(const __grid_constant__ EvalParams P, const int32_t* __restrict__ cand, int kc) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P.n_q;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        // kernel of the query: binary search in the CSR offsets
+        int lo = 0, hi = P.n_kernels;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (P.q_off[mid] <= q) lo = mid; else hi = mid;
+        }
+        const long long N = P.q_N[q];
+        float bv = INFINITY;
+        int bj = -1, st = 0;
+        for (int j = 0; j < kc; ++j) {
+            const int c = cand[q * kc + j];
+            if (c < 0 || c >= P.n_cfg) continue;
+            bool us;
+            const float v = eval_full<float>(P, lo, N, c, us);
+            if (!us) { st |= KLR_Q_BAD_METRIC; continue; }
+            if (v < bv || (v == bv && c < bj)) { bv = v; bj = c; }
+        }
+        if (bj < 0) st |= KLR_Q_NONE_FEASIBLE;
+        P.best[q] = bj;
+        reinterpret_cast<float*>(P.best_cycles)[q] = bv;
+        if (P.q_status) P.q_status[q] = st;
+    }
+}
+
 int64_t tie_capacity(int64_t n_q) {
     return std::max<int64_t>(65536, std::min<int64_t>(n_q, 1 << 22) / 4);
 }
@@ -648,6 +675,29 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
     if (st != KLR_OK || f64) return st;
     const int grid = (int)std::min<int64_t>((P.tie_cap + 127) / 128, (int64_t)c->n_sm * 4);
     tie_kernel<<<grid, 128, 0, stream>>>(P);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+klr_status klr_argmin_candidates(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
+                                 const int32_t* cfg, int n_cfg, const klr_queries* q,
+                                 const int32_t* cand, int k, int32_t* best_idx,
+                                 float* best_cycles, int32_t* q_status, void* stream_) {
+    KLR_REQUIRE(ctx, "klr_argmin_candidates: NULL context");
+    Context* c = reinterpret_cast<Context*>(ctx);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    EvalParams P;
+    klr_status st = prepare(c, prog, hw, cfg, n_cfg, q, KLR_F32, P);
+    if (st != KLR_OK) return st;
+    KLR_REQUIRE(k >= 1 && k <= 256, "klr_argmin_candidates: k %d not in 1..256", k);
+    if (P.n_q == 0 || P.n_kernels == 0) return KLR_OK;
+    KLR_REQUIRE(cand && best_idx && best_cycles, "klr_argmin_candidates: NULL array");
+    KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    P.best = best_idx;
+    P.best_cycles = best_cycles;
+    P.q_status = q_status;
+    const int grid = (int)std::min<int64_t>((P.n_q + 127) / 128, (int64_t)c->n_sm * 16);
+    candidates_kernel<<<grid, 128, 0, stream>>>(P, cand, k);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
 }

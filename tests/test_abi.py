@@ -23,8 +23,8 @@ def _lib_or_skip():
 
 def declared_symbols():
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:klr_status|const char\*|int|size_t)\s+(klr_\w+)\s*\(",
-                                 text, re.M)))
+    return sorted(set(re.findall(
+        r"^\s*(?:klr_status|const char\*|int|int64_t|size_t)\s+(klr_\w+)\s*\(", text, re.M)))
 
 
 def test_header_declares_the_boundary():

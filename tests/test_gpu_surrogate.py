@@ -1,0 +1,166 @@
+"""GPU tests of the learned proposer (the surrogate network's BF16 training and
+inference kernels) against the FP64 oracle, and of what it gains.
+
+Gradient tolerance, derived from the arithmetic: the kernels use BF16 operands
+(unit roundoff 2^-9) with FP32 accumulation.  The oracle is given the same
+BF16-rounded weights, coefficients and features, so the remaining difference is
+the BF16 rounding of the activations and backward signals between layers (a
+few roundings per path, each 2^-9): relative L2 error per parameter tensor
+within 4e-2, and the loss within 2e-2.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+HW_FEAT = np.ones(7, dtype=np.float32)
+
+
+@pytest.fixture(scope="module")
+def klr():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1911_02373_gb300 as k
+    return k
+
+
+@pytest.fixture(scope="module")
+def ctx(klr):
+    return klr.Context(0)
+
+
+def _bf16(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32)).bfloat16().double().numpy()
+
+
+def _init(klr, n_coef, seed):
+    from paper_1911_02373_gb300 import proposer
+    n = klr.mlp_param_count(n_coef)
+    keys = W.stream_keys(seed, (77,), np.arange(1, dtype=np.uint64))
+    z = W.normal(keys[0], np.arange(n, dtype=np.uint64))
+    return proposer.init_params(n_coef, z)
+
+
+def test_gradients_match_oracle(klr, ctx):
+    gt = W.ground_truth(31, 12, 3, 3, 8, 23, 10)
+    n_coef = 8 * gt.coef.shape[-1]
+    coef = gt.coef.reshape(12, n_coef).astype(np.float32)
+    rng = np.random.default_rng(0)
+    n = 300
+    kern = rng.integers(0, 12, n).astype(np.int32)
+    N = (2 ** rng.uniform(8, 23, n)).astype(np.int64)
+    cfg = klr.enumerate_configs(2)
+    ci = rng.integers(0, len(cfg), n).astype(np.int32)
+    target = rng.standard_normal(n).astype(np.float32)
+    init = _init(klr, n_coef, 5)
+    sur = klr.Surrogate(ctx, n_coef, init, HW_FEAT)
+    grads = torch.zeros(init.size, dtype=torch.float32, device="cuda")
+    t = lambda a: torch.tensor(a).cuda()
+    loss = sur.train_step(t(coef), t(cfg), t(kern), t(N), t(ci), t(target), 0.0, 0.0, False,
+                          grads=grads)
+    torch.cuda.synchronize()
+    g_gpu = grads.cpu().numpy().astype(np.float64)
+    # oracle with the kernels' BF16 inputs and weights (biases stay FP32)
+    p = omlp.unpack(init.astype(np.float64), n_coef)
+    for name in ("E", "W1", "W2", "W3", "W4"):
+        p[name] = _bf16(p[name])
+    feat = _bf16(omlp.features(N, cfg[ci], HW_FEAT))
+    loss_ref, g_ref = omlp.loss_and_grads(p, feat, _bf16(coef[kern]), target.astype(np.float64))
+    assert abs(float(loss.item()) - loss_ref) <= 2e-2 * abs(loss_ref)
+    gg = omlp.unpack(g_gpu, n_coef)
+    for name, _ in omlp.shapes(n_coef):
+        ref = np.asarray(g_ref[name], dtype=np.float64).reshape(-1)
+        got = np.asarray(gg[name]).reshape(-1)
+        rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+        assert rel <= 4e-2, (name, rel)
+    # predictions: same bound on the forward pass alone
+    pred = sur.predict(t(coef), t(cfg), t(kern), t(N), t(ci))
+    pr_ref, _ = omlp.forward(p, feat, _bf16(coef[kern]))
+    got = pred.cpu().numpy()
+    assert np.linalg.norm(got - pr_ref) <= 4e-2 * np.linalg.norm(pr_ref)
+
+
+def test_adamw_step_matches_oracle(klr, ctx):
+    gt = W.ground_truth(32, 4, 3, 3, 8, 23, 10)
+    n_coef = 8 * gt.coef.shape[-1]
+    coef = gt.coef.reshape(4, n_coef).astype(np.float32)
+    init = _init(klr, n_coef, 6)
+    sur = klr.Surrogate(ctx, n_coef, init, HW_FEAT)
+    rng = np.random.default_rng(1)
+    n = 64
+    cfg = klr.enumerate_configs(2)
+    t = lambda a: torch.tensor(a).cuda()
+    args = (t(coef), t(cfg), t(rng.integers(0, 4, n).astype(np.int32)),
+            t((2 ** rng.uniform(8, 23, n)).astype(np.int64)),
+            t(rng.integers(0, 51, n).astype(np.int32)), t(rng.standard_normal(n).astype(np.float32)))
+    grads = torch.zeros(init.size, dtype=torch.float32, device="cuda")
+    sur.train_step(*args, 1e-3, 0.01, True, grads=grads)
+    torch.cuda.synchronize()
+    g = grads.cpu().numpy().astype(np.float64)
+    want, m, v = omlp.adamw(init.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1,
+                            lr=1e-3, wd=0.01)
+    assert np.allclose(sur.params.cpu().numpy(), want, rtol=0, atol=2e-6)
+    assert np.allclose(sur.m.cpu().numpy(), m, rtol=1e-5, atol=1e-9)
+
+
+def test_trained_proposer_beats_random_candidates(klr, ctx):
+    from paper_1911_02373_gb300 import proposer
+    nk = 160
+    gt = W.ground_truth(33, nk, 3, 3, 8, 23, 10)
+    n_coef = 8 * gt.coef.shape[-1]
+    coef_np = gt.coef.astype(np.float32)
+    t = lambda a: torch.tensor(a).cuda()
+    coef3 = t(coef_np)
+    coef = coef3.reshape(nk, n_coef)
+    regs, smem = t(gt.regs), t(gt.smem)
+    cfg = t(klr.enumerate_configs(2))
+    hw = klr.make_hw(W.HARDWARE)
+    prog = klr.Context.program(coef3, regs, smem, n_vars=3, degree=3, n_scale_log2=23,
+                               b_scale_log2=10, metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+    # training rows: every (size, shape) of 64 log-spaced sizes, meaningful ones kept
+    sizes = W.log_spaced_sizes(64)
+    q = W.queries_per_kernel(nk, sizes)
+    qo, qn = t(q.offsets), t(q.sizes)
+    nq = len(q.sizes)
+    rq = torch.arange(nq, device="cuda").repeat_interleave(51)
+    rc = torch.arange(51, device="cuda").repeat(nq)
+    y = proposer.table_targets(ctx, prog, hw, cfg, qo, qn, rq, rc)
+    keep = torch.isfinite(y)
+    rq, rc, y = rq[keep], rc[keep], y[keep]
+    mu, sd = y.mean(), y.std()
+    target = ((y - mu) / sd).float().contiguous()
+    kern = (rq // 64).int().contiguous()
+    N = qn[rq].contiguous()
+    ci = rc.int().contiguous()
+    sur = klr.Surrogate(ctx, n_coef, _init(klr, n_coef, 7), HW_FEAT)
+    n = kern.numel()
+    keys = W.stream_keys(8, (78,), np.arange(40, dtype=np.uint64))
+    order = lambda ep: t(np.argsort(W.words(keys[ep], np.arange(n, dtype=np.uint64)), kind="stable"))
+    losses = proposer.train(sur, coef, cfg, kern, N, ci, target, batch=4096, epochs=8, lr=2e-3,
+                            order=order, log_every=20)
+    assert losses[-1] < 0.25 * losses[0], losses
+    # evaluation queries: 16 sizes per kernel not on the training grid
+    ev = np.unique(np.floor(np.exp2(np.linspace(8.3, 22.7, 16))).astype(np.int64))
+    qe = W.queries_per_kernel(nk, ev)
+    qeo, qen = t(qe.offsets), t(qe.sizes)
+    best, cyc, mg, st, _ = ctx.argmin(prog, hw, cfg, qeo, qen, out_dtype=klr.F32)
+    sb, sc, sst, cand = proposer.propose_and_rerank(ctx, sur, prog, hw, coef, regs, smem, cfg, qeo,
+                                                    qen, 8)
+    # random 8 candidates per query, re-ranked the same way
+    kr = W.stream_keys(9, (79,), np.arange(len(qe.sizes), dtype=np.uint64))
+    rnd = (W.words(kr[:, None], np.arange(8, dtype=np.uint64)[None, :]) % np.uint64(51)).astype(np.int32)
+    rb, rcyc, _ = klr.argmin_candidates(ctx, prog, hw, cfg, qeo, qen, t(rnd))
+    torch.cuda.synchronize()
+    c_best = cyc.cpu().numpy().astype(np.float64)
+    ok = np.isfinite(c_best)
+    reg_s = sc.cpu().numpy()[ok] / c_best[ok] - 1
+    reg_r = rcyc.cpu().numpy()[ok] / c_best[ok] - 1
+    reg_r = np.where(np.isfinite(reg_r), reg_r, 10.0)
+    assert np.all(reg_s >= -1e-5)
+    assert np.mean(reg_s) < 0.5 * np.mean(reg_r), (np.mean(reg_s), np.mean(reg_r))
+    assert np.median(reg_s) < 0.05
