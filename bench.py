@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of a CUDA graph")
-    ap.add_argument("--workload", default="batched", choices=["batched", "sweep3d", "surrogate"],
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "sweep3d", "surrogate", "precision"],
                     help="batched: fit + argmin (default metric); sweep3d: 3D evaluator sweep")
     ap.add_argument("--sweep-kernels", type=int, default=100000)
     ap.add_argument("--sweep-check-kernels", type=int, default=100,
@@ -53,6 +54,8 @@ def parse():
     ap.add_argument("--sur-epochs", type=int, default=2)
     ap.add_argument("--sur-queries-per-kernel", type=int, default=20)
     ap.add_argument("--sur-k", type=int, default=8)
+    ap.add_argument("--prec-fits", type=int, default=4096)
+    ap.add_argument("--prec-check-fits", type=int, default=64)
     ap.add_argument("--cpu-sample-kernels", type=int, default=0,
                     help="kernels in the bounded oracle sample (0: auto)")
     return ap.parse_args()
@@ -581,6 +584,75 @@ def run_surrogate(args):
                                 "within_1pct": float(np.mean(rreg <= 0.01))}}
 
 
+def run_precision(args):
+    """Precision split: 4096 fits of degree 3 (20 + 20 unknowns), 5,000 samples
+    each, N up to 2^30, noiseless and with 1% noise.  Every precision mode of
+    the Gram accumulation with 0-3 FP64 refinement passes; coefficient and
+    prediction error against the FP64 oracle on a seeded subsample of fits."""
+    import torch
+    import paper_1911_02373_gb300 as klr
+    import workloads as W
+    from oracle import rational
+    ctx = klr.Context(0)
+    nk = max(1, args.prec_fits // 8)
+    exps = rational.monomial_exponents(3, 3)
+    sizes = W.log_spaced_sizes(64, 8, 30)
+    shapes = np.ldexp(1.0, W.block_shape_exponents(2))
+    grid = np.array([(n, b0, b1) for n in sizes for (b0, b1) in shapes], dtype=np.float64)
+    xs_grid = rational.scale_variables(grid, 30, 10)
+    out = {}
+    for noise in (0.0, 0.01):
+        fb = W.fit_batch(args.seed + 5, nk, 5000, degree=3, n_hi_log2=30, noise=noise,
+                         dtype=np.float64)
+        n_fits = fb.n_fits
+        chk = W.subsample_kernels(args.seed + 6, n_fits, min(n_fits, args.prec_check_fits))
+        # the oracle on the same samples each mode reads (FP64, or FP32-rounded)
+        refs = {}
+        for key, xx_, yy_ in (("f64", fb.x, fb.y), ("f32", fb.x.astype(np.float32).astype(np.float64),
+                                                    fb.y.astype(np.float32).astype(np.float64))):
+            oc_, _, _ = rational.fit_batch(fb.offsets, xx_, yy_, 3, 3, 30, 10, fits=chk)
+            refs[key] = (oc_, np.stack([rational.predict(oc_[i], xs_grid, exps)
+                                        for i in range(len(chk))]))
+        off = torch.from_numpy(fb.offsets).cuda()
+        x64 = torch.from_numpy(np.ascontiguousarray(fb.x)).cuda()
+        y64 = torch.from_numpy(fb.y).cuda()
+        x32, y32 = x64.float(), y64.float()
+        ctx.reserve(n_fits, 0)
+        res = {}
+        for mode, prec, xx, yy in (("fp64", klr.FIT_FP64, x64, y64), ("df32", klr.FIT_DF32, x32, y32),
+                                   ("fp32", klr.FIT_FP32, x32, y32), ("tf32", klr.FIT_TF32, x64, y64),
+                                   ("bf16", klr.FIT_BF16, x64, y64)):
+            for refine in (0, 1, 3):
+                kw = dict(n_vars=3, degree=3, n_scale_log2=30, b_scale_log2=10, precision=prec,
+                          refine_iters=refine, coef_dtype=klr.F64)
+                ctx.fit(off, xx, yy, **kw)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                coef, st, dg = ctx.fit(off, xx, yy, **kw)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                oc, pref = refs["f32" if xx.dtype == torch.float32 else "f64"]
+                c = coef.cpu().numpy()[chk]
+                cerr = np.max(np.abs(c - oc), axis=1)
+                p = np.stack([rational.predict(c[i], xs_grid, exps) for i in range(len(chk))])
+                perr = np.max(np.abs(p - pref), axis=1) / np.max(np.abs(pref), axis=1)
+                res[f"{mode}_r{refine}"] = {
+                    "ms": ms, "fits_per_s": n_fits / (ms * 1e-3),
+                    "coef_err_median": float(np.median(cerr)), "coef_err_max": float(cerr.max()),
+                    "pred_rel_err_median": float(np.median(perr)),
+                    "pred_rel_err_max": float(perr.max()),
+                    "status_nonzero": int(np.count_nonzero(st.cpu().numpy() & ~8))}
+        out["noise_%g" % noise] = res
+    return {"metric": "fits/s and error vs the FP64 oracle by Gram precision",
+            "config": {"workload": "precision_split", "fits": nk * 8, "samples_per_fit": 5000,
+                       "degree": 3, "unknowns": 40, "n_max": 2 ** 30,
+                       "checked_fits": int(min(nk * 8, args.prec_check_fits)),
+                       "sample_dtype": "f64 (f32 for df32/fp32)"},
+            "results": out}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -618,6 +690,9 @@ def main():
         return
     if args.workload == "surrogate":
         print(json.dumps(run_surrogate(args)))
+        return
+    if args.workload == "precision":
+        print(json.dumps(run_precision(args)))
         return
     ws, rank, _ = dist_env()
     cb = None

@@ -35,6 +35,8 @@
 #include <cfloat>
 #include <type_traits>
 
+#include <cuda_bf16.h>
+
 #include "klr_common.cuh"
 
 namespace klr {
@@ -61,8 +63,13 @@ struct FitParams {
     int ld;        // leading dimension of the Gram matrix in shared memory
     int warp_smem; // bytes of shared memory per warp
     double* mom;   // scratch: n_fits x 3 x n_mom moment sums (FP64, or
-                   // double-word float2 pairs when mom_dw)
+                   // double-word float2 pairs when mom_dw), or n_fits x u x u
+                   // Gram matrices when gram_direct
     int mom_dw;
+    int gram_direct;
+    double gram_eps;  // unit roundoff of the Gram entries (sets shifts and thresholds)
+    double f_jit, f_null, f_rank;   // shift, noise and rank levels as multiples of
+                                    // gram_eps * trace
     int32_t* flags;// scratch: n_fits, bit 0 non-finite sample, bit 1 inexact DF32
     uint8_t exps[kMaxMoments][kMaxVars];
     uint8_t pair[kMaxBasis][kMaxBasis];
@@ -559,7 +566,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     const TS* Y = reinterpret_cast<const TS*>(P.y);
     const double n_scale = ldexp(1.0, -P.n_scale_log2);
     const double b_scale = ldexp(1.0, -P.b_scale_log2);
-    for (int i = lane; i < 3 * n_mom; i += 32) {
+    for (int i = lane; i < 3 * n_mom && !P.gram_direct; i += 32) {
         if (P.mom_dw) {
             const float2 g = reinterpret_cast<const float2*>(P.mom)[(int64_t)f * 3 * n_mom + i];
             mom[i] = (double)g.x + (double)g.y;
@@ -592,9 +599,14 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     for (int idx = lane; idx < u * u; idx += 32) {
         int i = idx / u, j = idx % u;
         if (j < i) continue;
-        int bi = i >= m, bj = j >= m;
-        double val = mom[(bi + bj) * n_mom + P.pair[i - bi * m][j - bj * m]];
-        if (bi != bj) val = -val;
+        double val;
+        if (P.gram_direct) {
+            val = P.mom[((int64_t)f * u + i) * u + j];
+        } else {
+            int bi = i >= m, bj = j >= m;
+            val = mom[(bi + bj) * n_mom + P.pair[i - bi * m][j - bj * m]];
+            if (bi != bj) val = -val;
+        }
         if (i == j) gdiag[i] = val;
         else G[i * ld + j] = val;
     }
@@ -623,8 +635,8 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     trace = warp_sum(trace);
 
     // ---- F3: smallest eigenpair by shifted inverse iteration ----------------
-    const double eps = DBL_EPSILON;
-    const double jitter = 4.0 * u * eps * trace;
+    const double eps = P.gram_eps;
+    const double jitter = P.f_jit * eps * trace;
     double shift = -jitter;                       // factor Ghat + jitter I
     bool ok = warp_cholesky(G, gdiag, u, ld, shift);
     if (!ok) {
@@ -639,13 +651,23 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     warp_orth_normalise(v, v, u, false);
     double theta = 0.0;
     if (ok) {
-        for (int it = 0; it < 3; ++it) {
+        // iterate until v stops moving (a large shift, as for the low-precision
+        // Gram matrices, converges slowly): change below 1e-11, or a stall
+        // (rate above 1/2) below 1e-8, at most 32 steps
+        double prev = 1.0;
+        for (int it = 0; it < 32; ++it) {
+            warp_copy(w, v, u);
             warp_chol_solve(G, u, ld, v);
             warp_orth_normalise(v, v, u, false);
+            double dv2 = 0.0;
+            for (int i = lane; i < u; i += 32) dv2 += (v[i] - w[i]) * (v[i] - w[i]);
+            dv2 = warp_sum(dv2);
+            if (it >= 2 && (dv2 <= 1e-22 || (dv2 <= 1e-16 && dv2 >= 0.25 * prev))) break;
+            prev = dv2;
         }
         warp_gram_matvec(G, gdiag, u, ld, v, t);
         theta = warp_dot(v, t, u);
-        if (theta > 64.0 * u * eps * trace) {
+        if (theta > P.f_null * eps * trace) {
             // A noisy fit: the smallest eigenvalue is well above round-off.  Each
             // round factors Ghat - sigma I for the largest sigma of a ladder
             // below the Rayleigh quotient that keeps the matrix positive
@@ -685,7 +707,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
         }
         warp_gram_matvec(G, gdiag, u, ld, w, t);
         theta2 = warp_dot(w, t, u);
-        if (theta2 <= 64.0 * u * eps * trace) status |= KLR_FIT_RANK_DEFICIENT;
+        if (theta2 <= P.f_rank * eps * trace) status |= KLR_FIT_RANK_DEFICIENT;
     }
 
     // ---- F4: FP64 refinement passes over the samples --------------------------
@@ -918,9 +940,10 @@ solve_lane_kernel(const __grid_constant__ FitParams P) {
         return shift + vw / ww;
     };
 
-    const double eps = DBL_EPSILON;
-    const double jitter = 4.0 * u * eps * trace;
-    const double null_level = 64.0 * u * eps * trace;
+    const double eps = P.gram_eps;
+    const double jitter = P.f_jit * eps * trace;
+    const double null_level = P.f_null * eps * trace;
+    const double rank_level = P.f_rank * eps * trace;
     double shift = -jitter;
     bool ok = cholesky(shift);
     if (!ok) {
@@ -1005,7 +1028,7 @@ solve_lane_kernel(const __grid_constant__ FitParams P) {
             theta2 = shift + zw / zz;
             project_normalise();
         }
-        if (theta2 <= null_level) status |= KLR_FIT_RANK_DEFICIENT;
+        if (theta2 <= rank_level) status |= KLR_FIT_RANK_DEFICIENT;
     }
     // c = D v, unit norm, sign rule
     double nrm = 0.0;
@@ -1197,9 +1220,10 @@ solve_lane_dw_kernel(const __grid_constant__ FitParams P) {
         return dv2 <= 1e-20f || (dv2 <= 1e-14f && dv2 >= 0.25f * prev);
     };
 
-    const float eps = ldexpf(1.0f, -44);   // double-word unit roundoff (approx.)
-    const dw jitter = dw_mul_f(trace, 4.0f * u * eps);
-    const dw null_level = dw_mul_f(trace, 64.0f * u * eps);
+    const float eps = (float)P.gram_eps;
+    const dw jitter = dw_mul_f(trace, (float)P.f_jit * eps);
+    const dw null_level = dw_mul_f(trace, (float)P.f_null * eps);
+    const dw rank_level = dw_mul_f(trace, (float)P.f_rank * eps);
     dw shift = dw_neg(jitter);
     bool ok = cholesky(shift);
     if (!ok) {
@@ -1284,7 +1308,7 @@ solve_lane_dw_kernel(const __grid_constant__ FitParams P) {
             theta2 = dw_add(shift, dw_div(zw.value(), zz.value()));
             project_normalise();
         }
-        if (!dw_gt(theta2, null_level)) status |= KLR_FIT_RANK_DEFICIENT;
+        if (!dw_gt(theta2, rank_level)) status |= KLR_FIT_RANK_DEFICIENT;
     }
     // c = D v, unit norm, sign rule
     dw_acc nrm2;
@@ -1491,9 +1515,10 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
         return dv2 <= 1e-20f || (dv2 <= 1e-14f && dv2 >= 0.25f * prev);
     };
 
-    const float eps = ldexpf(1.0f, -44);
-    const dw jitter = dw_mul_f(trace, 4.0f * u * eps);
-    const dw null_level = dw_mul_f(trace, 64.0f * u * eps);
+    const float eps = (float)P.gram_eps;
+    const dw jitter = dw_mul_f(trace, (float)P.f_jit * eps);
+    const dw null_level = dw_mul_f(trace, (float)P.f_null * eps);
+    const dw rank_level = dw_mul_f(trace, (float)P.f_rank * eps);
     dw shift = dw_neg(jitter);
     bool fact = cholesky(shift, ok);
     if (ok && !fact) {
@@ -1600,7 +1625,7 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
             if (ok) theta2 = dw_add(shift, dw_div(zwv, zzv));
             project_normalise(ok);
         }
-        if (ok && !dw_gt(theta2, null_level)) status |= KLR_FIT_RANK_DEFICIENT;
+        if (ok && !dw_gt(theta2, rank_level)) status |= KLR_FIT_RANK_DEFICIENT;
     }
     // c = D v, unit norm, sign rule; lane q writes coefficients i = q mod Q
     for (int i = q; i < u; i += Q) wv[i] = st2(dw_mul_f(ld2(vv[i]), Dv[i].x));
@@ -1639,6 +1664,172 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
         }
     }
 #undef LF
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core Gram matrix (KLR_FIT_TF32 / KLR_FIT_BF16): one warp per fit.
+// Each step the 32 lanes build the rows a_s = [Phi(x_s) | -y_s Phi(x_s)] of 32
+// samples in FP32 into shared memory; G += A^T A then runs as mma.sync with
+// the operands rounded to TF32 (m16n8k8) or BF16 (m16n8k16) and FP32
+// accumulation.  G goes to the scratch for the FP64 solver.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+template <typename TS, bool BF16, int MT, int NT>
+__global__ void __launch_bounds__(128)
+gram_tc_kernel(const __grid_constant__ FitParams P) {
+    constexpr int UP = MT * 16;                  // padded columns of A
+    constexpr int LDA = UP + 4;                  // shared-memory row stride (floats)
+    extern __shared__ __align__(16) float tcs[];
+    const int lane = lane_id();
+    const int wib = threadIdx.x >> 5;
+    const int f = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (f >= P.n_fits) return;
+    float* As = tcs + (size_t)wib * 32 * LDA;    // [sample][column]
+    const int nv = P.n_vars, m = P.m, u = P.u;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
+    const TS* X = reinterpret_cast<const TS*>(P.x);
+    const TS* Y = reinterpret_cast<const TS*>(P.y);
+    const float sN = ldexpf(1.0f, -P.n_scale_log2), sB = ldexpf(1.0f, -P.b_scale_log2);
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int a = 0; a < MT; ++a)
+#pragma unroll
+        for (int b = 0; b < NT; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    bool bad = false;
+    for (int64_t base = s0; base < s1; base += 32) {
+        const int64_t s = base + lane;
+        float* row = As + lane * LDA;
+        if (s < s1) {
+            float xs[kMaxVars];
+            for (int v = 0; v < nv; ++v) {
+                const TS raw = X[(int64_t)v * P.x_stride + s];
+                bad |= !isfinite(raw);
+                xs[v] = (float)raw * (v == 0 ? sN : sB);
+            }
+            const TS yr = Y[s];
+            bad |= !isfinite(yr);
+            const float yv = (float)yr;
+            for (int t = 0; t < m; ++t) {
+                float ph = 1.f;
+                for (int v = 0; v < nv; ++v)
+                    for (int e = 0; e < P.exps[t][v]; ++e) ph *= xs[v];
+                row[t] = ph;
+                row[m + t] = -yv * ph;
+            }
+            for (int j = u; j < UP; ++j) row[j] = 0.f;
+        } else {
+            for (int j = 0; j < UP; ++j) row[j] = 0.f;
+        }
+        __syncwarp();
+        if constexpr (!BF16) {
+#pragma unroll
+            for (int k0 = 0; k0 < 32; k0 += 8) {
+                uint32_t a[MT][4], b[NT][2];
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const int i0 = mt * 16;
+                    a[mt][0] = to_tf32(As[(k0 + tig) * LDA + i0 + gid]);
+                    a[mt][1] = to_tf32(As[(k0 + tig) * LDA + i0 + gid + 8]);
+                    a[mt][2] = to_tf32(As[(k0 + tig + 4) * LDA + i0 + gid]);
+                    a[mt][3] = to_tf32(As[(k0 + tig + 4) * LDA + i0 + gid + 8]);
+                }
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    b[nt][0] = to_tf32(As[(k0 + tig) * LDA + nt * 8 + gid]);
+                    b[nt][1] = to_tf32(As[(k0 + tig + 4) * LDA + nt * 8 + gid]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt)
+                        asm volatile(
+                            "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
+                            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                            : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]),
+                              "+f"(acc[mt][nt][3])
+                            : "r"(a[mt][0]), "r"(a[mt][1]), "r"(a[mt][2]), "r"(a[mt][3]),
+                              "r"(b[nt][0]), "r"(b[nt][1]));
+            }
+        } else {
+#pragma unroll
+            for (int k0 = 0; k0 < 32; k0 += 16) {
+                uint32_t a[MT][4], b[NT][2];
+                const int ka = k0 + 2 * tig;
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt) {
+                    const int i0 = mt * 16;
+                    a[mt][0] = pack_bf16(As[ka * LDA + i0 + gid], As[(ka + 1) * LDA + i0 + gid]);
+                    a[mt][1] = pack_bf16(As[ka * LDA + i0 + gid + 8], As[(ka + 1) * LDA + i0 + gid + 8]);
+                    a[mt][2] = pack_bf16(As[(ka + 8) * LDA + i0 + gid], As[(ka + 9) * LDA + i0 + gid]);
+                    a[mt][3] = pack_bf16(As[(ka + 8) * LDA + i0 + gid + 8],
+                                         As[(ka + 9) * LDA + i0 + gid + 8]);
+                }
+#pragma unroll
+                for (int nt = 0; nt < NT; ++nt) {
+                    b[nt][0] = pack_bf16(As[ka * LDA + nt * 8 + gid], As[(ka + 1) * LDA + nt * 8 + gid]);
+                    b[nt][1] = pack_bf16(As[(ka + 8) * LDA + nt * 8 + gid],
+                                         As[(ka + 9) * LDA + nt * 8 + gid]);
+                }
+#pragma unroll
+                for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < NT; ++nt)
+                        asm volatile(
+                            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+                            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+                            : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]),
+                              "+f"(acc[mt][nt][3])
+                            : "r"(a[mt][0]), "r"(a[mt][1]), "r"(a[mt][2]), "r"(a[mt][3]),
+                              "r"(b[nt][0]), "r"(b[nt][1]));
+            }
+        }
+        __syncwarp();
+    }
+    double* G = P.mom + (int64_t)f * u * u;
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const int r = mt * 16 + gid + h * 8, c = nt * 8 + 2 * tig + j;
+                    if (r < u && c < u) G[r * u + c] = (double)acc[mt][nt][h * 2 + j];
+                }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) P.flags[f] = bad ? 1 : 0;
+}
+
+template <typename TS, bool BF16>
+klr_status launch_gram_tc(const FitParams& P, cudaStream_t stream) {
+    const int wpb = 4;
+    const int blocks = (P.n_fits + wpb - 1) / wpb;
+    auto go = [&](auto kern, int mt) -> klr_status {
+        const size_t smem = sizeof(float) * 32 * (mt * 16 + 4) * wpb;
+        KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        kern<<<blocks, wpb * 32, smem, stream>>>(P);
+        KLR_CHECK_CUDA(cudaGetLastError());
+        return KLR_OK;
+    };
+    // M tiles of 16 rows and N tiles of 8 columns covering u
+    if (P.u <= 16) return go(gram_tc_kernel<TS, BF16, 1, 2>, 1);
+    if (P.u <= 32) return go(gram_tc_kernel<TS, BF16, 2, 4>, 2);
+    if (P.u <= 48) return go(gram_tc_kernel<TS, BF16, 3, 6>, 3);
+    return go(gram_tc_kernel<TS, BF16, 5, 10>, 5);
 }
 
 template <typename TS, int ACC>
@@ -1765,10 +1956,6 @@ extern "C" klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_o
     KLR_REQUIRE(b->x_stride >= 0, "klr_fit: x_stride < 0");
     if (b->precision == KLR_FIT_DF32)
         KLR_REQUIRE(b->sample_dtype == KLR_F32, "klr_fit: DF32 needs KLR_F32 samples");
-    if (b->precision == KLR_FIT_TF32 || b->precision == KLR_FIT_BF16) {
-        set_error("klr_fit: tensor-core precision modes are not built in this library");
-        return KLR_ENOTSUP;
-    }
     Basis basis;
     KLR_REQUIRE(make_basis(b->n_vars, b->degree, &basis), "klr_fit: no basis");
     const int m = basis.m, u = 2 * m;
@@ -1800,6 +1987,46 @@ extern "C" klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_o
     memcpy(P.exps, basis.exps, sizeof(P.exps));
     memcpy(P.pair, basis.pair, sizeof(P.pair));
 
+    // unit roundoff of the Gram entries in each mode (the accumulated error of
+    // the low-precision modes is a few of these, hence the factor 16)
+    // FP64/DF32: the error of an entry is tiny next to the spectrum, the levels
+    // carry a factor u; FP32/TF32/BF16: the levels sit at a few roundoffs of
+    // the trace, below the second eigenvalue of the fits they can resolve.
+    switch (b->precision) {
+        case KLR_FIT_FP64: P.gram_eps = ldexp(1.0, -53); break;
+        case KLR_FIT_DF32: P.gram_eps = ldexp(1.0, -44); break;
+        case KLR_FIT_FP32: P.gram_eps = ldexp(1.0, -24); break;
+        case KLR_FIT_TF32: P.gram_eps = ldexp(1.0, -11); break;
+        default: P.gram_eps = ldexp(1.0, -8); break;
+    }
+    if (b->precision == KLR_FIT_FP64 || b->precision == KLR_FIT_DF32) {
+        P.f_jit = 4.0 * u;
+        P.f_null = 64.0 * u;
+        P.f_rank = 8.0 * u;
+    } else {
+        P.f_jit = 2.0;
+        P.f_null = 8.0;
+        P.f_rank = 1.0;
+    }
+    const bool tc = b->precision == KLR_FIT_TF32 || b->precision == KLR_FIT_BF16;
+    if (tc) {
+        // tensor-core Gram matrix, then the FP64 warp solver (+ refinement)
+        const size_t bytes = 256 + (size_t)b->n_fits * ((size_t)u * u * sizeof(double) + 4);
+        klr_status st = ensure_workspace(c, bytes, stream);
+        if (st != KLR_OK) return st;
+        P.mom = reinterpret_cast<double*>(reinterpret_cast<char*>(c->ws) + 256);
+        P.flags = reinterpret_cast<int32_t*>(P.mom + (size_t)b->n_fits * u * u);
+        P.mom_dw = 0;
+        P.gram_direct = 1;
+        const bool s64 = b->sample_dtype == KLR_F64;
+        const bool bf = b->precision == KLR_FIT_BF16;
+        st = s64 ? (bf ? launch_gram_tc<double, true>(P, stream) : launch_gram_tc<double, false>(P, stream))
+                 : (bf ? launch_gram_tc<float, true>(P, stream) : launch_gram_tc<float, false>(P, stream));
+        if (st != KLR_OK) return st;
+        return s64 ? launch_solve_warp<double>(P, c->smem_optin, stream)
+                   : launch_solve_warp<float>(P, c->smem_optin, stream);
+    }
+    P.gram_direct = 0;
     klr_status st = ensure_workspace(c, fit_workspace_bytes(b->n_fits, basis.n_mom), stream);
     if (st != KLR_OK) return st;
     P.mom = reinterpret_cast<double*>(reinterpret_cast<char*>(c->ws) + 256);

@@ -177,3 +177,29 @@ def test_bad_arguments(klr, ctx):
     with pytest.raises(klr.KlrError) as e:
         gpu_fit(klr, ctx, fb, klr.FIT_FP64, 9)
     assert e.value.status == klr.EINVAL
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+def test_tensor_core_gram_with_refinement(klr, ctx, mode):
+    # Gram products on tensor cores with TF32/BF16 operands, then FP64
+    # refinement passes over the samples.  Each pass contracts the error by
+    # about eps / gap (eps = 2^-11 for TF32, 2^-8 for BF16): on the fits where
+    # that is small the passes reach the FP64 answer; elsewhere they cannot.
+    fb = W.fit_batch(43, 8, 400, degree=1, n_lo_log2=8, n_hi_log2=23, dtype=np.float64)
+    oc, ost, od = rational.fit_batch(fb.offsets, fb.x, fb.y, 3, 1, 23, 10)
+    gap = od[:, 1] ** 2 - od[:, 0] ** 2
+    eps = 2.0 ** -11 if mode == "tf32" else 2.0 ** -8
+    prec = klr.FIT_TF32 if mode == "tf32" else klr.FIT_BF16
+    errs = {}
+    for refine in (0, 2, 6):
+        coef, st, diag = gpu_fit(klr, ctx, fb, prec, refine)
+        assert np.all(st & ~klr.FIT_RANK_DEFICIENT == 0)
+        assert np.allclose(np.linalg.norm(coef, axis=1), 1.0, atol=1e-12)
+        assert np.all(diag[:, 3] == refine)
+        errs[refine] = np.max(np.abs(coef - oc), axis=1)
+    good = eps / gap < 0.02
+    if mode == "tf32":
+        assert good.sum() >= 4   # this seeded batch has six such fits
+    if good.any():
+        assert np.all(errs[6][good] <= 1e-9), errs[6][good]
+        assert np.all(errs[6][good] <= errs[0][good] + 1e-12)
