@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of a CUDA graph")
+    ap.add_argument("--kernels", type=int, default=0,
+                    help="kernels of the batched workload (0: the full 10,000)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="built-in launch shapes instead of the autotuned ones")
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "sweep3d", "surrogate", "precision"],
                     help="batched: fit + argmin (default metric); sweep3d: 3D evaluator sweep")
@@ -237,39 +241,59 @@ def run_klr(args):
                                degree=2, n_scale_log2=23, b_scale_log2=10,
                                metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
 
-    def fit(xx, yy, oo):
+    def fit(xx, yy, oo, autotune=False):
         ctx.fit(oo, xx, yy, n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10,
                 precision=klr.FIT_DF32, refine_iters=0, coef_dtype=klr.F32,
-                out=(coef, fst, fdg))
+                out=(coef, fst, fdg), autotune=autotune)
 
-    def choose(qoo, qnn):
-        ctx.argmin(prog, hw, cfg, qoo, qnn, out_dtype=klr.F32, out=(best, cyc, mrg, qst, lp))
+    def choose(qoo, qnn, autotune=False):
+        ctx.argmin(prog, hw, cfg, qoo, qnn, out_dtype=klr.F32, out=(best, cyc, mrg, qst, lp),
+                   autotune=autotune)
 
     stream = torch.cuda.current_stream()
+    # launch shapes picked by the library's autotuner for this workload's
+    # problem classes, before anything is captured
+    tuned = {}
+    if not args.no_autotune:
+        fit(x, y, off, autotune=True)
+        tuned["fit"] = ctx.last_tune
+        choose(qo, qn, autotune=True)
+        tuned["argmin"] = ctx.last_tune
     for _ in range(args.warmup):
         fit(x, y, off)
         choose(qo, qn)
     torch.cuda.synchronize()
-    # the step captured as two CUDA graphs (fit, argmin) replayed back to
-    # back; events recorded between the replays time each part
+    # the step captured as three CUDA graphs (fit stage F1-F2: moment sums;
+    # fit stage F3: null-vector solve; argmin E1-E5) replayed back to back;
+    # events recorded between the replays time each kernel on its stream
+    def gram():
+        ctx.fit(off, x, y, n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10,
+                precision=klr.FIT_DF32, refine_iters=0, coef_dtype=klr.F32,
+                out=(coef, fst, fdg), stage="gram")
+
+    def solve():
+        ctx.fit(off, x, y, n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10,
+                precision=klr.FIT_DF32, refine_iters=0, coef_dtype=klr.F32,
+                out=(coef, fst, fdg), stage="solve")
+
+    parts = [gram, solve, lambda: choose(qo, qn)]
     graphs = None
     if not args.no_graph:
         try:
-            g_fit, g_eval = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
-            with torch.cuda.graph(g_fit):
-                fit(x, y, off)
-            with torch.cuda.graph(g_eval):
-                choose(qo, qn)
+            gs = [torch.cuda.CUDAGraph() for _ in parts]
+            for g_, fn in zip(gs, parts):
+                with torch.cuda.graph(g_):
+                    fn()
             for _ in range(args.warmup):
-                g_fit.replay()
-                g_eval.replay()
+                for g_ in gs:
+                    g_.replay()
             torch.cuda.synchronize()
-            graphs = (g_fit, g_eval)
+            graphs = gs
         except Exception as e:  # report and fall back to eager launches
             print(f"graph capture failed: {e}", file=sys.stderr)
             graphs = None
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)] for _ in range(K)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -278,27 +302,23 @@ def run_klr(args):
         dist.barrier()
     torch.cuda.synchronize()
     start.record(stream)
-    fit_t, eval_t = [], []
     for k in range(K):
-        ev[k][0].record(stream)
-        if graphs is not None:
-            graphs[0].replay()
-        else:
-            fit(x, y, off)
-        ev[k][1].record(stream)
-        if graphs is not None:
-            graphs[1].replay()
-        else:
-            choose(qo, qn)
-        ev[k][2].record(stream)
+        for i, fn in enumerate(parts):
+            ev[k][i].record(stream)
+            if graphs is not None:
+                graphs[i].replay()
+            else:
+                fn()
+        ev[k][len(parts)].record(stream)
     stop.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ck = clocks.stop()
     total_ms = start.elapsed_time(stop)
-    fit_ms = float(np.mean([e[0].elapsed_time(e[1]) for e in ev]))
-    eval_ms = float(np.mean([e[1].elapsed_time(e[2]) for e in ev]))
+    part_ms = [float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev])) for i in range(len(parts))]
+    gram_ms, solve_ms, eval_ms = part_ms
+    fit_ms = gram_ms + solve_ms
     ms_step = total_ms / K
     if dist:
         t = torch.tensor([ms_step], device=dev)
@@ -341,7 +361,8 @@ def run_klr(args):
     except OSError:
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    fit_bytes = n_samples * 16 + (n_fits + 1) * 8 + n_fits * (2 * m * 4 + 4 + 32)
+    # moments stage: samples and offsets in, 3 x 35 double-FP32 sums + a flag out
+    fit_bytes = n_samples * 16 + (n_fits + 1) * 8 + n_fits * (3 * 35 * 8 + 4)
     sm_max = (ck or {}).get("sm_max_mhz") or 2070.0
     # double-FP32 moment accumulation: per sample and moment, three error-free
     # sums (6 FP32 ops + 1 compensation add each), two products and one FMA
@@ -365,17 +386,19 @@ def run_klr(args):
                    "samples": n_samples, "queries": n_q, "configs": wl["n_cfg"],
                    "evals": n_q * wl["n_cfg"], "fit_precision": "df32", "refine_iters": 0,
                    "l2": "inputs larger than L2 (1.31 GB of samples per step)",
-                   "launch": "CUDA graphs (fit, argmin)" if graphs is not None else "eager",
+                   "launch": ("CUDA graphs (fit moments, fit solve, argmin)" if graphs is not None
+                              else "eager"),
+                   "autotuned": {k: {"choice": v[0], "ms": v[1]} for k, v in tuned.items()},
                    "parallelism": f"replicas x{ws}"},
         "fits_per_s": ws * n_fits / (ms_step * 1e-3),
         "config_evals_per_s": ws * n_q * wl["n_cfg"] / (ms_step * 1e-3),
-        "kernel_ms": {"fit": fit_ms, "argmin": eval_ms},
-        "roofline": {"bound": "alu", "achieved": fit_ops / (fit_ms * 1e-3) / 1e12,
+        "kernel_ms": {"fit_moments": gram_ms, "fit_solve": solve_ms, "argmin": eval_ms},
+        "roofline": {"bound": "alu", "achieved": fit_ops / (gram_ms * 1e-3) / 1e12,
                      "peak": alu_peak / 1e12, "unit": "Tops/s (FP32 lane-ops)",
-                     "frac": fit_ops / (fit_ms * 1e-3) / alu_peak, "traffic": None,
-                     "kernel": "fit_kernel (double-FP32 moments)",
-                     "hbm_gbs": fit_bytes / (fit_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak,
-                     "hbm_frac": fit_bytes / (fit_ms * 1e-3) / 1e9 / hbm_peak,
+                     "frac": fit_ops / (gram_ms * 1e-3) / alu_peak, "traffic": None,
+                     "kernel": "moments_fast_kernel (double-FP32 moment sums, F1-F2)",
+                     "hbm_gbs": fit_bytes / (gram_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak,
+                     "hbm_frac": fit_bytes / (gram_ms * 1e-3) / 1e9 / hbm_peak,
                      "peak_source": "FP32 lanes x max SM clock (unit counts)"},
         "e2e": {"value": ws * n_q / (e2e_ms * 1e-3), "unit": "queries/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -680,6 +703,10 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.kernels and args.kernels != WORKLOAD["kernels"]:
+        # a smaller copy of the batched workload (profiling captures)
+        WORKLOAD["kernels"] = args.kernels
+        WORKLOAD["name"] = f"batched_fit_eval_fp32_{args.kernels}k"
     if args.impl == "reference":
         out = run_reference(args)
         if out:

@@ -158,6 +158,19 @@ klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* batch, void* coef_out,
                    int32_t coef_dtype, int32_t* fit_status, double* fit_diag,
                    void* stream);
 
+/* klr_fit in its two stages, for callers that time or schedule them apart.
+ * klr_fit_gram: F1-F2, the per-fit moment sums (or, in the TF32/BF16 modes,
+ * the tensor-core Gram matrices) into the context's scratch memory.
+ * klr_fit_solve: F3-F4 from that scratch, with klr_fit's outputs.  The pair
+ * gives bitwise the same outputs as klr_fit when klr_fit_solve follows
+ * klr_fit_gram for the same batch, on the same context and stream, with no
+ * other call of the context in between (otherwise the solve reads whatever
+ * the scratch holds: wrong results, not a fault).  Errors as klr_fit. */
+klr_status klr_fit_gram(klr_ctx* ctx, const klr_fit_batch* batch, void* stream);
+klr_status klr_fit_solve(klr_ctx* ctx, const klr_fit_batch* batch, void* coef_out,
+                         int32_t coef_dtype, int32_t* fit_status, double* fit_diag,
+                         void* stream);
+
 /* ---- E2-E5: the rational program ----------------------------------------- */
 
 /* Hardware parameters H.  Integer limits per SM feed the occupancy program of
@@ -234,6 +247,44 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
                       int32_t* best_idx, void* best_cycles, int32_t out_dtype,
                       float* margin, int32_t* q_status, int32_t* launch_out,
                       void* stream);
+
+/* ---- autotuning of the library's launch shapes ----------------------------
+ * The paper tunes the launch parameters of the user's kernels; these two calls
+ * tune the library's own.  Each runs the operation once per candidate launch
+ * shape (one untimed run, then three timed between CUDA events on `stream`),
+ * keeps the fastest in the context under the call's problem class (basis,
+ * precision, mode and log2 buckets of the batch sizes) and runs it once more,
+ * so the outputs are exactly those of klr_fit / klr_argmin with that shape.
+ * Later calls of the same class on this context, including calls captured
+ * into a CUDA graph, launch with the tuned shape; other classes keep the
+ * built-in default.
+ *   klr_autotune_fit: moments kernel warps per block (1, 2, 4), then lanes per
+ *     fit of the double-word solver (2, 4, 8) where that solver runs.
+ *   klr_autotune_argmin: evaluator threads per block (32, 64, 128, 256).
+ * Arguments are those of klr_fit / klr_argmin (same layouts, ownership and
+ * per-item status), plus choice_out (int32, host, may be NULL: the chosen
+ * shape code) and ms_out (float, host, may be NULL: its mean time per call in
+ * milliseconds).  Synchronises `stream`.  Returns KLR_EINVAL while `stream` is
+ * capturing a graph (tune before capturing) and the operation's own errors. */
+klr_status klr_autotune_fit(klr_ctx* ctx, const klr_fit_batch* batch, void* coef_out,
+                            int32_t coef_dtype, int32_t* fit_status, double* fit_diag,
+                            int32_t* choice_out, float* ms_out, void* stream);
+klr_status klr_autotune_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
+                               const int32_t* cfg, int n_cfg, const klr_queries* q,
+                               int32_t* best_idx, void* best_cycles, int32_t out_dtype,
+                               float* margin, int32_t* q_status, int32_t* launch_out,
+                               int32_t* choice_out, float* ms_out, void* stream);
+
+/* The context's tuned launch shapes as (problem-class key, shape code) pairs,
+ * to keep them across runs.  klr_tune_export writes up to `cap` pairs into the
+ * host arrays keys/choices (NULL allowed when cap is 0) and sets *n_out to
+ * the number the context holds.  klr_tune_import stores n pairs (replacing
+ * an existing key's choice); a code outside 0..255 is KLR_EINVAL and stores
+ * nothing.  A code is only meaningful for the operation and library version
+ * that produced it; out-of-range shape fields fall back to the nearest valid
+ * shape.  Host only, no device work. */
+klr_status klr_tune_export(klr_ctx* ctx, uint64_t* keys, int32_t* choices, int cap, int* n_out);
+klr_status klr_tune_import(klr_ctx* ctx, const uint64_t* keys, const int32_t* choices, int n);
 
 /* ---- learned proposer ------------------------------------------------------
  * The paper has no learned component; these calls add a surrogate of the

@@ -32,7 +32,9 @@ Q_OK, Q_BAD_METRIC, Q_NONE_FEASIBLE, Q_TIE_RESOLVED = 0, 1, 2, 4
 ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last_error",
                "klr_version", "klr_enumerate_configs", "klr_fit", "klr_eval", "klr_argmin",
                "klr_argmin_noalloc", "klr_mlp_param_count", "klr_mlp_train_step",
-               "klr_mlp_predict", "klr_propose", "klr_argmin_candidates")
+               "klr_mlp_predict", "klr_propose", "klr_argmin_candidates", "klr_autotune_fit",
+               "klr_autotune_argmin", "klr_tune_export", "klr_tune_import", "klr_fit_gram",
+               "klr_fit_solve")
 #: largest query count klr_argmin_noalloc accepts
 ARGMIN_NOALLOC_MAX_QUERIES = 65536
 
@@ -102,6 +104,15 @@ for _name, _args in {
                  ctypes.POINTER(Queries), _vp, ctypes.c_int32, _vp],
     "klr_argmin": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
                    ctypes.POINTER(Queries), _vp, _vp, ctypes.c_int32, _vp, _vp, _vp, _vp],
+    "klr_autotune_fit": [_vp, ctypes.POINTER(FitBatch), _vp, ctypes.c_int32, _vp, _vp,
+                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), _vp],
+    "klr_autotune_argmin": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
+                            ctypes.POINTER(Queries), _vp, _vp, ctypes.c_int32, _vp, _vp, _vp,
+                            ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), _vp],
+    "klr_fit_gram": [_vp, ctypes.POINTER(FitBatch), _vp],
+    "klr_fit_solve": [_vp, ctypes.POINTER(FitBatch), _vp, ctypes.c_int32, _vp, _vp, _vp],
+    "klr_tune_export": [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "klr_tune_import": [_vp, _vp, _vp, ctypes.c_int],
     "klr_argmin_noalloc": [ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
                            ctypes.POINTER(Queries), _vp, _vp, _vp, _vp, _vp, _vp],
     "klr_mlp_train_step": [_vp, ctypes.POINTER(MlpNet), _vp, _vp, ctypes.c_int,
@@ -185,10 +196,14 @@ class Context:
 
     # -- F1-F4 ---------------------------------------------------------------
     def fit(self, offsets, x, y, *, n_vars, degree, n_scale_log2, b_scale_log2,
-            precision=FIT_DF32, refine_iters=0, coef_dtype=None, out=None, stream=None):
+            precision=FIT_DF32, refine_iters=0, coef_dtype=None, out=None, stream=None,
+            autotune=False, stage=None):
         """Fit every CSR fit.  offsets: int64 (F+1,); x: (n_vars, S) float32/64
         rows (N, b0, b1[, b2]); y: (S,) same dtype.  Returns (coef, status, diag)
-        device tensors; ``out`` may pass preallocated (coef, status, diag)."""
+        device tensors; ``out`` may pass preallocated (coef, status, diag).
+        autotune=True times the candidate launch shapes first (klr_autotune_fit)
+        and records (choice, ms) in ``self.last_tune``.  stage='gram' or
+        'solve' runs one stage only (klr_fit_gram / klr_fit_solve)."""
         import torch
         sdt = F64 if x.dtype == torch.float64 else F32
         cdt = sdt if coef_dtype is None else coef_dtype
@@ -204,9 +219,44 @@ class Context:
         b = FitBatch(n_fits, n_vars, degree, n_scale_log2, b_scale_log2, sdt,
                      offsets.data_ptr(), x.data_ptr(), x.stride(0), y.data_ptr(),
                      precision, refine_iters)
-        _check("klr_fit", _lib.klr_fit(self._h, ctypes.byref(b), _ptr(coef), cdt, _ptr(status),
-                                       _ptr(diag), _stream(stream)))
+        if stage == "gram":
+            _check("klr_fit_gram", _lib.klr_fit_gram(self._h, ctypes.byref(b), _stream(stream)))
+        elif stage == "solve":
+            _check("klr_fit_solve", _lib.klr_fit_solve(self._h, ctypes.byref(b), _ptr(coef), cdt,
+                                                       _ptr(status), _ptr(diag), _stream(stream)))
+        elif stage is not None:
+            raise ValueError(f"stage {stage!r} is not 'gram' or 'solve'")
+        elif autotune:
+            ch, ms = ctypes.c_int32(-1), ctypes.c_float(0.0)
+            _check("klr_autotune_fit",
+                   _lib.klr_autotune_fit(self._h, ctypes.byref(b), _ptr(coef), cdt, _ptr(status),
+                                         _ptr(diag), ctypes.byref(ch), ctypes.byref(ms),
+                                         _stream(stream)))
+            self.last_tune = (ch.value, ms.value)
+        else:
+            _check("klr_fit", _lib.klr_fit(self._h, ctypes.byref(b), _ptr(coef), cdt,
+                                           _ptr(status), _ptr(diag), _stream(stream)))
         return coef, status, diag
+
+    # -- tuned launch shapes -------------------------------------------------
+    def tune_export(self):
+        """The context's tuned launch shapes: list of (key, choice)."""
+        n = ctypes.c_int(0)
+        _check("klr_tune_export", _lib.klr_tune_export(self._h, None, None, 0, ctypes.byref(n)))
+        keys = np.zeros(n.value, dtype=np.uint64)
+        ch = np.zeros(n.value, dtype=np.int32)
+        _check("klr_tune_export",
+               _lib.klr_tune_export(self._h, keys.ctypes.data_as(_vp), ch.ctypes.data_as(_vp),
+                                    n.value, ctypes.byref(n)))
+        return [(int(k), int(c)) for k, c in zip(keys, ch)]
+
+    def tune_import(self, pairs):
+        """Store (key, choice) pairs, e.g. from an earlier tune_export()."""
+        keys = np.ascontiguousarray([k for k, _ in pairs], dtype=np.uint64)
+        ch = np.ascontiguousarray([c for _, c in pairs], dtype=np.int32)
+        _check("klr_tune_import",
+               _lib.klr_tune_import(self._h, keys.ctypes.data_as(_vp), ch.ctypes.data_as(_vp),
+                                    len(pairs)))
 
     # -- E1-E5 ---------------------------------------------------------------
     @staticmethod
@@ -237,8 +287,10 @@ class Context:
         return out
 
     def argmin(self, prog: Program, hw: Hw, cfg, q_offsets, q_N, out_dtype=F32, out=None,
-               launch=True, stream=None):
-        """Per query: (best index, best cycles, margin, status, launch params)."""
+               launch=True, stream=None, autotune=False):
+        """Per query: (best index, best cycles, margin, status, launch params).
+        autotune=True times the candidate launch shapes first
+        (klr_autotune_argmin) and records (choice, ms) in ``self.last_tune``."""
         import torch
         n_q = q_N.numel()
         dev = q_N.device
@@ -252,10 +304,20 @@ class Context:
         else:
             best, cyc, margin, status, lp = out
         q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
-        _check("klr_argmin", _lib.klr_argmin(self._h, ctypes.byref(prog), ctypes.byref(hw),
-                                             _ptr(cfg), cfg.shape[0], ctypes.byref(q),
-                                             _ptr(best), _ptr(cyc), out_dtype, _ptr(margin),
-                                             _ptr(status), _ptr(lp), _stream(stream)))
+        if autotune:
+            ch, ms = ctypes.c_int32(-1), ctypes.c_float(0.0)
+            _check("klr_autotune_argmin",
+                   _lib.klr_autotune_argmin(self._h, ctypes.byref(prog), ctypes.byref(hw),
+                                            _ptr(cfg), cfg.shape[0], ctypes.byref(q), _ptr(best),
+                                            _ptr(cyc), out_dtype, _ptr(margin), _ptr(status),
+                                            _ptr(lp), ctypes.byref(ch), ctypes.byref(ms),
+                                            _stream(stream)))
+            self.last_tune = (ch.value, ms.value)
+        else:
+            _check("klr_argmin", _lib.klr_argmin(self._h, ctypes.byref(prog), ctypes.byref(hw),
+                                                 _ptr(cfg), cfg.shape[0], ctypes.byref(q),
+                                                 _ptr(best), _ptr(cyc), out_dtype, _ptr(margin),
+                                                 _ptr(status), _ptr(lp), _stream(stream)))
         return best, cyc, margin, status, lp
 
 

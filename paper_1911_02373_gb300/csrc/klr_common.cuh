@@ -5,7 +5,10 @@
 #include <stdint.h>
 
 #include <cstdio>
+#include <functional>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "klr.h"
 
@@ -43,7 +46,31 @@ struct Context {
     size_t smem_optin = 0;
     void* ws = nullptr;        // scratch memory owned by the context
     size_t ws_bytes = 0;
+    // launch shapes chosen by the autotuner, per problem class (key)
+    std::vector<std::pair<uint64_t, int32_t>> tuned;
+    int32_t forced = -1;       // >= 0 while the autotuner times a candidate
 };
+
+// ---------------------------------------------------------------------------
+// Autotuning of launch shapes.  A problem class is a key built from the
+// parameters that decide which shape is fastest (operation, basis, precision,
+// size buckets); a choice is an operation-specific shape code.
+// ---------------------------------------------------------------------------
+enum { TUNE_FIT = 1, TUNE_EVAL = 2 };
+
+uint64_t tune_key(int op, std::initializer_list<int64_t> parts);
+// the forced candidate, else the tuned choice for `key`, else `dflt`
+int32_t tune_choice(const Context* c, uint64_t key, int32_t dflt);
+void tune_store(Context* c, uint64_t key, int32_t choice);
+// floor(log2(max(v, 1))): size buckets of the keys
+int log2_bucket(int64_t v);
+// Time run() once per candidate (each forced in turn): one untimed launch,
+// then `reps` launches between CUDA events on `stream`.  Stores the fastest
+// under `key`, then runs it once more so the outputs are its own.  Refuses
+// (KLR_EINVAL) while `stream` is capturing a graph.
+klr_status tune_candidates(Context* c, uint64_t key, cudaStream_t stream, const int32_t* cand,
+                           int n_cand, int reps, const std::function<klr_status()>& run,
+                           int32_t* choice_out, float* ms_out);
 
 // Make sure the context scratch holds `bytes`; allocates only when the stream
 // is not capturing.  Returns KLR_ENOMEM during capture if too small.

@@ -41,6 +41,87 @@ klr_status ensure_workspace(Context* ctx, size_t bytes, cudaStream_t stream) {
     return KLR_OK;
 }
 
+uint64_t tune_key(int op, std::initializer_list<int64_t> parts) {
+    // FNV-1a over the parts
+    uint64_t h = 1469598103934665603ull ^ (uint64_t)op;
+    h *= 1099511628211ull;
+    for (int64_t p : parts) {
+        for (int i = 0; i < 8; ++i) {
+            h ^= (uint64_t)((p >> (8 * i)) & 0xff);
+            h *= 1099511628211ull;
+        }
+    }
+    return h;
+}
+
+int32_t tune_choice(const Context* c, uint64_t key, int32_t dflt) {
+    if (c->forced >= 0) return c->forced;
+    for (const auto& e : c->tuned)
+        if (e.first == key) return e.second;
+    return dflt;
+}
+
+void tune_store(Context* c, uint64_t key, int32_t choice) {
+    for (auto& e : c->tuned)
+        if (e.first == key) { e.second = choice; return; }
+    c->tuned.emplace_back(key, choice);
+}
+
+int log2_bucket(int64_t v) {
+    int b = 0;
+    while (v > 1) { v >>= 1; ++b; }
+    return b;
+}
+
+klr_status tune_candidates(Context* c, uint64_t key, cudaStream_t stream, const int32_t* cand,
+                           int n_cand, int reps, const std::function<klr_status()>& run,
+                           int32_t* choice_out, float* ms_out) {
+    KLR_REQUIRE(n_cand > 0 && reps > 0, "autotune: no candidates");
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    KLR_CHECK_CUDA(cudaStreamIsCapturing(stream, &cs));
+    KLR_REQUIRE(cs == cudaStreamCaptureStatusNone,
+                "autotune: the stream is capturing a graph (tune before capturing)");
+    cudaEvent_t e0, e1;
+    KLR_CHECK_CUDA(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        set_error("autotune: cudaEventCreate failed");
+        return KLR_ECUDA;
+    }
+    klr_status st = KLR_OK;
+    int32_t best = cand[0];
+    float best_ms = INFINITY;
+    for (int i = 0; i < n_cand && st == KLR_OK; ++i) {
+        c->forced = cand[i];
+        st = run();                                   // warm-up (and scratch sizing)
+        if (st != KLR_OK) break;
+        if (cudaEventRecord(e0, stream) != cudaSuccess) {
+            set_error("autotune: cudaEventRecord failed");
+            st = KLR_ECUDA;
+            break;
+        }
+        for (int r = 0; r < reps && st == KLR_OK; ++r) st = run();
+        if (st != KLR_OK) break;
+        float ms = 0.f;
+        if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            set_error("autotune: timing a candidate failed");
+            st = KLR_ECUDA;
+            break;
+        }
+        ms /= (float)reps;
+        if (ms < best_ms) { best_ms = ms; best = cand[i]; }
+    }
+    c->forced = -1;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != KLR_OK) return st;
+    tune_store(c, key, best);
+    if (choice_out) *choice_out = best;
+    if (ms_out) *ms_out = best_ms;
+    return run();
+}
+
 int n_monomials(int n_vars, int degree) {
     // C(n_vars + degree, degree)
     long r = 1;
@@ -140,6 +221,30 @@ klr_status klr_ctx_destroy(klr_ctx* ctx) {
 
 // Scratch needed by the library for `max_fits` fits and `max_queries` queries.
 size_t klr_workspace_bytes(int64_t max_fits, int64_t max_queries);
+
+klr_status klr_tune_export(klr_ctx* ctx, uint64_t* keys, int32_t* choices, int cap, int* n_out) {
+    KLR_REQUIRE(ctx != nullptr && n_out != nullptr, "klr_tune_export: NULL argument");
+    KLR_REQUIRE(cap >= 0 && (cap == 0 || (keys && choices)), "klr_tune_export: bad buffers");
+    const Context* c = reinterpret_cast<const Context*>(ctx);
+    const int n = (int)c->tuned.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        keys[i] = c->tuned[i].first;
+        choices[i] = c->tuned[i].second;
+    }
+    *n_out = n;
+    return KLR_OK;
+}
+
+klr_status klr_tune_import(klr_ctx* ctx, const uint64_t* keys, const int32_t* choices, int n) {
+    KLR_REQUIRE(ctx != nullptr && n >= 0 && (n == 0 || (keys && choices)),
+                "klr_tune_import: bad arguments");
+    for (int i = 0; i < n; ++i)
+        KLR_REQUIRE(choices[i] >= 0 && choices[i] <= 0xff, "klr_tune_import: choice %d out of range",
+                    choices[i]);
+    Context* c = reinterpret_cast<Context*>(ctx);
+    for (int i = 0; i < n; ++i) tune_store(c, keys[i], choices[i]);
+    return KLR_OK;
+}
 
 klr_status klr_ctx_reserve(klr_ctx* ctx, int64_t max_fits, int64_t max_queries) {
     KLR_REQUIRE(ctx != nullptr, "klr_ctx_reserve: ctx is NULL");

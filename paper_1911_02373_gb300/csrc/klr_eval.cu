@@ -584,16 +584,27 @@ klr_status launch_eval_t(Context* c, EvalParams& P, size_t smem, int threads, cu
     return KLR_OK;
 }
 
+// Problem class of an evaluation for the autotuner: basis, precision, mode,
+// |F| and log2 buckets of the queries per kernel and of the kernel count.
+uint64_t eval_tune_key(const EvalParams& P, bool f64) {
+    const int64_t per_kernel = P.n_kernels ? (P.n_q + P.n_kernels - 1) / P.n_kernels : 1;
+    return tune_key(TUNE_EVAL, {P.n_vars, P.degree, f64, P.table, P.n_cfg,
+                                log2_bucket(per_kernel), log2_bucket(P.n_kernels)});
+}
+
 klr_status launch_eval(Context* c, EvalParams& P, bool f64, cudaStream_t stream) {
     const size_t smem = eval_smem_bytes(P, f64 ? 8 : 4);
     if (smem > c->smem_optin) {
         set_error("evaluator needs %zu bytes of shared memory", smem);
         return KLR_ENOTSUP;
     }
-    // threads: enough for the queries of a typical kernel, in whole warps
+    // threads per block: the autotuned choice (32 << choice), else enough for
+    // the queries of a typical kernel, in whole warps
     const int64_t per_kernel = P.n_kernels ? (P.n_q + P.n_kernels - 1) / P.n_kernels : 1;
     int threads = 32;
     while (threads < 256 && threads < per_kernel) threads <<= 1;
+    const int32_t choice = tune_choice(c, eval_tune_key(P, f64), -1);
+    if (choice >= 0) threads = 32 << std::min(3, (int)choice);
     switch (P.degree * 2 + (f64 ? 1 : 0)) {
         case 2: return launch_eval_t<float, 1>(c, P, smem, threads, stream);
         case 3: return launch_eval_t<double, 1>(c, P, smem, threads, stream);
@@ -743,6 +754,28 @@ klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw, const i
     tie_kernel<<<grid, 128, 0, stream>>>(P);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
+}
+
+klr_status klr_autotune_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
+                               const int32_t* cfg, int n_cfg, const klr_queries* q,
+                               int32_t* best_idx, void* best_cycles, int32_t out_dtype,
+                               float* margin, int32_t* q_status, int32_t* launch_out,
+                               int32_t* choice_out, float* ms_out, void* stream_) {
+    KLR_REQUIRE(ctx, "klr_autotune_argmin: NULL context");
+    Context* c = reinterpret_cast<Context*>(ctx);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    auto run = [&]() -> klr_status {
+        return klr_argmin(ctx, prog, hw, cfg, n_cfg, q, best_idx, best_cycles, out_dtype, margin,
+                          q_status, launch_out, stream_);
+    };
+    EvalParams P;
+    klr_status st = prepare(c, prog, hw, cfg, n_cfg, q, out_dtype, P);
+    if (st != KLR_OK) return st;
+    if (P.n_q == 0 || P.n_kernels == 0) return run();
+    P.table = 0;
+    const int32_t cand[4] = {0, 1, 2, 3};           // 32, 64, 128, 256 threads per block
+    return tune_candidates(c, eval_tune_key(P, out_dtype == KLR_F64), stream, cand, 4, 3, run,
+                           choice_out, ms_out);
 }
 
 }  // extern "C"

@@ -32,6 +32,7 @@
 // inverse-iteration step (Knyazev-Neymeyr PINVIT) with the Cholesky factor as
 // preconditioner.  Used when refinement is asked for or the problem is too
 // large for a lane's share of shared memory.
+#include <algorithm>
 #include <cfloat>
 #include <type_traits>
 
@@ -1832,13 +1833,13 @@ klr_status launch_gram_tc(const FitParams& P, cudaStream_t stream) {
     return go(gram_tc_kernel<TS, BF16, 5, 10>, 5);
 }
 
+// wpb: warps (fits) per block, 1, 2 or 4 (an autotuned choice)
 template <typename TS, int ACC>
-klr_status launch_moments(const FitParams& P, int n_mom, int rec, cudaStream_t stream) {
+klr_status launch_moments(const FitParams& P, int n_mom, int rec, int wpb, cudaStream_t stream) {
     // lanes per sample (moment groups) so that a lane holds at most MAXT moments
     const size_t tc = ACC == ACC_FP64 ? 8 : 4;
     FitParams Q = P;
     Q.warp_smem = (int)((32 * rec * tc + 15) & ~(size_t)15);
-    const int wpb = 4;
     const int blocks = (P.n_fits + wpb - 1) / wpb;
     // specialised kernels for the common bases (degree 2 in 3 or 4 variables,
     // degree 3 in 3 variables)
@@ -1900,8 +1901,9 @@ klr_status launch_solve_lane_dw(const FitParams& P, cudaStream_t stream) {
     return KLR_OK;
 }
 
-klr_status launch_solve_group_dw(const FitParams& P, cudaStream_t stream) {
-    constexpr int Q = 4, GPW = 32 / Q;
+template <int Q>
+klr_status launch_solve_group_dw_q(const FitParams& P, cudaStream_t stream) {
+    constexpr int GPW = 32 / Q;
     FitParams Q_ = P;
     int stride = P.u * (P.u + 1) / 2 + 5 * P.u;
     if (stride % 2 == 0) ++stride;          // spread the groups over the banks
@@ -1912,6 +1914,13 @@ klr_status launch_solve_group_dw(const FitParams& P, cudaStream_t stream) {
     solve_group_dw_kernel<Q><<<(P.n_fits + GPW - 1) / GPW, 32, smem, stream>>>(Q_);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
+}
+
+// q_lanes: lanes per fit, 2, 4 or 8 (an autotuned choice)
+klr_status launch_solve_group_dw(const FitParams& P, int q_lanes, cudaStream_t stream) {
+    if (q_lanes == 2) return launch_solve_group_dw_q<2>(P, stream);
+    if (q_lanes == 8) return launch_solve_group_dw_q<8>(P, stream);
+    return launch_solve_group_dw_q<4>(P, stream);
 }
 
 klr_status launch_solve_lane(const FitParams& P, cudaStream_t stream) {
@@ -1929,13 +1938,31 @@ size_t fit_workspace_bytes(int64_t n_fits, int n_mom) {
     return 256 + (size_t)n_fits * (3 * (size_t)n_mom * sizeof(double) + sizeof(int32_t));
 }
 
+constexpr int32_t kFitDefaultChoice = 0x21;   // 4 warps per block, 4 lanes per fit
+
+// Problem class of a fit batch for the autotuner: basis, precision, sample
+// type, refinement on/off, and log2 buckets of the fit count and of the mean
+// samples per fit (x_stride is the sample count of the SoA layout).
+uint64_t fit_tune_key(const klr_fit_batch* b) {
+    const int64_t per_fit = b->n_fits > 0 ? b->x_stride / b->n_fits : 0;
+    return tune_key(TUNE_FIT, {b->n_vars, b->degree, b->precision, b->sample_dtype,
+                               b->refine_iters > 0, log2_bucket(b->n_fits),
+                               log2_bucket(per_fit)});
+}
+
 }  // namespace klr
 
 using namespace klr;
 
-extern "C" klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out,
-                              int32_t coef_dtype, int32_t* fit_status, double* fit_diag,
-                              void* stream_) {
+namespace {
+
+enum { STAGE_GRAM = 1, STAGE_SOLVE = 2 };
+
+// The fit in two stages: F1-F2 (moment sums, or the tensor-core Gram matrix,
+// into the context's scratch) and F3-F4 (the null-vector solve and any
+// refinement, from that scratch).
+klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_t coef_dtype,
+                    int32_t* fit_status, double* fit_diag, void* stream_, int stages) {
     KLR_REQUIRE(ctx && b, "klr_fit: NULL context or batch");
     Context* c = reinterpret_cast<Context*>(ctx);
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
@@ -1944,15 +1971,17 @@ extern "C" klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_o
     KLR_REQUIRE(b->degree >= 1 && b->degree <= 3, "klr_fit: degree %d not in 1..3", b->degree);
     KLR_REQUIRE(b->sample_dtype == KLR_F32 || b->sample_dtype == KLR_F64,
                 "klr_fit: bad sample_dtype");
-    KLR_REQUIRE(coef_dtype == KLR_F32 || coef_dtype == KLR_F64, "klr_fit: bad coef_dtype");
+    KLR_REQUIRE(!(stages & STAGE_SOLVE) || coef_dtype == KLR_F32 || coef_dtype == KLR_F64,
+                "klr_fit: bad coef_dtype");
     KLR_REQUIRE(b->precision >= KLR_FIT_FP64 && b->precision <= KLR_FIT_BF16,
                 "klr_fit: bad precision %d", b->precision);
     KLR_REQUIRE(b->refine_iters >= 0 && b->refine_iters <= 8, "klr_fit: refine_iters not in 0..8");
     KLR_REQUIRE(b->n_scale_log2 >= -64 && b->n_scale_log2 <= 64 &&
                 b->b_scale_log2 >= -64 && b->b_scale_log2 <= 64, "klr_fit: scale out of range");
     if (b->n_fits == 0) return KLR_OK;
-    KLR_REQUIRE(b->offsets && b->x && b->y && coef_out && fit_status,
-                "klr_fit: NULL device array");
+    KLR_REQUIRE(b->offsets && b->x && b->y, "klr_fit: NULL device array");
+    KLR_REQUIRE(!(stages & STAGE_SOLVE) || (coef_out && fit_status),
+                "klr_fit: NULL coef_out or fit_status");
     KLR_REQUIRE(b->x_stride >= 0, "klr_fit: x_stride < 0");
     if (b->precision == KLR_FIT_DF32)
         KLR_REQUIRE(b->sample_dtype == KLR_F32, "klr_fit: DF32 needs KLR_F32 samples");
@@ -1964,6 +1993,11 @@ extern "C" klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_o
         return KLR_ENOTSUP;
     }
     KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    // launch shapes: moments warps per block (bits 4-7: 1, 2, 4) and lanes
+    // per fit of the group solver (bits 0-3: 2, 4, 8)
+    const int32_t choice = tune_choice(c, fit_tune_key(b), kFitDefaultChoice);
+    const int wpb = 1 << std::min(2, (choice >> 4) & 15);
+    const int q_lanes = 2 << std::min(2, choice & 15);
 
     FitParams P;
     P.n_fits = b->n_fits;
@@ -2020,9 +2054,14 @@ extern "C" klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_o
         P.gram_direct = 1;
         const bool s64 = b->sample_dtype == KLR_F64;
         const bool bf = b->precision == KLR_FIT_BF16;
-        st = s64 ? (bf ? launch_gram_tc<double, true>(P, stream) : launch_gram_tc<double, false>(P, stream))
-                 : (bf ? launch_gram_tc<float, true>(P, stream) : launch_gram_tc<float, false>(P, stream));
-        if (st != KLR_OK) return st;
+        if (stages & STAGE_GRAM) {
+            st = s64 ? (bf ? launch_gram_tc<double, true>(P, stream)
+                           : launch_gram_tc<double, false>(P, stream))
+                     : (bf ? launch_gram_tc<float, true>(P, stream)
+                           : launch_gram_tc<float, false>(P, stream));
+            if (st != KLR_OK) return st;
+        }
+        if (!(stages & STAGE_SOLVE)) return KLR_OK;
         return s64 ? launch_solve_warp<double>(P, c->smem_optin, stream)
                    : launch_solve_warp<float>(P, c->smem_optin, stream);
     }
@@ -2034,25 +2073,83 @@ extern "C" klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_o
     P.mom_dw = b->precision != KLR_FIT_FP64;
     const int rec = b->n_vars * (2 * b->degree + 1) + 3;
     const bool s64 = b->sample_dtype == KLR_F64;
-    switch (b->precision) {
+    if (stages & STAGE_GRAM) switch (b->precision) {
         case KLR_FIT_FP64:
-            st = s64 ? launch_moments<double, ACC_FP64>(P, basis.n_mom, rec, stream)
-                     : launch_moments<float, ACC_FP64>(P, basis.n_mom, rec, stream);
+            st = s64 ? launch_moments<double, ACC_FP64>(P, basis.n_mom, rec, wpb, stream)
+                     : launch_moments<float, ACC_FP64>(P, basis.n_mom, rec, wpb, stream);
             break;
         case KLR_FIT_DF32:
-            st = launch_moments<float, ACC_DF32>(P, basis.n_mom, rec, stream);
+            st = launch_moments<float, ACC_DF32>(P, basis.n_mom, rec, wpb, stream);
             break;
         case KLR_FIT_FP32:
-            st = s64 ? launch_moments<double, ACC_FP32>(P, basis.n_mom, rec, stream)
-                     : launch_moments<float, ACC_FP32>(P, basis.n_mom, rec, stream);
+            st = s64 ? launch_moments<double, ACC_FP32>(P, basis.n_mom, rec, wpb, stream)
+                     : launch_moments<float, ACC_FP32>(P, basis.n_mom, rec, wpb, stream);
             break;
         default:
             set_error("klr_fit: unsupported precision");
             return KLR_ENOTSUP;
     }
+    if (b->precision != KLR_FIT_FP64 && b->precision != KLR_FIT_DF32 &&
+        b->precision != KLR_FIT_FP32) {
+        set_error("klr_fit: unsupported precision");
+        return KLR_ENOTSUP;
+    }
     if (st != KLR_OK) return st;
+    if (!(stages & STAGE_SOLVE)) return KLR_OK;
     if (b->refine_iters == 0 && u <= kLaneMaxU)
-        return P.mom_dw ? launch_solve_group_dw(P, stream) : launch_solve_lane(P, stream);
+        return P.mom_dw ? launch_solve_group_dw(P, q_lanes, stream) : launch_solve_lane(P, stream);
     return s64 ? launch_solve_warp<double>(P, c->smem_optin, stream)
                : launch_solve_warp<float>(P, c->smem_optin, stream);
+}
+
+}  // namespace
+
+extern "C" klr_status klr_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out,
+                              int32_t coef_dtype, int32_t* fit_status, double* fit_diag,
+                              void* stream) {
+    return fit_impl(ctx, b, coef_out, coef_dtype, fit_status, fit_diag, stream,
+                    STAGE_GRAM | STAGE_SOLVE);
+}
+
+extern "C" klr_status klr_fit_gram(klr_ctx* ctx, const klr_fit_batch* b, void* stream) {
+    return fit_impl(ctx, b, nullptr, KLR_F32, nullptr, nullptr, stream, STAGE_GRAM);
+}
+
+extern "C" klr_status klr_fit_solve(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out,
+                                    int32_t coef_dtype, int32_t* fit_status, double* fit_diag,
+                                    void* stream) {
+    return fit_impl(ctx, b, coef_out, coef_dtype, fit_status, fit_diag, stream, STAGE_SOLVE);
+}
+
+extern "C" klr_status klr_autotune_fit(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out,
+                                       int32_t coef_dtype, int32_t* fit_status, double* fit_diag,
+                                       int32_t* choice_out, float* ms_out, void* stream_) {
+    KLR_REQUIRE(ctx && b, "klr_autotune_fit: NULL context or batch");
+    Context* c = reinterpret_cast<Context*>(ctx);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    auto run = [&]() -> klr_status {
+        return klr_fit(ctx, b, coef_out, coef_dtype, fit_status, fit_diag, stream_);
+    };
+    if (b->n_fits == 0) return run();
+    const uint64_t key = fit_tune_key(b);
+    const int u = 2 * n_monomials(b->n_vars, b->degree);
+    const bool tc = b->precision == KLR_FIT_TF32 || b->precision == KLR_FIT_BF16;
+    const bool group = !tc && b->precision != KLR_FIT_FP64 && b->refine_iters == 0 &&
+                       u <= kLaneMaxU;
+    if (tc) {   // one launch shape: time it so the outputs and timing are reported alike
+        const int32_t only = kFitDefaultChoice;
+        return tune_candidates(c, key, stream, &only, 1, 3, run, choice_out, ms_out);
+    }
+    // the two stages are independent: moments block shape first, then the
+    // solver's lanes per fit with the chosen moments shape
+    const int32_t s0 = kFitDefaultChoice & 15;
+    const int32_t cm[3] = {0x00 | s0, 0x10 | s0, 0x20 | s0};
+    int32_t best = kFitDefaultChoice;
+    klr_status st = tune_candidates(c, key, stream, cm, 3, 3, run, &best, ms_out);
+    if (st != KLR_OK || !group) {
+        if (st == KLR_OK && choice_out) *choice_out = best;
+        return st;
+    }
+    const int32_t cs[3] = {(best & 0xF0) | 0, (best & 0xF0) | 1, (best & 0xF0) | 2};
+    return tune_candidates(c, key, stream, cs, 3, 3, run, choice_out, ms_out);
 }

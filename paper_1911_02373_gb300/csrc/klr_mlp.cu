@@ -73,7 +73,8 @@ struct GemmArgs {
     int64_t ldcb;
     const float* Z;             // EPI_DGELU: pre-activation to differentiate
     int64_t ldz;
-    int kchunk;                 // K per grid z-slice (split-K, EPI_F32 only: atomic adds)
+    int kchunk;                 // K per grid z-slice (split-K, EPI_F32 only)
+    float* part;                // split-K slices [z][M][N], summed in z order; NULL: no split
 };
 
 constexpr int BM = 128, BN = 64, BK = 32, PADK = 40;
@@ -173,8 +174,10 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __grid_constant__ 
                     float v = acc[mt][nt][h * 2 + j];
                     if (g.bias && blockIdx.z == 0) v += g.bias[col];
                     if (EPI == EPI_F32) {
-                        if (gridDim.z > 1) atomicAdd(&g.C32[(int64_t)row * g.ldc32 + col], v);
-                        else g.C32[(int64_t)row * g.ldc32 + col] = v;
+                        if (gridDim.z > 1)
+                            g.part[((int64_t)blockIdx.z * g.M + row) * g.N + col] = v;
+                        else
+                            g.C32[(int64_t)row * g.ldc32 + col] = v;
                     } else if (EPI == EPI_GELU) {
                         if (g.C32) g.C32[(int64_t)row * g.ldc32 + col] = v;
                         g.Cb[(int64_t)row * g.ldcb + col] = __float2bfloat16(gelu(v));
@@ -187,22 +190,46 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const __grid_constant__ 
                 }
 }
 
-// Launch; with EPI_F32 and few output tiles the K range is split over grid z
-// (the output must then be zeroed by the caller: slices add atomically).
+// Deterministic reductions.  Every sum over rows (split-K slices, bias
+// gradients, the loss) is formed as fixed partial slices and then added in
+// slice order, so a training step is bitwise reproducible: no atomics.
+constexpr int kSplitSlots = 304;                  // split-K: slices x output tiles
+constexpr int kRedBlocks = 152;                   // row-sum partial slices
+constexpr int64_t kPartFloats = (int64_t)kSplitSlots * BM * BN;
+
+// out[(i / width) * ldo + i % width] = sum over z in order of part[z * count + i]
+__global__ void reduce_slices_kernel(const float* __restrict__ part, int nz, int64_t count,
+                                     int width, float* __restrict__ out, int64_t ldo) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float acc = 0.f;
+        for (int z = 0; z < nz; ++z) acc += part[z * count + i];
+        out[(i / width) * ldo + i % width] = acc;
+    }
+}
+
+// Launch; with EPI_F32, a slice buffer and few output tiles the K range is
+// split over grid z and the slices are summed afterwards in z order.
 template <bool TA, bool TB, int EPI>
 klr_status gemm(const GemmArgs& g_in, cudaStream_t s) {
     if (g_in.M <= 0 || g_in.N <= 0 || g_in.K <= 0) return KLR_OK;
     GemmArgs g = g_in;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, 1);
     int splits = 1;
-    if (EPI == EPI_F32) {
+    if (EPI == EPI_F32 && g.part) {
         const int tiles = grid.x * grid.y;
-        splits = std::max(1, std::min(304 / tiles, (g.K + 4 * BK - 1) / (4 * BK)));
+        splits = std::max(1, std::min(kSplitSlots / tiles, (g.K + 4 * BK - 1) / (4 * BK)));
     }
     g.kchunk = ((g.K + splits - 1) / splits + BK - 1) / BK * BK;
     grid.z = (g.K + g.kchunk - 1) / g.kchunk;
     gemm_bf16_kernel<TA, TB, EPI><<<grid, 128, 0, s>>>(g);
     KLR_CHECK_CUDA(cudaGetLastError());
+    if (grid.z > 1) {
+        const int64_t count = (int64_t)g.M * g.N;
+        reduce_slices_kernel<<<(int)std::min<int64_t>((count + 255) / 256, 4 * 152), 256, 0, s>>>(
+            g.part, (int)grid.z, count, g.N, g.C32, g.ldc32);
+        KLR_CHECK_CUDA(cudaGetLastError());
+    }
     return KLR_OK;
 }
 
@@ -283,19 +310,34 @@ __global__ void last_forward_kernel(const __nv_bfloat16* __restrict__ A3,
     }
 }
 
-// dpred = 2 (pred - target) / n; loss += sum (pred - target)^2 / n
+// Sum over the block in a fixed order (warp trees, then warp sums in order);
+// the result is valid in thread 0.
+__device__ float block_sum(float v) {
+    __shared__ float wsum[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    float r = 0.f;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += wsum[i];
+    __syncthreads();
+    return r;
+}
+
+// dpred = 2 (pred - target) / n; part[block] = this block's share of
+// sum (pred - target)^2 / n (the loss is the in-order sum of the slices)
 __global__ void loss_kernel(const float* __restrict__ pred, const float* __restrict__ target,
-                            int64_t n, float* __restrict__ dpred, float* loss) {
-    float part = 0.f;
+                            int64_t n, float* __restrict__ dpred, float* __restrict__ part) {
+    float acc = 0.f;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x) {
         const float d = pred[r] - target[r];
         dpred[r] = 2.0f * d / (float)n;
-        part += d * d / (float)n;
+        acc += d * d / (float)n;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, part);
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
 }
 
 // dZ3[r][h] = dpred[r] w4[h] gelu'(Z3[r][h])
@@ -312,28 +354,46 @@ __global__ void last_backward_kernel(const float* __restrict__ dpred,
     }
 }
 
-// out[h] += sum_r w[r] X[r][h] (w NULL: 1) over the rows of a chunk per block
+// part[block][h] = sum_r w[r] X[r][h] (w NULL: 1) over block's contiguous
+// chunk of ceil(n / gridDim.x) rows
 __global__ void colsum_kernel(const __nv_bfloat16* __restrict__ X, const float* __restrict__ w,
-                              int64_t n, int width, float* __restrict__ out) {
-    const int64_t rows_per = 256;
+                              int64_t n, int width, float* __restrict__ part) {
+    const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * rows_per;
     const int64_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
     for (int h = threadIdx.x; h < width; h += blockDim.x) {
         float s = 0.f;
         for (int64_t r = r0; r < r1; ++r)
             s += (w ? w[r] : 1.0f) * __bfloat162float(X[r * width + h]);
-        atomicAdd(out + h, s);
+        part[(int64_t)blockIdx.x * width + h] = s;
     }
 }
 
-__global__ void sum_kernel(const float* __restrict__ x, int64_t n, float* out) {
-    float part = 0.f;
+// part[block] = this block's grid-stride share of sum_r x[r]
+__global__ void sum_kernel(const float* __restrict__ x, int64_t n, float* __restrict__ part) {
+    float acc = 0.f;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
          r += (int64_t)gridDim.x * blockDim.x)
-        part += x[r];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, part);
+        acc += x[r];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+int red_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, kRedBlocks)); }
+
+// out[0..width) = sum over rows of w[r] X[r][:] (deterministic)
+void colsum(const __nv_bfloat16* X, const float* w, int64_t n, int width, float* part, float* out,
+            cudaStream_t s) {
+    const int nb = red_blocks(n);
+    colsum_kernel<<<nb, 256, 0, s>>>(X, w, n, width, part);
+    reduce_slices_kernel<<<1, 256, 0, s>>>(part, nb, width, width, out, 0);
+}
+
+// out[0] = sum over rows of x[r] (deterministic)
+void rowsum(const float* x, int64_t n, float* part, float* out, cudaStream_t s) {
+    const int nb = red_blocks(n);
+    sum_kernel<<<nb, 256, 0, s>>>(x, n, part);
+    reduce_slices_kernel<<<1, 32, 0, s>>>(part, nb, 1, 1, out, 0);
 }
 
 __global__ void adamw_kernel(float* __restrict__ p, const float* __restrict__ g,
@@ -357,7 +417,7 @@ __global__ void adamw_kernel(float* __restrict__ p, const float* __restrict__ g,
 // ---------------------------------------------------------------------------
 struct MlpWs {
     __nv_bfloat16 *pb, *X0, *CR, *A1, *A2, *A3, *dZa, *dZb, *dE, *emb_table;
-    float *Z1, *Z2, *Z3, *pred, *dpred, *grads, *loss;
+    float *Z1, *Z2, *Z3, *pred, *dpred, *grads, *loss, *part;
 };
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -377,6 +437,7 @@ size_t mlp_ws_bytes(int64_t n, int n_coef, int64_t n_kernels_table, bool train) 
         b += align256(2 * (size_t)n * EMB);                   // dE (embedding grads)
         b += align256(4 * (size_t)o.total);                   // grads
         b += 256;                                              // loss
+        b += align256(4 * (size_t)kPartFloats);               // reduction slices
     }
     return b;
 }
@@ -404,6 +465,7 @@ MlpWs carve(void* base, int64_t n, int n_coef, int64_t n_kernels_table, bool tra
         w.dE = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n * EMB));
         w.grads = reinterpret_cast<float*>(take(4 * (size_t)o.total));
         w.loss = reinterpret_cast<float*>(take(256));
+        w.part = reinterpret_cast<float*>(take(4 * (size_t)kPartFloats));
     }
     return w;
 }
@@ -532,10 +594,14 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, con
     g.ldcb = IN;
     if ((st = gemm<false, false, EPI_BF16>(g, s)) != KLR_OK) return st;
     if ((st = forward_hidden(w, net->params, o, n, true, s)) != KLR_OK) return st;
-    loss_kernel<<<blocks_for(n, 256), 256, 0, s>>>(w.pred, rows->target, n, w.dpred, w.loss);
+    {
+        const int nb = red_blocks(n);
+        loss_kernel<<<nb, 256, 0, s>>>(w.pred, rows->target, n, w.dpred, w.part);
+        reduce_slices_kernel<<<1, 32, 0, s>>>(w.part, nb, 1, 1, w.loss, 0);
+    }
     // output layer
-    colsum_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(w.A3, w.dpred, n, H, w.grads + o.W4);
-    sum_kernel<<<blocks_for(n, 256), 256, 0, s>>>(w.dpred, n, w.grads + o.b4);
+    colsum(w.A3, w.dpred, n, H, w.part, w.grads + o.W4, s);
+    rowsum(w.dpred, n, w.part, w.grads + o.b4, s);
     last_backward_kernel<<<blocks_for(n * H, 256), 256, 0, s>>>(w.dpred, w.pb + o.W4, w.Z3, n, w.dZa);
     KLR_CHECK_CUDA(cudaGetLastError());
     // layer 3: dW3 = dZ3^T A2, db3, dZ2 = (dZ3 W3) * gelu'(Z2)
@@ -549,8 +615,9 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, con
     gw.ldb = H;
     gw.C32 = w.grads + o.W3;
     gw.ldc32 = H;
+    gw.part = w.part;
     if ((st = gemm<true, true, EPI_F32>(gw, s)) != KLR_OK) return st;
-    colsum_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(w.dZa, nullptr, n, H, w.grads + o.b3);
+    colsum(w.dZa, nullptr, n, H, w.part, w.grads + o.b3, s);
     GemmArgs gx{};
     gx.M = (int)n;
     gx.N = H;
@@ -569,7 +636,7 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, con
     gw.B = w.A1;
     gw.C32 = w.grads + o.W2;
     if ((st = gemm<true, true, EPI_F32>(gw, s)) != KLR_OK) return st;
-    colsum_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(w.dZb, nullptr, n, H, w.grads + o.b2);
+    colsum(w.dZb, nullptr, n, H, w.part, w.grads + o.b2, s);
     gx.A = w.dZb;
     gx.B = w.pb + o.W2;
     gx.Cb = w.dZa;
@@ -583,7 +650,7 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, con
     gw.C32 = w.grads + o.W1;
     gw.ldc32 = IN;
     if ((st = gemm<true, true, EPI_F32>(gw, s)) != KLR_OK) return st;
-    colsum_kernel<<<(int)((n + 255) / 256), 256, 0, s>>>(w.dZa, nullptr, n, H, w.grads + o.b1);
+    colsum(w.dZa, nullptr, n, H, w.part, w.grads + o.b1, s);
     GemmArgs ge{};
     ge.M = (int)n;
     ge.N = EMB;
@@ -606,6 +673,7 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, con
     gE.ldb = nc;
     gE.C32 = w.grads + o.E;
     gE.ldc32 = nc;
+    gE.part = w.part;
     if ((st = gemm<true, true, EPI_F32>(gE, s)) != KLR_OK) return st;
     if (grads_out)
         KLR_CHECK_CUDA(cudaMemcpyAsync(grads_out, w.grads, 4 * (size_t)o.total,
