@@ -1354,16 +1354,145 @@ solve_lane_dw_kernel(const __grid_constant__ FitParams P) {
 #undef WV
 }
 
+// Group-solver steps, out of line so that the kernel holds one copy of each
+// (its schedule calls them from several places).  Q lanes serve one fit; lane
+// q = lane % Q owns rows i = q (mod Q) of the packed lower factor Lf (row i
+// starts at i (i + 1) / 2; the diagonal slots are not used by these steps).
+#define GLF(i, j) Lf[(i) * ((i) + 1) / 2 + (j)]
+
+// Cholesky factor of (D G D - shift I), G from the moment sums M (pair table
+// `pair`, m monomials, n_mom moments per power of y), into Lf (strictly lower
+// part) and rinv (1 / diagonal).  Writes only when `write`; returns the
+// group's success (false also when not writing).
+template <int Q>
+__device__ __noinline__ bool group_cholesky(float2* Lf, float2* rinv, const float2* M,
+                                            const uint8_t (*pair)[kMaxBasis], const float2* Dv,
+                                            int m, int u, int n_mom, dw shift, bool write) {
+    const unsigned full = 0xffffffffu;
+    const int q = (threadIdx.x & 31) % Q;
+    auto ld2 = [](const float2 v) -> dw { return dw{v.x, v.y}; };
+    auto st2 = [](dw x) -> float2 { return make_float2(x.h, x.l); };
+    auto gh = [&](int i, int j) -> dw {
+        const int bi = i >= m, bj = j >= m;
+        const float2 gg = M[(bi + bj) * n_mom + pair[i - bi * m][j - bj * m]];
+        const float sc = ((bi != bj) ? -1.f : 1.f) * Dv[i].x * Dv[j].x;
+        return dw{gg.x * sc, gg.y * sc};
+    };
+    bool good = write;
+    for (int j = 0; j < u; ++j) {
+        dw_acc a;
+        a.init(dw{0.f, 0.f});
+        for (int k = q; k < j; k += Q) {
+            const dw x = ld2(GLF(j, k));
+            a.add_prod(x, x);
+        }
+        dw sum = a.value();
+#pragma unroll
+        for (int o = 1; o < Q; o <<= 1) {
+            const dw y{__shfl_xor_sync(full, sum.h, o), __shfl_xor_sync(full, sum.l, o)};
+            sum = dw_add(sum, y);
+        }
+        const dw sjj = dw_sub(dw_sub(gh(j, j), shift), sum);
+        good = good && (sjj.h > 0.f);
+        const dw r = good ? dw_div(dw{1.f, 0.f}, dw_sqrt(sjj)) : dw{1.f, 0.f};
+        if (good && q == 0) rinv[j] = st2(r);
+        for (int i = j + 1 + ((q - (j + 1) % Q) + Q) % Q; i < u; i += Q) {
+            dw_acc t0, t1;
+            t0.init(gh(i, j));
+            t1.init(dw{0.f, 0.f});
+            int k = 0;
+            for (; k + 1 < j; k += 2) {
+                t0.sub_prod(ld2(GLF(i, k)), ld2(GLF(j, k)));
+                t1.sub_prod(ld2(GLF(i, k + 1)), ld2(GLF(j, k + 1)));
+            }
+            if (k < j) t0.sub_prod(ld2(GLF(i, k)), ld2(GLF(j, k)));
+            if (good) GLF(i, j) = st2(dw_mul(dw_add(t0.value(), t1.value()), r));
+        }
+        __syncwarp();
+    }
+    return good;
+}
+
+// w <- (L L^T)^-1 w, column-oriented.  Lane q keeps the rows i = q + r Q
+// it owns as unnormalised Dot2 accumulators in registers (r < MAXR, a
+// compile-time count, so the updates of different rows are independent
+// instructions); the finished component of column j is broadcast from its
+// owner by shuffles.  Only L is read from shared memory.
+template <int Q, int MAXR>
+__device__ __noinline__ void group_tri_solve(float2* wv, const float2* Lf, const float2* rinv,
+                                             int u, bool write) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, q = lane % Q;
+    auto ld2 = [](const float2 v) -> dw { return dw{v.x, v.y}; };
+    auto st2 = [](dw x) -> float2 { return make_float2(x.h, x.l); };
+    const int gbase = lane & ~(Q - 1);
+    dw_acc a[MAXR];
+    dw x[MAXR];
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+        const int i = q + r * Q;
+        a[r].init(i < u ? ld2(wv[i]) : dw{0.f, 0.f});
+        x[r] = dw{0.f, 0.f};
+    }
+    // forward: L y = w
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+#pragma unroll 1
+        for (int jj = 0; jj < Q; ++jj) {
+            const int j = r * Q + jj;
+            if (j >= u) break;
+            const dw aj = a[r].value();
+            dw yj{__shfl_sync(full, aj.h, gbase | jj), __shfl_sync(full, aj.l, gbase | jj)};
+            yj = dw_mul(yj, ld2(rinv[j]));
+            if (q == jj) x[r] = yj;
+#pragma unroll
+            for (int r2 = r; r2 < MAXR; ++r2) {
+                const int i = q + r2 * Q;
+                if (i > j && i < u) a[r2].sub_prod(ld2(GLF(i, j)), yj);
+            }
+        }
+    }
+    // backward: L^T x = y
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) a[r].init(x[r]);
+#pragma unroll
+    for (int r = MAXR - 1; r >= 0; --r) {
+#pragma unroll 1
+        for (int jj = Q - 1; jj >= 0; --jj) {
+            const int j = r * Q + jj;
+            if (j >= u) continue;
+            const dw bj = a[r].value();
+            dw xj{__shfl_sync(full, bj.h, gbase | jj), __shfl_sync(full, bj.l, gbase | jj)};
+            xj = dw_mul(xj, ld2(rinv[j]));
+            if (q == jj) x[r] = xj;
+#pragma unroll
+            for (int r2 = 0; r2 <= r; ++r2) {
+                const int i = q + r2 * Q;
+                if (i < j) a[r2].sub_prod(ld2(GLF(j, i)), xj);
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) {
+        const int i = q + r * Q;
+        if (write && i < u) wv[i] = st2(x[r]);
+    }
+    __syncwarp();
+}
+
+#undef GLF
+
 // The double-word solver with Q lanes per fit (32 / Q fits per warp).  Each
 // fit's factor lives in shared memory (packed lower triangle, 8-byte pairs);
 // row i of the factor is computed by lane i % Q of the fit's group, so a fit's
 // dependency chains are Q times shorter than with one lane per fit and four
 // times as many fits fit in an SM's shared memory per warp.  The triangular
-// solves are column-oriented (each lane updates the rows it owns), so they
-// need no reductions.  Control flow is uniform across the warp: every group
-// runs the same schedule and a group that has finished (or failed) keeps
-// running it with its writes switched off.
-template <int Q>
+// solves are column-oriented (each lane updates the rows it owns, at most
+// MAXR, held in registers), so they need no reductions.  Control flow is
+// uniform across the warp: every group runs the same schedule and a group
+// that has finished (or failed) keeps running it with its writes switched off.
+template <int Q, int MAXR>
 __global__ void __launch_bounds__(32)
 solve_group_dw_kernel(const __grid_constant__ FitParams P) {
     constexpr int GPW = 32 / Q;
@@ -1381,8 +1510,7 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
     float2* rinv = Lf + nL;
     float2* vv = rinv + u;
     float2* wv = vv + u;
-    float2* av = wv + u;                          // Dot2 accumulators of the solves
-    float2* Dv = av + u;
+    float2* Dv = wv + u;
     auto ld2 = [](const float2 v) -> dw { return dw{v.x, v.y}; };
     auto st2 = [](dw x) -> float2 { return make_float2(x.h, x.l); };
     const unsigned full = 0xffffffffu;
@@ -1429,63 +1557,10 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
     // Cholesky of (Ghat - shift I) for groups with `write`; returns the
     // group's success (false also for groups not writing)
     auto cholesky = [&](dw shift, bool write) -> bool {
-        bool good = write;
-        for (int j = 0; j < u; ++j) {
-            dw_acc a;
-            a.init(dw{0.f, 0.f});
-            for (int k = q; k < j; k += Q) {
-                const dw x = ld2(LF(j, k));
-                a.add_prod(x, x);
-            }
-            const dw sjj = dw_sub(dw_sub(gh(j, j), shift), gsum(a.value()));
-            good = good && (sjj.h > 0.f);
-            const dw r = good ? dw_div(dw{1.f, 0.f}, dw_sqrt(sjj)) : dw{1.f, 0.f};
-            if (good && q == 0) rinv[j] = st2(r);
-            for (int i = j + 1 + ((q - (j + 1) % Q) + Q) % Q; i < u; i += Q) {
-                dw_acc t0, t1;
-                t0.init(gh(i, j));
-                t1.init(dw{0.f, 0.f});
-                int k = 0;
-                for (; k + 1 < j; k += 2) {
-                    t0.sub_prod(ld2(LF(i, k)), ld2(LF(j, k)));
-                    t1.sub_prod(ld2(LF(i, k + 1)), ld2(LF(j, k + 1)));
-                }
-                if (k < j) t0.sub_prod(ld2(LF(i, k)), ld2(LF(j, k)));
-                if (good) LF(i, j) = st2(dw_mul(dw_add(t0.value(), t1.value()), r));
-            }
-            __syncwarp();
-        }
-        return good;
+        return group_cholesky<Q>(Lf, rinv, M, P.pair, Dv, m, u, n_mom, shift, write);
     };
-    // w <- (L L^T)^-1 w, column-oriented; av holds per-row Dot2 accumulators
-    auto solve = [&](bool write) {
-        for (int i = q; i < u; i += Q) av[i] = wv[i];
-        __syncwarp();
-        for (int j = 0; j < u; ++j) {
-            const dw xj = dw_mul(ld2(av[j]), ld2(rinv[j]));   // final y_j (av[j] complete)
-            for (int i = j + 1 + ((q - (j + 1) % Q) + Q) % Q; i < u; i += Q) {
-                dw_acc a;
-                a.init(ld2(av[i]));
-                a.sub_prod(ld2(LF(i, j)), xj);
-                if (write) av[i] = st2(a.value());
-            }
-            if (write && q == j % Q) wv[j] = st2(xj);
-            __syncwarp();
-        }
-        for (int i = q; i < u; i += Q) av[i] = wv[i];
-        __syncwarp();
-        for (int j = u - 1; j >= 0; --j) {
-            const dw xj = dw_mul(ld2(av[j]), ld2(rinv[j]));
-            for (int i = q; i < j; i += Q) {
-                dw_acc a;
-                a.init(ld2(av[i]));
-                a.sub_prod(ld2(LF(j, i)), xj);
-                if (write) av[i] = st2(a.value());
-            }
-            if (write && q == j % Q) wv[j] = st2(xj);
-            __syncwarp();
-        }
-    };
+    // w <- (L L^T)^-1 w for groups with `write`
+    auto solve = [&](bool write) { group_tri_solve<Q, MAXR>(wv, Lf, rinv, u, write); };
     auto gdot = [&](const float2* a, const float2* b) -> dw {
         dw_acc s;
         s.init(dw{0.f, 0.f});
@@ -1914,26 +1989,37 @@ klr_status launch_solve_lane_dw(const FitParams& P, cudaStream_t stream) {
     return KLR_OK;
 }
 
-template <int Q>
+template <int Q, int MAXR>
 klr_status launch_solve_group_dw_q(const FitParams& P, cudaStream_t stream) {
     constexpr int GPW = 32 / Q;
+    if (P.u > Q * MAXR) {
+        set_error("group solver: %d unknowns exceed %d rows per lane", P.u, MAXR);
+        return KLR_ENOTSUP;
+    }
     FitParams Q_ = P;
-    int stride = P.u * (P.u + 1) / 2 + 5 * P.u;
+    int stride = P.u * (P.u + 1) / 2 + 4 * P.u;   // L, 1/L_jj, v, w, D
     if (stride % 2 == 0) ++stride;          // spread the groups over the banks
     Q_.ld = stride;
     const size_t smem = sizeof(float2) * (size_t)stride * GPW;
-    KLR_CHECK_CUDA(cudaFuncSetAttribute(solve_group_dw_kernel<Q>,
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(solve_group_dw_kernel<Q, MAXR>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    solve_group_dw_kernel<Q><<<(P.n_fits + GPW - 1) / GPW, 32, smem, stream>>>(Q_);
+    solve_group_dw_kernel<Q, MAXR><<<(P.n_fits + GPW - 1) / GPW, 32, smem, stream>>>(Q_);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
 }
 
 // q_lanes: lanes per fit, 2, 4 or 8 (an autotuned choice)
+// (rows per lane: enough for 20 unknowns, the degree-2 basis in (N, b0, b1),
+// else for the solver's limit of 30)
 klr_status launch_solve_group_dw(const FitParams& P, int q_lanes, cudaStream_t stream) {
-    if (q_lanes == 2) return launch_solve_group_dw_q<2>(P, stream);
-    if (q_lanes == 8) return launch_solve_group_dw_q<8>(P, stream);
-    return launch_solve_group_dw_q<4>(P, stream);
+    const bool small = P.u <= 20;
+    if (q_lanes == 2)
+        return small ? launch_solve_group_dw_q<2, 10>(P, stream)
+                     : launch_solve_group_dw_q<2, 15>(P, stream);
+    if (q_lanes == 8)
+        return small ? launch_solve_group_dw_q<8, 3>(P, stream)
+                     : launch_solve_group_dw_q<8, 4>(P, stream);
+    return small ? launch_solve_group_dw_q<4, 5>(P, stream) : launch_solve_group_dw_q<4, 8>(P, stream);
 }
 
 klr_status launch_solve_lane(const FitParams& P, cudaStream_t stream) {
