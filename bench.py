@@ -31,6 +31,11 @@ import numpy as np  # noqa: E402
 WORKLOAD = dict(name="batched_fit_eval_fp32", kernels=10000, metrics=8, counts=(50, 2000),
                 noise=0.01, degree=2, n_vars=3, n_hi_log2=23, sizes_per_kernel=64, n_cfg=51)
 METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
+# DRAM bytes (read + write) per sample of the moments kernel, from one ncu
+# capture of the 3,000-kernel copy of this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum over its samples); the traffic of a full launch scales
+# with the sample count.  Summary: profiles/moments_fast_kernel_batched_3000k.md
+MOMENTS_DRAM_BYTES_PER_SAMPLE = 16.79
 
 
 def parse():
@@ -395,7 +400,9 @@ def run_klr(args):
         "kernel_ms": {"fit_moments": gram_ms, "fit_solve": solve_ms, "argmin": eval_ms},
         "roofline": {"bound": "alu", "achieved": fit_ops / (gram_ms * 1e-3) / 1e12,
                      "peak": alu_peak / 1e12, "unit": "Tops/s (FP32 lane-ops)",
-                     "frac": fit_ops / (gram_ms * 1e-3) / alu_peak, "traffic": None,
+                     "frac": fit_ops / (gram_ms * 1e-3) / alu_peak,
+                     "traffic": MOMENTS_DRAM_BYTES_PER_SAMPLE * n_samples,
+                     "traffic_algorithmic": fit_bytes,
                      "kernel": "moments_fast_kernel (double-FP32 moment sums, F1-F2)",
                      "hbm_gbs": fit_bytes / (gram_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak,
                      "hbm_frac": fit_bytes / (gram_ms * 1e-3) / 1e9 / hbm_peak,
