@@ -74,3 +74,64 @@ def test_features():
     assert f[0, 0] == 8 / 23 and f[1, 0] == 1.0
     assert f[0, 1] == 0.5 and f[1, 2] == 0.3 and f[1, 3] == 0.0
     assert np.all(f[:, 11:] == 0) and math.isclose(f[0, 10], 0.6)
+
+
+def _tiny_head(seed=2, n=6, n_coef=24, n_out=5):
+    rng = np.random.default_rng(seed)
+    flat = rng.standard_normal(mlp.param_count(n_coef, n_out)) * 0.2
+    feat = mlp.features(2.0 ** rng.uniform(8, 23, n), None, rng.standard_normal(7) * 0.3)
+    coef = rng.standard_normal((n, n_coef)) * 0.3
+    target = rng.standard_normal((n, n_out))
+    target[rng.random((n, n_out)) < 0.3] = np.inf          # shapes that are not meaningful
+    return flat, feat, coef, target
+
+
+def test_per_query_head_gradients_match_finite_differences():
+    n_coef, n_out = 24, 5
+    flat, feat, coef, target = _tiny_head(n_coef=n_coef, n_out=n_out)
+    assert np.all(feat[:, 1:4] == 0.0)
+    p = mlp.unpack(flat, n_coef, n_out)
+    loss, g = mlp.loss_and_grads(p, feat, coef, target)
+    gflat = mlp.pack(g, n_coef, n_out)
+    assert gflat.shape == flat.shape
+    rng = np.random.default_rng(3)
+    idx = np.concatenate([rng.choice(len(flat), 50, replace=False),
+                          np.arange(len(flat) - 6 * 256 - 5, len(flat))[::97]])
+    h = 1e-6
+    for i in idx:
+        fp, fm = flat.copy(), flat.copy()
+        fp[i] += h
+        fm[i] -= h
+        lp, _ = mlp.loss_and_grads(mlp.unpack(fp, n_coef, n_out), feat, coef, target)
+        lm, _ = mlp.loss_and_grads(mlp.unpack(fm, n_coef, n_out), feat, coef, target)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - gflat[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, gflat[i])
+
+
+def test_per_query_head_masked_loss():
+    n_coef, n_out = 24, 5
+    flat, feat, coef, target = _tiny_head(n_coef=n_coef, n_out=n_out)
+    p = mlp.unpack(flat, n_coef, n_out)
+    pred, _ = mlp.forward(p, feat, coef, per_query=True)
+    mask = np.isfinite(target)
+    loss, g = mlp.loss_and_grads(p, feat, coef, target)
+    # the loss is the mean squared error over the finite targets only
+    assert np.isclose(loss, np.mean((pred[mask] - target[mask]) ** 2), rtol=1e-14)
+    # a masked output receives no gradient through its row of W4 and b4
+    masked_cols = np.nonzero(~mask.any(axis=0))[0]
+    for c in masked_cols:
+        assert np.all(g["W4"][c] == 0.0) and g["b4"][c] == 0.0
+    # changing a masked target changes nothing
+    t2 = target.copy()
+    t2[~mask] = -np.inf
+    loss2, g2 = mlp.loss_and_grads(p, feat, coef, t2)
+    assert loss2 == loss and np.array_equal(mlp.pack(g2, n_coef, n_out), mlp.pack(g, n_coef, n_out))
+    # with every target finite, one output column and zero shape features the
+    # per-query form is the per-row form on the same rows
+    flat1 = flat[:mlp.param_count(n_coef, 1)]
+    p1 = mlp.unpack(flat1, n_coef, 1)
+    t1 = np.random.default_rng(4).standard_normal((len(feat), 1))
+    lq, gq = mlp.loss_and_grads(p1, feat, coef, t1)
+    lr_, gr = mlp.loss_and_grads(p1, feat, coef, t1[:, 0])
+    assert np.isclose(lq, lr_, rtol=1e-14)
+    assert np.allclose(mlp.pack(gq, n_coef, 1), mlp.pack(gr, n_coef, 0), rtol=1e-12, atol=1e-15)
