@@ -60,7 +60,10 @@ def parse():
                     help="kernels of the 3D sweep checked against the oracle")
     ap.add_argument("--sur-kernels", type=int, default=50000)
     ap.add_argument("--sur-rows-per-kernel", type=int, default=400)
-    ap.add_argument("--sur-epochs", type=int, default=2)
+    ap.add_argument("--sur-epochs", type=int, default=30)
+    ap.add_argument("--sur-form", default="query", choices=["query", "row"],
+                    help="surrogate output form: per (kernel, N) query or per (kernel, N, shape) row")
+    ap.add_argument("--sur-lr", type=float, default=2e-3)
     ap.add_argument("--sur-queries-per-kernel", type=int, default=20)
     ap.add_argument("--sur-k", type=int, default=8)
     ap.add_argument("--prec-fits", type=int, default=4096)
@@ -523,26 +526,45 @@ def run_surrogate(args):
     hw = klr.make_hw(W.HARDWARE)
     prog = klr.Context.program(coef3, regs, smem, n_vars=3, degree=3, n_scale_log2=23,
                                b_scale_log2=10, metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
-    # training rows: (size, shape) pairs drawn per kernel over 64 log-spaced sizes
+    # training rows over 64 log-spaced sizes per kernel; targets are per-query
+    # centred log2 cycles of the FP32 rational program
     sizes = W.log_spaced_sizes(64)
     q = W.queries_per_kernel(nk, sizes)
     R = args.sur_rows_per_kernel
     keys = W.stream_keys(seed, (90,), np.arange(nk, dtype=np.uint64))
-    draw = W.words(keys[:, None], np.arange(R, dtype=np.uint64)[None, :]) % np.uint64(64 * 51)
-    draw = draw.astype(np.int64)
-    row_q = (np.arange(nk)[:, None] * 64 + draw // 51).reshape(-1)
-    row_c = (draw % 51).reshape(-1)
-    y = proposer.table_targets(ctx, prog, hw, cfg, t(q.offsets), t(q.sizes), t(row_q), t(row_c))
-    keep = torch.isfinite(y)
-    rq, rc, y = t(row_q)[keep], t(row_c)[keep], y[keep]
-    mu, sd = float(y.mean()), float(y.std())
-    target = ((y - mu) / sd).float().contiguous()
+    per_query = args.sur_form == "query"
+    if per_query:
+        # (kernel, N) rows: R // 51 sizes per kernel, every shape as an output
+        nsz = max(1, R // 51)
+        draw = W.words(keys[:, None], np.arange(nsz, dtype=np.uint64)[None, :]) % np.uint64(64)
+        row_q = (np.arange(nk)[:, None] * 64 + draw.astype(np.int64)).reshape(-1)
+        table = proposer.query_table(ctx, prog, hw, cfg, t(q.offsets), t(q.sizes))
+        rq = t(row_q)
+        target = table[rq]
+        keep = torch.isfinite(target).any(dim=1)
+        rq, target = rq[keep], target[keep].contiguous()
+        ci = None
+        n_out, batch = 51, 4096
+    else:
+        # (kernel, N, shape) rows drawn per kernel
+        draw = W.words(keys[:, None], np.arange(R, dtype=np.uint64)[None, :]) % np.uint64(64 * 51)
+        draw = draw.astype(np.int64)
+        row_q = (np.arange(nk)[:, None] * 64 + draw // 51).reshape(-1)
+        row_c = (draw % 51).reshape(-1)
+        y = proposer.table_targets(ctx, prog, hw, cfg, t(q.offsets), t(q.sizes), t(row_q),
+                                   t(row_c))
+        keep = torch.isfinite(y)
+        rq, rc, target = t(row_q)[keep], t(row_c)[keep], y[keep].contiguous()
+        ci = rc.int().contiguous()
+        n_out, batch = 0, 65536
     kern = (rq // 64).int().contiguous()
     N = t(q.sizes)[rq].contiguous()
-    ci = rc.int().contiguous()
     n_rows = kern.numel()
-    z = W.normal(W.stream_key(seed, 91), np.arange(klr.mlp_param_count(n_coef), dtype=np.uint64))
-    sur = klr.Surrogate(ctx, n_coef, proposer.init_params(n_coef, z), np.ones(7))
+    n_tuples = int(torch.isfinite(target).sum())
+    z = W.normal(W.stream_key(seed, 91),
+                 np.arange(klr.mlp_param_count(n_coef, n_out), dtype=np.uint64))
+    sur = klr.Surrogate(ctx, n_coef, proposer.init_params(n_coef, z, n_out), np.ones(7),
+                        n_out=n_out)
     okeys = W.stream_keys(seed, (92,), np.arange(args.sur_epochs, dtype=np.uint64))
     order = lambda ep: torch.argsort(t(W.words(okeys[ep], np.arange(n_rows, dtype=np.uint64))
                                        .view(np.int64)))
@@ -550,12 +572,12 @@ def run_surrogate(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    losses = proposer.train(sur, coef, cfg, kern, N, ci, target, batch=65536,
-                            epochs=args.sur_epochs, lr=2e-3, order=order, log_every=50)
+    losses = proposer.train(sur, coef, cfg, kern, N, ci, target, batch=batch,
+                            epochs=args.sur_epochs, lr=args.sur_lr, order=order, log_every=50)
     e1.record()
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
-    steps = args.sur_epochs * ((n_rows + 65535) // 65536)
+    steps = args.sur_epochs * ((n_rows + batch - 1) // batch)
     # evaluation queries: sizes off the training grid
     qk = args.sur_queries_per_kernel
     ek = W.stream_keys(seed, (93,), np.arange(nk, dtype=np.uint64))
@@ -597,13 +619,15 @@ def run_surrogate(args):
             "value": n_q / (sur_ms * 1e-3), "unit": "queries/s", "n_gpus": 1, "steps": K,
             "higher_is_better": True, "dtype": "bf16 (network), f32 (re-rank)",
             "data": "synthetic (seeded rational ground truth)",
-            "config": {"workload": "learned_proposer", "kernels": nk, "degree": 3,
-                       "train_rows": n_rows, "epochs": args.sur_epochs, "batch": 65536,
-                       "train_steps": steps, "queries": n_q, "k": args.sur_k, "configs": 51},
+            "config": {"workload": "learned_proposer", "form": args.sur_form, "kernels": nk,
+                       "degree": 3, "train_rows": n_rows, "train_tuples": n_tuples,
+                       "epochs": args.sur_epochs, "batch": batch, "train_steps": steps,
+                       "queries": n_q, "k": args.sur_k, "configs": 51},
             "plain_sweep": {"ms": plain_ms, "queries_per_s": n_q / (plain_ms * 1e-3)},
             "surrogate_path": {"ms": sur_ms, "propose_ms": prop_ms,
                                "speedup_vs_plain": plain_ms / sur_ms},
             "train": {"ms": train_ms, "rows_per_s": n_rows * args.sur_epochs / (train_ms * 1e-3),
+                      "tuples_per_s": n_tuples * args.sur_epochs / (train_ms * 1e-3),
                       "loss_first": losses[0], "loss_last": losses[-1], "prep_s": prep_s},
             "regret_top1": {"mean": float(np.mean(np.minimum(reg, 10))),
                             "median": pct(reg, 50), "p90": pct(reg, 90), "p99": pct(reg, 99),

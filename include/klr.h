@@ -300,13 +300,22 @@ klr_status klr_tune_import(klr_ctx* ctx, const uint64_t* keys, const int32_t* ch
  *          log2 b1 / 10, log2 b2 / 10 (0 for 2D shapes), the 7 hardware
  *          features hw_feat[7], then zeros
  *   a1 = gelu(x0 W1^T + b1)  W1: 256 x 80;  a2 = gelu(a1 W2^T + b2)  W2: 256 x 256
- *   a3 = gelu(a2 W3^T + b3)  W3: 256 x 256; pred = a3 W4^T + b4      W4: 1 x 256
+ *   a3 = gelu(a2 W3^T + b3)  W3: 256 x 256; pred = a3 W4^T + b4      W4: k x 256
  *   gelu(z) = z/2 (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))).
+ * Two output forms (n_out in klr_mlp):
+ *   n_out = 0, per row: k = 1; a row is (kernel, N, block shape); loss = mean
+ *     squared error of pred against target[n].
+ *   n_out = |F| > 0, per query: k = n_out; a row is (kernel, N), its shape
+ *     features are 0 and output c predicts shape c; target is n x n_out and
+ *     non-finite entries (shapes that are not meaningful) are masked: loss =
+ *     sum of squared errors over the finite targets / their count.  51
+ *     outputs per row cost about 1/40 of 51 per-row evaluations.
  * The parameter vector holds E, W1, b1, W2, b2, W3, b3, W4, b4 in that order;
- * klr_mlp_param_count(n_coef) floats.  pred is trained against a target the
- * caller chooses (normalised log2 cycles). */
+ * klr_mlp_param_count(n_coef, n_out) floats.  pred is trained against a
+ * target the caller chooses (normalised log2 cycles). */
 typedef struct klr_mlp {
     int32_t n_coef;        /* coefficients per kernel, a multiple of 8        */
+    int32_t n_out;         /* 0: per-row output; 1..256: per-query outputs    */
     float* params;         /* device, param_count floats (FP32 master copy)   */
     float* adam_m;         /* device, param_count floats (training only)      */
     float* adam_v;         /* device, param_count floats (training only)      */
@@ -314,7 +323,9 @@ typedef struct klr_mlp {
     float hw_feat[7];      /* hardware features fed to every row              */
 } klr_mlp;
 
-/* Rows for the network: row r is (kernel[r], N[r], block shape cfg[cfg_idx[r]]). */
+/* Rows for the network: row r is (kernel[r], N[r], block shape cfg[cfg_idx[r]]);
+ * for a per-query network cfg_idx is ignored (may be NULL) and target holds
+ * n x n_out values. */
 typedef struct klr_mlp_rows {
     int64_t n;
     const int32_t* kernel;   /* device [n], indexes coef rows                 */
@@ -323,8 +334,9 @@ typedef struct klr_mlp_rows {
     const float* target;     /* device [n] (training only)                    */
 } klr_mlp_rows;
 
-/* Number of parameters for n_coef coefficients per kernel. */
-int64_t klr_mlp_param_count(int32_t n_coef);
+/* Number of parameters for n_coef coefficients per kernel and n_out outputs
+ * (0: per-row form); 0 for arguments out of range. */
+int64_t klr_mlp_param_count(int32_t n_coef, int32_t n_out);
 
 /* One training step on a batch (n <= 262144): forward, mean-squared-error
  * loss, backward, and (if apply_update) one AdamW step with bias correction,
@@ -337,16 +349,27 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef,
                               float lr, float weight_decay, int apply_update,
                               float* loss_out, float* grads_out, void* stream);
 
-/* Forward pass for a batch of rows (n <= 262144): pred_out device [n] FP32. */
+/* Forward pass for a batch of rows (n <= 262144): pred_out device FP32, [n]
+ * per row or [n x n_out] per query. */
 klr_status klr_mlp_predict(klr_ctx* ctx, const klr_mlp* net, const float* coef,
                            const int32_t* cfg, int n_cfg, const klr_mlp_rows* rows,
                            float* pred_out, void* stream);
+
+/* Training targets from an FP32 cycles table (klr_eval output, n_rows x
+ * n_cfg): out[r][c] = log2 cycles[r][c] minus the mean of log2 cycles over
+ * row r's finite positive entries (a per-query offset does not change which
+ * shape is best), NaN where the entry is not finite or not positive.  Device
+ * arrays; asynchronous on `stream`. */
+klr_status klr_mlp_query_targets(const float* cycles, int64_t n_rows, int32_t n_cfg, float* out,
+                                 void* stream);
 
 /* Proposal: for every query of q (CSR by kernel) predict all n_cfg shapes and
  * keep the k (1..16) of least predicted value among the meaningful ones
  * (B_active > 0, T <= T_max, every b_i <= N; integer occupancy as in
  * klr_argmin).  cand_out: device int32 [n_queries x k], -1 past the number of
- * meaningful shapes.  regs, smem: device int32 [n_kernels]. */
+ * meaningful shapes.  regs, smem: device int32 [n_kernels].  A per-query
+ * network needs n_out == n_cfg (else KLR_EINVAL) and runs once per query; a
+ * per-row network runs once per (query, shape). */
 klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float* coef,
                        const int32_t* regs, const int32_t* smem, int32_t n_kernels,
                        const klr_hw* hw, const int32_t* cfg, int n_cfg,

@@ -34,7 +34,7 @@ ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last
                "klr_argmin_noalloc", "klr_mlp_param_count", "klr_mlp_train_step",
                "klr_mlp_predict", "klr_propose", "klr_argmin_candidates", "klr_autotune_fit",
                "klr_autotune_argmin", "klr_tune_export", "klr_tune_import", "klr_fit_gram",
-               "klr_fit_solve")
+               "klr_fit_solve", "klr_mlp_query_targets")
 #: largest query count klr_argmin_noalloc accepts
 ARGMIN_NOALLOC_MAX_QUERIES = 65536
 
@@ -78,7 +78,7 @@ class Queries(ctypes.Structure):
 
 
 class MlpNet(ctypes.Structure):
-    _fields_ = [("n_coef", ctypes.c_int32), ("params", ctypes.c_void_p),
+    _fields_ = [("n_coef", ctypes.c_int32), ("n_out", ctypes.c_int32), ("params", ctypes.c_void_p),
                 ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
                 ("step", ctypes.c_int64), ("hw_feat", ctypes.c_float * 7)]
 
@@ -91,7 +91,7 @@ class MlpRows(ctypes.Structure):
 _vp = ctypes.c_void_p
 _lib.klr_last_error.restype = ctypes.c_char_p
 _lib.klr_mlp_param_count.restype = ctypes.c_int64
-_lib.klr_mlp_param_count.argtypes = [ctypes.c_int32]
+_lib.klr_mlp_param_count.argtypes = [ctypes.c_int32, ctypes.c_int32]
 _lib.klr_version.restype = ctypes.c_int
 for _name, _args in {
     "klr_ctx_create": [ctypes.POINTER(_vp), ctypes.c_int],
@@ -110,6 +110,7 @@ for _name, _args in {
                             ctypes.POINTER(Queries), _vp, _vp, ctypes.c_int32, _vp, _vp, _vp,
                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), _vp],
     "klr_fit_gram": [_vp, ctypes.POINTER(FitBatch), _vp],
+    "klr_mlp_query_targets": [_vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp],
     "klr_fit_solve": [_vp, ctypes.POINTER(FitBatch), _vp, ctypes.c_int32, _vp, _vp, _vp],
     "klr_tune_export": [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "klr_tune_import": [_vp, _vp, _vp, ctypes.c_int],
@@ -321,33 +322,40 @@ class Context:
         return best, cyc, margin, status, lp
 
 
-def mlp_param_count(n_coef: int) -> int:
-    return int(_lib.klr_mlp_param_count(n_coef))
+def mlp_param_count(n_coef: int, n_out: int = 0) -> int:
+    """Parameters of the surrogate: per-row output (n_out 0) or n_out
+    per-query outputs."""
+    return int(_lib.klr_mlp_param_count(n_coef, n_out))
 
 
 class Surrogate:
     """The learned proposer's parameters and optimiser state (device tensors)
     and the calls that train and use it.  ``init`` is the initial FP32
-    parameter vector (drawn by the caller's seeded generator)."""
+    parameter vector (drawn by the caller's seeded generator).  n_out = 0:
+    one output per (kernel, N, shape) row; n_out = |F|: one output per shape
+    for a (kernel, N) row (targets n x n_out, non-finite entries masked)."""
 
-    def __init__(self, ctx: "Context", n_coef: int, init, hw_feat):
+    def __init__(self, ctx: "Context", n_coef: int, init, hw_feat, n_out: int = 0):
         import torch
         self.ctx = ctx
         self.n_coef = n_coef
-        n = mlp_param_count(n_coef)
+        self.n_out = n_out
+        n = mlp_param_count(n_coef, n_out)
         init = torch.as_tensor(init, dtype=torch.float32)
         if init.numel() != n:
             raise ValueError(f"init has {init.numel()} values, the network {n}")
         self.params = init.cuda().contiguous()
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
-        self.net = MlpNet(n_coef, self.params.data_ptr(), self.m.data_ptr(), self.v.data_ptr(), 0)
+        self.net = MlpNet(n_coef, n_out, self.params.data_ptr(), self.m.data_ptr(),
+                          self.v.data_ptr(), 0)
         for i in range(7):
             self.net.hw_feat[i] = float(hw_feat[i])
 
     @staticmethod
     def _rows(kernel, N, cfg_idx, target=None):
-        return MlpRows(kernel.numel(), kernel.data_ptr(), N.data_ptr(), cfg_idx.data_ptr(),
+        return MlpRows(kernel.numel(), kernel.data_ptr(), N.data_ptr(),
+                       None if cfg_idx is None else cfg_idx.data_ptr(),
                        None if target is None else target.data_ptr())
 
     def train_step(self, coef, cfg, kernel, N, cfg_idx, target, lr, weight_decay=0.0,
@@ -366,7 +374,8 @@ class Surrogate:
     def predict(self, coef, cfg, kernel, N, cfg_idx, out=None, stream=None):
         import torch
         if out is None:
-            out = torch.empty(kernel.numel(), dtype=torch.float32, device=coef.device)
+            shape = (kernel.numel(), self.n_out) if self.n_out else (kernel.numel(),)
+            out = torch.empty(shape, dtype=torch.float32, device=coef.device)
         rows = self._rows(kernel, N, cfg_idx)
         _check("klr_mlp_predict",
                _lib.klr_mlp_predict(self.ctx._h, ctypes.byref(self.net), _ptr(coef), _ptr(cfg),
@@ -383,6 +392,18 @@ class Surrogate:
                                 _ptr(smem), regs.numel(), ctypes.byref(hw), _ptr(cfg),
                                 cfg.shape[0], ctypes.byref(q), k, _ptr(out), _stream(stream)))
         return out
+
+
+def query_targets(cycles, out=None, stream=None):
+    """Per-query centred log2 cycles of an FP32 cycles table (n_q, n_cfg);
+    NaN where a shape is not meaningful (klr_mlp_query_targets)."""
+    import torch
+    if out is None:
+        out = torch.empty_like(cycles)
+    _check("klr_mlp_query_targets",
+           _lib.klr_mlp_query_targets(_ptr(cycles), cycles.shape[0], cycles.shape[1], _ptr(out),
+                                      _stream(stream)))
+    return out
 
 
 def argmin_candidates(ctx: "Context", prog: Program, hw: Hw, cfg, q_offsets, q_N, cand,

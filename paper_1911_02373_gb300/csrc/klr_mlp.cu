@@ -1,9 +1,11 @@
 // Learned proposer: BF16 training and inference kernels of the surrogate MLP.
 //
-// The paper has no learned component.  The network predicts log cycles of a
-// (kernel, N, block shape) row from the shape, the size, the hardware and a
-// learned 64-d embedding of the kernel's fitted coefficients (layout in
-// klr.h).  Dense layers run on the tensor cores through mma.sync m16n8k16
+// The paper has no learned component.  The network predicts log cycles from
+// the size, the hardware and a learned 64-d embedding of the kernel's fitted
+// coefficients (layout in klr.h), in one of two output forms: per row (one
+// output for a (kernel, N, block shape) row whose features include the
+// shape) or per query (one output per block shape for a (kernel, N) row, the
+// shape features zero; loss masked to the meaningful shapes).  Dense layers run on the tensor cores through mma.sync m16n8k16
 // (BF16 operands, FP32 accumulation) in one tiled GEMM kernel whose operands
 // may each be stored transposed, so the forward pass, the input gradients and
 // the weight gradients all use it; bias, GELU and the GELU derivative are fused
@@ -27,7 +29,9 @@ struct Offsets {
     int64_t E, W1, b1, W2, b2, W3, b3, W4, b4, total;
 };
 
-Offsets offsets(int n_coef) {
+// n_out: 0 for the per-row output, else the per-query output count
+Offsets offsets(int n_coef, int n_out) {
+    const int k = n_out > 0 ? n_out : 1;
     Offsets o;
     o.E = 0;
     o.W1 = o.E + (int64_t)EMB * n_coef;
@@ -37,10 +41,14 @@ Offsets offsets(int n_coef) {
     o.W3 = o.b2 + H;
     o.b3 = o.W3 + (int64_t)H * H;
     o.W4 = o.b3 + H;
-    o.b4 = o.W4 + H;
-    o.total = o.b4 + 1;
+    o.b4 = o.W4 + (int64_t)k * H;
+    o.total = o.b4 + k;
     return o;
 }
+
+// outputs per row and the padded row length of their BF16 copy
+int out_cols(int n_out) { return n_out > 0 ? n_out : 1; }
+int out_ld(int n_out) { return (out_cols(n_out) + 7) & ~7; }
 
 __device__ __forceinline__ float gelu(float z) {
     const float c = 0.7978845608028654f;   // sqrt(2 / pi)
@@ -256,16 +264,20 @@ struct RowArgs {
     __nv_bfloat16* CR;          // n x n_coef gathered coefficients, or NULL
 };
 
-// feature block of X0 and the gathered coefficient rows
+// feature block of X0 and the gathered coefficient rows (cfg_idx NULL:
+// per-query rows, shape features 0)
 __global__ void gather_rows_kernel(const __grid_constant__ RowArgs a) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < a.n;
          r += (int64_t)gridDim.x * blockDim.x) {
-        const int c = a.cfg_idx[r];
         float f[FEAT];
         f[0] = log2f((float)a.N[r]) * (1.0f / 23.0f);
-        f[1] = log2f((float)a.cfg[3 * c]) * 0.1f;
-        f[2] = log2f((float)a.cfg[3 * c + 1]) * 0.1f;
-        f[3] = log2f((float)a.cfg[3 * c + 2]) * 0.1f;
+        f[1] = f[2] = f[3] = 0.f;
+        if (a.cfg_idx) {
+            const int c = a.cfg_idx[r];
+            f[1] = log2f((float)a.cfg[3 * c]) * 0.1f;
+            f[2] = log2f((float)a.cfg[3 * c + 1]) * 0.1f;
+            f[3] = log2f((float)a.cfg[3 * c + 2]) * 0.1f;
+        }
         for (int i = 0; i < 7; ++i) f[4 + i] = a.hw[i];
         for (int i = 11; i < FEAT; ++i) f[i] = 0.f;
         for (int i = 0; i < FEAT; ++i) a.X0[r * IN + i] = __float2bfloat16(f[i]);
@@ -354,18 +366,62 @@ __global__ void last_backward_kernel(const float* __restrict__ dpred,
     }
 }
 
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(float v) { return v; }
+
 // part[block][h] = sum_r w[r] X[r][h] (w NULL: 1) over block's contiguous
 // chunk of ceil(n / gridDim.x) rows
-__global__ void colsum_kernel(const __nv_bfloat16* __restrict__ X, const float* __restrict__ w,
-                              int64_t n, int width, float* __restrict__ part) {
+template <typename T>
+__global__ void colsum_kernel(const T* __restrict__ X, const float* __restrict__ w, int64_t n,
+                              int width, float* __restrict__ part) {
     const int64_t rows_per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t r0 = blockIdx.x * rows_per;
     const int64_t r1 = r0 + rows_per < n ? r0 + rows_per : n;
     for (int h = threadIdx.x; h < width; h += blockDim.x) {
         float s = 0.f;
-        for (int64_t r = r0; r < r1; ++r)
-            s += (w ? w[r] : 1.0f) * __bfloat162float(X[r * width + h]);
+        for (int64_t r = r0; r < r1; ++r) s += (w ? w[r] : 1.0f) * to_f32(X[r * width + h]);
         part[(int64_t)blockIdx.x * width + h] = s;
+    }
+}
+
+// per-query head: part[block] = this block's count of finite targets
+__global__ void count_finite_kernel(const float* __restrict__ target, int64_t total,
+                                    float* __restrict__ part) {
+    float acc = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        acc += isfinite(target[i]) ? 1.0f : 0.0f;
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// per-query head: with V = *count finite targets, dpred = 2 (pred - t) / V
+// where t is finite (else 0), part[block] = the block's share of the loss
+__global__ void masked_loss_kernel(const float* __restrict__ pred, const float* __restrict__ target,
+                                   int64_t total, const float* __restrict__ count,
+                                   float* __restrict__ dpred, float* __restrict__ part) {
+    const float inv = 1.0f / fmaxf(*count, 1.0f);
+    float acc = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float t = target[i];
+        const float d = isfinite(t) ? pred[i] - t : 0.f;
+        dpred[i] = 2.0f * d * inv;
+        acc += d * d * inv;
+    }
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// BF16 copy of an n x cols FP32 matrix with rows padded to ld (pads zero)
+__global__ void pad_bf16_kernel(const float* __restrict__ x, int64_t n, int cols, int ld,
+                                __nv_bfloat16* __restrict__ y) {
+    const int64_t total = n * ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / ld;
+        const int c = (int)(i - r * ld);
+        y[i] = __float2bfloat16(c < cols ? x[r * cols + c] : 0.f);
     }
 }
 
@@ -382,10 +438,11 @@ __global__ void sum_kernel(const float* __restrict__ x, int64_t n, float* __rest
 int red_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, kRedBlocks)); }
 
 // out[0..width) = sum over rows of w[r] X[r][:] (deterministic)
-void colsum(const __nv_bfloat16* X, const float* w, int64_t n, int width, float* part, float* out,
+template <typename T>
+void colsum(const T* X, const float* w, int64_t n, int width, float* part, float* out,
             cudaStream_t s) {
     const int nb = red_blocks(n);
-    colsum_kernel<<<nb, 256, 0, s>>>(X, w, n, width, part);
+    colsum_kernel<T><<<nb, 256, 0, s>>>(X, w, n, width, part);
     reduce_slices_kernel<<<1, 256, 0, s>>>(part, nb, width, width, out, 0);
 }
 
@@ -416,19 +473,20 @@ __global__ void adamw_kernel(float* __restrict__ p, const float* __restrict__ g,
 // Workspace of one batch
 // ---------------------------------------------------------------------------
 struct MlpWs {
-    __nv_bfloat16 *pb, *X0, *CR, *A1, *A2, *A3, *dZa, *dZb, *dE, *emb_table;
-    float *Z1, *Z2, *Z3, *pred, *dpred, *grads, *loss, *part;
+    __nv_bfloat16 *pb, *X0, *CR, *A1, *A2, *A3, *dZa, *dZb, *dE, *emb_table, *dpb;
+    float *Z1, *Z2, *Z3, *pred, *dpred, *grads, *loss, *part, *count;
 };
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
-size_t mlp_ws_bytes(int64_t n, int n_coef, int64_t n_kernels_table, bool train) {
-    const Offsets o = offsets(n_coef);
+size_t mlp_ws_bytes(int64_t n, int n_coef, int n_out, int64_t n_kernels_table, bool train) {
+    const Offsets o = offsets(n_coef, n_out);
+    const size_t oc = (size_t)out_cols(n_out);
     size_t b = 0;
     b += align256(2 * (size_t)o.total);                       // pb
     b += align256(2 * (size_t)n * IN);                        // X0
     b += align256(2 * (size_t)n * H) * 3;                     // A1..A3
-    b += align256(4 * (size_t)n) * 2;                         // pred, dpred
+    b += align256(4 * (size_t)n * oc) * 2;                    // pred, dpred
     b += align256(2 * (size_t)n_kernels_table * EMB);         // emb table
     if (train) {
         b += align256(2 * (size_t)n * n_coef);                // CR
@@ -438,12 +496,15 @@ size_t mlp_ws_bytes(int64_t n, int n_coef, int64_t n_kernels_table, bool train) 
         b += align256(4 * (size_t)o.total);                   // grads
         b += 256;                                              // loss
         b += align256(4 * (size_t)kPartFloats);               // reduction slices
+        b += 256;                                              // count
+        b += align256(2 * (size_t)n * out_ld(n_out));         // dpb
     }
     return b;
 }
 
-MlpWs carve(void* base, int64_t n, int n_coef, int64_t n_kernels_table, bool train) {
-    const Offsets o = offsets(n_coef);
+MlpWs carve(void* base, int64_t n, int n_coef, int n_out, int64_t n_kernels_table, bool train) {
+    const Offsets o = offsets(n_coef, n_out);
+    const size_t oc = (size_t)out_cols(n_out);
     char* p = reinterpret_cast<char*>(base);
     auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
     MlpWs w{};
@@ -452,8 +513,8 @@ MlpWs carve(void* base, int64_t n, int n_coef, int64_t n_kernels_table, bool tra
     w.A1 = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n * H));
     w.A2 = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n * H));
     w.A3 = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n * H));
-    w.pred = reinterpret_cast<float*>(take(4 * (size_t)n));
-    w.dpred = reinterpret_cast<float*>(take(4 * (size_t)n));
+    w.pred = reinterpret_cast<float*>(take(4 * (size_t)n * oc));
+    w.dpred = reinterpret_cast<float*>(take(4 * (size_t)n * oc));
     w.emb_table = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n_kernels_table * EMB));
     if (train) {
         w.CR = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n * n_coef));
@@ -466,6 +527,8 @@ MlpWs carve(void* base, int64_t n, int n_coef, int64_t n_kernels_table, bool tra
         w.grads = reinterpret_cast<float*>(take(4 * (size_t)o.total));
         w.loss = reinterpret_cast<float*>(take(256));
         w.part = reinterpret_cast<float*>(take(4 * (size_t)kPartFloats));
+        w.count = reinterpret_cast<float*>(take(256));
+        w.dpb = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n * out_ld(n_out)));
     }
     return w;
 }
@@ -475,9 +538,10 @@ int blocks_for(int64_t n, int threads) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
 }
 
-// Forward of the three hidden layers and the output for rows whose X0 is set.
-klr_status forward_hidden(const MlpWs& w, const float* params, const Offsets& o, int64_t n,
-                          bool keep_z, cudaStream_t s) {
+// Forward of the three hidden layers and the output for rows whose X0 is set
+// (pred: n values per row, or n x n_out for the per-query head).
+klr_status forward_hidden(const MlpWs& w, const float* params, const Offsets& o, int n_out,
+                          int64_t n, bool keep_z, cudaStream_t s) {
     klr_status st;
     GemmArgs g{};
     g.M = (int)n;
@@ -508,6 +572,21 @@ klr_status forward_hidden(const MlpWs& w, const float* params, const Offsets& o,
     g.C32 = keep_z ? w.Z3 : nullptr;
     g.Cb = w.A3;
     if ((st = gemm<false, false, EPI_GELU>(g, s)) != KLR_OK) return st;
+    if (n_out > 0) {
+        // pred = A3 W4^T + b4 on the tensor cores
+        GemmArgs go{};
+        go.M = (int)n;
+        go.N = n_out;
+        go.K = H;
+        go.A = w.A3;
+        go.lda = H;
+        go.B = w.pb + o.W4;
+        go.ldb = H;
+        go.bias = params + o.b4;
+        go.C32 = w.pred;
+        go.ldc32 = n_out;
+        return gemm<false, false, EPI_F32>(go, s);
+    }
     last_forward_kernel<<<blocks_for(n * 32, 256), 256, 0, s>>>(w.A3, w.pb + o.W4, params + o.b4,
                                                                 n, w.pred);
     KLR_CHECK_CUDA(cudaGetLastError());
@@ -518,15 +597,17 @@ klr_status check_net(const klr_mlp* net) {
     KLR_REQUIRE(net && net->params, "NULL network or parameters");
     KLR_REQUIRE(net->n_coef > 0 && net->n_coef % 8 == 0 && net->n_coef <= 4096,
                 "n_coef %d must be a positive multiple of 8", net->n_coef);
+    KLR_REQUIRE(net->n_out >= 0 && net->n_out <= 256, "n_out %d not in 0..256", net->n_out);
     return KLR_OK;
 }
 
-klr_status check_rows(const klr_mlp_rows* rows, bool need_target) {
+klr_status check_rows(const klr_mlp_rows* rows, bool need_target, bool per_query) {
     KLR_REQUIRE(rows, "NULL rows");
     KLR_REQUIRE(rows->n >= 0 && rows->n <= kMaxRows, "rows n %lld not in 0..%lld",
                 (long long)rows->n, (long long)kMaxRows);
     if (rows->n > 0)
-        KLR_REQUIRE(rows->kernel && rows->N && rows->cfg_idx && (!need_target || rows->target),
+        KLR_REQUIRE(rows->kernel && rows->N && (per_query || rows->cfg_idx) &&
+                        (!need_target || rows->target),
                     "NULL row array");
     return KLR_OK;
 }
@@ -539,9 +620,9 @@ using namespace klr;
 
 extern "C" {
 
-int64_t klr_mlp_param_count(int32_t n_coef) {
-    if (n_coef <= 0) return 0;
-    return offsets(n_coef).total;
+int64_t klr_mlp_param_count(int32_t n_coef, int32_t n_out) {
+    if (n_coef <= 0 || n_out < 0 || n_out > 256) return 0;
+    return offsets(n_coef, n_out).total;
 }
 
 klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, const int32_t* cfg,
@@ -551,7 +632,8 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, con
     KLR_REQUIRE(ctx, "klr_mlp_train_step: NULL context");
     klr_status st = check_net(net);
     if (st != KLR_OK) return st;
-    if ((st = check_rows(rows, true)) != KLR_OK) return st;
+    const int no = net->n_out;
+    if ((st = check_rows(rows, true, no > 0)) != KLR_OK) return st;
     KLR_REQUIRE(net->adam_m && net->adam_v, "klr_mlp_train_step: NULL optimiser state");
     KLR_REQUIRE(coef && cfg && n_cfg > 0, "klr_mlp_train_step: NULL coef or cfg");
     KLR_REQUIRE(std::isfinite(lr) && lr >= 0 && std::isfinite(weight_decay) && weight_decay >= 0,
@@ -562,9 +644,9 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, con
     if (n == 0) return KLR_OK;
     KLR_CHECK_CUDA(cudaSetDevice(c->device));
     const int nc = net->n_coef;
-    const Offsets o = offsets(nc);
-    if ((st = ensure_workspace(c, mlp_ws_bytes(n, nc, 0, true), s)) != KLR_OK) return st;
-    const MlpWs w = carve(c->ws, n, nc, 0, true);
+    const Offsets o = offsets(nc, no);
+    if ((st = ensure_workspace(c, mlp_ws_bytes(n, nc, no, 0, true), s)) != KLR_OK) return st;
+    const MlpWs w = carve(c->ws, n, nc, no, 0, true);
     KLR_CHECK_CUDA(cudaMemsetAsync(w.grads, 0, 4 * (size_t)o.total, s));
     KLR_CHECK_CUDA(cudaMemsetAsync(w.loss, 0, sizeof(float), s));
     cast_bf16_kernel<<<blocks_for(o.total, 256), 256, 0, s>>>(net->params, w.pb, o.total);
@@ -572,7 +654,7 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, con
     ra.n = n;
     ra.kernel = rows->kernel;
     ra.N = rows->N;
-    ra.cfg_idx = rows->cfg_idx;
+    ra.cfg_idx = no > 0 ? nullptr : rows->cfg_idx;
     ra.cfg = cfg;
     ra.coef = coef;
     ra.n_coef = nc;
@@ -593,17 +675,57 @@ klr_status klr_mlp_train_step(klr_ctx* ctx, klr_mlp* net, const float* coef, con
     g.Cb = w.X0 + FEAT;
     g.ldcb = IN;
     if ((st = gemm<false, false, EPI_BF16>(g, s)) != KLR_OK) return st;
-    if ((st = forward_hidden(w, net->params, o, n, true, s)) != KLR_OK) return st;
-    {
+    if ((st = forward_hidden(w, net->params, o, no, n, true, s)) != KLR_OK) return st;
+    if (no > 0) {
+        // per-query head: masked loss over the finite targets
+        const int64_t total = n * no;
+        const int nb = red_blocks(total);
+        count_finite_kernel<<<nb, 256, 0, s>>>(rows->target, total, w.part);
+        reduce_slices_kernel<<<1, 32, 0, s>>>(w.part, nb, 1, 1, w.count, 0);
+        masked_loss_kernel<<<nb, 256, 0, s>>>(w.pred, rows->target, total, w.count, w.dpred,
+                                              w.part);
+        reduce_slices_kernel<<<1, 32, 0, s>>>(w.part, nb, 1, 1, w.loss, 0);
+        const int ld = out_ld(no);
+        pad_bf16_kernel<<<blocks_for(n * ld, 256), 256, 0, s>>>(w.dpred, n, no, ld, w.dpb);
+        KLR_CHECK_CUDA(cudaGetLastError());
+        // output layer: dW4 = dpred^T A3, db4, dZ3 = (dpred W4) * gelu'(Z3)
+        GemmArgs g4{};
+        g4.M = no;
+        g4.N = H;
+        g4.K = (int)n;
+        g4.A = w.dpb;
+        g4.lda = ld;
+        g4.B = w.A3;
+        g4.ldb = H;
+        g4.C32 = w.grads + o.W4;
+        g4.ldc32 = H;
+        g4.part = w.part;
+        if ((st = gemm<true, true, EPI_F32>(g4, s)) != KLR_OK) return st;
+        colsum<float>(w.dpred, nullptr, n, no, w.part, w.grads + o.b4, s);
+        GemmArgs gz{};
+        gz.M = (int)n;
+        gz.N = H;
+        gz.K = no;
+        gz.A = w.dpb;
+        gz.lda = ld;
+        gz.B = w.pb + o.W4;
+        gz.ldb = H;
+        gz.Cb = w.dZa;
+        gz.ldcb = H;
+        gz.Z = w.Z3;
+        gz.ldz = H;
+        if ((st = gemm<false, true, EPI_DGELU>(gz, s)) != KLR_OK) return st;
+    } else {
         const int nb = red_blocks(n);
         loss_kernel<<<nb, 256, 0, s>>>(w.pred, rows->target, n, w.dpred, w.part);
         reduce_slices_kernel<<<1, 32, 0, s>>>(w.part, nb, 1, 1, w.loss, 0);
+        // output layer
+        colsum(w.A3, w.dpred, n, H, w.part, w.grads + o.W4, s);
+        rowsum(w.dpred, n, w.part, w.grads + o.b4, s);
+        last_backward_kernel<<<blocks_for(n * H, 256), 256, 0, s>>>(w.dpred, w.pb + o.W4, w.Z3, n,
+                                                                   w.dZa);
+        KLR_CHECK_CUDA(cudaGetLastError());
     }
-    // output layer
-    colsum(w.A3, w.dpred, n, H, w.part, w.grads + o.W4, s);
-    rowsum(w.dpred, n, w.part, w.grads + o.b4, s);
-    last_backward_kernel<<<blocks_for(n * H, 256), 256, 0, s>>>(w.dpred, w.pb + o.W4, w.Z3, n, w.dZa);
-    KLR_CHECK_CUDA(cudaGetLastError());
     // layer 3: dW3 = dZ3^T A2, db3, dZ2 = (dZ3 W3) * gelu'(Z2)
     GemmArgs gw{};
     gw.M = H;
@@ -697,7 +819,8 @@ klr_status klr_mlp_predict(klr_ctx* ctx, const klr_mlp* net, const float* coef, 
     KLR_REQUIRE(ctx, "klr_mlp_predict: NULL context");
     klr_status st = check_net(net);
     if (st != KLR_OK) return st;
-    if ((st = check_rows(rows, false)) != KLR_OK) return st;
+    const int no = net->n_out;
+    if ((st = check_rows(rows, false, no > 0)) != KLR_OK) return st;
     KLR_REQUIRE(coef && cfg && n_cfg > 0 && (rows->n == 0 || pred_out),
                 "klr_mlp_predict: NULL coef, cfg or output");
     Context* c = reinterpret_cast<Context*>(ctx);
@@ -706,19 +829,19 @@ klr_status klr_mlp_predict(klr_ctx* ctx, const klr_mlp* net, const float* coef, 
     if (n == 0) return KLR_OK;
     KLR_CHECK_CUDA(cudaSetDevice(c->device));
     const int nc = net->n_coef;
-    const Offsets o = offsets(nc);
+    const Offsets o = offsets(nc, no);
     // rows carry their own coefficient gather and embedding GEMM
     const size_t extra = align256(2 * (size_t)n * nc);
-    if ((st = ensure_workspace(c, mlp_ws_bytes(n, nc, 0, false) + extra, s)) != KLR_OK) return st;
-    MlpWs w = carve(c->ws, n, nc, 0, false);
-    w.CR = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(c->ws) +
-                                            mlp_ws_bytes(n, nc, 0, false));
+    const size_t base = mlp_ws_bytes(n, nc, no, 0, false);
+    if ((st = ensure_workspace(c, base + extra, s)) != KLR_OK) return st;
+    MlpWs w = carve(c->ws, n, nc, no, 0, false);
+    w.CR = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(c->ws) + base);
     cast_bf16_kernel<<<blocks_for(o.total, 256), 256, 0, s>>>(net->params, w.pb, o.total);
     RowArgs ra{};
     ra.n = n;
     ra.kernel = rows->kernel;
     ra.N = rows->N;
-    ra.cfg_idx = rows->cfg_idx;
+    ra.cfg_idx = no > 0 ? nullptr : rows->cfg_idx;
     ra.cfg = cfg;
     ra.coef = coef;
     ra.n_coef = nc;
@@ -737,12 +860,64 @@ klr_status klr_mlp_predict(klr_ctx* ctx, const klr_mlp* net, const float* coef, 
     g.Cb = w.X0 + FEAT;
     g.ldcb = IN;
     if ((st = gemm<false, false, EPI_BF16>(g, s)) != KLR_OK) return st;
-    if ((st = forward_hidden(w, net->params, o, n, false, s)) != KLR_OK) return st;
-    KLR_CHECK_CUDA(cudaMemcpyAsync(pred_out, w.pred, 4 * (size_t)n, cudaMemcpyDeviceToDevice, s));
+    if ((st = forward_hidden(w, net->params, o, no, n, false, s)) != KLR_OK) return st;
+    KLR_CHECK_CUDA(cudaMemcpyAsync(pred_out, w.pred, 4 * (size_t)n * out_cols(no),
+                                   cudaMemcpyDeviceToDevice, s));
     return KLR_OK;
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Training targets from a cycles table: per-query centred log2 cycles.
+// ---------------------------------------------------------------------------
+namespace klr {
+namespace {
+
+// one warp per query row: out = log2(cycles) - mean over the row's finite
+// positive entries of log2(cycles); NaN where the entry is not finite or not
+// positive (a shape that is not meaningful)
+__global__ void query_targets_kernel(const float* __restrict__ cyc, int64_t n_rows, int n_cfg,
+                                     float* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < n_rows;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const float* row = cyc + r * n_cfg;
+        float sum = 0.f, cnt = 0.f;
+        for (int c = lane; c < n_cfg; c += 32) {
+            const float v = row[c];
+            if (isfinite(v) && v > 0.f) {
+                sum += log2f(v);
+                cnt += 1.f;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        }
+        const float mean = cnt > 0.f ? sum / cnt : 0.f;
+        for (int c = lane; c < n_cfg; c += 32) {
+            const float v = row[c];
+            out[r * n_cfg + c] = (isfinite(v) && v > 0.f) ? log2f(v) - mean : __int_as_float(0x7fc00000);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace klr
+
+extern "C" klr_status klr_mlp_query_targets(const float* cycles, int64_t n_rows, int32_t n_cfg,
+                                            float* out, void* stream_) {
+    KLR_REQUIRE(n_rows >= 0 && n_cfg >= 1, "klr_mlp_query_targets: bad sizes");
+    if (n_rows == 0) return KLR_OK;
+    KLR_REQUIRE(cycles && out, "klr_mlp_query_targets: NULL array");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
+    klr::query_targets_kernel<<<klr::blocks_for(n_rows * 32, 256), 256, 0, s>>>(cycles, n_rows,
+                                                                               n_cfg, out);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
 
 // ---------------------------------------------------------------------------
 // Proposal: every shape of every query through the network, top-k of the
@@ -804,7 +979,23 @@ __global__ void propose_rows_kernel(const __grid_constant__ ProposeArgs a) {
     }
 }
 
+// per-query head: one row per query (shape features 0)
+__global__ void propose_query_rows_kernel(const __grid_constant__ ProposeArgs a) {
+    for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < a.nq;
+         qi += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = a.q0 + qi;
+        a.row_kernel[qi] = kernel_of(a.q_off, a.n_kernels, q);
+        float f[FEAT];
+        f[0] = log2f((float)a.q_N[q]) * (1.0f / 23.0f);
+        f[1] = f[2] = f[3] = 0.f;
+        for (int i = 0; i < 7; ++i) f[4 + i] = a.hw[i];
+        for (int i = 11; i < FEAT; ++i) f[i] = 0.f;
+        for (int i = 0; i < FEAT; ++i) a.X0[qi * IN + i] = __float2bfloat16(f[i]);
+    }
+}
+
 // one thread per query: the k smallest predictions among meaningful shapes
+// (predictions laid out [query][shape] in both output forms)
 __global__ void topk_kernel(const __grid_constant__ ProposeArgs a) {
     for (int64_t qi = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; qi < a.nq;
          qi += (int64_t)gridDim.x * blockDim.x) {
@@ -855,15 +1046,19 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream_);
     KLR_CHECK_CUDA(cudaSetDevice(c->device));
     const int nc = net->n_coef;
-    const Offsets o = offsets(nc);
-    const int64_t qchunk = std::max<int64_t>(1, kMaxRows / n_cfg);
-    const int64_t rows = qchunk * n_cfg;
+    const int no = net->n_out;
+    KLR_REQUIRE(no == 0 || no == n_cfg, "klr_propose: the network has %d outputs for %d shapes",
+                no, n_cfg);
+    const Offsets o = offsets(nc, no);
+    // per row: one network row per (query, shape); per query: one per query
+    const int64_t qchunk = no > 0 ? kMaxRows : std::max<int64_t>(1, kMaxRows / n_cfg);
+    const int64_t rows = no > 0 ? qchunk : qchunk * n_cfg;
     // workspace: network buffers for `rows` rows + per-kernel embeddings + row tables
-    const size_t base = mlp_ws_bytes(rows, nc, n_kernels, false);
+    const size_t base = mlp_ws_bytes(rows, nc, no, n_kernels, false);
     const size_t extra = align256(2 * (size_t)n_kernels * nc) + align256(4 * (size_t)rows) * 2 +
                          align256(8 * (size_t)rows) * 2;
     if ((st = ensure_workspace(c, base + extra, s)) != KLR_OK) return st;
-    MlpWs w = carve(c->ws, rows, nc, n_kernels, false);
+    MlpWs w = carve(c->ws, rows, nc, no, n_kernels, false);
     char* p = reinterpret_cast<char*>(c->ws) + base;
     __nv_bfloat16* coef_b = reinterpret_cast<__nv_bfloat16*>(p);
     p += align256(2 * (size_t)n_kernels * nc);
@@ -916,11 +1111,14 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
         a.cand = cand_out;
         for (int i = 0; i < 7; ++i) a.hw[i] = net->hw_feat[i];
         a.X0 = w.X0;
-        const int64_t nr = nq * n_cfg;
-        propose_rows_kernel<<<blocks_for(nr, 256), 256, 0, s>>>(a);
+        const int64_t nr = no > 0 ? nq : nq * n_cfg;
+        if (no > 0)
+            propose_query_rows_kernel<<<blocks_for(nr, 256), 256, 0, s>>>(a);
+        else
+            propose_rows_kernel<<<blocks_for(nr, 256), 256, 0, s>>>(a);
         embed_rows_kernel<<<blocks_for(nr * EMB, 256), 256, 0, s>>>(row_kernel, nr, w.emb_table, w.X0);
         KLR_CHECK_CUDA(cudaGetLastError());
-        if ((st = forward_hidden(w, net->params, o, nr, false, s)) != KLR_OK) return st;
+        if ((st = forward_hidden(w, net->params, o, no, nr, false, s)) != KLR_OK) return st;
         topk_kernel<<<blocks_for(nq, 128), 128, 0, s>>>(a);
         KLR_CHECK_CUDA(cudaGetLastError());
     }

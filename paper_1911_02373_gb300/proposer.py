@@ -1,12 +1,14 @@
 """Learned proposer: training set, training loop and the propose-then-re-rank
 argmin, all through the library's C ABI.
 
-The surrogate network predicts log2 cycles of a (kernel, N, block shape) row;
-its training targets come from the rational program itself (klr_eval).  At
-query time the network proposes the k most promising meaningful shapes
-(klr_propose) and the exact rational program re-ranks them
-(klr_argmin_candidates), so the plain method remains the judge.  Random numbers
-(initial weights, training rows, batch order) are inputs drawn by the caller.
+The surrogate network predicts per-query centred log2 cycles, either of a
+(kernel, N, block shape) row (per-row form) or of every shape of a (kernel, N)
+query at once (per-query form).  Its training targets come from the rational
+program itself (klr_eval, then klr_mlp_query_targets).  At query time the
+network proposes the k most promising meaningful shapes (klr_propose) and the
+exact rational program re-ranks them (klr_argmin_candidates), so the plain
+method remains the judge.  Random numbers (initial weights, training rows,
+batch order) are inputs drawn by the caller.
 """
 from __future__ import annotations
 
@@ -14,18 +16,19 @@ import math
 
 import numpy as np
 
-from . import F32, Context, Surrogate, argmin_candidates, mlp_param_count
+from . import F32, Context, Surrogate, argmin_candidates, mlp_param_count, query_targets
 
 FEAT, EMB, IN, H = 16, 64, 80, 256
 
 
-def init_params(n_coef: int, normals: np.ndarray) -> np.ndarray:
+def init_params(n_coef: int, normals: np.ndarray, n_out: int = 0) -> np.ndarray:
     """Scale standard normals into initial parameters: weights ~ N(0, 1/fan_in)
     (E, W1..W3 with GELU gain 2, W4 with gain 1), biases zero."""
-    n = mlp_param_count(n_coef)
+    n = mlp_param_count(n_coef, n_out)
+    k = max(1, n_out)
     z = np.asarray(normals, dtype=np.float64)[:n].copy()
     shapes = [((EMB, n_coef), 1.0), ((H, IN), 2.0), ((H,), 0.0), ((H, H), 2.0), ((H,), 0.0),
-              ((H, H), 2.0), ((H,), 0.0), ((1, H), 1.0), ((1,), 0.0)]
+              ((H, H), 2.0), ((H,), 0.0), ((k, H), 1.0), ((k,), 0.0)]
     o = 0
     for shape, gain in shapes:
         cnt = int(np.prod(shape))
@@ -35,20 +38,26 @@ def init_params(n_coef: int, normals: np.ndarray) -> np.ndarray:
     return z.astype(np.float32)
 
 
-def table_targets(ctx: Context, prog, hw, cfg, q_offsets, q_N, row_query, row_cfg):
-    """log2 cycles of rows (query index, shape index) from the FP32 rational
-    program; rows whose shape is not meaningful come back as +inf."""
-    import torch
+def query_table(ctx: Context, prog, hw, cfg, q_offsets, q_N):
+    """(n_q, n_cfg) per-query centred log2 cycles from the FP32 rational
+    program; NaN where a shape is not meaningful."""
     table = ctx.eval(prog, hw, cfg, q_offsets, q_N, out_dtype=F32)
-    vals = table[row_query.long(), row_cfg.long()]
-    return torch.log2(vals)
+    return query_targets(table)
+
+
+def table_targets(ctx: Context, prog, hw, cfg, q_offsets, q_N, row_query, row_cfg):
+    """Per-query centred log2 cycles of rows (query index, shape index);
+    rows whose shape is not meaningful come back as NaN."""
+    t = query_table(ctx, prog, hw, cfg, q_offsets, q_N)
+    return t[row_query.long(), row_cfg.long()]
 
 
 def train(sur: Surrogate, coef, cfg, kernel, N, cfg_idx, target, *, batch, epochs, lr,
           order, weight_decay=0.0, log_every=0):
     """Mini-batch AdamW over the rows for `epochs` passes.  order(epoch) gives
     the permutation of rows for that epoch (device int64).  Cosine learning-rate
-    decay from lr.  Returns the per-step losses (host floats)."""
+    decay from lr.  A per-query network takes cfg_idx None and target
+    (rows, n_out).  Returns the per-step losses (host floats)."""
     import torch
     n = kernel.numel()
     steps_per_epoch = max(1, (n + batch - 1) // batch)
@@ -63,8 +72,8 @@ def train(sur: Surrogate, coef, cfg, kernel, N, cfg_idx, target, *, batch, epoch
             frac = step / max(1, total - 1)
             cur = lr * 0.5 * (1.0 + math.cos(math.pi * frac))
             sur.train_step(coef, cfg, kernel[idx].contiguous(), N[idx].contiguous(),
-                           cfg_idx[idx].contiguous(), target[idx].contiguous(), cur,
-                           weight_decay, True, loss)
+                           None if cfg_idx is None else cfg_idx[idx].contiguous(),
+                           target[idx].contiguous(), cur, weight_decay, True, loss)
             if log_every and step % log_every == 0:
                 losses.append(float(loss.item()))
             step += 1

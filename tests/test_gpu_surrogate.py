@@ -38,12 +38,12 @@ def _bf16(a):
     return torch.tensor(np.asarray(a, dtype=np.float32)).bfloat16().double().numpy()
 
 
-def _init(klr, n_coef, seed):
+def _init(klr, n_coef, seed, n_out=0):
     from paper_1911_02373_gb300 import proposer
-    n = klr.mlp_param_count(n_coef)
+    n = klr.mlp_param_count(n_coef, n_out)
     keys = W.stream_keys(seed, (77,), np.arange(1, dtype=np.uint64))
     z = W.normal(keys[0], np.arange(n, dtype=np.uint64))
-    return proposer.init_params(n_coef, z)
+    return proposer.init_params(n_coef, z, n_out)
 
 
 def test_gradients_match_oracle(klr, ctx):
@@ -83,6 +83,59 @@ def test_gradients_match_oracle(klr, ctx):
     pr_ref, _ = omlp.forward(p, feat, _bf16(coef[kern]))
     got = pred.cpu().numpy()
     assert np.linalg.norm(got - pr_ref) <= 4e-2 * np.linalg.norm(pr_ref)
+
+
+def test_head_gradients_match_oracle(klr, ctx):
+    """The per-query form: 51 outputs per (kernel, N) row, masked targets."""
+    gt = W.ground_truth(35, 10, 3, 3, 8, 23, 10)
+    n_coef = 8 * gt.coef.shape[-1]
+    coef = gt.coef.reshape(10, n_coef).astype(np.float32)
+    rng = np.random.default_rng(5)
+    n, n_out = 260, 51
+    kern = rng.integers(0, 10, n).astype(np.int32)
+    N = (2 ** rng.uniform(8, 23, n)).astype(np.int64)
+    target = rng.standard_normal((n, n_out)).astype(np.float32)
+    target[rng.random((n, n_out)) < 0.25] = np.nan
+    cfg = klr.enumerate_configs(2)
+    init = _init(klr, n_coef, 9, n_out)
+    sur = klr.Surrogate(ctx, n_coef, init, HW_FEAT, n_out=n_out)
+    grads = torch.zeros(init.size, dtype=torch.float32, device="cuda")
+    t = lambda a: torch.tensor(a).cuda()
+    loss = sur.train_step(t(coef), t(cfg), t(kern), t(N), None, t(target), 0.0, 0.0, False,
+                          grads=grads)
+    torch.cuda.synchronize()
+    g_gpu = grads.cpu().numpy().astype(np.float64)
+    p = omlp.unpack(init.astype(np.float64), n_coef, n_out)
+    for name in ("E", "W1", "W2", "W3", "W4"):
+        p[name] = _bf16(p[name])
+    feat = _bf16(omlp.features(N, None, HW_FEAT))
+    loss_ref, g_ref = omlp.loss_and_grads(p, feat, _bf16(coef[kern]), target.astype(np.float64))
+    assert abs(float(loss.item()) - loss_ref) <= 2e-2 * abs(loss_ref)
+    gg = omlp.unpack(g_gpu, n_coef, n_out)
+    for name, _ in omlp.shapes(n_coef, n_out):
+        ref = np.asarray(g_ref[name], dtype=np.float64).reshape(-1)
+        got = np.asarray(gg[name]).reshape(-1)
+        rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-30)
+        assert rel <= 4e-2, (name, rel)
+    pred = sur.predict(t(coef), t(cfg), t(kern), t(N), None)
+    pr_ref, _ = omlp.forward(p, feat, _bf16(coef[kern]), per_query=True)
+    got = pred.cpu().numpy()
+    assert got.shape == (n, n_out)
+    assert np.linalg.norm(got - pr_ref) <= 4e-2 * np.linalg.norm(pr_ref)
+
+
+def test_query_targets_are_centred_log2_cycles(klr, ctx):
+    rng = np.random.default_rng(6)
+    cyc = (2.0 ** rng.uniform(5, 30, (300, 51))).astype(np.float32)
+    cyc[rng.random((300, 51)) < 0.3] = np.inf
+    cyc[7, :] = np.inf                       # a query with no meaningful shape
+    got = klr.query_targets(torch.tensor(cyc).cuda()).cpu().numpy()
+    lg = np.log2(cyc.astype(np.float64))
+    fin = np.isfinite(lg)
+    mean = np.array([lg[r][fin[r]].mean() if fin[r].any() else 0.0 for r in range(300)])
+    want = np.where(fin, lg - mean[:, None], np.nan)
+    assert np.array_equal(np.isnan(got), ~fin)
+    assert np.allclose(got[fin], want[fin], rtol=0, atol=2e-5)
 
 
 def test_adamw_step_matches_oracle(klr, ctx):
@@ -161,8 +214,7 @@ def test_trained_proposer_beats_random_candidates(klr, ctx):
     y = proposer.table_targets(ctx, prog, hw, cfg, qo, qn, rq, rc)
     keep = torch.isfinite(y)
     rq, rc, y = rq[keep], rc[keep], y[keep]
-    mu, sd = y.mean(), y.std()
-    target = ((y - mu) / sd).float().contiguous()
+    target = y.float().contiguous()
     kern = (rq // 64).int().contiguous()
     N = qn[rq].contiguous()
     ci = rc.int().contiguous()
@@ -181,6 +233,57 @@ def test_trained_proposer_beats_random_candidates(klr, ctx):
     sb, sc, sst, cand = proposer.propose_and_rerank(ctx, sur, prog, hw, coef, regs, smem, cfg, qeo,
                                                     qen, 8)
     # random 8 candidates per query, re-ranked the same way
+    kr = W.stream_keys(9, (79,), np.arange(len(qe.sizes), dtype=np.uint64))
+    rnd = (W.words(kr[:, None], np.arange(8, dtype=np.uint64)[None, :]) % np.uint64(51)).astype(np.int32)
+    rb, rcyc, _ = klr.argmin_candidates(ctx, prog, hw, cfg, qeo, qen, t(rnd))
+    torch.cuda.synchronize()
+    c_best = cyc.cpu().numpy().astype(np.float64)
+    ok = np.isfinite(c_best)
+    reg_s = sc.cpu().numpy()[ok] / c_best[ok] - 1
+    reg_r = rcyc.cpu().numpy()[ok] / c_best[ok] - 1
+    reg_r = np.where(np.isfinite(reg_r), reg_r, 10.0)
+    assert np.all(reg_s >= -1e-5)
+    assert np.mean(reg_s) < 0.5 * np.mean(reg_r), (np.mean(reg_s), np.mean(reg_r))
+    assert np.median(reg_s) < 0.05
+
+
+def test_trained_head_proposer_beats_random_candidates(klr, ctx):
+    """The per-query form trained on the same programs: one row per (kernel, N)
+    with 51 masked targets."""
+    from paper_1911_02373_gb300 import proposer
+    nk = 160
+    gt = W.ground_truth(33, nk, 3, 3, 8, 23, 10)
+    n_coef = 8 * gt.coef.shape[-1]
+    t = lambda a: torch.tensor(a).cuda()
+    coef3 = t(gt.coef.astype(np.float32))
+    coef = coef3.reshape(nk, n_coef)
+    regs, smem = t(gt.regs), t(gt.smem)
+    cfg = t(klr.enumerate_configs(2))
+    hw = klr.make_hw(W.HARDWARE)
+    prog = klr.Context.program(coef3, regs, smem, n_vars=3, degree=3, n_scale_log2=23,
+                               b_scale_log2=10, metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+    sizes = W.log_spaced_sizes(64)
+    q = W.queries_per_kernel(nk, sizes)
+    qo, qn = t(q.offsets), t(q.sizes)
+    target = proposer.query_table(ctx, prog, hw, cfg, qo, qn)
+    keep = torch.isfinite(target).any(dim=1)
+    rows = torch.nonzero(keep)[:, 0]
+    kern = (rows // 64).int().contiguous()
+    N = qn[rows].contiguous()
+    target = target[rows].contiguous()
+    sur = klr.Surrogate(ctx, n_coef, _init(klr, n_coef, 10, 51), HW_FEAT, n_out=51)
+    n = kern.numel()
+    keys = W.stream_keys(8, (80,), np.arange(200, dtype=np.uint64))
+    order = lambda ep: t(np.argsort(W.words(keys[ep], np.arange(n, dtype=np.uint64)), kind="stable"))
+    losses = proposer.train(sur, coef, cfg, kern, N, None, target, batch=512, epochs=120, lr=2e-3,
+                            order=order, log_every=20)
+    assert losses[-1] < 0.25 * losses[0], losses
+    ev = np.unique(np.floor(np.exp2(np.linspace(8.3, 22.7, 16))).astype(np.int64))
+    qe = W.queries_per_kernel(nk, ev)
+    qeo, qen = t(qe.offsets), t(qe.sizes)
+    best, cyc, mg, st, _ = ctx.argmin(prog, hw, cfg, qeo, qen, out_dtype=klr.F32)
+    sb, sc, sst, cand = proposer.propose_and_rerank(ctx, sur, prog, hw, coef, regs, smem, cfg, qeo,
+                                                    qen, 8)
     kr = W.stream_keys(9, (79,), np.arange(len(qe.sizes), dtype=np.uint64))
     rnd = (W.words(kr[:, None], np.arange(8, dtype=np.uint64)[None, :]) % np.uint64(51)).astype(np.int32)
     rb, rcyc, _ = klr.argmin_candidates(ctx, prog, hw, cfg, qeo, qen, t(rnd))
