@@ -376,9 +376,11 @@ klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float* coef,
                        const klr_queries* q, int k, int32_t* cand_out, void* stream);
 
 /* Exact re-ranking (Section IV, step 5, restricted to candidates): per query,
- * the candidate of least cycles by FP32 evaluation of the rational program
- * (ties: lowest shape index; none usable: -1).  cand: device int32
- * [n_queries x k] shape indices (-1 entries skipped).  best_cycles: device
+ * the meaningful candidate of least cycles by the FP32 rational program as
+ * klr_argmin's sweep evaluates it (per kernel, only the proposed shapes are
+ * specialised); ties go to the lowest shape index; no meaningful candidate:
+ * -1 and KLR_Q_NONE_FEASIBLE.  cand: device int32 [n_queries x k] shape
+ * indices (entries outside 0..n_cfg-1 are skipped).  best_cycles: device
  * float [n_queries]; q_status: device int32 [n_queries] or NULL. */
 klr_status klr_argmin_candidates(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
                                  const int32_t* cfg, int n_cfg, const klr_queries* q,

@@ -62,6 +62,8 @@ struct EvalParams {
     int* tie_count;
     TieRecord* ties;
     int64_t tie_cap;
+    const int32_t* cand;        // candidate mode: n_q x kc shape indices, or NULL
+    int kc;
     uint8_t exps[kMaxBasis][kMaxVars];
 };
 
@@ -111,7 +113,7 @@ __device__ __forceinline__ long long ceil_div(long long a, long long b) { return
 
 // Full (unspecialised) evaluation of one (kernel, N, configuration) in
 // precision T: the same algorithm as the oracle.  FP64 re-decides FP32
-// near-ties; FP32 re-ranks proposed candidates.
+// near-ties.
 template <typename T>
 __device__ T eval_full(const EvalParams& P, int k, long long N, int c, bool& usable) {
     const int m = P.m, u = P.u, nv = P.n_vars;
@@ -209,21 +211,112 @@ struct CfgInfo {
     unsigned wave;    // B_active * #SMs: blocks per full wave
 };
 
+// Cycles of configuration c for one query (N, its scaled xN) from the
+// specialised per-kernel tables; +inf when c is not meaningful or its metrics
+// are invalid (then KLR_Q_BAD_METRIC is added to st).
+template <typename T, int D>
+__device__ __forceinline__ T eval_cfg(const EvalParams& P, const CfgInfo* __restrict__ cinfo,
+                                      const float* __restrict__ wave_rcp,
+                                      const T* __restrict__ spec, const T* lo, const T* sc,
+                                      unsigned n_sm, long long N, bool small, T xN, int c,
+                                      int& st) {
+    constexpr int NC = 2 * (D + 1);
+    const CfgInfo ci = cinfo[c];
+    const int B = ci.B;
+    const bool meaningful = B > 0 && ci.b0 <= N && ci.b1 <= N && ci.b2 <= N;
+    T e = (T)INFINITY;
+    if (meaningful) {
+        T a[8 * NC];
+        const T* sp = spec + (size_t)c * 8 * NC;
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int t = 0; t < 2 * NC; ++t) {
+                const float4 f4 = reinterpret_cast<const float4*>(sp)[t];
+                a[4 * t] = f4.x; a[4 * t + 1] = f4.y; a[4 * t + 2] = f4.z; a[4 * t + 3] = f4.w;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4 * NC; ++t) {
+                const double2 d2 = reinterpret_cast<const double2*>(sp)[t];
+                a[2 * t] = d2.x; a[2 * t + 1] = d2.y;
+            }
+        }
+        T L[8];
+        bool valid = true;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const T* ai = a + i * NC;
+            T p = ai[D], qq = ai[2 * D + 1];
+#pragma unroll
+            for (int j = D - 1; j >= 0; --j) {
+                p = p * xN + ai[j];
+                qq = qq * xN + ai[D + 1 + j];
+            }
+            const T g = qdiv<T>(p, qq);
+            valid = valid && (qq != T(0)) && isfinite(g);
+            L[i] = lo[i] + sc[i] * fabs(g);
+        }
+        if (valid) {
+            long long nb, asm_, rep;
+            if (small) {
+                const unsigned n32 = (unsigned)N, t32 = (unsigned)ci.T;
+                const unsigned nb32 = ci.t_shift >= 0 ? (n32 + t32 - 1) >> ci.t_shift
+                                                      : (n32 + t32 - 1) / t32;
+                nb = nb32;
+                if (nb32 <= n_sm) {
+                    asm_ = nb32;
+                    rep = 1;   // ceil(nb / (B nb)) with B >= 1
+                } else {
+                    asm_ = n_sm;
+                    rep = udiv_small(nb32 + ci.wave - 1, ci.wave, wave_rcp[c]);
+                }
+            } else {
+                nb = ceil_div(N, (long long)ci.T);
+                asm_ = min((long long)n_sm, nb);
+                rep = ceil_div(nb, (long long)B * asm_);
+            }
+            e = mwpcwp<T>(L, (T)ci.W, (T)B, (T)asm_, (T)rep, P);
+            if (!isfinite(e)) { e = (T)INFINITY; st |= KLR_Q_BAD_METRIC; }
+        } else {
+            st |= KLR_Q_BAD_METRIC;
+        }
+    }
+    return e;
+}
+
 template <typename T, int D>
 __global__ void __launch_bounds__(256)
 eval_kernel(const __grid_constant__ EvalParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned cmask[8];             // candidate mode: shapes in use (n_cfg <= 256)
     constexpr int NC = 2 * (D + 1);           // coefficients per (config, metric)
     const int m = P.m, u = P.u, n_cfg = P.n_cfg;
+    constexpr bool kMonoTable = sizeof(T) == 4;   // FP32: block-shape monomials in a table
     T* coef_s = reinterpret_cast<T*>(smem_raw);                 // 8 x u
     T* spec = coef_s + 8 * u;                                   // n_cfg x 8 x NC
-    CfgInfo* cinfo = reinterpret_cast<CfgInfo*>(spec + (size_t)n_cfg * 8 * NC);
+    T* bmon = spec + (size_t)n_cfg * 8 * NC;                    // n_cfg x m (FP32 only)
+    CfgInfo* cinfo = reinterpret_cast<CfgInfo*>(bmon + (kMonoTable ? (size_t)n_cfg * m : 0));
     float* wave_rcp = reinterpret_cast<float*>(cinfo + n_cfg);
     const T n_scale = (T)ldexp(1.0, -P.n_scale_log2);
     T lo[8], sc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) { lo[i] = (T)P.lo[i]; sc[i] = (T)P.sc[i]; }
     const unsigned n_sm = (unsigned)P.n_sm;
+    // the block-shape part of every monomial, once per block (the same
+    // products, in the same order, as the per-entry loop below)
+    if (kMonoTable) {
+        for (int idx = threadIdx.x; idx < n_cfg * m; idx += blockDim.x) {
+            const int c = idx / m, t = idx - c * m;
+            T xb[3];
+            xb[0] = (T)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
+            xb[1] = (T)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
+            xb[2] = (T)ldexp((double)P.cfg[3 * c + 2], -P.b_scale_log2);
+            T bm = T(1);
+            for (int v = 1; v < P.n_vars; ++v)
+                for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
+            bmon[idx] = bm;
+        }
+    }
 
     for (int k = blockIdx.x; k < P.n_kernels; k += gridDim.x) {
         const int64_t qa = P.q_off[k], qb = P.q_off[k + 1];
@@ -232,6 +325,15 @@ eval_kernel(const __grid_constant__ EvalParams P) {
         for (int i = threadIdx.x; i < 8 * u; i += blockDim.x) {
             if (P.coef_f64) coef_s[i] = (T)reinterpret_cast<const double*>(P.coef)[(int64_t)k * 8 * u + i];
             else coef_s[i] = (T)reinterpret_cast<const float*>(P.coef)[(int64_t)k * 8 * u + i];
+        }
+        // candidate mode: the shapes proposed for any of this kernel's queries
+        if (P.cand) {
+            for (int i = threadIdx.x; i < 8; i += blockDim.x) cmask[i] = 0u;
+            __syncthreads();
+            for (int64_t i = qa * P.kc + threadIdx.x; i < qb * P.kc; i += blockDim.x) {
+                const int c = P.cand[i];
+                if (c >= 0 && c < n_cfg) atomicOr(&cmask[c >> 5], 1u << (c & 31));
+            }
         }
         const int R = P.regs[k], Z = P.smem[k];
         for (int c = threadIdx.x; c < n_cfg; c += blockDim.x) {
@@ -256,6 +358,7 @@ eval_kernel(const __grid_constant__ EvalParams P) {
         // fold the block shape into univariate polynomials in the scaled N
         for (int idx = threadIdx.x; idx < n_cfg * 8; idx += blockDim.x) {
             const int c = idx >> 3, i = idx & 7;
+            if (P.cand && !((cmask[c >> 5] >> (c & 31)) & 1u)) continue;
             T xb[3];
             xb[0] = (T)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
             xb[1] = (T)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
@@ -267,8 +370,12 @@ eval_kernel(const __grid_constant__ EvalParams P) {
                 for (int j = 0; j <= D; ++j) acc[s][j] = T(0);
             for (int t = 0; t < m; ++t) {
                 T bm = T(1);
-                for (int v = 1; v < P.n_vars; ++v)
-                    for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
+                if (kMonoTable) {
+                    bm = bmon[c * m + t];
+                } else {
+                    for (int v = 1; v < P.n_vars; ++v)
+                        for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
+                }
                 const int j = P.exps[t][0];
                 const T a = coef_s[i * u + t] * bm, b = coef_s[i * u + m + t] * bm;
 #pragma unroll
@@ -284,6 +391,40 @@ eval_kernel(const __grid_constant__ EvalParams P) {
         }
         __syncthreads();
 
+        if (P.cand && P.kc <= 32 && (P.kc & (P.kc - 1)) == 0) {
+            // candidate mode: one (query, candidate) pair per lane, kc lanes
+            // per query, reduced by shuffles to the least (cycles, index)
+            const int kc = P.kc;
+            const int64_t npairs = (qb - qa) * kc;
+            const int64_t span = (npairs + 31) & ~(int64_t)31;   // whole warps
+            for (int64_t pi = threadIdx.x; pi < span; pi += blockDim.x) {
+                const bool valid = pi < npairs;
+                const int64_t q = qa + (valid ? pi / kc : 0);
+                const int j = (int)(pi & (kc - 1));
+                const int c = valid ? P.cand[q * kc + j] : -1;
+                int st = 0;
+                T e = (T)INFINITY;
+                if (c >= 0 && c < n_cfg) {
+                    const long long N = P.q_N[q];
+                    e = eval_cfg<T, D>(P, cinfo, wave_rcp, spec, lo, sc, n_sm, N, N < (1LL << 24),
+                                       (T)N * n_scale, c, st);
+                }
+                int ci = e < (T)INFINITY ? c : 0x7fffffff;
+                for (int o = 1; o < kc; o <<= 1) {
+                    const T oe = __shfl_xor_sync(0xffffffffu, e, o);
+                    const int oc = __shfl_xor_sync(0xffffffffu, ci, o);
+                    st |= __shfl_xor_sync(0xffffffffu, st, o);
+                    if (oe < e || (oe == e && oc < ci)) { e = oe; ci = oc; }
+                }
+                if (valid && j == 0) {
+                    const bool none = !(e < (T)INFINITY);
+                    P.best[q] = none ? -1 : ci;
+                    reinterpret_cast<T*>(P.best_cycles)[q] = e;
+                    if (P.q_status) P.q_status[q] = st | (none ? KLR_Q_NONE_FEASIBLE : 0);
+                }
+            }
+            continue;
+        }
         for (int64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) {
             const long long N = P.q_N[q];
             const bool small = N < (1LL << 24);   // 32-bit wave counts exact
@@ -293,69 +434,18 @@ eval_kernel(const __grid_constant__ EvalParams P) {
 #pragma unroll
             for (int j = 0; j < kTopK; ++j) { topv[j] = (T)INFINITY; topi[j] = -1; }
             int st = 0;
+            T cbv = (T)INFINITY;           // candidate mode: best value and index
+            int cbj = -1;
+            const int n_it = P.cand ? P.kc : n_cfg;
 #pragma unroll 1
-            for (int c = 0; c < n_cfg; ++c) {
-                const CfgInfo ci = cinfo[c];
-                const int B = ci.B;
-                const bool meaningful = B > 0 && ci.b0 <= N && ci.b1 <= N && ci.b2 <= N;
-                T e = (T)INFINITY;
-                if (meaningful) {
-                    T a[8 * NC];
-                    const T* sp = spec + (size_t)c * 8 * NC;
-                    if constexpr (sizeof(T) == 4) {
-#pragma unroll
-                        for (int t = 0; t < 2 * NC; ++t) {
-                            const float4 f4 = reinterpret_cast<const float4*>(sp)[t];
-                            a[4 * t] = f4.x; a[4 * t + 1] = f4.y; a[4 * t + 2] = f4.z; a[4 * t + 3] = f4.w;
-                        }
-                    } else {
-#pragma unroll
-                        for (int t = 0; t < 4 * NC; ++t) {
-                            const double2 d2 = reinterpret_cast<const double2*>(sp)[t];
-                            a[2 * t] = d2.x; a[2 * t + 1] = d2.y;
-                        }
-                    }
-                    T L[8];
-                    bool valid = true;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) {
-                        const T* ai = a + i * NC;
-                        T p = ai[D], qq = ai[2 * D + 1];
-#pragma unroll
-                        for (int j = D - 1; j >= 0; --j) {
-                            p = p * xN + ai[j];
-                            qq = qq * xN + ai[D + 1 + j];
-                        }
-                        const T g = qdiv<T>(p, qq);
-                        valid = valid && (qq != T(0)) && isfinite(g);
-                        L[i] = lo[i] + sc[i] * fabs(g);
-                    }
-                    if (valid) {
-                        long long nb, asm_, rep;
-                        if (small) {
-                            const unsigned n32 = (unsigned)N, t32 = (unsigned)ci.T;
-                            const unsigned nb32 = ci.t_shift >= 0 ? (n32 + t32 - 1) >> ci.t_shift
-                                                                  : (n32 + t32 - 1) / t32;
-                            nb = nb32;
-                            if (nb32 <= n_sm) {
-                                asm_ = nb32;
-                                rep = 1;   // ceil(nb / (B nb)) with B >= 1
-                            } else {
-                                asm_ = n_sm;
-                                rep = udiv_small(nb32 + ci.wave - 1, ci.wave, wave_rcp[c]);
-                            }
-                        } else {
-                            nb = ceil_div(N, (long long)ci.T);
-                            asm_ = min((long long)n_sm, nb);
-                            rep = ceil_div(nb, (long long)B * asm_);
-                        }
-                        e = mwpcwp<T>(L, (T)ci.W, (T)B, (T)asm_, (T)rep, P);
-                        if (!isfinite(e)) { e = (T)INFINITY; st |= KLR_Q_BAD_METRIC; }
-                    } else {
-                        st |= KLR_Q_BAD_METRIC;
-                    }
-                }
-                if (P.table) {
+            for (int it = 0; it < n_it; ++it) {
+                const int c = P.cand ? P.cand[q * P.kc + it] : it;
+                if (c < 0 || c >= n_cfg) continue;
+                T e = eval_cfg<T, D>(P, cinfo, wave_rcp, spec, lo, sc, n_sm, N, small, xN, c, st);
+                if (P.cand) {
+                    // lowest value, ties to the lowest shape index
+                    if (e < cbv || (e == cbv && e < (T)INFINITY && c < cbj)) { cbv = e; cbj = c; }
+                } else if (P.table) {
                     reinterpret_cast<T*>(P.cycles)[q * n_cfg + c] = e;
                 } else if (e < topv[kTopK - 1]) {
                     // insert into the sorted top-k; ties keep the lower index first
@@ -372,6 +462,13 @@ eval_kernel(const __grid_constant__ EvalParams P) {
                 }
             }
             if (P.table) continue;
+            if (P.cand) {
+                if (cbj < 0) st |= KLR_Q_NONE_FEASIBLE;
+                P.best[q] = cbj;
+                reinterpret_cast<T*>(P.best_cycles)[q] = cbv;
+                if (P.q_status) P.q_status[q] = st;
+                continue;
+            }
             const int bi = topi[0];
             if (bi < 0) st |= KLR_Q_NONE_FEASIBLE;
             float mg = 0.f;
@@ -437,35 +534,6 @@ tie_kernel(const __grid_constant__ EvalParams P) {
         reinterpret_cast<float*>(P.best_cycles)[rec.q] = (float)bv;
         if (P.margin) P.margin[rec.q] = isfinite(sv) ? (float)((sv - bv) / bv) : INFINITY;
         write_launch(P, rec.q, N, bj);
-    }
-}
-
-// Exact re-ranking of proposed candidates: one thread per query.
-__global__ void __launch_bounds__(128)
-candidates_kernel(const __grid_constant__ EvalParams P, const int32_t* __restrict__ cand, int kc) {
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < P.n_q;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        // kernel of the query: binary search in the CSR offsets
-        int lo = 0, hi = P.n_kernels;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (P.q_off[mid] <= q) lo = mid; else hi = mid;
-        }
-        const long long N = P.q_N[q];
-        float bv = INFINITY;
-        int bj = -1, st = 0;
-        for (int j = 0; j < kc; ++j) {
-            const int c = cand[q * kc + j];
-            if (c < 0 || c >= P.n_cfg) continue;
-            bool us;
-            const float v = eval_full<float>(P, lo, N, c, us);
-            if (!us) { st |= KLR_Q_BAD_METRIC; continue; }
-            if (v < bv || (v == bv && c < bj)) { bv = v; bj = c; }
-        }
-        if (bj < 0) st |= KLR_Q_NONE_FEASIBLE;
-        P.best[q] = bj;
-        reinterpret_cast<float*>(P.best_cycles)[q] = bv;
-        if (P.q_status) P.q_status[q] = st;
     }
 }
 
@@ -567,7 +635,8 @@ klr_status prepare(Context* c, const klr_program* prog, const klr_hw* hw, const 
 
 size_t eval_smem_bytes(const EvalParams& P, size_t tsz) {
     const int NC = 2 * (P.degree + 1);
-    size_t b = tsz * (8 * (size_t)P.u + (size_t)P.n_cfg * 8 * NC);
+    size_t b = tsz * (8 * (size_t)P.u + (size_t)P.n_cfg * 8 * NC +
+                      (tsz == 4 ? (size_t)P.n_cfg * P.m : 0));
     b = (b + 15) & ~(size_t)15;
     return b + (sizeof(CfgInfo) + sizeof(float)) * (size_t)P.n_cfg;
 }
@@ -588,7 +657,8 @@ klr_status launch_eval_t(Context* c, EvalParams& P, size_t smem, int threads, cu
 // |F| and log2 buckets of the queries per kernel and of the kernel count.
 uint64_t eval_tune_key(const EvalParams& P, bool f64) {
     const int64_t per_kernel = P.n_kernels ? (P.n_q + P.n_kernels - 1) / P.n_kernels : 1;
-    return tune_key(TUNE_EVAL, {P.n_vars, P.degree, f64, P.table, P.n_cfg,
+    const int mode = P.table ? 1 : (P.cand ? 2 : 0);
+    return tune_key(TUNE_EVAL, {P.n_vars, P.degree, f64, mode, P.n_cfg,
                                 log2_bucket(per_kernel), log2_bucket(P.n_kernels)});
 }
 
@@ -599,8 +669,10 @@ klr_status launch_eval(Context* c, EvalParams& P, bool f64, cudaStream_t stream)
         return KLR_ENOTSUP;
     }
     // threads per block: the autotuned choice (32 << choice), else enough for
-    // the queries of a typical kernel, in whole warps
-    const int64_t per_kernel = P.n_kernels ? (P.n_q + P.n_kernels - 1) / P.n_kernels : 1;
+    // the queries (candidate mode: query-candidate pairs) of a typical kernel,
+    // in whole warps
+    int64_t per_kernel = P.n_kernels ? (P.n_q + P.n_kernels - 1) / P.n_kernels : 1;
+    if (P.cand) per_kernel *= P.kc;
     int threads = 32;
     while (threads < 256 && threads < per_kernel) threads <<= 1;
     const int32_t choice = tune_choice(c, eval_tune_key(P, f64), -1);
@@ -704,13 +776,15 @@ klr_status klr_argmin_candidates(klr_ctx* ctx, const klr_program* prog, const kl
     if (P.n_q == 0 || P.n_kernels == 0) return KLR_OK;
     KLR_REQUIRE(cand && best_idx && best_cycles, "klr_argmin_candidates: NULL array");
     KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    // the specialised evaluator in candidate mode: per kernel, only the
+    // proposed shapes are specialised and evaluated
+    P.table = 0;
     P.best = best_idx;
     P.best_cycles = best_cycles;
     P.q_status = q_status;
-    const int grid = (int)std::min<int64_t>((P.n_q + 127) / 128, (int64_t)c->n_sm * 16);
-    candidates_kernel<<<grid, 128, 0, stream>>>(P, cand, k);
-    KLR_CHECK_CUDA(cudaGetLastError());
-    return KLR_OK;
+    P.cand = cand;
+    P.kc = k;
+    return launch_eval(c, P, false, stream);
 }
 
 klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw, const int32_t* cfg,

@@ -50,13 +50,20 @@ Offsets offsets(int n_coef, int n_out) {
 int out_cols(int n_out) { return n_out > 0 ? n_out : 1; }
 int out_ld(int n_out) { return (out_cols(n_out) + 7) & ~7; }
 
+// tanh by the hardware approximation (relative error about 2^-11, below the
+// BF16 rounding of the activations it feeds)
+__device__ __forceinline__ float tanh_hw(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ float gelu(float z) {
     const float c = 0.7978845608028654f;   // sqrt(2 / pi)
-    return 0.5f * z * (1.0f + tanhf(c * (z + 0.044715f * z * z * z)));
+    return 0.5f * z * (1.0f + tanh_hw(c * (z + 0.044715f * z * z * z)));
 }
 __device__ __forceinline__ float gelu_grad(float z) {
     const float c = 0.7978845608028654f;
-    const float t = tanhf(c * (z + 0.044715f * z * z * z));
+    const float t = tanh_hw(c * (z + 0.044715f * z * z * z));
     return 0.5f * (1.0f + t) + 0.5f * z * (1.0f - t * t) * c * (1.0f + 3.0f * 0.044715f * z * z);
 }
 
@@ -593,6 +600,469 @@ klr_status forward_hidden(const MlpWs& w, const float* params, const Offsets& o,
     return KLR_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Inference on the 5th-generation tensor cores: the whole network for a tile
+// of 128 rows in one CTA.  Per layer, the weights (pre-packed once per call
+// in the shared-memory image below) arrive by one bulk asynchronous copy
+// completing on an mbarrier; one thread issues the tcgen05.mma chain (BF16
+// operands from shared memory, FP32 accumulator of 128 lanes x N columns in
+// tensor memory); the epilogue reads the accumulator back with tcgen05.ld,
+// adds the bias, applies GELU and writes BF16 activations into the operand
+// buffer of the next layer, so activations never leave the SM.  The next
+// layer's weights are copied while the epilogue runs.
+//
+// Operand image (K-major, 128-byte swizzle): a matrix of R rows and K
+// columns is stored as K/64 blocks of R x 128 bytes; row r of a block holds
+// its 64 elements as eight 16-byte chunks, chunk c at position c ^ (r mod 8);
+// rows come in groups of 8 (1024 bytes).  Matrix descriptors: start address,
+// stride 1024 bytes between 8-row groups, 128-byte swizzle; each K step of 16
+// elements advances the start address by 32 bytes within a block.
+// ---------------------------------------------------------------------------
+constexpr int kTileRows = 128;
+constexpr int kFusedThreads = 256;
+constexpr int kKPad1 = 128;                 // layer-1 K (80) padded to whole blocks
+
+__host__ __device__ inline uint32_t swz_off(int r, int k, int rows) {
+    const int kb = k >> 6, kk = k & 63;
+    return (uint32_t)(kb * rows * 128 + (r >> 3) * 1024 + (r & 7) * 128 +
+                      (((kk >> 3) ^ (r & 7)) << 4) + (kk & 7) * 2);
+}
+
+// packed weight images: W1 (256 x 128, K 80 + zero pad), W2, W3 (256 x 256),
+// W4 (np x 256, rows past the outputs zero)
+struct Packed {
+    int64_t w1, w2, w3, w4, total;          // byte offsets
+};
+Packed packed_layout(int np) {
+    Packed p;
+    p.w1 = 0;
+    p.w2 = p.w1 + (int64_t)H * kKPad1 * 2;
+    p.w3 = p.w2 + (int64_t)H * H * 2;
+    p.w4 = p.w3 + (int64_t)H * H * 2;
+    p.total = p.w4 + (int64_t)np * H * 2;
+    return p;
+}
+
+// one thread per 16-byte chunk of the packed images
+__global__ void pack_weights_kernel(const __nv_bfloat16* __restrict__ pb, Offsets o, int n_outs,
+                                    int np, Packed pk, unsigned char* __restrict__ img) {
+    const int64_t c1 = (int64_t)H * kKPad1 / 8, c2 = (int64_t)H * H / 8, c4 = (int64_t)np * H / 8;
+    const int64_t total = c1 + 2 * c2 + c4;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = i;
+        const __nv_bfloat16* src;
+        int K, rows, rows_valid;
+        int64_t dst;
+        if (j < c1) {
+            src = pb + o.W1; K = IN; rows = H; rows_valid = H; dst = pk.w1;
+        } else if ((j -= c1) < c2) {
+            src = pb + o.W2; K = H; rows = H; rows_valid = H; dst = pk.w2;
+        } else if ((j -= c2) < c2) {
+            src = pb + o.W3; K = H; rows = H; rows_valid = H; dst = pk.w3;
+        } else {
+            j -= c2;
+            src = pb + o.W4; K = H; rows = np; rows_valid = n_outs; dst = pk.w4;
+        }
+        const int kpad = (K == IN) ? kKPad1 : K;
+        const int r = (int)(j / (kpad / 8)), k = (int)(j % (kpad / 8)) * 8;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (r < rows_valid && k < K) v = *reinterpret_cast<const uint4*>(src + (int64_t)r * K + k);
+        *reinterpret_cast<uint4*>(img + dst + swz_off(r, k, rows)) = v;
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)1 << 16;                  // leading byte offset: unused with this layout
+    d |= (uint64_t)(1024u >> 4) << 32;       // stride byte offset between 8-row groups
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    d |= (uint64_t)2 << 61;                  // 128-byte swizzle
+    return d;
+}
+
+// kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+// K-major, M x N
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+    // bounded: about a second of polling at most
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     "selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok) : "r"(smem_addr(mbar)), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// thread 0: bulk-copy `bytes` (multiple of 16) of a packed image into shared
+// memory, completing on mbar
+__device__ __forceinline__ void tma_load(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_addr(mbar)), "r"(bytes) : "memory");
+    constexpr uint32_t kChunk = 32768;
+    for (uint32_t o = 0; o < bytes; o += kChunk) {
+        const uint32_t n = bytes - o < kChunk ? bytes - o : kChunk;
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes "
+                     "[%0], [%1], %2, [%3];"
+                     :: "r"(smem_addr(static_cast<unsigned char*>(dst) + o)),
+                        "l"(static_cast<const unsigned char*>(src) + o), "r"(n),
+                        "r"(smem_addr(mbar))
+                     : "memory");
+    }
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct FusedArgs {
+    const __nv_bfloat16* X0;     // n x IN, row-major
+    const unsigned char* img;    // packed weight images
+    Packed pk;
+    const float* params;         // FP32 parameters (biases)
+    Offsets o;
+    int64_t n;
+    int n_out;                   // outputs written per row (1 for the per-row form)
+    int np;                      // output columns computed (multiple of 16, >= n_out)
+    float* pred;                 // n x n_out
+    int* err;                    // set when a wait gave up
+    // proposal mode (per-query form): rows are queries q0.. of the CSR list;
+    // the input tile is built here and the layer-4 epilogue keeps the k
+    // least predictions among the meaningful shapes instead of writing pred
+    int propose;
+    int64_t q0;
+    const int64_t* q_off;
+    const int64_t* q_N;
+    int32_t n_kernels;
+    const __nv_bfloat16* emb_table;   // n_kernels x EMB
+    float hw[7];
+    const int32_t* cfg;
+    const uint8_t* occ;               // n_kernels x n_out: B_active > 0
+    int k;                            // 1..16
+    int32_t* cand;                    // n_queries x k
+};
+
+// kernel of a query by binary search in the CSR offsets
+__device__ int32_t kernel_of(const int64_t* off, int32_t nk, int64_t q) {
+    int32_t lo = 0, hi = nk;   // off[lo] <= q < off[hi]
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (off[mid] <= q) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Dynamic shared memory: 1 KB alignment slack + activations (128 x 256) +
+// weights (256 x 256).
+constexpr size_t kFusedSmem = 1024 + (size_t)kTileRows * H * 2 + (size_t)H * H * 2;
+
+__global__ void __launch_bounds__(kFusedThreads, 1)
+fused_forward_kernel(const __grid_constant__ FusedArgs a) {
+    extern __shared__ unsigned char fsm_raw[];
+    unsigned char* As = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(fsm_raw) + 1023) & ~(uintptr_t)1023);
+    unsigned char* Bs = As + kTileRows * H * 2;
+    __shared__ uint64_t mbar_w, mbar_mma;
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    __shared__ int32_t tile_kernel[kTileRows];       // proposal mode: each row's kernel
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t n_tiles = (a.n + kTileRows - 1) / kTileRows;
+    if ((int64_t)blockIdx.x >= n_tiles) return;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar_w)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar_mma)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_base)), "r"((uint32_t)H));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    uint32_t pw = 0, pm = 0;
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const int row_in_tile = 32 * (warp & 3) + lane;
+    const int half = warp >> 2;
+    if (tid == 0) tma_load(Bs, a.img + a.pk.w1, (uint32_t)(H * kKPad1 * 2), &mbar_w);
+    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int64_t r0 = t * kTileRows;
+        if (a.propose) {
+            // rows are queries: features (log2 N / 23, shape features 0, the
+            // hardware vector) and the kernel's embedding
+            if (tid < kTileRows) {
+                const int64_t gr = r0 + tid;
+                tile_kernel[tid] = gr < a.n ? kernel_of(a.q_off, a.n_kernels, a.q0 + gr) : 0;
+            }
+            __syncthreads();
+            for (int c = tid; c < kTileRows * (IN / 8); c += kFusedThreads) {
+                const int r = c / (IN / 8), ch = c % (IN / 8);
+                const int64_t gr = r0 + r;
+                unsigned char* dst = As + swz_off(r, ch * 8, kTileRows);
+                if (ch < 2) {
+                    float f[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) f[i] = 0.f;
+                    if (gr < a.n) {
+                        if (ch == 0) {
+                            f[0] = log2f((float)a.q_N[a.q0 + gr]) * (1.0f / 23.0f);
+                            for (int i = 0; i < 4; ++i) f[4 + i] = a.hw[i];
+                        } else {
+                            for (int i = 0; i < 3; ++i) f[i] = a.hw[4 + i];
+                        }
+                    }
+                    uint32_t w[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+                        w[i] = *reinterpret_cast<const uint32_t*>(&h2);
+                    }
+                    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else {
+                    const void* src = a.emb_table + (int64_t)tile_kernel[r] * EMB + (ch - 2) * 8;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                 :: "r"(smem_addr(dst)), "l"(src), "r"(gr < a.n ? 16u : 0u)
+                                 : "memory");
+                }
+            }
+        } else
+        // input tile: 128 rows x 80 columns into blocks 0-1 of the operand image
+        for (int c = tid; c < kTileRows * (IN / 8); c += kFusedThreads) {
+            const int r = c / (IN / 8), k = (c % (IN / 8)) * 8;
+            const int64_t gr = r0 + r;
+            const void* src = a.X0 + (gr < a.n ? gr : 0) * IN + k;
+            const uint32_t dst = smem_addr(As + swz_off(r, k, kTileRows));
+            const uint32_t bytes = gr < a.n ? 16u : 0u;     // rows past n: zeros
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                         :: "r"(dst), "l"(src), "r"(bytes) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        for (int layer = 0; layer < 4; ++layer) {
+            const int K = layer == 0 ? IN : H;
+            const int N = layer == 3 ? a.np : H;
+            if (!mbar_wait(&mbar_w, pw)) abort_flag = 1;
+            pw ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (abort_flag) break;
+            if (tid == 0) {
+                const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+                const uint32_t idesc = umma_idesc_bf16(kTileRows, N);
+                for (int s = 0; s < K / 16; ++s) {
+                    const int kb = s >> 2, ks = s & 3;
+                    umma_bf16(tmem, umma_desc(a0 + kb * kTileRows * 128 + ks * 32),
+                              umma_desc(b0 + kb * N * 128 + ks * 32), idesc, s > 0);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_addr(&mbar_mma)) : "memory");
+            }
+            if (!mbar_wait(&mbar_mma, pm)) abort_flag = 1;
+            pm ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            // the weights buffer is free: copy the next layer's (or the next
+            // tile's first layer's) weights while the epilogue runs
+            if (tid == 0 && !abort_flag) {
+                if (layer == 0) tma_load(Bs, a.img + a.pk.w2, (uint32_t)(H * H * 2), &mbar_w);
+                else if (layer == 1) tma_load(Bs, a.img + a.pk.w3, (uint32_t)(H * H * 2), &mbar_w);
+                else if (layer == 2) tma_load(Bs, a.img + a.pk.w4, (uint32_t)(a.np * H * 2), &mbar_w);
+                else if (t + gridDim.x < n_tiles)
+                    tma_load(Bs, a.img + a.pk.w1, (uint32_t)(H * kKPad1 * 2), &mbar_w);
+            }
+            if (layer < 3) {
+                const float* bias = a.params + (layer == 0 ? a.o.b1 : layer == 1 ? a.o.b2 : a.o.b3);
+                for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+                    uint32_t packed[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float x0 = gelu(v[2 * j] + __ldg(bias + c0 + 2 * j));
+                        const float x1 = gelu(v[2 * j + 1] + __ldg(bias + c0 + 2 * j + 1));
+                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+                        packed[j] = *reinterpret_cast<const uint32_t*>(&h2);
+                    }
+                    *reinterpret_cast<uint4*>(As + swz_off(row_in_tile, c0, kTileRows)) =
+                        make_uint4(packed[0], packed[1], packed[2], packed[3]);
+                    *reinterpret_cast<uint4*>(As + swz_off(row_in_tile, c0 + 8, kTileRows)) =
+                        make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                }
+            } else if (a.propose) {
+                // the k least predictions among the meaningful shapes of the
+                // row's query (warps 0-3 hold every row of the tile)
+                if (half == 0) {
+                    const int64_t gr = r0 + row_in_tile;
+                    const int64_t q = a.q0 + (gr < a.n ? gr : 0);
+                    const long long N = a.q_N[q];
+                    const int32_t kk = tile_kernel[row_in_tile];
+                    const uint8_t* occ = a.occ + (int64_t)kk * a.n_out;
+                    const float* bias = a.params + a.o.b4;
+                    float bv[16];
+                    int bi[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) { bv[j] = INFINITY; bi[j] = -1; }
+                    for (int c0 = 0; c0 < a.np; c0 += 8) {
+                        float v[8];
+                        tmem_ld8(tmem + lane_base + (uint32_t)c0, v);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const int c = c0 + j;
+                            if (c >= a.n_out || !occ[c]) continue;
+                            if (!(a.cfg[3 * c] <= N && a.cfg[3 * c + 1] <= N && a.cfg[3 * c + 2] <= N))
+                                continue;
+                            float x = v[j] + __ldg(bias + c);
+                            int xi = c;
+#pragma unroll
+                            for (int m = 0; m < 16; ++m) {
+                                if (m < a.k && x < bv[m]) {
+                                    const float tv = bv[m]; const int ti = bi[m];
+                                    bv[m] = x; bi[m] = xi;
+                                    x = tv; xi = ti;
+                                }
+                            }
+                        }
+                    }
+                    if (gr < a.n) {
+#pragma unroll
+                        for (int m = 0; m < 16; ++m)
+                            if (m < a.k) a.cand[q * a.k + m] = bi[m];
+                    }
+                }
+            } else {
+                const int64_t gr = r0 + row_in_tile;
+                const float* bias = a.params + a.o.b4;
+                const int cols = a.np >> 1;
+                for (int c0 = half * cols; c0 < half * cols + cols; c0 += 8) {
+                    float v[8];
+                    tmem_ld8(tmem + lane_base + (uint32_t)c0, v);
+                    if (gr < a.n) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (c0 + j < a.n_out)
+                                a.pred[gr * a.n_out + c0 + j] = v[j] + __ldg(bias + c0 + j);
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+        }
+        if (abort_flag) break;
+    }
+    if (abort_flag) {
+        // a wait gave up: every prediction of this CTA's tiles NaN (proposal
+        // mode: no candidates)
+        if (tid == 0) atomicExch(a.err, 1);
+        for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+            const int64_t e = min((t + 1) * kTileRows, a.n);
+            if (a.propose) {
+                for (int64_t i = t * kTileRows * a.k + tid; i < e * a.k; i += kFusedThreads)
+                    a.cand[a.q0 * a.k + i] = -1;
+            } else {
+                for (int64_t i = t * kTileRows * a.n_out + tid; i < e * a.n_out; i += kFusedThreads)
+                    a.pred[i] = __int_as_float(0x7fc00000);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"((uint32_t)H));
+}
+
+// Packed weight images for the fused kernel, from the BF16 parameter copy;
+// fills the image fields of `a` (outputs, padded output columns).
+klr_status pack_weights(const MlpWs& w, const float* params, const Offsets& o, int n_out,
+                        unsigned char* img, int* err, FusedArgs& a, cudaStream_t s) {
+    const int outs = out_cols(n_out);
+    const int np = (outs + 15) & ~15;
+    const Packed pk = packed_layout(np);
+    pack_weights_kernel<<<blocks_for(pk.total / 16, 256), 256, 0, s>>>(w.pb, o, outs, np, pk, img);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    a.img = img;
+    a.pk = pk;
+    a.params = params;
+    a.o = o;
+    a.n_out = outs;
+    a.np = np;
+    a.err = err;
+    return KLR_OK;
+}
+
+klr_status launch_fused(const Context* c, const FusedArgs& a, cudaStream_t s) {
+    if (a.n == 0) return KLR_OK;
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(fused_forward_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kFusedSmem));
+    const int64_t tiles = (a.n + kTileRows - 1) / kTileRows;
+    const int grid = (int)std::min<int64_t>(tiles, c->n_sm);
+    fused_forward_kernel<<<grid, kFusedThreads, kFusedSmem, s>>>(a);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+// Forward pass of rows whose X0 is set, on the tensor cores (one CTA per SM
+// over tiles of 128 rows); pred as in forward_hidden.
+klr_status fused_forward(const Context* c, const MlpWs& w, const float* params, const Offsets& o,
+                         int n_out, int64_t n, unsigned char* img, int* err, cudaStream_t s) {
+    if (n == 0) return KLR_OK;
+    FusedArgs a{};
+    klr_status st = pack_weights(w, params, o, n_out, img, err, a, s);
+    if (st != KLR_OK) return st;
+    a.X0 = w.X0;
+    a.n = n;
+    a.pred = w.pred;
+    return launch_fused(c, a, s);
+}
+
+// scratch of the fused forward: packed weights (at most 448 KB) and a flag
+constexpr size_t kFusedScratch = 512 * 1024;
+
 klr_status check_net(const klr_mlp* net) {
     KLR_REQUIRE(net && net->params, "NULL network or parameters");
     KLR_REQUIRE(net->n_coef > 0 && net->n_coef % 8 == 0 && net->n_coef <= 4096,
@@ -833,9 +1303,11 @@ klr_status klr_mlp_predict(klr_ctx* ctx, const klr_mlp* net, const float* coef, 
     // rows carry their own coefficient gather and embedding GEMM
     const size_t extra = align256(2 * (size_t)n * nc);
     const size_t base = mlp_ws_bytes(n, nc, no, 0, false);
-    if ((st = ensure_workspace(c, base + extra, s)) != KLR_OK) return st;
+    if ((st = ensure_workspace(c, base + extra + kFusedScratch, s)) != KLR_OK) return st;
     MlpWs w = carve(c->ws, n, nc, no, 0, false);
     w.CR = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<char*>(c->ws) + base);
+    unsigned char* img = reinterpret_cast<unsigned char*>(c->ws) + base + extra;
+    int* err = reinterpret_cast<int*>(img + kFusedScratch - 256);
     cast_bf16_kernel<<<blocks_for(o.total, 256), 256, 0, s>>>(net->params, w.pb, o.total);
     RowArgs ra{};
     ra.n = n;
@@ -860,7 +1332,7 @@ klr_status klr_mlp_predict(klr_ctx* ctx, const klr_mlp* net, const float* coef, 
     g.Cb = w.X0 + FEAT;
     g.ldcb = IN;
     if ((st = gemm<false, false, EPI_BF16>(g, s)) != KLR_OK) return st;
-    if ((st = forward_hidden(w, net->params, o, no, n, false, s)) != KLR_OK) return st;
+    if ((st = fused_forward(c, w, net->params, o, no, n, img, err, s)) != KLR_OK) return st;
     KLR_CHECK_CUDA(cudaMemcpyAsync(pred_out, w.pred, 4 * (size_t)n * out_cols(no),
                                    cudaMemcpyDeviceToDevice, s));
     return KLR_OK;
@@ -946,16 +1418,19 @@ struct ProposeArgs {
     int32_t* cand;
     float hw[7];
     __nv_bfloat16* X0;
+    uint8_t* occ;                   // [n_kernels x n_cfg]: 1 where B_active > 0
 };
 
-// kernel of a query by binary search in the CSR offsets
-__device__ int32_t kernel_of(const int64_t* off, int32_t nk, int64_t q) {
-    int32_t lo = 0, hi = nk;   // off[lo] <= q < off[hi]
-    while (hi - lo > 1) {
-        const int32_t mid = (lo + hi) >> 1;
-        if (off[mid] <= q) lo = mid; else hi = mid;
+// occupancy of every (kernel, shape), once per proposal call
+__global__ void occupancy_table_kernel(const __grid_constant__ ProposeArgs a) {
+    const int64_t total = (int64_t)a.n_kernels * a.n_cfg;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t kk = (int32_t)(i / a.n_cfg);
+        const int c = (int)(i - (int64_t)kk * a.n_cfg);
+        const long long T = (long long)a.cfg[3 * c] * a.cfg[3 * c + 1] * a.cfg[3 * c + 2];
+        a.occ[i] = occupancy_blocks(T, a.regs[kk], a.smem[kk], a.Bm, a.Wm, a.Rm, a.Zm, a.Tmax) > 0;
     }
-    return lo;
 }
 
 __global__ void propose_rows_kernel(const __grid_constant__ ProposeArgs a) {
@@ -1005,11 +1480,10 @@ __global__ void topk_kernel(const __grid_constant__ ProposeArgs a) {
         float bv[16];
         int bi[16];
         for (int j = 0; j < a.k; ++j) { bv[j] = INFINITY; bi[j] = -1; }
+        const uint8_t* occ = a.occ + (int64_t)kk * a.n_cfg;
         for (int c = 0; c < a.n_cfg; ++c) {
             const long long b0 = a.cfg[3 * c], b1 = a.cfg[3 * c + 1], b2 = a.cfg[3 * c + 2];
-            const long long T = b0 * b1 * b2;
-            const int B = occupancy_blocks(T, a.regs[kk], a.smem[kk], a.Bm, a.Wm, a.Rm, a.Zm, a.Tmax);
-            const bool ok = B > 0 && b0 <= N && (a.dims < 2 || b1 <= N) && (a.dims < 3 || b2 <= N);
+            const bool ok = occ[c] && b0 <= N && (a.dims < 2 || b1 <= N) && (a.dims < 3 || b2 <= N);
             if (!ok) continue;
             float v = a.pred[qi * a.n_cfg + c];
             if (!(v < bv[a.k - 1])) continue;
@@ -1050,13 +1524,15 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
     KLR_REQUIRE(no == 0 || no == n_cfg, "klr_propose: the network has %d outputs for %d shapes",
                 no, n_cfg);
     const Offsets o = offsets(nc, no);
-    // per row: one network row per (query, shape); per query: one per query
+    // per row: one network row per (query, shape), in chunks; per query: the
+    // fused kernel builds its rows itself and needs no row buffers
     const int64_t qchunk = no > 0 ? kMaxRows : std::max<int64_t>(1, kMaxRows / n_cfg);
-    const int64_t rows = no > 0 ? qchunk : qchunk * n_cfg;
+    const int64_t rows = no > 0 ? 0 : qchunk * n_cfg;
     // workspace: network buffers for `rows` rows + per-kernel embeddings + row tables
     const size_t base = mlp_ws_bytes(rows, nc, no, n_kernels, false);
     const size_t extra = align256(2 * (size_t)n_kernels * nc) + align256(4 * (size_t)rows) * 2 +
-                         align256(8 * (size_t)rows) * 2;
+                         align256(8 * (size_t)rows) * 2 + align256((size_t)n_kernels * n_cfg) +
+                         kFusedScratch;
     if ((st = ensure_workspace(c, base + extra, s)) != KLR_OK) return st;
     MlpWs w = carve(c->ws, rows, nc, no, n_kernels, false);
     char* p = reinterpret_cast<char*>(c->ws) + base;
@@ -1069,6 +1545,11 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
     int64_t* row_N = reinterpret_cast<int64_t*>(p);
     p += align256(8 * (size_t)rows);
     int64_t* row_query = reinterpret_cast<int64_t*>(p);
+    p += align256(8 * (size_t)rows);
+    uint8_t* occ = reinterpret_cast<uint8_t*>(p);
+    p += align256((size_t)n_kernels * n_cfg);
+    unsigned char* img = reinterpret_cast<unsigned char*>(p);
+    int* err = reinterpret_cast<int*>(img + kFusedScratch - 256);
     cast_bf16_kernel<<<blocks_for(o.total, 256), 256, 0, s>>>(net->params, w.pb, o.total);
     cast_bf16_kernel<<<blocks_for((int64_t)n_kernels * nc, 256), 256, 0, s>>>(
         coef, coef_b, (int64_t)n_kernels * nc);
@@ -1084,6 +1565,40 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
     g.Cb = w.emb_table;
     g.ldcb = EMB;
     if ((st = gemm<false, false, EPI_BF16>(g, s)) != KLR_OK) return st;
+    {
+        ProposeArgs ta{};
+        ta.n_kernels = n_kernels;
+        ta.n_cfg = n_cfg;
+        ta.cfg = cfg;
+        ta.regs = regs;
+        ta.smem = smem;
+        ta.Bm = hw->max_blocks_per_sm;
+        ta.Wm = hw->max_warps_per_sm;
+        ta.Rm = hw->regs_per_sm;
+        ta.Zm = hw->smem_per_sm;
+        ta.Tmax = hw->max_threads_per_block;
+        ta.occ = occ;
+        occupancy_table_kernel<<<blocks_for((int64_t)n_kernels * n_cfg, 256), 256, 0, s>>>(ta);
+        KLR_CHECK_CUDA(cudaGetLastError());
+    }
+    if (no > 0) {
+        // per-query form: features, network and top-k in one tensor-core kernel
+        FusedArgs fa{};
+        if ((st = pack_weights(w, net->params, o, no, img, err, fa, s)) != KLR_OK) return st;
+        fa.propose = 1;
+        fa.q_off = q->q_offsets;
+        fa.q_N = q->q_N;
+        fa.n_kernels = n_kernels;
+        fa.emb_table = w.emb_table;
+        for (int i = 0; i < 7; ++i) fa.hw[i] = net->hw_feat[i];
+        fa.cfg = cfg;
+        fa.occ = occ;
+        fa.k = k;
+        fa.cand = cand_out;
+        fa.q0 = 0;
+        fa.n = q->n_queries;
+        return launch_fused(c, fa, s);
+    }
     for (int64_t q0 = 0; q0 < q->n_queries; q0 += qchunk) {
         const int64_t nq = std::min(qchunk, q->n_queries - q0);
         ProposeArgs a{};
@@ -1111,6 +1626,7 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
         a.cand = cand_out;
         for (int i = 0; i < 7; ++i) a.hw[i] = net->hw_feat[i];
         a.X0 = w.X0;
+        a.occ = occ;
         const int64_t nr = no > 0 ? nq : nq * n_cfg;
         if (no > 0)
             propose_query_rows_kernel<<<blocks_for(nr, 256), 256, 0, s>>>(a);
@@ -1118,7 +1634,7 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
             propose_rows_kernel<<<blocks_for(nr, 256), 256, 0, s>>>(a);
         embed_rows_kernel<<<blocks_for(nr * EMB, 256), 256, 0, s>>>(row_kernel, nr, w.emb_table, w.X0);
         KLR_CHECK_CUDA(cudaGetLastError());
-        if ((st = forward_hidden(w, net->params, o, no, nr, false, s)) != KLR_OK) return st;
+        if ((st = fused_forward(c, w, net->params, o, no, nr, img, err, s)) != KLR_OK) return st;
         topk_kernel<<<blocks_for(nq, 128), 128, 0, s>>>(a);
         KLR_CHECK_CUDA(cudaGetLastError());
     }

@@ -128,3 +128,44 @@ def test_bad_arguments_return_einval(klr, ctx):
     assert e.value.status == klr.EINVAL
     with pytest.raises(klr.KlrError):
         ctx.eval(prog, hw, torch.zeros((300, 3), dtype=torch.int32).cuda(), qo, qn)
+
+
+def test_candidate_rerank_matches_oracle(klr, ctx):
+    """klr_argmin_candidates: per query the least-cycles meaningful shape among
+    its candidates (ties to the lowest index), against the oracle's cycles
+    table restricted to the same candidates."""
+    gt = G.make_program(6, 48)
+    coef = gt.coef.astype(np.float32)
+    q = W.queries_per_kernel(48, W.log_spaced_sizes(64))
+    n_q, kc = len(q.sizes), 8
+    keys = W.stream_keys(41, (3,), np.arange(n_q, dtype=np.uint64))
+    cand = (W.words(keys[:, None], np.arange(kc, dtype=np.uint64)[None, :]) % np.uint64(56))
+    cand = cand.astype(np.int32) - 2          # -2..53: some skipped entries, some duplicates
+    ct = torch.tensor(coef).cuda()
+    prog = G.gpu_program(klr, ct, gt, torch)
+    hw = klr.make_hw(W.HARDWARE)
+    cfg = torch.tensor(klr.enumerate_configs(2)).cuda()
+    best, cyc, st = klr.argmin_candidates(ctx, prog, hw, cfg, torch.tensor(q.offsets).cuda(),
+                                          torch.tensor(q.sizes).cuda(), torch.tensor(cand).cuda())
+    torch.cuda.synchronize()
+    best, cyc, st = best.cpu().numpy(), cyc.cpu().numpy().astype(np.float64), st.cpu().numpy()
+    ref = G.oracle_choose(coef, gt, q.offsets, q.sizes)
+    table = ref["cycles"].reshape(n_q, -1)
+    bnd = ref["boundary"].reshape(n_q, -1)
+    strict = 0
+    for r in range(n_q):
+        cs = sorted(set(int(c) for c in cand[r] if 0 <= c < 51))
+        vals = [(table[r, c], c) for c in cs if np.isfinite(table[r, c])]
+        if not vals:
+            assert best[r] == -1 and (st[r] & klr.Q_NONE_FEASIBLE), r
+            continue
+        vals.sort()
+        bv, bc = vals[0]
+        margin = (vals[1][0] - bv) / bv if len(vals) > 1 else np.inf
+        if margin > 1e-6 and bnd[r, bc] > 1e-5:
+            strict += 1
+            assert best[r] == bc, (r, best[r], bc, margin)
+            assert abs(cyc[r] - bv) <= 1e-4 * bv
+        else:
+            assert best[r] in cs and table[r, best[r]] <= bv * (1 + 4e-4)
+    assert strict > 0.9 * n_q
