@@ -600,6 +600,9 @@ def run_surrogate(args):
         b.record()
         torch.cuda.synchronize()
         return a.elapsed_time(b) / K, r
+    # the plain sweep with its autotuned launch shape (a fair baseline)
+    ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=klr.F32, autotune=True)
+    plain_tune = ctx.last_tune
     plain_ms, plain = timed(lambda: ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=klr.F32))
     sur_ms, surr = timed(lambda: proposer.propose_and_rerank(ctx, sur, prog, hw, coef, regs, smem,
                                                              cfg, qo, qn, args.sur_k))
@@ -623,7 +626,8 @@ def run_surrogate(args):
                        "degree": 3, "train_rows": n_rows, "train_tuples": n_tuples,
                        "epochs": args.sur_epochs, "batch": batch, "train_steps": steps,
                        "queries": n_q, "k": args.sur_k, "configs": 51},
-            "plain_sweep": {"ms": plain_ms, "queries_per_s": n_q / (plain_ms * 1e-3)},
+            "plain_sweep": {"ms": plain_ms, "queries_per_s": n_q / (plain_ms * 1e-3),
+                            "autotuned_threads": 32 << plain_tune[0]},
             "surrogate_path": {"ms": sur_ms, "propose_ms": prop_ms,
                                "speedup_vs_plain": plain_ms / sur_ms},
             "train": {"ms": train_ms, "rows_per_s": n_rows * args.sur_epochs / (train_ms * 1e-3),

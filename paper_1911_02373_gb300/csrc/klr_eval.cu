@@ -674,7 +674,8 @@ klr_status launch_eval(Context* c, EvalParams& P, bool f64, cudaStream_t stream)
     int64_t per_kernel = P.n_kernels ? (P.n_q + P.n_kernels - 1) / P.n_kernels : 1;
     if (P.cand) per_kernel *= P.kc;
     int threads = 32;
-    while (threads < 256 && threads < per_kernel) threads <<= 1;
+    const int cap = P.cand ? 128 : 256;   // candidate mode: more blocks per SM
+    while (threads < cap && threads < per_kernel) threads <<= 1;
     const int32_t choice = tune_choice(c, eval_tune_key(P, f64), -1);
     if (choice >= 0) threads = 32 << std::min(3, (int)choice);
     switch (P.degree * 2 + (f64 ? 1 : 0)) {

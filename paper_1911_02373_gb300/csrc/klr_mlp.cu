@@ -769,6 +769,7 @@ struct FusedArgs {
     // least predictions among the meaningful shapes instead of writing pred
     int propose;
     int64_t q0;
+    const int32_t* q_kernel;          // kernel of every query
     const int64_t* q_off;
     const int64_t* q_N;
     int32_t n_kernels;
@@ -794,6 +795,7 @@ __device__ int32_t kernel_of(const int64_t* off, int32_t nk, int64_t q) {
 // weights (256 x 256).
 constexpr size_t kFusedSmem = 1024 + (size_t)kTileRows * H * 2 + (size_t)H * H * 2;
 
+template <int KMAX>
 __global__ void __launch_bounds__(kFusedThreads, 1)
 fused_forward_kernel(const __grid_constant__ FusedArgs a) {
     extern __shared__ unsigned char fsm_raw[];
@@ -804,6 +806,8 @@ fused_forward_kernel(const __grid_constant__ FusedArgs a) {
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     __shared__ int32_t tile_kernel[kTileRows];       // proposal mode: each row's kernel
+    __shared__ float bias_s[4 * H];                  // b1, b2, b3, b4 (np <= 256)
+    __shared__ int32_t cfg_max[H];                   // proposal mode: largest block dimension
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_tiles = (a.n + kTileRows - 1) / kTileRows;
     if ((int64_t)blockIdx.x >= n_tiles) return;
@@ -827,6 +831,15 @@ fused_forward_kernel(const __grid_constant__ FusedArgs a) {
     const int row_in_tile = 32 * (warp & 3) + lane;
     const int half = warp >> 2;
     if (tid == 0) tma_load(Bs, a.img + a.pk.w1, (uint32_t)(H * kKPad1 * 2), &mbar_w);
+    for (int i = tid; i < 4 * H; i += kFusedThreads) {
+        const int l = i / H, c = i - l * H;
+        const int64_t off = l == 0 ? a.o.b1 : l == 1 ? a.o.b2 : l == 2 ? a.o.b3 : a.o.b4;
+        bias_s[i] = (l < 3 || c < a.n_out) ? a.params[off + c] : 0.f;
+    }
+    if (a.propose)
+        for (int c = tid; c < a.n_out; c += kFusedThreads)
+            cfg_max[c] = max(a.cfg[3 * c], max(a.cfg[3 * c + 1], a.cfg[3 * c + 2]));
+    __syncthreads();
     for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const int64_t r0 = t * kTileRows;
         if (a.propose) {
@@ -834,7 +847,7 @@ fused_forward_kernel(const __grid_constant__ FusedArgs a) {
             // hardware vector) and the kernel's embedding
             if (tid < kTileRows) {
                 const int64_t gr = r0 + tid;
-                tile_kernel[tid] = gr < a.n ? kernel_of(a.q_off, a.n_kernels, a.q0 + gr) : 0;
+                tile_kernel[tid] = gr < a.n ? a.q_kernel[a.q0 + gr] : 0;
             }
             __syncthreads();
             for (int c = tid; c < kTileRows * (IN / 8); c += kFusedThreads) {
@@ -914,15 +927,15 @@ fused_forward_kernel(const __grid_constant__ FusedArgs a) {
                     tma_load(Bs, a.img + a.pk.w1, (uint32_t)(H * kKPad1 * 2), &mbar_w);
             }
             if (layer < 3) {
-                const float* bias = a.params + (layer == 0 ? a.o.b1 : layer == 1 ? a.o.b2 : a.o.b3);
+                const float* bias = bias_s + layer * H;
                 for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
                     float v[16];
                     tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
                     uint32_t packed[8];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const float x0 = gelu(v[2 * j] + __ldg(bias + c0 + 2 * j));
-                        const float x1 = gelu(v[2 * j + 1] + __ldg(bias + c0 + 2 * j + 1));
+                        const float x0 = gelu(v[2 * j] + bias[c0 + 2 * j]);
+                        const float x1 = gelu(v[2 * j + 1] + bias[c0 + 2 * j + 1]);
                         const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
                         packed[j] = *reinterpret_cast<const uint32_t*>(&h2);
                     }
@@ -933,48 +946,67 @@ fused_forward_kernel(const __grid_constant__ FusedArgs a) {
                 }
             } else if (a.propose) {
                 // the k least predictions among the meaningful shapes of the
-                // row's query (warps 0-3 hold every row of the tile)
-                if (half == 0) {
-                    const int64_t gr = r0 + row_in_tile;
-                    const int64_t q = a.q0 + (gr < a.n ? gr : 0);
-                    const long long N = a.q_N[q];
-                    const int32_t kk = tile_kernel[row_in_tile];
-                    const uint8_t* occ = a.occ + (int64_t)kk * a.n_out;
-                    const float* bias = a.params + a.o.b4;
-                    float bv[16];
-                    int bi[16];
+                // row's query: each half of the warps keeps a sorted list for
+                // its half of the columns, then half 0 merges the two
+                const int64_t gr = r0 + row_in_tile;
+                const int64_t q = a.q0 + (gr < a.n ? gr : 0);
+                const long long N = a.q_N[q];
+                const int32_t kk = tile_kernel[row_in_tile];
+                const uint8_t* occ = a.occ + (int64_t)kk * a.n_out;
+                const float* bias = bias_s + 3 * H;
+                float bv[KMAX];
+                int bi[KMAX];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) { bv[j] = INFINITY; bi[j] = -1; }
-                    for (int c0 = 0; c0 < a.np; c0 += 8) {
-                        float v[8];
-                        tmem_ld8(tmem + lane_base + (uint32_t)c0, v);
+                for (int j = 0; j < KMAX; ++j) { bv[j] = INFINITY; bi[j] = -1; }
+                const int cols = a.np >> 1;
+                for (int c0 = half * cols; c0 < half * cols + cols; c0 += 8) {
+                    float v[8];
+                    tmem_ld8(tmem + lane_base + (uint32_t)c0, v);
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int c = c0 + j;
-                            if (c >= a.n_out || !occ[c]) continue;
-                            if (!(a.cfg[3 * c] <= N && a.cfg[3 * c + 1] <= N && a.cfg[3 * c + 2] <= N))
-                                continue;
-                            float x = v[j] + __ldg(bias + c);
-                            int xi = c;
+                    for (int j = 0; j < 8; ++j) {
+                        const int c = c0 + j;
+                        if (c >= a.n_out || cfg_max[c] > N || !occ[c]) continue;
+                        float x = v[j] + bias[c];
+                        int xi = c;
 #pragma unroll
-                            for (int m = 0; m < 16; ++m) {
-                                if (m < a.k && x < bv[m]) {
-                                    const float tv = bv[m]; const int ti = bi[m];
-                                    bv[m] = x; bi[m] = xi;
-                                    x = tv; xi = ti;
-                                }
+                        for (int m = 0; m < KMAX; ++m) {
+                            if (x < bv[m]) {
+                                const float tv = bv[m]; const int ti = bi[m];
+                                bv[m] = x; bi[m] = xi;
+                                x = tv; xi = ti;
                             }
                         }
                     }
-                    if (gr < a.n) {
+                }
+                // half 1 hands its list over through the (now free) operand buffer
+                float* sv = reinterpret_cast<float*>(As);
+                int* si = reinterpret_cast<int*>(As) + kTileRows * KMAX;
+                if (half == 1) {
 #pragma unroll
-                        for (int m = 0; m < 16; ++m)
-                            if (m < a.k) a.cand[q * a.k + m] = bi[m];
+                    for (int m = 0; m < KMAX; ++m) {
+                        sv[row_in_tile * KMAX + m] = bv[m];
+                        si[row_in_tile * KMAX + m] = bi[m];
+                    }
+                }
+                __syncthreads();
+                if (half == 0 && gr < a.n) {
+                    // merge: equal values keep half 0's (lower) index first
+                    int ia = 0, ib = 0;
+                    for (int m = 0; m < a.k; ++m) {
+                        float va = INFINITY, vb = INFINITY;
+                        int xa = -1, xb = -1;
+#pragma unroll
+                        for (int j = 0; j < KMAX; ++j) if (j == ia) { va = bv[j]; xa = bi[j]; }
+                        if (ib < KMAX) { vb = sv[row_in_tile * KMAX + ib]; xb = si[row_in_tile * KMAX + ib]; }
+                        int pick;
+                        if (xb >= 0 && (xa < 0 || vb < va)) { pick = xb; ++ib; }
+                        else { pick = xa; if (xa >= 0) ++ia; }
+                        a.cand[q * a.k + m] = pick;
                     }
                 }
             } else {
                 const int64_t gr = r0 + row_in_tile;
-                const float* bias = a.params + a.o.b4;
+                const float* bias = bias_s + 3 * H;
                 const int cols = a.np >> 1;
                 for (int c0 = half * cols; c0 < half * cols + cols; c0 += 8) {
                     float v[8];
@@ -983,7 +1015,7 @@ fused_forward_kernel(const __grid_constant__ FusedArgs a) {
 #pragma unroll
                         for (int j = 0; j < 8; ++j)
                             if (c0 + j < a.n_out)
-                                a.pred[gr * a.n_out + c0 + j] = v[j] + __ldg(bias + c0 + j);
+                                a.pred[gr * a.n_out + c0 + j] = v[j] + bias[c0 + j];
                     }
                 }
             }
@@ -1036,14 +1068,17 @@ klr_status pack_weights(const MlpWs& w, const float* params, const Offsets& o, i
 
 klr_status launch_fused(const Context* c, const FusedArgs& a, cudaStream_t s) {
     if (a.n == 0) return KLR_OK;
-    KLR_CHECK_CUDA(cudaFuncSetAttribute(fused_forward_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kFusedSmem));
     const int64_t tiles = (a.n + kTileRows - 1) / kTileRows;
     const int grid = (int)std::min<int64_t>(tiles, c->n_sm);
-    fused_forward_kernel<<<grid, kFusedThreads, kFusedSmem, s>>>(a);
-    KLR_CHECK_CUDA(cudaGetLastError());
-    return KLR_OK;
+    auto go = [&](auto kern) -> klr_status {
+        KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kFusedSmem));
+        kern<<<grid, kFusedThreads, kFusedSmem, s>>>(a);
+        KLR_CHECK_CUDA(cudaGetLastError());
+        return KLR_OK;
+    };
+    // top-k lists of 8 or 16 entries (proposal mode)
+    return a.k > 8 ? go(fused_forward_kernel<16>) : go(fused_forward_kernel<8>);
 }
 
 // Forward pass of rows whose X0 is set, on the tensor cores (one CTA per SM
@@ -1421,6 +1456,14 @@ struct ProposeArgs {
     uint8_t* occ;                   // [n_kernels x n_cfg]: 1 where B_active > 0
 };
 
+// the kernel of every query, from the CSR offsets (one thread per kernel)
+__global__ void query_kernel_map_kernel(const int64_t* __restrict__ q_off, int32_t n_kernels,
+                                        int32_t* __restrict__ q_kernel) {
+    for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_kernels;
+         k += gridDim.x * blockDim.x)
+        for (int64_t q = q_off[k]; q < q_off[k + 1]; ++q) q_kernel[q] = k;
+}
+
 // occupancy of every (kernel, shape), once per proposal call
 __global__ void occupancy_table_kernel(const __grid_constant__ ProposeArgs a) {
     const int64_t total = (int64_t)a.n_kernels * a.n_cfg;
@@ -1532,7 +1575,7 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
     const size_t base = mlp_ws_bytes(rows, nc, no, n_kernels, false);
     const size_t extra = align256(2 * (size_t)n_kernels * nc) + align256(4 * (size_t)rows) * 2 +
                          align256(8 * (size_t)rows) * 2 + align256((size_t)n_kernels * n_cfg) +
-                         kFusedScratch;
+                         kFusedScratch + (no > 0 ? align256(4 * (size_t)q->n_queries) : 0);
     if ((st = ensure_workspace(c, base + extra, s)) != KLR_OK) return st;
     MlpWs w = carve(c->ws, rows, nc, no, n_kernels, false);
     char* p = reinterpret_cast<char*>(c->ws) + base;
@@ -1550,6 +1593,8 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
     p += align256((size_t)n_kernels * n_cfg);
     unsigned char* img = reinterpret_cast<unsigned char*>(p);
     int* err = reinterpret_cast<int*>(img + kFusedScratch - 256);
+    p += kFusedScratch;
+    int32_t* q_kernel = reinterpret_cast<int32_t*>(p);
     cast_bf16_kernel<<<blocks_for(o.total, 256), 256, 0, s>>>(net->params, w.pb, o.total);
     cast_bf16_kernel<<<blocks_for((int64_t)n_kernels * nc, 256), 256, 0, s>>>(
         coef, coef_b, (int64_t)n_kernels * nc);
@@ -1586,6 +1631,10 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
         FusedArgs fa{};
         if ((st = pack_weights(w, net->params, o, no, img, err, fa, s)) != KLR_OK) return st;
         fa.propose = 1;
+        query_kernel_map_kernel<<<blocks_for(n_kernels, 128), 128, 0, s>>>(q->q_offsets, n_kernels,
+                                                                          q_kernel);
+        KLR_CHECK_CUDA(cudaGetLastError());
+        fa.q_kernel = q_kernel;
         fa.q_off = q->q_offsets;
         fa.q_N = q->q_N;
         fa.n_kernels = n_kernels;
