@@ -60,7 +60,7 @@ def parse():
                     help="kernels of the 3D sweep checked against the oracle")
     ap.add_argument("--sur-kernels", type=int, default=50000)
     ap.add_argument("--sur-rows-per-kernel", type=int, default=400)
-    ap.add_argument("--sur-epochs", type=int, default=30)
+    ap.add_argument("--sur-epochs", type=int, default=100)
     ap.add_argument("--sur-form", default="query", choices=["query", "row"],
                     help="surrogate output form: per (kernel, N) query or per (kernel, N, shape) row")
     ap.add_argument("--sur-lr", type=float, default=2e-3)
