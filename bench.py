@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="built-in launch shapes instead of the autotuned ones")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "sweep3d", "surrogate", "precision"],
+                    choices=["batched", "sweep3d", "surrogate", "precision", "history"],
                     help="batched: fit + argmin (default metric); sweep3d: 3D evaluator sweep")
     ap.add_argument("--sweep-kernels", type=int, default=100000)
     ap.add_argument("--sweep-check-kernels", type=int, default=100,
@@ -642,6 +642,78 @@ def run_surrogate(args):
                                 "within_1pct": float(np.mean(rreg <= 0.01))}}
 
 
+def run_history(args):
+    """Runtime history: the batched workload's 640,000 queries against its
+    ground-truth programs, answered by the plain FP32 argmin, then through the
+    history (first call: every query evaluated and recorded; later calls:
+    every query answered from the table)."""
+    import torch
+    import paper_1911_02373_gb300 as klr
+    import workloads as W
+    wl = WORKLOAD
+    nk = wl["kernels"]
+    gt = W.ground_truth(args.seed, nk, 3, 2, 8, 23, 10)
+    q = W.queries_per_kernel(nk, W.log_spaced_sizes(wl["sizes_per_kernel"]))
+    dev = torch.device("cuda", 0)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    ctx = klr.Context(0)
+    n_q = len(q.sizes)
+    ctx.reserve(0, n_q)
+    prog = klr.Context.program(t(gt.coef.astype(np.float32)), t(gt.regs), t(gt.smem), n_vars=3,
+                               degree=2, n_scale_log2=23, b_scale_log2=10,
+                               metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+    hw = klr.make_hw(W.HARDWARE)
+    cfg = t(klr.enumerate_configs(2))
+    qo, qn = t(q.offsets), t(q.sizes)
+    hist = klr.History(ctx, 21)
+    out = [torch.empty(n_q, device=dev, dtype=d)
+           for d in (torch.int32, torch.float32, torch.float32, torch.int32)]
+    out.append(torch.empty((n_q, 6), device=dev, dtype=torch.int32))
+    K = max(3, args.steps)
+
+    def timed(fn, reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+    ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=klr.F32, out=tuple(out), autotune=True)
+    plain_ms = timed(lambda: ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=klr.F32, out=tuple(out)), K)
+    ref = [o.clone() for o in out]
+
+    def fill():
+        hist.clear()
+        klr.argmin_history(ctx, hist, prog, hw, cfg, qo, qn, out=tuple(out))
+    fill_ms = timed(fill, K)
+    hit_ms = timed(lambda: klr.argmin_history(ctx, hist, prog, hw, cfg, qo, qn, out=tuple(out)), K)
+    st = out[3].cpu().numpy()
+    same = all(torch.equal(a, b) for i, (a, b) in enumerate(zip(out, ref)) if i != 3)
+    # hit path bytes per query: N (8), the probed key and value (a 32-byte
+    # sector each), outputs (best, cycles, margin, status: 16; launch: 24)
+    hit_bytes = n_q * (8 + 32 + 32 + 16 + 24)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    hist.close()
+    return {"metric": "argmin queries/s answered from the runtime history",
+            "value": n_q / (hit_ms * 1e-3), "unit": "queries/s", "n_gpus": 1, "steps": K,
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded rational ground truth)",
+            "config": {"workload": "history", "kernels": nk, "queries": n_q, "configs": 51,
+                       "slots": 1 << 21},
+            "plain_argmin_ms": plain_ms, "fill_ms": fill_ms, "hit_ms": hit_ms,
+            "speedup_hit_vs_plain": plain_ms / hit_ms,
+            "all_hits": bool(np.all(st & klr.Q_HISTORY)), "outputs_equal_plain": bool(same),
+            "roofline": {"bound": "hbm", "achieved": hit_bytes / (hit_ms * 1e-3) / 1e9,
+                         "peak": hbm_peak, "unit": "GB/s",
+                         "frac": hit_bytes / (hit_ms * 1e-3) / 1e9 / hbm_peak, "traffic": None}}
+
+
 def run_precision(args):
     """Precision split: 4096 fits of degree 3 (20 + 20 unknowns), 5,000 samples
     each, N up to 2^30, noiseless and with 1% noise.  Every precision mode of
@@ -755,6 +827,9 @@ def main():
         return
     if args.workload == "precision":
         print(json.dumps(run_precision(args)))
+        return
+    if args.workload == "history":
+        print(json.dumps(run_history(args)))
         return
     ws, rank, _ = dist_env()
     cb = None

@@ -88,6 +88,7 @@ typedef int32_t klr_status;
                                    non-finite metric; it was skipped           */
 #define KLR_Q_NONE_FEASIBLE  2  /* no meaningful configuration: best = -1      */
 #define KLR_Q_TIE_RESOLVED   4  /* FP32 near-tie re-decided in FP64            */
+#define KLR_Q_HISTORY        8  /* answered from the runtime history            */
 
 typedef struct klr_ctx klr_ctx;
 
@@ -247,6 +248,35 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
                       int32_t* best_idx, void* best_cycles, int32_t out_dtype,
                       float* margin, int32_t* q_status, int32_t* launch_out,
                       void* stream);
+
+/* ---- runtime history ---------------------------------------------------------
+ * Section III-B: the tool keeps a runtime history of its decisions so that
+ * later launches get theirs at once.  A history is a device hash table from
+ * (kernel index, N) to the outputs of klr_argmin (FP32 mode): best index,
+ * best cycles, margin and status.  It belongs to one program, hardware
+ * description and configuration set; clear it when any of them changes.
+ *   klr_history_create: 2^capacity_log2 slots (10..30; 24 bytes each) on the
+ *     context's device; KLR_ENOMEM if the allocation fails.  Synchronous.
+ *   klr_history_clear: forget every entry (asynchronous on `stream`).
+ *   klr_history_destroy: synchronises the device and frees the table.
+ *   klr_argmin_history: klr_argmin with out_dtype KLR_F32 and the same
+ *     arguments, where every query whose (kernel, N) is in the history takes
+ *     its outputs from there (q_status adds KLR_Q_HISTORY) and is not
+ *     evaluated (a kernel whose queries all hit is skipped); the evaluated
+ *     queries are recorded afterwards (linear probing over at most 64 slots;
+ *     a query that finds no free slot, or has N >= 2^40, is not recorded).
+ *     The outputs equal klr_argmin's for the same program.  The context's
+ *     scratch holds one byte per query more than klr_argmin's (sized by
+ *     klr_ctx_reserve). */
+typedef struct klr_history klr_history;
+klr_status klr_history_create(klr_ctx* ctx, int32_t capacity_log2, klr_history** out);
+klr_status klr_history_clear(klr_history* hist, void* stream);
+klr_status klr_history_destroy(klr_history* hist);
+klr_status klr_argmin_history(klr_ctx* ctx, klr_history* hist, const klr_program* prog,
+                              const klr_hw* hw, const int32_t* cfg, int n_cfg,
+                              const klr_queries* q, int32_t* best_idx, float* best_cycles,
+                              float* margin, int32_t* q_status, int32_t* launch_out,
+                              void* stream);
 
 /* ---- autotuning of the library's launch shapes ----------------------------
  * The paper tunes the launch parameters of the user's kernels; these two calls

@@ -26,7 +26,7 @@ OK, EINVAL, ECUDA, ENOMEM, ENOTSUP = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 FIT_FP64, FIT_DF32, FIT_FP32, FIT_TF32, FIT_BF16 = 0, 1, 2, 3, 4
 FIT_OK, FIT_EMPTY, FIT_NONFINITE, FIT_RANK_DEFICIENT, FIT_INEXACT, FIT_SOLVE_FAILED = 0, 1, 2, 4, 8, 16
-Q_OK, Q_BAD_METRIC, Q_NONE_FEASIBLE, Q_TIE_RESOLVED = 0, 1, 2, 4
+Q_OK, Q_BAD_METRIC, Q_NONE_FEASIBLE, Q_TIE_RESOLVED, Q_HISTORY = 0, 1, 2, 4, 8
 
 #: every entry point declared in include/klr.h
 ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last_error",
@@ -34,7 +34,8 @@ ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last
                "klr_argmin_noalloc", "klr_mlp_param_count", "klr_mlp_train_step",
                "klr_mlp_predict", "klr_propose", "klr_argmin_candidates", "klr_autotune_fit",
                "klr_autotune_argmin", "klr_tune_export", "klr_tune_import", "klr_fit_gram",
-               "klr_fit_solve", "klr_mlp_query_targets")
+               "klr_fit_solve", "klr_mlp_query_targets", "klr_history_create",
+               "klr_history_clear", "klr_history_destroy", "klr_argmin_history")
 #: largest query count klr_argmin_noalloc accepts
 ARGMIN_NOALLOC_MAX_QUERIES = 65536
 
@@ -110,6 +111,11 @@ for _name, _args in {
                             ctypes.POINTER(Queries), _vp, _vp, ctypes.c_int32, _vp, _vp, _vp,
                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), _vp],
     "klr_fit_gram": [_vp, ctypes.POINTER(FitBatch), _vp],
+    "klr_history_create": [_vp, ctypes.c_int32, ctypes.POINTER(_vp)],
+    "klr_history_clear": [_vp, _vp],
+    "klr_history_destroy": [_vp],
+    "klr_argmin_history": [_vp, _vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
+                           ctypes.POINTER(Queries), _vp, _vp, _vp, _vp, _vp, _vp],
     "klr_mlp_query_targets": [_vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp],
     "klr_fit_solve": [_vp, ctypes.POINTER(FitBatch), _vp, ctypes.c_int32, _vp, _vp, _vp],
     "klr_tune_export": [_vp, _vp, _vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
@@ -320,6 +326,53 @@ class Context:
                                                  _ptr(best), _ptr(cyc), out_dtype, _ptr(margin),
                                                  _ptr(status), _ptr(lp), _stream(stream)))
         return best, cyc, margin, status, lp
+
+
+class History:
+    """Runtime history of argmin decisions on the context's device: a hash
+    table from (kernel index, N) to the outputs (klr_history_*)."""
+
+    def __init__(self, ctx: "Context", capacity_log2: int = 20):
+        self._h = ctypes.c_void_p()
+        _check("klr_history_create",
+               _lib.klr_history_create(ctx._h, capacity_log2, ctypes.byref(self._h)))
+
+    def clear(self, stream=None):
+        _check("klr_history_clear", _lib.klr_history_clear(self._h, _stream(stream)))
+
+    def close(self):
+        if self._h:
+            _lib.klr_history_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def argmin_history(ctx: "Context", hist: History, prog: Program, hw: Hw, cfg, q_offsets, q_N,
+                   out=None, stream=None):
+    """FP32 argmin answered from the history where it can be, the rest
+    evaluated and recorded (klr_argmin_history).  Returns (best, cycles,
+    margin, status, launch)."""
+    import torch
+    n_q = q_N.numel()
+    dev = q_N.device
+    if out is None:
+        out = (torch.empty(n_q, device=dev, dtype=torch.int32),
+               torch.empty(n_q, device=dev, dtype=torch.float32),
+               torch.empty(n_q, device=dev, dtype=torch.float32),
+               torch.empty(n_q, device=dev, dtype=torch.int32),
+               torch.empty((n_q, 6), device=dev, dtype=torch.int32))
+    best, cyc, margin, status, lp = out
+    q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+    _check("klr_argmin_history",
+           _lib.klr_argmin_history(ctx._h, hist._h, ctypes.byref(prog), ctypes.byref(hw), _ptr(cfg),
+                                   cfg.shape[0], ctypes.byref(q), _ptr(best), _ptr(cyc),
+                                   _ptr(margin), _ptr(status), _ptr(lp), _stream(stream)))
+    return out
 
 
 def mlp_param_count(n_coef: int, n_out: int = 0) -> int:

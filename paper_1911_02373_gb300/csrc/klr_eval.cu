@@ -64,6 +64,7 @@ struct EvalParams {
     int64_t tie_cap;
     const int32_t* cand;        // candidate mode: n_q x kc shape indices, or NULL
     int kc;
+    const uint8_t* done;        // history mode: 1 for queries answered already, or NULL
     uint8_t exps[kMaxBasis][kMaxVars];
 };
 
@@ -321,6 +322,12 @@ eval_kernel(const __grid_constant__ EvalParams P) {
     for (int k = blockIdx.x; k < P.n_kernels; k += gridDim.x) {
         const int64_t qa = P.q_off[k], qb = P.q_off[k + 1];
         if (qa == qb) continue;
+        if (P.done) {
+            // history mode: nothing to do for a kernel whose queries all hit
+            int open = 0;
+            for (int64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) open |= !P.done[q];
+            if (!__syncthreads_or(open)) continue;
+        }
         __syncthreads();   // previous kernel's tables no longer in use
         for (int i = threadIdx.x; i < 8 * u; i += blockDim.x) {
             if (P.coef_f64) coef_s[i] = (T)reinterpret_cast<const double*>(P.coef)[(int64_t)k * 8 * u + i];
@@ -426,6 +433,7 @@ eval_kernel(const __grid_constant__ EvalParams P) {
             continue;
         }
         for (int64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) {
+            if (P.done && P.done[q]) continue;
             const long long N = P.q_N[q];
             const bool small = N < (1LL << 24);   // 32-bit wave counts exact
             const T xN = (T)N * n_scale;
@@ -688,6 +696,96 @@ klr_status launch_eval(Context* c, EvalParams& P, bool f64, cudaStream_t stream)
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Runtime history (Section III-B: the tool keeps a history of its decisions
+// so that later launches of the same kernel at the same size get the result
+// at once): an open-addressing hash table on the device from (kernel, N) to
+// the argmin outputs.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kEmptyKey = ~0ull;
+constexpr int kMaxProbe = 64;
+
+struct History {
+    int device;
+    int64_t cap;                 // slots, a power of two
+    unsigned long long* keys;    // kernel << 40 | N, or kEmptyKey
+    int4* vals;                  // best, cycles bits, margin bits, status
+};
+
+// splitmix64 finaliser (Steele, Lea and Flood)
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+// key of a query, or kEmptyKey when it cannot be stored (N >= 2^40)
+__device__ __forceinline__ uint64_t history_key(int32_t k, long long N) {
+    if (N < 0 || N >= (1LL << 40) || k < 0 || k >= (1 << 23)) return kEmptyKey;
+    return ((uint64_t)k << 40) | (uint64_t)N;
+}
+
+// look every query up (one warp per kernel over its queries); hits write
+// their outputs and are marked done
+__global__ void history_lookup_kernel(const __grid_constant__ EvalParams P, History h,
+                                      uint8_t* __restrict__ done) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t wk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wk < P.n_kernels;
+         wk += ((int64_t)gridDim.x * blockDim.x) >> 5)
+    for (int64_t q = P.q_off[wk] + lane; q < P.q_off[wk + 1]; q += 32) {
+        const long long N = P.q_N[q];
+        const uint64_t key = history_key((int32_t)wk, N);
+        uint8_t hit = 0;
+        if (key != kEmptyKey) {
+            uint64_t i = mix64(key) & (uint64_t)(h.cap - 1);
+            for (int p = 0; p < kMaxProbe; ++p, i = (i + 1) & (uint64_t)(h.cap - 1)) {
+                const uint64_t kk = h.keys[i];
+                if (kk == kEmptyKey) break;
+                if (kk == key) {
+                    const int4 v = h.vals[i];
+                    P.best[q] = v.x;
+                    reinterpret_cast<float*>(P.best_cycles)[q] = __int_as_float(v.y);
+                    if (P.margin) P.margin[q] = __int_as_float(v.z);
+                    if (P.q_status) P.q_status[q] = v.w | KLR_Q_HISTORY;
+                    write_launch(P, q, N, v.x);
+                    hit = 1;
+                    break;
+                }
+            }
+        }
+        done[q] = hit;
+    }
+}
+
+// record the evaluated queries (one warp per kernel; a full probe window
+// leaves a query out)
+__global__ void history_insert_kernel(const __grid_constant__ EvalParams P, History h,
+                                      const uint8_t* __restrict__ done) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t wk = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; wk < P.n_kernels;
+         wk += ((int64_t)gridDim.x * blockDim.x) >> 5)
+    for (int64_t q = P.q_off[wk] + lane; q < P.q_off[wk + 1]; q += 32) {
+        if (done[q]) continue;
+        const uint64_t key = history_key((int32_t)wk, P.q_N[q]);
+        if (key == kEmptyKey) continue;
+        const int32_t b = P.best[q];
+        int4 v;
+        v.x = b;
+        v.y = __float_as_int(reinterpret_cast<const float*>(P.best_cycles)[q]);
+        v.z = __float_as_int(P.margin ? P.margin[q] : 0.f);
+        v.w = P.q_status ? P.q_status[q] : (b < 0 ? KLR_Q_NONE_FEASIBLE : 0);
+        uint64_t i = mix64(key) & (uint64_t)(h.cap - 1);
+        for (int p = 0; p < kMaxProbe; ++p, i = (i + 1) & (uint64_t)(h.cap - 1)) {
+            const unsigned long long prev = atomicCAS(h.keys + i, kEmptyKey, key);
+            if (prev == kEmptyKey) { h.vals[i] = v; break; }
+            if (prev == key) break;      // recorded by another query with the same key
+        }
+    }
+}
+
 }  // namespace
 
 size_t fit_workspace_bytes(int64_t n_fits, int n_mom);
@@ -696,7 +794,9 @@ size_t fit_workspace_bytes(int64_t n_fits, int n_mom);
 // moment sums (sized here for fits of total degree <= 2 in up to four
 // variables) and the argmin's tie records.
 size_t workspace_bytes(int64_t max_fits, int64_t max_queries) {
-    const size_t ties = 256 + sizeof(TieRecord) * (size_t)tie_capacity(max_queries);
+    // tie records, then the history mode's per-query mask
+    const size_t ties = 256 + sizeof(TieRecord) * (size_t)tie_capacity(max_queries) +
+                        (((size_t)max_queries + 255) & ~(size_t)255);
     return std::max(ties, fit_workspace_bytes(max_fits, n_monomials(4, 4)));
 }
 
@@ -851,6 +951,93 @@ klr_status klr_autotune_argmin(klr_ctx* ctx, const klr_program* prog, const klr_
     const int32_t cand[4] = {0, 1, 2, 3};           // 32, 64, 128, 256 threads per block
     return tune_candidates(c, eval_tune_key(P, out_dtype == KLR_F64), stream, cand, 4, 3, run,
                            choice_out, ms_out);
+}
+
+klr_status klr_history_create(klr_ctx* ctx, int32_t capacity_log2, klr_history** out) {
+    KLR_REQUIRE(ctx && out, "klr_history_create: NULL context or output");
+    KLR_REQUIRE(capacity_log2 >= 10 && capacity_log2 <= 30,
+                "klr_history_create: capacity_log2 %d not in 10..30", capacity_log2);
+    Context* c = reinterpret_cast<Context*>(ctx);
+    KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    History* h = new History();
+    h->device = c->device;
+    h->cap = (int64_t)1 << capacity_log2;
+    if (cudaMalloc(&h->keys, sizeof(unsigned long long) * h->cap) != cudaSuccess ||
+        cudaMalloc(&h->vals, sizeof(int4) * h->cap) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->keys) cudaFree(h->keys);
+        delete h;
+        set_error("klr_history_create: cudaMalloc of %lld slots failed", (long long)(1LL << capacity_log2));
+        return KLR_ENOMEM;
+    }
+    KLR_CHECK_CUDA(cudaMemset(h->keys, 0xFF, sizeof(unsigned long long) * h->cap));
+    KLR_CHECK_CUDA(cudaDeviceSynchronize());
+    *out = reinterpret_cast<klr_history*>(h);
+    return KLR_OK;
+}
+
+klr_status klr_history_destroy(klr_history* hist) {
+    if (!hist) return KLR_OK;
+    History* h = reinterpret_cast<History*>(hist);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->keys);
+    cudaFree(h->vals);
+    delete h;
+    return KLR_OK;
+}
+
+klr_status klr_history_clear(klr_history* hist, void* stream_) {
+    KLR_REQUIRE(hist, "klr_history_clear: NULL history");
+    History* h = reinterpret_cast<History*>(hist);
+    KLR_CHECK_CUDA(cudaSetDevice(h->device));
+    KLR_CHECK_CUDA(cudaMemsetAsync(h->keys, 0xFF, sizeof(unsigned long long) * h->cap,
+                                   reinterpret_cast<cudaStream_t>(stream_)));
+    return KLR_OK;
+}
+
+klr_status klr_argmin_history(klr_ctx* ctx, klr_history* hist, const klr_program* prog,
+                              const klr_hw* hw, const int32_t* cfg, int n_cfg,
+                              const klr_queries* q, int32_t* best_idx, float* best_cycles,
+                              float* margin, int32_t* q_status, int32_t* launch_out,
+                              void* stream_) {
+    KLR_REQUIRE(ctx && hist, "klr_argmin_history: NULL context or history");
+    Context* c = reinterpret_cast<Context*>(ctx);
+    History* h = reinterpret_cast<History*>(hist);
+    KLR_REQUIRE(h->device == c->device, "klr_argmin_history: history of another device");
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    EvalParams P;
+    klr_status st = prepare(c, prog, hw, cfg, n_cfg, q, KLR_F32, P);
+    if (st != KLR_OK) return st;
+    if (P.n_q == 0 || P.n_kernels == 0) return KLR_OK;
+    KLR_REQUIRE(best_idx && best_cycles, "klr_argmin_history: NULL best_idx or best_cycles");
+    KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    P.table = 0;
+    P.best = best_idx;
+    P.best_cycles = best_cycles;
+    P.margin = margin;
+    P.q_status = q_status;
+    P.launch = launch_out;
+    st = ensure_workspace(c, workspace_bytes(0, P.n_q), stream);
+    if (st != KLR_OK) return st;
+    P.tie_count = reinterpret_cast<int*>(c->ws);
+    P.ties = reinterpret_cast<TieRecord*>(reinterpret_cast<char*>(c->ws) + 256);
+    P.tie_cap = tie_capacity(P.n_q);
+    uint8_t* done = reinterpret_cast<uint8_t*>(c->ws) + 256 + sizeof(TieRecord) * (size_t)P.tie_cap;
+    KLR_CHECK_CUDA(cudaMemsetAsync(P.tie_count, 0, sizeof(int), stream));
+    // one warp per kernel
+    const int grid = (int)std::min<int64_t>(((int64_t)P.n_kernels * 32 + 255) / 256,
+                                            (int64_t)c->n_sm * 16);
+    history_lookup_kernel<<<grid, 256, 0, stream>>>(P, *h, done);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    P.done = done;
+    if ((st = launch_eval(c, P, false, stream)) != KLR_OK) return st;
+    const int tgrid = (int)std::min<int64_t>((P.tie_cap + 127) / 128, (int64_t)c->n_sm * 4);
+    tie_kernel<<<tgrid, 128, 0, stream>>>(P);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    history_insert_kernel<<<grid, 256, 0, stream>>>(P, *h, done);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
 }
 
 }  // extern "C"
