@@ -109,6 +109,32 @@ def argmin(cycles: np.ndarray):
     return best, val, margin
 
 
+def refine(cycles: np.ndarray, warps: np.ndarray, eps: float):
+    """Section IV, step 5's refinement among near-optimal configurations.
+
+    The paper allows a secondary performance metric to choose among the
+    configurations that optimise the estimate up to some margin, and names
+    hardware occupancy among the performance metrics; it fixes neither the
+    margin nor the metric.  Reading: among the configurations with cycles
+    <= (1 + eps) x the least cycles, take the one with the most active warps
+    per SM; ties by fewer cycles, then by the lower index.
+
+    cycles: (Q, C) with inf where not meaningful; warps: (Q, C) or (C,)
+    W_active.  Returns best index per row (-1 when nothing is finite)."""
+    cycles = np.atleast_2d(cycles)
+    warps = np.broadcast_to(warps, cycles.shape)
+    best = np.full(cycles.shape[0], -1, dtype=np.int64)
+    for r in range(cycles.shape[0]):
+        row = cycles[r]
+        fin = np.isfinite(row)
+        if not fin.any():
+            continue
+        lo = row[fin].min()
+        near = [c for c in range(len(row)) if fin[c] and row[c] <= lo * (1.0 + eps)]
+        best[r] = min(near, key=lambda c: (-int(warps[r, c]), row[c], c))
+    return best
+
+
 def launch_params(best_cfg, N: int):
     """(gx, gy, gz, bx, by, bz): block shape and grid = ceil(N / b_i) per used
     dimension (Section V-A's grid file for square data), 1 elsewhere."""

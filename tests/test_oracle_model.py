@@ -182,3 +182,38 @@ def test_argmin_permutation_invariance():
 def test_launch_params():
     assert program.launch_params((32, 8), 1000) == (32, 125, 1, 32, 8, 1)
     assert program.launch_params((4, 4, 2), 9) == (3, 3, 5, 4, 4, 2)
+
+
+def test_refine_reduces_to_argmin_and_prefers_occupancy():
+    from oracle import program as P
+    rng = np.random.default_rng(11)
+    cyc = rng.uniform(100, 200, (40, 12))
+    cyc[rng.random((40, 12)) < 0.2] = np.inf
+    cyc[5, :] = np.inf
+    W = rng.integers(1, 64, 12)
+    # eps = 0: the plain argmin (lowest index among equal values)
+    cyc[7, 3] = cyc[7, 9] = cyc[7][np.isfinite(cyc[7])].min() - 1.0
+    b0 = P.refine(cyc, W, 0.0)
+    want, _, _ = P.argmin(cyc)
+    # with eps = 0 equal values can still differ in warps: only exact ties move
+    exact = np.array([np.sum(cyc[r] == cyc[r][np.isfinite(cyc[r])].min()) == 1 if np.isfinite(cyc[r]).any()
+                      else True for r in range(40)])
+    assert np.array_equal(b0[exact], want[exact])
+    assert b0[5] == -1
+    # brute force for a larger margin
+    eps = 0.1
+    b = P.refine(cyc, W, eps)
+    for r in range(40):
+        fin = np.isfinite(cyc[r])
+        if not fin.any():
+            continue
+        lo = cyc[r][fin].min()
+        cand = [c for c in range(12) if fin[c] and cyc[r, c] <= lo * (1 + eps)]
+        wmax = max(W[c] for c in cand)
+        assert W[b[r]] == wmax and b[r] in cand
+        assert cyc[r, b[r]] == min(cyc[r, c] for c in cand if W[c] == wmax)
+    # a wider margin never lowers the occupancy of the choice
+    for e1, e2 in ((0.0, 0.05), (0.05, 0.2), (0.2, 1.0)):
+        b1, b2 = P.refine(cyc, W, e1), P.refine(cyc, W, e2)
+        ok = b1 >= 0
+        assert np.all(W[b2[ok]] >= W[b1[ok]])
