@@ -49,10 +49,11 @@ def metrics(coef8: np.ndarray, xs: np.ndarray, exps: list, lo, scale):
 
 def kernel_occupancy(regs: int, smem: int, configs, hw):
     """(B_active, W_active) per configuration for one kernel (integers)."""
-    B = np.array([occupancy.active_blocks(math.prod(c), int(regs), int(smem), hw)
-                  for c in configs], dtype=np.int64)
-    W = np.array([occupancy.active_warps(int(b), math.prod(c), hw)
-                  for b, c in zip(B, configs)], dtype=np.int64)
+    # Python integers throughout: the products in Fig. 1's tests exceed 32 bits
+    T = [int(math.prod(int(v) for v in c)) for c in configs]
+    B = np.array([occupancy.active_blocks(t, int(regs), int(smem), hw) for t in T],
+                 dtype=np.int64)
+    W = np.array([occupancy.active_warps(int(b), t, hw) for b, t in zip(B, T)], dtype=np.int64)
     return B, W
 
 
