@@ -89,6 +89,7 @@ typedef int32_t klr_status;
 #define KLR_Q_NONE_FEASIBLE  2  /* no meaningful configuration: best = -1      */
 #define KLR_Q_TIE_RESOLVED   4  /* FP32 near-tie re-decided in FP64            */
 #define KLR_Q_HISTORY        8  /* answered from the runtime history            */
+#define KLR_Q_REFINED       16  /* secondary metric chose another configuration */
 
 typedef struct klr_ctx klr_ctx;
 
@@ -248,6 +249,22 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
                       int32_t* best_idx, void* best_cycles, int32_t out_dtype,
                       float* margin, int32_t* q_status, int32_t* launch_out,
                       void* stream);
+
+/* Section IV, step 5: several configurations may optimise the estimate up to
+ * some margin, and a secondary performance metric may refine the choice.
+ * The paper fixes neither; this call takes occupancy, a metric the paper
+ * names: per query, among the configurations whose cycles in cycles_table
+ * (klr_eval's FP32 output for the same queries, n_queries x n_cfg, +inf where
+ * not meaningful) are <= (1 + eps) times the least (compared in FP64), the one
+ * with the most active warps per SM (Eq. 1); ties by fewer cycles, then the
+ * lower index.  best_idx, best_cycles (its cycles), q_status (device, or NULL:
+ * KLR_Q_REFINED when the choice differs from the first least-cycles
+ * configuration, KLR_Q_NONE_FEASIBLE when nothing is finite).  eps >= 0;
+ * eps = 0 gives the plain argmin except among exact ties. */
+klr_status klr_argmin_refined(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
+                              const int32_t* cfg, int n_cfg, const klr_queries* q,
+                              const float* cycles_table, double eps, int32_t* best_idx,
+                              float* best_cycles, int32_t* q_status, void* stream);
 
 /* ---- runtime history ---------------------------------------------------------
  * Section III-B: the tool keeps a runtime history of its decisions so that

@@ -26,7 +26,7 @@ OK, EINVAL, ECUDA, ENOMEM, ENOTSUP = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 FIT_FP64, FIT_DF32, FIT_FP32, FIT_TF32, FIT_BF16 = 0, 1, 2, 3, 4
 FIT_OK, FIT_EMPTY, FIT_NONFINITE, FIT_RANK_DEFICIENT, FIT_INEXACT, FIT_SOLVE_FAILED = 0, 1, 2, 4, 8, 16
-Q_OK, Q_BAD_METRIC, Q_NONE_FEASIBLE, Q_TIE_RESOLVED, Q_HISTORY = 0, 1, 2, 4, 8
+Q_OK, Q_BAD_METRIC, Q_NONE_FEASIBLE, Q_TIE_RESOLVED, Q_HISTORY, Q_REFINED = 0, 1, 2, 4, 8, 16
 
 #: every entry point declared in include/klr.h
 ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last_error",
@@ -35,7 +35,8 @@ ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last
                "klr_mlp_predict", "klr_propose", "klr_argmin_candidates", "klr_autotune_fit",
                "klr_autotune_argmin", "klr_tune_export", "klr_tune_import", "klr_fit_gram",
                "klr_fit_solve", "klr_mlp_query_targets", "klr_history_create",
-               "klr_history_clear", "klr_history_destroy", "klr_argmin_history")
+               "klr_history_clear", "klr_history_destroy", "klr_argmin_history",
+               "klr_argmin_refined")
 #: largest query count klr_argmin_noalloc accepts
 ARGMIN_NOALLOC_MAX_QUERIES = 65536
 
@@ -113,6 +114,8 @@ for _name, _args in {
     "klr_fit_gram": [_vp, ctypes.POINTER(FitBatch), _vp],
     "klr_history_create": [_vp, ctypes.c_int32, ctypes.POINTER(_vp)],
     "klr_history_clear": [_vp, _vp],
+    "klr_argmin_refined": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
+                           ctypes.POINTER(Queries), _vp, ctypes.c_double, _vp, _vp, _vp, _vp],
     "klr_history_destroy": [_vp],
     "klr_argmin_history": [_vp, _vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
                            ctypes.POINTER(Queries), _vp, _vp, _vp, _vp, _vp, _vp],
@@ -372,6 +375,26 @@ def argmin_history(ctx: "Context", hist: History, prog: Program, hw: Hw, cfg, q_
            _lib.klr_argmin_history(ctx._h, hist._h, ctypes.byref(prog), ctypes.byref(hw), _ptr(cfg),
                                    cfg.shape[0], ctypes.byref(q), _ptr(best), _ptr(cyc),
                                    _ptr(margin), _ptr(status), _ptr(lp), _stream(stream)))
+    return out
+
+
+def argmin_refined(ctx: "Context", prog: Program, hw: Hw, cfg, q_offsets, q_N, cycles_table,
+                   eps: float, out=None, stream=None):
+    """Secondary-metric refinement (occupancy) among the configurations
+    within (1 + eps) of the least cycles of klr_eval's FP32 table
+    (klr_argmin_refined).  Returns (best, cycles, status)."""
+    import torch
+    n_q = q_N.numel()
+    if out is None:
+        out = (torch.empty(n_q, dtype=torch.int32, device=q_N.device),
+               torch.empty(n_q, dtype=torch.float32, device=q_N.device),
+               torch.empty(n_q, dtype=torch.int32, device=q_N.device))
+    best, cyc, st = out
+    q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+    _check("klr_argmin_refined",
+           _lib.klr_argmin_refined(ctx._h, ctypes.byref(prog), ctypes.byref(hw), _ptr(cfg),
+                                   cfg.shape[0], ctypes.byref(q), _ptr(cycles_table), float(eps),
+                                   _ptr(best), _ptr(cyc), _ptr(st), _stream(stream)))
     return out
 
 

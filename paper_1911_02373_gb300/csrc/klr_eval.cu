@@ -697,6 +697,50 @@ klr_status launch_eval(Context* c, EvalParams& P, bool f64, cudaStream_t stream)
 }
 
 
+// Section IV, step 5's refinement from a cycles table: one warp per kernel
+// (the kernel's warps per SM for every shape staged once), one lane per query.
+constexpr int kRefineWarps = 4;
+__global__ void __launch_bounds__(32 * kRefineWarps)
+refine_kernel(const __grid_constant__ EvalParams P, const float* __restrict__ table, double eps) {
+    __shared__ int warps_s[kRefineWarps][kMaxCfg];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int* W = warps_s[wib];
+    for (int64_t k = (int64_t)blockIdx.x * kRefineWarps + wib; k < P.n_kernels;
+         k += (int64_t)gridDim.x * kRefineWarps) {
+        const int R = P.regs[k], Z = P.smem[k];
+        for (int c = lane; c < P.n_cfg; c += 32) {
+            const long long T = (long long)P.cfg[3 * c] * P.cfg[3 * c + 1] * P.cfg[3 * c + 2];
+            int B = active_blocks(T, R, Z, P);
+            if (T > P.T_max) B = 0;
+            W[c] = (int)min((long long)B * T / 32, (long long)P.W_max);
+        }
+        __syncwarp();
+        for (int64_t q = P.q_off[k] + lane; q < P.q_off[k + 1]; q += 32) {
+            const float* row = table + q * P.n_cfg;
+            float lo = INFINITY;
+            int first = -1;
+            for (int c = 0; c < P.n_cfg; ++c)
+                if (row[c] < lo) { lo = row[c]; first = c; }
+            int best = first, st = 0;
+            if (first < 0) {
+                st = KLR_Q_NONE_FEASIBLE;
+            } else {
+                const double thr = (double)lo * (1.0 + eps);
+                for (int c = 0; c < P.n_cfg; ++c) {
+                    const float v = row[c];
+                    if (!((double)v <= thr) || c == best) continue;
+                    if (W[c] > W[best] || (W[c] == W[best] && v < row[best])) best = c;
+                }
+                if (best != first) st = KLR_Q_REFINED;
+            }
+            P.best[q] = best;
+            reinterpret_cast<float*>(P.best_cycles)[q] = best >= 0 ? row[best] : INFINITY;
+            if (P.q_status) P.q_status[q] = st;
+        }
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Runtime history (Section III-B: the tool keeps a history of its decisions
 // so that later launches of the same kernel at the same size get the result
@@ -1036,6 +1080,30 @@ klr_status klr_argmin_history(klr_ctx* ctx, klr_history* hist, const klr_program
     tie_kernel<<<tgrid, 128, 0, stream>>>(P);
     KLR_CHECK_CUDA(cudaGetLastError());
     history_insert_kernel<<<grid, 256, 0, stream>>>(P, *h, done);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+klr_status klr_argmin_refined(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
+                              const int32_t* cfg, int n_cfg, const klr_queries* q,
+                              const float* cycles_table, double eps, int32_t* best_idx,
+                              float* best_cycles, int32_t* q_status, void* stream_) {
+    KLR_REQUIRE(ctx, "klr_argmin_refined: NULL context");
+    KLR_REQUIRE(std::isfinite(eps) && eps >= 0.0, "klr_argmin_refined: eps must be >= 0");
+    Context* c = reinterpret_cast<Context*>(ctx);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    EvalParams P;
+    klr_status st = prepare(c, prog, hw, cfg, n_cfg, q, KLR_F32, P);
+    if (st != KLR_OK) return st;
+    if (P.n_q == 0 || P.n_kernels == 0) return KLR_OK;
+    KLR_REQUIRE(cycles_table && best_idx && best_cycles, "klr_argmin_refined: NULL array");
+    KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    P.best = best_idx;
+    P.best_cycles = best_cycles;
+    P.q_status = q_status;
+    const int grid = (int)std::min<int64_t>((P.n_kernels + kRefineWarps - 1) / kRefineWarps,
+                                            (int64_t)c->n_sm * 16);
+    refine_kernel<<<grid, 32 * kRefineWarps, 0, stream>>>(P, cycles_table, eps);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
 }

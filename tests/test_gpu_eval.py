@@ -169,3 +169,58 @@ def test_candidate_rerank_matches_oracle(klr, ctx):
         else:
             assert best[r] in cs and table[r, best[r]] <= bv * (1 + 4e-4)
     assert strict > 0.9 * n_q
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.02, 0.2])
+def test_refined_choice_matches_oracle(klr, ctx, eps):
+    """klr_argmin_refined on klr_eval's table against the oracle's refinement of
+    its own FP64 table, wherever the decision is clear of the FP32/FP64
+    difference (1e-4 relative) at the margin and between the finalists."""
+    from oracle import program as oprog
+    gt = G.make_program(6, 48)
+    coef = gt.coef.astype(np.float32)
+    q = W.queries_per_kernel(48, W.log_spaced_sizes(64))
+    ct = torch.tensor(coef).cuda()
+    prog = G.gpu_program(klr, ct, gt, torch)
+    hw = klr.make_hw(W.HARDWARE)
+    cfg_np = klr.enumerate_configs(2)
+    cfg = torch.tensor(cfg_np).cuda()
+    qo, qn = torch.tensor(q.offsets).cuda(), torch.tensor(q.sizes).cuda()
+    table = ctx.eval(prog, hw, cfg, qo, qn, out_dtype=klr.F32)
+    best, cyc, st = klr.argmin_refined(ctx, prog, hw, cfg, qo, qn, table, eps)
+    torch.cuda.synchronize()
+    best, cyc, st = best.cpu().numpy(), cyc.cpu().numpy(), st.cpu().numpy()
+    tab = table.cpu().numpy().astype(np.float64)
+    ref = G.oracle_choose(coef, gt, q.offsets, q.sizes)
+    otab = ref["cycles"].reshape(len(q.sizes), -1)
+    configs = [tuple(int(v) for v in c) for c in cfg_np[:, :2]]
+    strict = 0
+    for k in range(48):
+        _, Wk = oprog.kernel_occupancy(int(gt.regs[k]), int(gt.smem[k]), configs, W.HARDWARE)
+        for r in range(int(q.offsets[k]), int(q.offsets[k + 1])):
+            row = otab[r]
+            want = oprog.refine(row[None, :], Wk, eps)[0]
+            fin = np.isfinite(row)
+            if want < 0:
+                assert best[r] == -1 and (st[r] & klr.Q_NONE_FEASIBLE)
+                continue
+            # every GPU choice is valid on the GPU's own table
+            gfin = np.isfinite(tab[r])
+            glo = tab[r][gfin].min()
+            assert tab[r, best[r]] <= glo * (1 + eps) and cyc[r] == np.float32(tab[r, best[r]])
+            near = [c for c in range(len(row)) if fin[c] and row[c] <= row[fin].min() * (1 + eps)]
+            lo = row[fin].min()
+            thr = lo * (1 + eps)
+            # entries that FP32 rounding could move across the margin (the
+            # least itself is always inside)
+            clear_margin = not np.any(fin & (np.abs(row - thr) <= 1e-4 * thr) & (row > lo))
+            others = [c for c in near if c != want]
+            clear_pick = all(Wk[c] < Wk[want] or abs(row[c] - row[want]) > 1e-4 * row[want]
+                             for c in others)
+            if clear_margin and clear_pick:
+                strict += 1
+                assert best[r] == want, (r, best[r], want)
+                if np.sum(fin & (row <= lo * (1 + 1e-4))) == 1:      # unambiguous least cycles
+                    first = int(np.argmin(np.where(fin, row, np.inf)))
+                    assert bool(st[r] & klr.Q_REFINED) == (want != first)
+    assert strict > 0.8 * len(q.sizes)
