@@ -335,21 +335,39 @@ def run_klr(args):
     fit_status = fst.cpu().numpy()
     q_status = qst.cpu().numpy()
 
-    # end to end through the public API: pinned host inputs in, results out
+    # end to end through the public API: pinned host inputs in, results out,
+    # every step.  The inputs of step i+1 are copied on a second stream into
+    # a second set of device buffers while step i computes.
     E = args.e2e_steps
     best_h = torch.empty(n_q, dtype=torch.int32).pin_memory()
     cyc_h = torch.empty(n_q, dtype=torch.float32).pin_memory()
+    bufs = [(off, x, y, qo, qn),
+            tuple(torch.empty_like(t_) for t_ in (off, x, y, qo, qn))]
+    hosts = (off_h, x_h, y_h, qo_h, qn_h)
+    copy_stream = torch.cuda.Stream(device=dev)
+    h2d_done = [torch.cuda.Event() for _ in range(2)]
+    used = [torch.cuda.Event() for _ in range(2)]
+
+    def h2d(i):
+        with torch.cuda.stream(copy_stream):
+            if i >= 2:
+                copy_stream.wait_event(used[i % 2])
+            for d_, h_ in zip(bufs[i % 2], hosts):
+                d_.copy_(h_, non_blocking=True)
+            h2d_done[i % 2].record(copy_stream)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(E):
-        off.copy_(off_h, non_blocking=True)
-        x.copy_(x_h, non_blocking=True)
-        y.copy_(y_h, non_blocking=True)
-        qo.copy_(qo_h, non_blocking=True)
-        qn.copy_(qn_h, non_blocking=True)
-        fit(x, y, off)
-        choose(qo, qn)
+    copy_stream.wait_event(e0)
+    h2d(0)
+    for i in range(E):
+        if i + 1 < E:
+            h2d(i + 1)
+        stream.wait_event(h2d_done[i % 2])
+        o_, x_, y_, qo_, qn_ = bufs[i % 2]
+        fit(x_, y_, o_)
+        choose(qo_, qn_)
+        used[i % 2].record(stream)
         best_h.copy_(best, non_blocking=True)
         cyc_h.copy_(cyc, non_blocking=True)
     e1.record(stream)
