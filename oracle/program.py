@@ -58,13 +58,13 @@ def kernel_occupancy(regs: int, smem: int, configs, hw):
 
 
 def evaluate_kernel(coef8, regs, smem, sizes, configs, hw, metric_lo, metric_scale,
-                    n_vars, degree, n_scale_log2, b_scale_log2):
+                    n_vars, degree, n_scale_log2, b_scale_log2, var_degree=None):
     """Cycles of every (query size, configuration) of one kernel.
 
     Returns dict of arrays shaped (n_sizes, n_cfg): cycles (inf where not
     meaningful or invalid), meaningful, valid, branch, boundary (margin of the
     branch decisions)."""
-    exps = rational.monomial_exponents(n_vars, degree)
+    exps = rational.monomial_exponents(n_vars, degree, var_degree)
     cfg = np.array(configs, dtype=np.int64)                  # (C, dims)
     N = np.asarray(sizes, dtype=np.int64)                    # (Q,)
     T = np.prod(cfg, axis=1)                                 # (C,)
@@ -161,7 +161,8 @@ def choose(program: dict, hw: dict, configs, q_offsets, q_sizes, kernels=None):
         ev = evaluate_kernel(program["coef"][k], program["regs"][k], program["smem"][k],
                              q_sizes[a:b], configs, hw, program["metric_lo"],
                              program["metric_scale"], program["n_vars"], program["degree"],
-                             program["n_scale_log2"], program["b_scale_log2"])
+                             program["n_scale_log2"], program["b_scale_log2"],
+                             program.get("var_degree"))
         best, val, margin = argmin(ev["cycles"])
         st = np.where(np.any(ev["meaningful"] & ~ev["valid"], axis=1), Q_BAD_METRIC, Q_OK)
         st = st | np.where(best < 0, Q_NONE_FEASIBLE, 0)

@@ -44,8 +44,16 @@ RANK_TOL = 1e-12
 SIGN_TOL = 1e-12
 
 
-def monomial_exponents(n_vars: int, degree: int) -> list:
-    """Exponent tuples of all monomials of total degree <= degree, graded lex."""
+def monomial_exponents(n_vars: int, degree: int, var_degree=None) -> list:
+    """Exponent tuples of the basis, graded lex: every monomial of total degree
+    <= degree, or, with per-variable bounds var_degree (Section V-E: the
+    degree of each variable bounded separately), every monomial whose exponent
+    of variable v is <= var_degree[v]."""
+    if var_degree is not None and var_degree[0] > 0:
+        bounds = [int(var_degree[v]) for v in range(n_vars)]
+        out = [e for e in itertools.product(*[range(b, -1, -1) for b in bounds])]
+        # by total degree, then decreasing exponent tuple
+        return sorted((tuple(e) for e in out), key=lambda e: (sum(e), [-v for v in e]))
     out = []
     for d in range(degree + 1):
         for e in itertools.product(range(d, -1, -1), repeat=n_vars):
@@ -110,14 +118,14 @@ def normalise(c: np.ndarray, m: int) -> np.ndarray:
 
 
 def fit_one(x: np.ndarray, y: np.ndarray, n_vars: int, degree: int,
-            n_scale_log2: int, b_scale_log2: int):
+            n_scale_log2: int, b_scale_log2: int, var_degree=None):
     """Fit one rational function.
 
     x: (n_vars, S) raw sample coordinates, y: (S,) metric values.
     Returns (coef (2m,), status, diag) with diag = (sigma_min/sigma_max,
     sigma_2nd_min/sigma_max, rms of A c over samples).
     """
-    exps = monomial_exponents(n_vars, degree)
+    exps = monomial_exponents(n_vars, degree, var_degree)
     m = len(exps)
     u = 2 * m
     y = np.asarray(y, dtype=np.float64)
@@ -143,20 +151,21 @@ def fit_one(x: np.ndarray, y: np.ndarray, n_vars: int, degree: int,
     return c, status, diag
 
 
-def fit_batch(offsets, x, y, n_vars, degree, n_scale_log2, b_scale_log2, fits=None):
+def fit_batch(offsets, x, y, n_vars, degree, n_scale_log2, b_scale_log2, fits=None,
+              var_degree=None):
     """Fit every fit f (or the subset ``fits``) of a CSR batch.
 
     offsets: (F+1,), x: (n_vars, S), y: (S,).  Returns coef (len, 2m), status,
     diag (len, 3)."""
     fits = range(len(offsets) - 1) if fits is None else fits
-    m = n_monomials(n_vars, degree)
+    m = len(monomial_exponents(n_vars, degree, var_degree))
     coef = np.zeros((len(fits), 2 * m))
     status = np.zeros(len(fits), dtype=np.int32)
     diag = np.zeros((len(fits), 3))
     for i, f in enumerate(fits):
         a, b = int(offsets[f]), int(offsets[f + 1])
         coef[i], status[i], diag[i] = fit_one(x[:, a:b], y[a:b], n_vars, degree,
-                                              n_scale_log2, b_scale_log2)
+                                              n_scale_log2, b_scale_log2, var_degree)
     return coef, status, diag
 
 
@@ -165,3 +174,17 @@ def predict(coef: np.ndarray, xs: np.ndarray, exps: list) -> np.ndarray:
     m = len(exps)
     phi = monomials(xs, exps)
     return np.sum(phi * coef[..., :m], axis=-1) / np.sum(phi * coef[..., m:], axis=-1)
+
+
+def relative_rms(coef: np.ndarray, x: np.ndarray, y: np.ndarray, n_vars: int, degree: int,
+                 n_scale_log2: int, b_scale_log2: int, var_degree=None) -> float:
+    """Root mean square of (p/q - y) / y over samples (x (n_vars, S) raw, y (S,)):
+    the held-out error by which a basis is chosen."""
+    exps = monomial_exponents(n_vars, degree, var_degree)
+    xs = scale_variables(np.asarray(x, dtype=np.float64).T, n_scale_log2, b_scale_log2)
+    y = np.asarray(y, dtype=np.float64)
+    if y.size == 0:
+        return 0.0
+    g = predict(np.asarray(coef, dtype=np.float64), xs, exps)
+    return float(np.sqrt(np.mean(((g - y) / y) ** 2)))
+

@@ -6,6 +6,7 @@
 * equilibration, sign and rank-deficiency rules;
 * degree 0 against its closed form.
 """
+import itertools
 import math
 
 import numpy as np
@@ -154,3 +155,56 @@ def test_sign_rule_and_sample_permutation():
     xs = rational.scale_variables(fb.x[:, a:b].T, 23, 10)
     assert np.allclose(rational.predict(c3, xs, exps), 2 * rational.predict(c1, xs, exps),
                        rtol=1e-9)
+
+
+def test_box_basis_is_the_per_variable_bounds():
+    from oracle import rational
+    for n_vars, vd in ((3, (1, 1, 1)), (3, (2, 1, 1)), (3, (3, 1, 0)), (4, (2, 1, 1, 1))):
+        exps = rational.monomial_exponents(n_vars, 0, vd)
+        want = set(itertools.product(*[range(d + 1) for d in vd]))
+        assert set(exps) == want and len(exps) == len(want)
+        keys = [(sum(e), tuple(-v for v in e)) for e in exps]
+        assert keys == sorted(keys)                 # graded, then decreasing tuples
+        assert exps[0] == (0,) * n_vars
+    # the box (d, d, d) contains the total-degree-d basis
+    assert set(rational.monomial_exponents(3, 2)) <= set(rational.monomial_exponents(3, 0, (2, 2, 2)))
+
+
+def test_box_basis_exact_recovery():
+    from oracle import rational
+    vd = (2, 1, 1)
+    fb = W.fit_batch(51, 2, 150, degree=2, var_degree=vd, dtype=np.float64)
+    coef, st, _ = rational.fit_batch(fb.offsets, fb.x, fb.y, 3, 2, 23, 10, var_degree=vd)
+    m = len(rational.monomial_exponents(3, 0, vd))
+    assert coef.shape == (16, 2 * m) and np.all(st == 0)
+    truth = fb.truth.coef.reshape(16, 2 * m)
+    truth = truth / np.linalg.norm(truth, axis=1, keepdims=True)
+    truth *= np.sign(truth[:, m:m + 1])
+    assert np.max(np.abs(coef - truth)) < 1e-9
+
+
+def test_relative_rms_closed_form_and_selection():
+    from oracle import rational
+    # p/q = (1 + x_N) / 2 on the constant-plus-N basis of the box (1, 0, 0)
+    vd = (1, 0, 0)
+    exps = rational.monomial_exponents(3, 0, vd)
+    assert exps == [(0, 0, 0), (1, 0, 0)]
+    coef = np.array([1.0, 1.0, 2.0, 0.0])
+    N = np.array([2.0 ** 20, 2.0 ** 22, 2.0 ** 23])
+    x = np.vstack([N, np.full(3, 32.0), np.full(3, 8.0)])
+    g = (1 + N / 2.0 ** 23) / 2
+    y = g * np.array([1.0, 1.1, 0.9])
+    want = math.sqrt(np.mean(((g - y) / y) ** 2))
+    assert abs(rational.relative_rms(coef, x, y, 3, 0, 23, 10, vd) - want) < 1e-15
+    assert rational.relative_rms(coef, x, g, 3, 0, 23, 10, vd) == 0.0
+    # held-out selection: the true box fits the held-out samples better than a
+    # smaller box, and as well as a larger one
+    fb = W.fit_batch(52, 1, 400, degree=2, var_degree=(2, 1, 1), dtype=np.float64)
+    f = 3
+    a, b = int(fb.offsets[f]), int(fb.offsets[f + 1])
+    tr, ho = slice(a, a + 300), slice(a + 300, b)
+    errs = {}
+    for cand in ((1, 1, 1), (2, 1, 1), (3, 1, 1)):
+        c, _, _ = rational.fit_one(fb.x[:, tr], fb.y[tr], 3, 0, 23, 10, cand)
+        errs[cand] = rational.relative_rms(c, fb.x[:, ho], fb.y[ho], 3, 0, 23, 10, cand)
+    assert errs[(2, 1, 1)] < 1e-9 and errs[(3, 1, 1)] < 1e-9 and errs[(1, 1, 1)] > 1e-4

@@ -123,15 +123,21 @@ def log_spaced_sizes(count: int, lo_log2: int = 8, hi_log2: int = 23) -> np.ndar
     return np.floor(v + 0.5).astype(np.int64)
 
 
-def term_exponents(n_vars: int, degree: int) -> np.ndarray:
-    """Exponents of the ground-truth polynomial terms: total degree <= degree, by
+def term_exponents(n_vars: int, degree: int, var_degree=None) -> np.ndarray:
+    """Exponents of the ground-truth polynomial terms: total degree <= degree
+    (or, with var_degree, exponent <= var_degree[v] in variable v), by total
     degree, then decreasing lexicographic order (the coefficient order the
     library documents)."""
+    box = var_degree is not None and var_degree[0] > 0
+    top = sum(int(v) for v in var_degree[:n_vars]) if box else degree
     out = []
-    for d in range(degree + 1):
+    for d in range(top + 1):
         for e in itertools.product(range(d, -1, -1), repeat=n_vars):
-            if sum(e) == d:
-                out.append(e)
+            if sum(e) != d:
+                continue
+            if box and any(e[v] > var_degree[v] for v in range(n_vars)):
+                continue
+            out.append(e)
     return np.array(out, dtype=np.int64)
 
 
@@ -227,6 +233,7 @@ class GroundTruth:
     regs: np.ndarray          # (n_kernels,) int32, registers per thread
     smem: np.ndarray          # (n_kernels,) int32, shared memory bytes per block
     attempts: np.ndarray = field(default=None)  # redraws used per (kernel, metric)
+    var_degree: tuple = None  # per-variable degree bounds of the basis, or None
 
     @property
     def n_terms(self) -> int:
@@ -234,7 +241,7 @@ class GroundTruth:
 
     def values(self, kernel: np.ndarray, metric: np.ndarray, x: np.ndarray) -> np.ndarray:
         """g(x) = p(x)/q(x) for rows (kernel[i], metric[i], x[i] unscaled)."""
-        exps = term_exponents(self.n_vars, self.degree)
+        exps = term_exponents(self.n_vars, self.degree, self.var_degree)
         xs = scale_points(x, self.n_scale_log2, self.b_scale_log2)
         phi = _monomials(xs, exps)
         c = self.coef[kernel, metric]
@@ -252,12 +259,14 @@ def scale_points(x: np.ndarray, n_scale_log2: int, b_scale_log2: int) -> np.ndar
 
 def ground_truth(seed: int, n_kernels: int, n_vars: int = 3, degree: int = 2,
                  n_lo_log2: int = 8, n_hi_log2: int = 23, b_scale_log2: int = 10,
-                 q_floor: float = 0.5, max_attempts: int = 64, kernels=None) -> GroundTruth:
+                 q_floor: float = 0.5, max_attempts: int = 64, kernels=None,
+                 var_degree=None) -> GroundTruth:
     """Coefficients U(-1,1), +3 on the denominator's constant term, redrawn
     (next attempt id) until min q >= q_floor over every block shape and every
     N in [2^n_lo_log2, 2^n_hi_log2].  ``kernels`` selects a subset of the
-    n_kernels kernel ids (same values as in the full set)."""
-    exps = term_exponents(n_vars, degree)
+    n_kernels kernel ids (same values as in the full set).  ``var_degree``:
+    draw in the per-variable-bounds basis instead of the total-degree one."""
+    exps = term_exponents(n_vars, degree, var_degree)
     m = len(exps)
     shapes = block_shape_exponents(n_vars - 1)
     xb = np.ldexp(1.0, shapes - b_scale_log2)
@@ -288,7 +297,8 @@ def ground_truth(seed: int, n_kernels: int, n_vars: int = 3, degree: int = 2,
     return GroundTruth(n_vars, degree, n_hi_log2, b_scale_log2,
                        coef.reshape(n_kernels, N_METRICS, 2 * m),
                        regs.astype(np.int32), smem.astype(np.int32),
-                       attempts.reshape(n_kernels, N_METRICS))
+                       attempts.reshape(n_kernels, N_METRICS),
+                       None if var_degree is None else tuple(int(v) for v in var_degree))
 
 
 # ---------------------------------------------------------------------------
@@ -315,7 +325,7 @@ class FitBatch:
 def fit_batch(seed: int, n_kernels: int, counts, n_vars: int = 3, degree: int = 2,
               n_lo_log2: int = 8, n_hi_log2: int = 23, b_scale_log2: int = 10,
               noise: float = 0.0, dtype=np.float32, replace: bool | None = None,
-              truth: GroundTruth | None = None, kernels=None) -> FitBatch:
+              truth: GroundTruth | None = None, kernels=None, var_degree=None) -> FitBatch:
     """Samples for every (kernel, metric) of a seeded ground truth.
 
     ``counts``: an int (same count for every fit) or a (lo, hi) pair, meaning a
@@ -326,7 +336,7 @@ def fit_batch(seed: int, n_kernels: int, counts, n_vars: int = 3, degree: int = 
     """
     if truth is None:
         truth = ground_truth(seed, n_kernels, n_vars, degree, n_lo_log2, n_hi_log2,
-                             b_scale_log2, kernels=kernels)
+                             b_scale_log2, kernels=kernels, var_degree=var_degree)
     kid = np.arange(n_kernels) if kernels is None else np.asarray(kernels, dtype=np.int64)
     n_fits = len(kid) * N_METRICS
     # global fit ids: the streams of a fit do not depend on which others are drawn
@@ -373,7 +383,7 @@ def fit_batch(seed: int, n_kernels: int, counts, n_vars: int = 3, degree: int = 
     gx[:, 0] = np.ldexp(1.0, gk)
     gx[:, 1:] = np.ldexp(1.0, np.tile(shapes, (n_sizes, 1)))
     phi = _monomials(scale_points(gx, n_hi_log2, b_scale_log2),
-                     term_exponents(n_vars, degree))
+                     term_exponents(n_vars, degree, truth.var_degree))
     m = phi.shape[1]
     cf = truth.coef.reshape(n_fits, 2 * m)
     y = np.empty(S)
