@@ -208,3 +208,16 @@ def test_relative_rms_closed_form_and_selection():
         c, _, _ = rational.fit_one(fb.x[:, tr], fb.y[tr], 3, 0, 23, 10, cand)
         errs[cand] = rational.relative_rms(c, fb.x[:, ho], fb.y[ho], 3, 0, 23, 10, cand)
     assert errs[(2, 1, 1)] < 1e-9 and errs[(3, 1, 1)] < 1e-9 and errs[(1, 1, 1)] > 1e-4
+
+
+def test_choose_basis_rule():
+    from oracle import rational
+    sizes = [8, 12, 16]
+    E = np.array([[1e-3, 2e-12, 1e-12],      # both larger bases exact: the smaller of them
+                  [9.3e-4, 9.4e-4, 9e-4],    # within 5% + floor of the least: the smallest
+                  [1e-3, 5e-4, 4e-4],        # 5e-4 > 4.2e-4: only the largest qualifies
+                  [np.nan, np.inf, 3e-3],    # non-finite never qualifies
+                  [np.nan, np.nan, np.nan]])
+    assert list(rational.choose_basis(E, sizes)) == [1, 0, 2, 2, -1]
+    # equal sizes: the earlier candidate
+    assert list(rational.choose_basis([[1e-6, 1e-6]], [8, 8])) == [0]
