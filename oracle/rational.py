@@ -190,13 +190,15 @@ def relative_rms(coef: np.ndarray, x: np.ndarray, y: np.ndarray, n_vars: int, de
 
 
 
-def choose_basis(errors: np.ndarray, sizes, tol: float = 0.05, floor: float = 1e-9) -> np.ndarray:
+def choose_basis(errors: np.ndarray, sizes, tol: float = 0.05, floor: float = 1e-6) -> np.ndarray:
     """Per fit (row of errors, one column per candidate basis): the candidate
     with the fewest monomials (sizes; ties by column order) among those whose
     held-out error is <= (1 + tol) x the least error + floor.  A reading of
     Section V-E, which leaves the choice of degree bounds open: prefer the
     smaller model unless a larger one predicts held-out samples clearly
-    better.  Non-finite errors never qualify (-1 when none is finite)."""
+    better; errors below the floor (default 1e-6, above the relative rounding
+    of FP32 samples) count as equal.  Non-finite errors never qualify (-1
+    when none is finite)."""
     errors = np.atleast_2d(np.asarray(errors, dtype=np.float64))
     out = np.full(errors.shape[0], -1, dtype=np.int64)
     for f in range(errors.shape[0]):
