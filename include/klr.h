@@ -149,6 +149,13 @@ typedef struct klr_fit_batch {
     const void* y;         /* device, y[s]                                    */
     int32_t precision;     /* KLR_FIT_*                                        */
     int32_t refine_iters;  /* FP64 refinement passes over the samples, 0..8   */
+    int32_t var_degree[4]; /* all 0: the total-degree basis of `degree`; else
+                            * var_degree[0] >= 1: the basis of every monomial
+                            * with exponent <= var_degree[v] in variable v
+                            * (0..3 each, at most 35 monomials; Section V-E's
+                            * per-variable degree bounds); `degree` is then
+                            * ignored.  Ordered by total degree, then by
+                            * decreasing exponent tuple.                       */
 } klr_fit_batch;
 
 /* coef_out: device, n_fits x 2m elements of coef_dtype (row-major).
@@ -172,6 +179,15 @@ klr_status klr_fit_gram(klr_ctx* ctx, const klr_fit_batch* batch, void* stream);
 klr_status klr_fit_solve(klr_ctx* ctx, const klr_fit_batch* batch, void* coef_out,
                          int32_t coef_dtype, int32_t* fit_status, double* fit_diag,
                          void* stream);
+
+/* Held-out error of fitted coefficients (for choosing among bases, Section
+ * V-E): per fit, sqrt(mean over its samples s of (((p/q)(x_s) - y_s) / y_s)^2)
+ * in FP64, with the batch's basis (degree or var_degree), scaling and CSR
+ * samples (precision and refine_iters are ignored).  coef: device, n_fits x 2m
+ * of coef_dtype.  err_out: device, n_fits doubles (0 for a fit without
+ * samples; NaN where q vanishes or a sample is not finite). */
+klr_status klr_fit_heldout(klr_ctx* ctx, const klr_fit_batch* batch, const void* coef,
+                           int32_t coef_dtype, double* err_out, void* stream);
 
 /* ---- E2-E5: the rational program ----------------------------------------- */
 
@@ -209,6 +225,7 @@ typedef struct klr_program {
     const int32_t* smem;   /* device, n_kernels: shared memory bytes/block Z  */
     double metric_lo[8];
     double metric_scale[8];
+    int32_t var_degree[4]; /* the basis of the fits, as in klr_fit_batch      */
 } klr_program;
 
 /* Queries, grouped by kernel: kernel k asks for data sizes

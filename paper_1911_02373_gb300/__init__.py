@@ -36,7 +36,7 @@ ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last
                "klr_autotune_argmin", "klr_tune_export", "klr_tune_import", "klr_fit_gram",
                "klr_fit_solve", "klr_mlp_query_targets", "klr_history_create",
                "klr_history_clear", "klr_history_destroy", "klr_argmin_history",
-               "klr_argmin_refined")
+               "klr_argmin_refined", "klr_fit_heldout")
 #: largest query count klr_argmin_noalloc accepts
 ARGMIN_NOALLOC_MAX_QUERIES = 65536
 
@@ -54,7 +54,8 @@ class FitBatch(ctypes.Structure):
                 ("b_scale_log2", ctypes.c_int32), ("sample_dtype", ctypes.c_int32),
                 ("offsets", ctypes.c_void_p), ("x", ctypes.c_void_p),
                 ("x_stride", ctypes.c_int64), ("y", ctypes.c_void_p),
-                ("precision", ctypes.c_int32), ("refine_iters", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
+                ("var_degree", ctypes.c_int32 * 4)]
 
 
 class Hw(ctypes.Structure):
@@ -71,7 +72,8 @@ class Program(ctypes.Structure):
                 ("degree", ctypes.c_int32), ("n_scale_log2", ctypes.c_int32),
                 ("b_scale_log2", ctypes.c_int32), ("coef_dtype", ctypes.c_int32),
                 ("coef", ctypes.c_void_p), ("regs", ctypes.c_void_p), ("smem", ctypes.c_void_p),
-                ("metric_lo", ctypes.c_double * 8), ("metric_scale", ctypes.c_double * 8)]
+                ("metric_lo", ctypes.c_double * 8), ("metric_scale", ctypes.c_double * 8),
+                ("var_degree", ctypes.c_int32 * 4)]
 
 
 class Queries(ctypes.Structure):
@@ -112,6 +114,7 @@ for _name, _args in {
                             ctypes.POINTER(Queries), _vp, _vp, ctypes.c_int32, _vp, _vp, _vp,
                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), _vp],
     "klr_fit_gram": [_vp, ctypes.POINTER(FitBatch), _vp],
+    "klr_fit_heldout": [_vp, ctypes.POINTER(FitBatch), _vp, ctypes.c_int32, _vp, _vp],
     "klr_history_create": [_vp, ctypes.c_int32, ctypes.POINTER(_vp)],
     "klr_history_clear": [_vp, _vp],
     "klr_argmin_refined": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
@@ -207,18 +210,20 @@ class Context:
     # -- F1-F4 ---------------------------------------------------------------
     def fit(self, offsets, x, y, *, n_vars, degree, n_scale_log2, b_scale_log2,
             precision=FIT_DF32, refine_iters=0, coef_dtype=None, out=None, stream=None,
-            autotune=False, stage=None):
+            autotune=False, stage=None, var_degree=None):
         """Fit every CSR fit.  offsets: int64 (F+1,); x: (n_vars, S) float32/64
         rows (N, b0, b1[, b2]); y: (S,) same dtype.  Returns (coef, status, diag)
         device tensors; ``out`` may pass preallocated (coef, status, diag).
         autotune=True times the candidate launch shapes first (klr_autotune_fit)
         and records (choice, ms) in ``self.last_tune``.  stage='gram' or
-        'solve' runs one stage only (klr_fit_gram / klr_fit_solve)."""
+        'solve' runs one stage only (klr_fit_gram / klr_fit_solve).
+        var_degree: per-variable degree bounds of the basis (else the
+        total-degree basis of ``degree``)."""
         import torch
         sdt = F64 if x.dtype == torch.float64 else F32
         cdt = sdt if coef_dtype is None else coef_dtype
         n_fits = offsets.numel() - 1
-        m = _n_monomials(n_vars, degree)
+        m = _n_monomials(n_vars, degree, var_degree)
         if out is None:
             coef = torch.empty((n_fits, 2 * m), device=x.device,
                                dtype=torch.float64 if cdt == F64 else torch.float32)
@@ -229,6 +234,7 @@ class Context:
         b = FitBatch(n_fits, n_vars, degree, n_scale_log2, b_scale_log2, sdt,
                      offsets.data_ptr(), x.data_ptr(), x.stride(0), y.data_ptr(),
                      precision, refine_iters)
+        _set_var_degree(b, var_degree)
         if stage == "gram":
             _check("klr_fit_gram", _lib.klr_fit_gram(self._h, ctypes.byref(b), _stream(stream)))
         elif stage == "solve":
@@ -247,6 +253,23 @@ class Context:
             _check("klr_fit", _lib.klr_fit(self._h, ctypes.byref(b), _ptr(coef), cdt,
                                            _ptr(status), _ptr(diag), _stream(stream)))
         return coef, status, diag
+
+    def fit_heldout(self, offsets, x, y, coef, *, n_vars, degree, n_scale_log2, b_scale_log2,
+                    var_degree=None, out=None, stream=None):
+        """Per fit, the RMS relative error of coef on the CSR samples
+        (klr_fit_heldout); a float64 device tensor."""
+        import torch
+        sdt = F64 if x.dtype == torch.float64 else F32
+        cdt = F64 if coef.dtype == torch.float64 else F32
+        n_fits = offsets.numel() - 1
+        if out is None:
+            out = torch.empty(n_fits, device=x.device, dtype=torch.float64)
+        b = FitBatch(n_fits, n_vars, degree, n_scale_log2, b_scale_log2, sdt,
+                     offsets.data_ptr(), x.data_ptr(), x.stride(0), y.data_ptr(), FIT_FP64, 0)
+        _set_var_degree(b, var_degree)
+        _check("klr_fit_heldout", _lib.klr_fit_heldout(self._h, ctypes.byref(b), _ptr(coef), cdt,
+                                                       _ptr(out), _stream(stream)))
+        return out
 
     # -- tuned launch shapes -------------------------------------------------
     def tune_export(self):
@@ -271,11 +294,14 @@ class Context:
     # -- E1-E5 ---------------------------------------------------------------
     @staticmethod
     def program(coef, regs, smem, *, n_vars, degree, n_scale_log2, b_scale_log2,
-                metric_lo, metric_scale) -> Program:
+                metric_lo, metric_scale, var_degree=None) -> Program:
+        """The rational program of n_kernels x 8 fitted metrics (coef
+        n_kernels x 8 x 2m); var_degree: per-variable bounds of the basis."""
         import torch
         p = Program(regs.numel(), n_vars, degree, n_scale_log2, b_scale_log2,
                     F64 if coef.dtype == torch.float64 else F32,
                     coef.data_ptr(), regs.data_ptr(), smem.data_ptr())
+        _set_var_degree(p, var_degree)
         for i in range(8):
             p.metric_lo[i] = float(metric_lo[i])
             p.metric_scale[i] = float(metric_scale[i])
@@ -514,6 +540,17 @@ def argmin_noalloc(prog: Program, hw: Hw, cfg, q_offsets, q_N, out, stream=None)
     return out
 
 
-def _n_monomials(n_vars: int, degree: int) -> int:
+def _n_monomials(n_vars: int, degree: int, var_degree=None) -> int:
+    """Basis size: total degree <= degree, or per-variable bounds var_degree."""
+    if var_degree is not None and var_degree[0] > 0:
+        m = 1
+        for v in range(n_vars):
+            m *= int(var_degree[v]) + 1
+        return m
     from math import comb
     return comb(n_vars + degree, degree)
+
+
+def _set_var_degree(struct, var_degree):
+    for i in range(4):
+        struct.var_degree[i] = int(var_degree[i]) if var_degree is not None and i < len(var_degree) else 0

@@ -85,15 +85,20 @@ constexpr int kMaxMoments = 210;  // C(4 + 6, 6): monomials of degree <= 2d
 
 struct Basis {
     int n_vars;
-    int degree;
-    int m;        // basis size, degree <= d
-    int n_mom;    // monomials of degree <= 2d (the basis is its prefix)
-    uint8_t exps[kMaxMoments][kMaxVars];   // exponents, graded lex
+    int degree;   // total degree bound, or the largest total degree of a box basis
+    int box;      // 1: per-variable degree bounds
+    int d_n;      // largest exponent of N in the basis
+    int m;        // basis size
+    int n_mom;    // monomials that are products of two basis monomials (the basis first)
+    uint8_t exps[kMaxMoments][kMaxVars];   // exponents: the basis, then the other moments
     uint8_t pair[kMaxBasis][kMaxBasis];    // index of exps[i] + exps[j]
 };
 
-// Fill `b` for (n_vars, degree); false if out of range.
-bool make_basis(int n_vars, int degree, Basis* b);
+// Fill `b` for (n_vars, degree), or, when var_degree is not NULL and
+// var_degree[0] > 0, for the per-variable bounds var_degree[0..n_vars) (the
+// box basis of Section V-E); false if out of range.  Within each part,
+// monomials are ordered by total degree, then by decreasing exponent tuple.
+bool make_basis(int n_vars, int degree, const int32_t* var_degree, Basis* b);
 int n_monomials(int n_vars, int degree);
 
 // ---------------------------------------------------------------------------

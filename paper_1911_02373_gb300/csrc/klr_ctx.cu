@@ -129,38 +129,66 @@ int n_monomials(int n_vars, int degree) {
     return (int)r;
 }
 
-bool make_basis(int n_vars, int degree, Basis* b) {
-    if (n_vars < 1 || n_vars > kMaxVars || degree < 0 || degree > 3) return false;
+bool make_basis(int n_vars, int degree, const int32_t* var_degree, Basis* b) {
+    const bool box = var_degree && var_degree[0] > 0;
+    if (n_vars < 1 || n_vars > kMaxVars) return false;
+    if (!box && (degree < 0 || degree > 3)) return false;
+    if (box)
+        for (int v = 0; v < n_vars; ++v)
+            if (var_degree[v] < 0 || var_degree[v] > 3) return false;
     std::memset(b, 0, sizeof(*b));
     b->n_vars = n_vars;
-    b->degree = degree;
+    b->box = box ? 1 : 0;
     // graded: for each total degree, exponent tuples in decreasing lex order
-    std::vector<std::vector<int>> list;
-    for (int d = 0; d <= 2 * degree; ++d) {
-        std::vector<int> e(n_vars, 0);
-        // enumerate tuples with sum d in decreasing lexicographic order
+    struct Rec {
+        static void go(int pos, int left, std::vector<int>& cur,
+                       std::vector<std::vector<int>>& out) {
+            int nv = (int)cur.size();
+            if (pos == nv - 1) {
+                cur[pos] = left;
+                out.push_back(cur);
+                return;
+            }
+            for (int v = left; v >= 0; --v) {
+                cur[pos] = v;
+                go(pos + 1, left - v, cur, out);
+            }
+        }
+    };
+    int top = 2 * degree;
+    if (box) {
+        top = 0;
+        for (int v = 0; v < n_vars; ++v) top += 2 * var_degree[v];
+    }
+    auto within = [&](const std::vector<int>& t, int scale) {
+        if (!box) return true;
+        for (int v = 0; v < n_vars; ++v)
+            if (t[v] > scale * var_degree[v]) return false;
+        return true;
+    };
+    std::vector<std::vector<int>> basis, rest;
+    for (int d = 0; d <= top; ++d) {
         std::vector<std::vector<int>> level;
         std::vector<int> cur(n_vars, 0);
-        // recursive lambda over positions
-        struct Rec {
-            static void go(int pos, int left, std::vector<int>& cur,
-                           std::vector<std::vector<int>>& out) {
-                int nv = (int)cur.size();
-                if (pos == nv - 1) {
-                    cur[pos] = left;
-                    out.push_back(cur);
-                    return;
-                }
-                for (int v = left; v >= 0; --v) {
-                    cur[pos] = v;
-                    go(pos + 1, left - v, cur, out);
-                }
-            }
-        };
         Rec::go(0, d, cur, level);
-        for (auto& t : level) list.push_back(t);
-        if (d == degree) b->m = (int)list.size();
+        for (auto& t : level) {
+            const bool in_basis = box ? within(t, 1) : d <= degree;
+            if (in_basis) basis.push_back(t);
+            else if (within(t, 2)) rest.push_back(t);
+        }
     }
+    std::vector<std::vector<int>> list = basis;
+    for (auto& t : rest) list.push_back(t);
+    b->m = (int)basis.size();
+    b->degree = degree;
+    b->d_n = 0;
+    for (auto& t : basis) {
+        int s = 0;
+        for (int v = 0; v < n_vars; ++v) s += t[v];
+        if (box) b->degree = std::max(b->degree, s);
+        b->d_n = std::max(b->d_n, t[0]);
+    }
+    if (box) b->degree = std::min(b->degree, 3);
     b->n_mom = (int)list.size();
     if (b->n_mom > kMaxMoments || b->m > kMaxBasis) return false;
     for (int i = 0; i < b->n_mom; ++i)

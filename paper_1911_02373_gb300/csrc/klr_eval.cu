@@ -586,7 +586,9 @@ klr_status prepare(Context* c, const klr_program* prog, const klr_hw* hw, const 
     KLR_REQUIRE(prog && hw && q, "klr_eval/argmin: NULL program, hw or queries");
     KLR_REQUIRE(prog->n_kernels >= 0, "n_kernels < 0");
     KLR_REQUIRE(prog->n_vars == 3 || prog->n_vars == 4, "n_vars %d not 3 or 4", prog->n_vars);
-    KLR_REQUIRE(prog->degree >= 1 && prog->degree <= 3, "degree %d not in 1..3", prog->degree);
+    const bool box = prog->var_degree[0] > 0;
+    KLR_REQUIRE(box || (prog->degree >= 1 && prog->degree <= 3), "degree %d not in 1..3",
+                prog->degree);
     KLR_REQUIRE(prog->coef_dtype == KLR_F32 || prog->coef_dtype == KLR_F64, "bad coef_dtype");
     KLR_REQUIRE(out_dtype == KLR_F32 || out_dtype == KLR_F64, "bad out_dtype");
     KLR_REQUIRE(n_cfg >= 1 && n_cfg <= kMaxCfg, "n_cfg %d not in 1..%d", n_cfg, kMaxCfg);
@@ -604,12 +606,13 @@ klr_status prepare(Context* c, const klr_program* prog, const klr_hw* hw, const 
         KLR_REQUIRE(prog->coef && prog->regs && prog->smem && cfg && q->q_offsets && q->q_N,
                     "NULL device array");
     Basis basis;
-    KLR_REQUIRE(make_basis(prog->n_vars, prog->degree, &basis), "no basis");
+    KLR_REQUIRE(make_basis(prog->n_vars, prog->degree, prog->var_degree, &basis), "no basis");
     memset(&P, 0, sizeof(P));
     P.n_kernels = prog->n_kernels;
     P.n_vars = prog->n_vars;
     P.dims = prog->n_vars - 1;
-    P.degree = prog->degree;
+    // the specialised polynomials in N have the basis's largest power of N
+    P.degree = box ? basis.d_n : prog->degree;
     P.m = basis.m;
     P.u = 2 * basis.m;
     P.n_scale_log2 = prog->n_scale_log2;

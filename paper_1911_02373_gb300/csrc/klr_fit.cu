@@ -51,6 +51,7 @@ enum { ACC_FP64 = 0, ACC_DF32 = 1, ACC_FP32 = 2 };
 
 struct FitParams {
     int n_fits, n_vars, degree, m, u, n_mom;
+    int box;       // per-variable degree bounds (degree: the largest bound)
     int n_scale_log2, b_scale_log2;
     const int64_t* offsets;
     const void* x;
@@ -1941,9 +1942,12 @@ klr_status launch_moments(const FitParams& P, int n_mom, int rec, int wpb, cudaS
         KLR_CHECK_CUDA(cudaGetLastError());
         return KLR_OK;
     };
-    if (P.n_vars == 3 && P.degree == 2) return fast(moments_fast_kernel<TS, ACC, 3, 4, 4, 9>, 35);
-    if (P.n_vars == 4 && P.degree == 2) return fast(moments_fast_kernel<TS, ACC, 4, 4, 8, 9>, 70);
-    if (P.n_vars == 3 && P.degree == 3) return fast(moments_fast_kernel<TS, ACC, 3, 6, 8, 11>, 84);
+    if (!P.box && P.n_vars == 3 && P.degree == 2)
+        return fast(moments_fast_kernel<TS, ACC, 3, 4, 4, 9>, 35);
+    if (!P.box && P.n_vars == 4 && P.degree == 2)
+        return fast(moments_fast_kernel<TS, ACC, 4, 4, 8, 9>, 70);
+    if (!P.box && P.n_vars == 3 && P.degree == 3)
+        return fast(moments_fast_kernel<TS, ACC, 3, 6, 8, 11>, 84);
     const size_t smem = (size_t)Q.warp_smem * wpb;
     auto generic = [&](auto kern) -> klr_status {
         KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2031,6 +2035,48 @@ klr_status launch_solve_lane(const FitParams& P, cudaStream_t stream) {
     return KLR_OK;
 }
 
+
+// Held-out error of fitted rational functions: one warp per fit, lanes over
+// its samples, in FP64: sqrt(mean(((p/q)(x_s) - y_s) / y_s)^2).
+template <typename TS>
+__global__ void __launch_bounds__(128)
+heldout_kernel(const __grid_constant__ FitParams P, double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int f = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (f >= P.n_fits) return;
+    const int m = P.m, nv = P.n_vars;
+    const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
+    const TS* X = reinterpret_cast<const TS*>(P.x);
+    const TS* Y = reinterpret_cast<const TS*>(P.y);
+    const double sN = ldexp(1.0, -P.n_scale_log2), sB = ldexp(1.0, -P.b_scale_log2);
+    double acc = 0.0;
+    for (int64_t s = s0 + lane; s < s1; s += 32) {
+        double pw[kMaxVars][4];
+        for (int v = 0; v < nv; ++v) {
+            const double xv = (double)X[(int64_t)v * P.x_stride + s] * (v == 0 ? sN : sB);
+            pw[v][0] = 1.0;
+            for (int e = 1; e < 4; ++e) pw[v][e] = pw[v][e - 1] * xv;
+        }
+        double p = 0.0, q = 0.0;
+        for (int t = 0; t < m; ++t) {
+            double phi = 1.0;
+            for (int v = 0; v < nv; ++v) phi *= pw[v][P.exps[t][v]];
+            const double a = P.coef_f64 ? reinterpret_cast<const double*>(P.coef)[(int64_t)f * P.u + t]
+                                        : (double)reinterpret_cast<const float*>(P.coef)[(int64_t)f * P.u + t];
+            const double b = P.coef_f64 ? reinterpret_cast<const double*>(P.coef)[(int64_t)f * P.u + m + t]
+                                        : (double)reinterpret_cast<const float*>(P.coef)[(int64_t)f * P.u + m + t];
+            p += a * phi;
+            q += b * phi;
+        }
+        const double y = (double)Y[s];
+        const double r = (p / q - y) / y;
+        acc += r * r;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[f] = s1 > s0 ? sqrt(acc / (double)(s1 - s0)) : 0.0;
+}
+
 }  // namespace
 
 size_t fit_workspace_bytes(int64_t n_fits, int n_mom) {
@@ -2046,7 +2092,8 @@ uint64_t fit_tune_key(const klr_fit_batch* b) {
     const int64_t per_fit = b->n_fits > 0 ? b->x_stride / b->n_fits : 0;
     return tune_key(TUNE_FIT, {b->n_vars, b->degree, b->precision, b->sample_dtype,
                                b->refine_iters > 0, log2_bucket(b->n_fits),
-                               log2_bucket(per_fit)});
+                               log2_bucket(per_fit), b->var_degree[0], b->var_degree[1],
+                               b->var_degree[2], b->var_degree[3]});
 }
 
 }  // namespace klr
@@ -2067,7 +2114,9 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
     KLR_REQUIRE(b->n_fits >= 0, "klr_fit: n_fits < 0");
     KLR_REQUIRE(b->n_vars == 3 || b->n_vars == 4, "klr_fit: n_vars %d not 3 or 4", b->n_vars);
-    KLR_REQUIRE(b->degree >= 1 && b->degree <= 3, "klr_fit: degree %d not in 1..3", b->degree);
+    const bool box = b->var_degree[0] > 0;
+    KLR_REQUIRE(box || (b->degree >= 1 && b->degree <= 3), "klr_fit: degree %d not in 1..3",
+                b->degree);
     KLR_REQUIRE(b->sample_dtype == KLR_F32 || b->sample_dtype == KLR_F64,
                 "klr_fit: bad sample_dtype");
     KLR_REQUIRE(!(stages & STAGE_SOLVE) || coef_dtype == KLR_F32 || coef_dtype == KLR_F64,
@@ -2085,7 +2134,9 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     if (b->precision == KLR_FIT_DF32)
         KLR_REQUIRE(b->sample_dtype == KLR_F32, "klr_fit: DF32 needs KLR_F32 samples");
     Basis basis;
-    KLR_REQUIRE(make_basis(b->n_vars, b->degree, &basis), "klr_fit: no basis");
+    KLR_REQUIRE(make_basis(b->n_vars, b->degree, b->var_degree, &basis),
+                "klr_fit: no basis (per-variable bounds must be 0..3, at most %d monomials)",
+                kMaxBasis);
     const int m = basis.m, u = 2 * m;
     if (b->refine_iters > 0 && u > kRefineMaxU) {
         set_error("klr_fit: refinement supports at most %d unknowns (have %d)", kRefineMaxU, u);
@@ -2101,7 +2152,13 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     FitParams P;
     P.n_fits = b->n_fits;
     P.n_vars = b->n_vars;
+    // the moments kernel tabulates powers up to twice the largest bound
+    P.box = box ? 1 : 0;
     P.degree = b->degree;
+    if (box) {
+        P.degree = 0;
+        for (int v = 0; v < b->n_vars; ++v) P.degree = std::max(P.degree, (int)b->var_degree[v]);
+    }
     P.m = m;
     P.u = u;
     P.n_mom = basis.n_mom;
@@ -2170,7 +2227,7 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     P.mom = reinterpret_cast<double*>(reinterpret_cast<char*>(c->ws) + 256);
     P.flags = reinterpret_cast<int32_t*>(P.mom + (size_t)b->n_fits * 3 * basis.n_mom);
     P.mom_dw = b->precision != KLR_FIT_FP64;
-    const int rec = b->n_vars * (2 * b->degree + 1) + 3;
+    const int rec = b->n_vars * (2 * P.degree + 1) + 3;
     const bool s64 = b->sample_dtype == KLR_F64;
     if (stages & STAGE_GRAM) switch (b->precision) {
         case KLR_FIT_FP64:
@@ -2231,7 +2288,9 @@ extern "C" klr_status klr_autotune_fit(klr_ctx* ctx, const klr_fit_batch* b, voi
     };
     if (b->n_fits == 0) return run();
     const uint64_t key = fit_tune_key(b);
-    const int u = 2 * n_monomials(b->n_vars, b->degree);
+    Basis basis;
+    KLR_REQUIRE(make_basis(b->n_vars, b->degree, b->var_degree, &basis), "klr_autotune_fit: no basis");
+    const int u = 2 * basis.m;
     const bool tc = b->precision == KLR_FIT_TF32 || b->precision == KLR_FIT_BF16;
     const bool group = !tc && b->precision != KLR_FIT_FP64 && b->refine_iters == 0 &&
                        u <= kLaneMaxU;
@@ -2252,3 +2311,43 @@ extern "C" klr_status klr_autotune_fit(klr_ctx* ctx, const klr_fit_batch* b, voi
     const int32_t cs[3] = {(best & 0xF0) | 0, (best & 0xF0) | 1, (best & 0xF0) | 2};
     return tune_candidates(c, key, stream, cs, 3, 3, run, choice_out, ms_out);
 }
+
+extern "C" klr_status klr_fit_heldout(klr_ctx* ctx, const klr_fit_batch* b, const void* coef,
+                                      int32_t coef_dtype, double* err_out, void* stream_) {
+    KLR_REQUIRE(ctx && b, "klr_fit_heldout: NULL context or batch");
+    Context* c = reinterpret_cast<Context*>(ctx);
+    cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+    KLR_REQUIRE(b->n_fits >= 0, "klr_fit_heldout: n_fits < 0");
+    KLR_REQUIRE(b->n_vars == 3 || b->n_vars == 4, "klr_fit_heldout: n_vars %d not 3 or 4", b->n_vars);
+    KLR_REQUIRE(b->sample_dtype == KLR_F32 || b->sample_dtype == KLR_F64,
+                "klr_fit_heldout: bad sample_dtype");
+    KLR_REQUIRE(coef_dtype == KLR_F32 || coef_dtype == KLR_F64, "klr_fit_heldout: bad coef_dtype");
+    const bool box = b->var_degree[0] > 0;
+    KLR_REQUIRE(box || (b->degree >= 1 && b->degree <= 3), "klr_fit_heldout: degree %d not in 1..3",
+                b->degree);
+    if (b->n_fits == 0) return KLR_OK;
+    KLR_REQUIRE(b->offsets && b->x && b->y && coef && err_out, "klr_fit_heldout: NULL array");
+    Basis basis;
+    KLR_REQUIRE(make_basis(b->n_vars, b->degree, b->var_degree, &basis), "klr_fit_heldout: no basis");
+    KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    FitParams P{};
+    P.n_fits = b->n_fits;
+    P.n_vars = b->n_vars;
+    P.m = basis.m;
+    P.u = 2 * basis.m;
+    P.n_scale_log2 = b->n_scale_log2;
+    P.b_scale_log2 = b->b_scale_log2;
+    P.offsets = b->offsets;
+    P.x = b->x;
+    P.x_stride = b->x_stride;
+    P.y = b->y;
+    P.coef = const_cast<void*>(coef);
+    P.coef_f64 = coef_dtype == KLR_F64;
+    memcpy(P.exps, basis.exps, sizeof(P.exps));
+    const int grid = (int)(((int64_t)b->n_fits * 32 + 127) / 128);
+    if (b->sample_dtype == KLR_F64) heldout_kernel<double><<<grid, 128, 0, stream>>>(P, err_out);
+    else heldout_kernel<float><<<grid, 128, 0, stream>>>(P, err_out);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
