@@ -56,7 +56,7 @@ def parse():
                     choices=["batched", "sweep3d", "surrogate", "precision", "history"],
                     help="batched: fit + argmin (default metric); sweep3d: 3D evaluator sweep")
     ap.add_argument("--sweep-kernels", type=int, default=100000)
-    ap.add_argument("--sweep-check-kernels", type=int, default=100,
+    ap.add_argument("--sweep-check-kernels", type=int, default=1000,
                     help="kernels of the 3D sweep checked against the oracle")
     ap.add_argument("--sur-kernels", type=int, default=50000)
     ap.add_argument("--sur-rows-per-kernel", type=int, default=400)
@@ -443,6 +443,22 @@ def run_klr(args):
 SWEEP = dict(name="sweep3d_fp32_fp64", n_vars=4, degree=2, n_hi_log2=23, sizes=256, n_cfg=251)
 
 
+def sweep_oracle_chunk(job):
+    """Oracle choice for a chunk of the 3D sweep's kernels (run in a spawned
+    worker): returns best, margin and the boundary margin of the best."""
+    import workloads as W
+    from oracle import configs as ocfg, program as oprog
+    coef, regs, smem, sizes = job
+    nk = len(regs)
+    q = W.queries_per_kernel(nk, sizes)
+    prog = dict(coef=coef, regs=regs, smem=smem, n_vars=4, degree=2, n_scale_log2=23,
+                b_scale_log2=10, metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+    ref = oprog.choose(prog, W.HARDWARE, ocfg.enumerate_configs(3), q.offsets, q.sizes)
+    rows = np.arange(len(q.sizes))
+    bnd = np.where(ref["best"] >= 0, ref["boundary"][rows, np.maximum(ref["best"], 0)], np.inf)
+    return ref["best"], ref["margin"], bnd
+
+
 def run_sweep3d(args):
     """3D block shapes: every kernel x 256 data sizes x 251 shapes, evaluated by
     the FP32 sweep (FP64 near-ties) and by the FP64 sweep, with argmin agreement
@@ -490,15 +506,21 @@ def run_sweep3d(args):
                      "config_evals_per_s": n_q * SWEEP["n_cfg"] / (ms * 1e-3),
                      "hbm_gbs": moved / (ms * 1e-3) / 1e9}
         results[name] = [b.cpu().numpy() for b in bufs[:2]]
-    # oracle on a seeded subsample of kernels
-    from oracle import configs as ocfg, program as oprog
+    # oracle on a seeded subsample of kernels, in spawned worker processes
+    import multiprocessing as mp
+    t_or = time.time()
     ks = W.subsample_kernels(args.seed + 11, nk, min(nk, args.sweep_check_kernels))
     rows = np.concatenate([np.arange(q.offsets[k], q.offsets[k + 1]) for k in ks])
-    prog = dict(coef=gt.coef, regs=gt.regs, smem=gt.smem, n_vars=4, degree=2, n_scale_log2=23,
-                b_scale_log2=10, metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
-    ref = oprog.choose(prog, W.HARDWARE, ocfg.enumerate_configs(3), q.offsets, q.sizes, ks)
-    bnd = np.where(ref["best"] >= 0, ref["boundary"][np.arange(len(rows)), np.maximum(ref["best"], 0)],
-                   np.inf)
+    n_workers = max(1, min(16, os.cpu_count() or 1))
+    chunks = np.array_split(ks, n_workers * 4)
+    jobs = [(gt.coef[c], gt.regs[c], gt.smem[c], sizes) for c in chunks if len(c)]
+    with mp.get_context("spawn").Pool(n_workers) as pool:
+        parts = pool.map(sweep_oracle_chunk, jobs)
+    ref_best = np.concatenate([p_[0] for p_ in parts])
+    ref_margin = np.concatenate([p_[1] for p_ in parts])
+    bnd = np.concatenate([p_[2] for p_ in parts])
+    oracle_s = time.time() - t_or
+    ref = {"best": ref_best, "margin": ref_margin}
     strict = (ref["margin"] > 1e-6) & (bnd > 1e-5)
     agree = {}
     for name in ("f32", "f64"):
@@ -517,7 +539,8 @@ def run_sweep3d(args):
             "data": "synthetic (seeded rational ground truth)",
             "config": {"workload": SWEEP["name"], "kernels": nk, "sizes_per_kernel": SWEEP["sizes"],
                        "configs": SWEEP["n_cfg"], "queries": n_q,
-                       "check_kernels": int(len(ks))},
+                       "check_kernels": int(len(ks)), "check_queries": int(len(rows)),
+                       "oracle_s": oracle_s, "oracle_workers": n_workers},
             "fp32": out["f32"], "fp64": out["f64"],
             "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
             "agreement_vs_oracle": agree}
