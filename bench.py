@@ -73,6 +73,24 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seed(seed: int, rank: int) -> int:
+    """Seed of a rank's own copy of the workload (weak scaling: replicas)."""
+    return seed + 1000 * rank
+
+
+def whole_job(ms_local: float, units_local: float, dist=None, device="cpu"):
+    """Step time and work of the whole job: the slowest rank's time and the
+    units of all ranks (no data-path collective: this is the measurement)."""
+    if dist is None:
+        return float(ms_local), float(units_local)
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -218,7 +236,7 @@ def run_klr(args):
     import paper_1911_02373_gb300 as klr
     import workloads as W
 
-    seed = args.seed + 1000 * rank
+    seed = rank_seed(args.seed, rank)
     fb, q = make_inputs(seed)
     wl = WORKLOAD
     n_fits, n_q = fb.n_fits, len(q.sizes)
@@ -327,11 +345,7 @@ def run_klr(args):
     part_ms = [float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev])) for i in range(len(parts))]
     gram_ms, solve_ms, eval_ms = part_ms
     fit_ms = gram_ms + solve_ms
-    ms_step = total_ms / K
-    if dist:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step, units = whole_job(total_ms / K, n_q, dist, dev)
     fit_status = fst.cpu().numpy()
     q_status = qst.cpu().numpy()
 
@@ -372,7 +386,7 @@ def run_klr(args):
         cyc_h.copy_(cyc, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / E
+    e2e_ms, e2e_units = whole_job(e0.elapsed_time(e1) / E, n_q, dist, dev)
     h2d = sum(t.numel() * t.element_size() for t in (off_h, x_h, y_h, qo_h, qn_h))
     d2h = best_h.numel() * 4 + cyc_h.numel() * 4
 
@@ -397,7 +411,7 @@ def run_klr(args):
     alu_peak = 152 * 128 * sm_max * 1e6   # FP32 lanes x clock: lane-ops/s
     out = {
         "metric": METRIC,
-        "value": ws * n_q / (ms_step * 1e-3),
+        "value": units / (ms_step * 1e-3),
         "unit": "queries/s",
         "n_gpus": ws,
         "steps": K,
@@ -416,8 +430,8 @@ def run_klr(args):
                               else "eager"),
                    "autotuned": {k: {"choice": v[0], "ms": v[1]} for k, v in tuned.items()},
                    "parallelism": f"replicas x{ws}"},
-        "fits_per_s": ws * n_fits / (ms_step * 1e-3),
-        "config_evals_per_s": ws * n_q * wl["n_cfg"] / (ms_step * 1e-3),
+        "fits_per_s": units / n_q * n_fits / (ms_step * 1e-3),
+        "config_evals_per_s": units * wl["n_cfg"] / (ms_step * 1e-3),
         "kernel_ms": {"fit_moments": gram_ms, "fit_solve": solve_ms, "argmin": eval_ms},
         "roofline": {"bound": "alu", "achieved": fit_ops / (gram_ms * 1e-3) / 1e12,
                      "peak": alu_peak / 1e12, "unit": "Tops/s (FP32 lane-ops)",
@@ -428,7 +442,7 @@ def run_klr(args):
                      "hbm_gbs": fit_bytes / (gram_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak,
                      "hbm_frac": fit_bytes / (gram_ms * 1e-3) / 1e9 / hbm_peak,
                      "peak_source": "FP32 lanes x max SM clock (unit counts)"},
-        "e2e": {"value": ws * n_q / (e2e_ms * 1e-3), "unit": "queries/s",
+        "e2e": {"value": e2e_units / (e2e_ms * 1e-3), "unit": "queries/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": 4 * K,
         "clocks": ck,
