@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--impl", default="klr", choices=["klr", "reference"])
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-copy-streams", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of a CUDA graph")
     ap.add_argument("--kernels", type=int, default=0,
@@ -358,26 +359,41 @@ def run_klr(args):
     bufs = [(off, x, y, qo, qn),
             tuple(torch.empty_like(t_) for t_ in (off, x, y, qo, qn))]
     hosts = (off_h, x_h, y_h, qo_h, qn_h)
-    copy_stream = torch.cuda.Stream(device=dev)
-    h2d_done = [torch.cuda.Event() for _ in range(2)]
+    # the copies of a step are split into chunks over several streams (the
+    # host link is not saturated by a single copy)
+    n_cs = args.e2e_copy_streams
+    copy_streams = [torch.cuda.Stream(device=dev) for _ in range(n_cs)]
+    copy_stream = copy_streams[0]
+    h2d_done = [[torch.cuda.Event() for _ in range(n_cs)] for _ in range(2)]
     used = [torch.cuda.Event() for _ in range(2)]
+    pieces = []
+    for j, (d_, h_) in enumerate(zip(bufs[0], hosts)):
+        n = h_.numel()
+        cuts = np.linspace(0, n, n_cs + 1).astype(np.int64) if n > (1 << 20) else np.array([0, n])
+        for c in range(len(cuts) - 1):
+            pieces.append((j, int(cuts[c]), int(cuts[c + 1])))
 
     def h2d(i):
-        with torch.cuda.stream(copy_stream):
-            if i >= 2:
-                copy_stream.wait_event(used[i % 2])
-            for d_, h_ in zip(bufs[i % 2], hosts):
-                d_.copy_(h_, non_blocking=True)
-            h2d_done[i % 2].record(copy_stream)
+        for c_, cs in enumerate(copy_streams):
+            with torch.cuda.stream(cs):
+                if i >= 2:
+                    cs.wait_event(used[i % 2])
+                for pi, (j, a_, b_) in enumerate(pieces):
+                    if pi % n_cs == c_:
+                        bufs[i % 2][j].view(-1)[a_:b_].copy_(hosts[j].view(-1)[a_:b_],
+                                                            non_blocking=True)
+                h2d_done[i % 2][c_].record(cs)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    copy_stream.wait_event(e0)
+    for cs in copy_streams:
+        cs.wait_event(e0)
     h2d(0)
     for i in range(E):
         if i + 1 < E:
             h2d(i + 1)
-        stream.wait_event(h2d_done[i % 2])
+        for ev_ in h2d_done[i % 2]:
+            stream.wait_event(ev_)
         o_, x_, y_, qo_, qn_ = bufs[i % 2]
         fit(x_, y_, o_)
         choose(qo_, qn_)
