@@ -157,6 +157,15 @@ __device__ T eval_full(const EvalParams& P, int k, long long N, int c, bool& usa
     return mwpcwp<T>(L, (T)W, (T)B, (T)asm_, (T)rep, P);
 }
 
+// Section IV step 4's meaningful configurations: some block is active, the
+// shape fits the thread limit and no block side exceeds N.
+__device__ __noinline__ bool e_meaningful(const EvalParams& P, int k, long long N, int c) {
+    const long long b0 = P.cfg[3 * c], b1 = P.cfg[3 * c + 1], b2 = P.cfg[3 * c + 2];
+    const long long Tt = b0 * b1 * b2;
+    return active_blocks(Tt, P.regs[k], P.smem[k], P) > 0 && Tt <= P.T_max && b0 <= N &&
+           (P.dims < 2 || b1 <= N) && (P.dims < 3 || b2 <= N);
+}
+
 __device__ double eval_full_f64(const EvalParams& P, int k, long long N, int c, bool& usable) {
     return eval_full<double>(P, k, N, c, usable);
 }
@@ -509,6 +518,184 @@ eval_kernel(const __grid_constant__ EvalParams P) {
         }
     }
 }
+
+// ---------------------------------------------------------------------------
+// Candidate re-rank with one warp per kernel: the kernel's coefficients, the
+// union of the shapes proposed for its queries (at most kSlots specialised
+// per kernel; others are evaluated unspecialised) and their specialised
+// polynomials live in the warp's own shared memory, so warps never wait on
+// one another; lanes then take (query, candidate) pairs, kc lanes per query.
+// ---------------------------------------------------------------------------
+constexpr int kSlots = 48, kRerankWarps = 4;
+
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+// bytes of one warp's region
+__host__ __device__ inline int rerank_slots(int n_cfg) { return n_cfg < kSlots ? n_cfg : kSlots; }
+__host__ __device__ inline size_t rerank_warp_bytes(int u, int n_cfg, int nc) {
+    const size_t ns = (size_t)rerank_slots(n_cfg);
+    return align16(4 * (size_t)8 * u) + align16(4 * ns * 8 * nc) + align16(sizeof(CfgInfo) * ns) +
+           align16(4 * ns) + align16(4 * ns) + align16(2 * (size_t)n_cfg) + 32;
+}
+
+template <int D>
+__global__ void __launch_bounds__(32 * kRerankWarps)
+rerank_kernel(const __grid_constant__ EvalParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NC = 2 * (D + 1);
+    const int m = P.m, u = P.u, n_cfg = P.n_cfg, kc = P.kc, n_slot = rerank_slots(n_cfg);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned full = 0xffffffffu;
+    float* bmon = reinterpret_cast<float*>(smem_raw);                 // n_cfg x m
+    unsigned char* wb = smem_raw + align16(4 * (size_t)n_cfg * m) +
+                        (size_t)w * rerank_warp_bytes(u, n_cfg, NC);
+    float* coef_s = reinterpret_cast<float*>(wb);
+    wb += align16(4 * (size_t)8 * u);
+    float* spec = reinterpret_cast<float*>(wb);
+    wb += align16(4 * (size_t)n_slot * 8 * NC);
+    CfgInfo* cinfo = reinterpret_cast<CfgInfo*>(wb);
+    wb += align16(sizeof(CfgInfo) * (size_t)n_slot);
+    float* wrcp = reinterpret_cast<float*>(wb);
+    wb += align16(4 * (size_t)n_slot);
+    int* slot_cfg = reinterpret_cast<int*>(wb);
+    wb += align16(4 * (size_t)n_slot);
+    int16_t* slot_of = reinterpret_cast<int16_t*>(wb);
+    wb += align16(2 * (size_t)n_cfg);
+    unsigned* mask = reinterpret_cast<unsigned*>(wb);                 // 8 words
+    const float n_scale = (float)ldexp(1.0, -P.n_scale_log2);
+    float lo[8], sc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { lo[i] = (float)P.lo[i]; sc[i] = (float)P.sc[i]; }
+    const unsigned n_sm = (unsigned)P.n_sm;
+    for (int idx = threadIdx.x; idx < n_cfg * m; idx += blockDim.x) {
+        const int c = idx / m, t = idx - c * m;
+        float xb[3];
+        xb[0] = (float)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
+        xb[1] = (float)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
+        xb[2] = (float)ldexp((double)P.cfg[3 * c + 2], -P.b_scale_log2);
+        float bm = 1.f;
+        for (int v = 1; v < P.n_vars; ++v)
+            for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
+        bmon[idx] = bm;
+    }
+    __syncthreads();
+    for (int64_t k = (int64_t)blockIdx.x * kRerankWarps + w; k < P.n_kernels;
+         k += (int64_t)gridDim.x * kRerankWarps) {
+        const int64_t qa = P.q_off[k], qb = P.q_off[k + 1];
+        if (qa == qb) continue;
+        for (int i = lane; i < 8 * u; i += 32) {
+            coef_s[i] = P.coef_f64 ? (float)reinterpret_cast<const double*>(P.coef)[k * 8 * u + i]
+                                   : reinterpret_cast<const float*>(P.coef)[k * 8 * u + i];
+        }
+        if (lane < 8) mask[lane] = 0u;
+        __syncwarp();
+        for (int64_t i = qa * kc + lane; i < qb * kc; i += 32) {
+            const int c = P.cand[i];
+            if (c >= 0 && c < n_cfg) atomicOr(&mask[c >> 5], 1u << (c & 31));
+        }
+        __syncwarp();
+        // slots for the proposed shapes, in shape order
+        int n_slots = 0;
+        for (int c0 = 0; c0 < n_cfg; c0 += 32) {
+            const int c = c0 + lane;
+            const bool bit = c < n_cfg && ((mask[c >> 5] >> (c & 31)) & 1u);
+            const unsigned bal = __ballot_sync(full, bit);
+            const int pos = n_slots + __popc(bal & ((1u << lane) - 1u));
+            if (c < n_cfg) slot_of[c] = (int16_t)((bit && pos < n_slot) ? pos : -1);
+            if (bit && pos < n_slot) slot_cfg[pos] = c;
+            n_slots += __popc(bal);
+        }
+        const int n_used = min(n_slots, n_slot);
+        __syncwarp();
+        const int R = P.regs[k], Z = P.smem[k];
+        for (int s = lane; s < n_used; s += 32) {
+            const int c = slot_cfg[s];
+            const long long b0 = P.cfg[3 * c], b1 = P.cfg[3 * c + 1], b2 = P.cfg[3 * c + 2];
+            const long long Tt = b0 * b1 * b2;
+            int B = active_blocks(Tt, R, Z, P);
+            if (Tt > P.T_max) B = 0;
+            CfgInfo ci;
+            ci.T = (int)Tt;
+            ci.B = B;
+            ci.W = (int)min((long long)B * Tt / 32, (long long)P.W_max);
+            ci.b0 = (int)b0;
+            ci.b1 = P.dims >= 2 ? (int)b1 : 1;
+            ci.b2 = P.dims >= 3 ? (int)b2 : 1;
+            ci.t_shift = (Tt > 0 && (Tt & (Tt - 1)) == 0) ? __ffsll(Tt) - 1 : -1;
+            ci.wave = (unsigned)max(B, 1) * n_sm;
+            cinfo[s] = ci;
+            wrcp[s] = 1.0f / (float)ci.wave;
+        }
+        for (int idx = lane; idx < n_used * 8; idx += 32) {
+            const int s = idx >> 3, i = idx & 7, c = slot_cfg[s];
+            float acc[2][D + 1];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int j = 0; j <= D; ++j) acc[a][j] = 0.f;
+            for (int t = 0; t < m; ++t) {
+                const float bm = bmon[c * m + t];
+                const int j = P.exps[t][0];
+                const float a = coef_s[i * u + t] * bm, b = coef_s[i * u + m + t] * bm;
+#pragma unroll
+                for (int jj = 0; jj <= D; ++jj)
+                    if (jj == j) { acc[0][jj] += a; acc[1][jj] += b; }
+            }
+            float* sp = spec + (size_t)idx * NC;
+#pragma unroll
+            for (int j = 0; j <= D; ++j) {
+                sp[j] = acc[0][j];
+                sp[D + 1 + j] = acc[1][j];
+            }
+        }
+        __syncwarp();
+        const int64_t npairs = (qb - qa) * kc;
+        const int64_t span = (npairs + 31) & ~(int64_t)31;
+        for (int64_t pi = lane; pi < span; pi += 32) {
+            const bool valid = pi < npairs;
+            const int64_t q = qa + (valid ? pi / kc : 0);
+            const int j = (int)(pi & (kc - 1));
+            const int c = valid ? P.cand[q * kc + j] : -1;
+            int st = 0;
+            float e = INFINITY;
+            if (c >= 0 && c < n_cfg) {
+                const long long N = P.q_N[q];
+                const int s = slot_of[c];
+                if (s >= 0) {
+                    e = eval_cfg<float, D>(P, cinfo, wrcp, spec, lo, sc, n_sm, N, N < (1LL << 24),
+                                           (float)N * n_scale, s, st);
+                } else {
+                    // beyond the specialised slots: the unspecialised form
+                    bool us;
+                    e = eval_full<float>(P, (int)k, N, c, us);
+                    if (!us) {
+                        // meaningful but with an invalid metric: flagged
+                        if (e_meaningful(P, (int)k, N, c)) st |= KLR_Q_BAD_METRIC;
+                        e = INFINITY;
+                    } else if (!isfinite(e)) {
+                        e = INFINITY;
+                        st |= KLR_Q_BAD_METRIC;
+                    }
+                }
+            }
+            int ci = e < INFINITY ? c : 0x7fffffff;
+            for (int o = 1; o < kc; o <<= 1) {
+                const float oe = __shfl_xor_sync(full, e, o);
+                const int oc = __shfl_xor_sync(full, ci, o);
+                st |= __shfl_xor_sync(full, st, o);
+                if (oe < e || (oe == e && oc < ci)) { e = oe; ci = oc; }
+            }
+            if (valid && j == 0) {
+                const bool none = !(e < INFINITY);
+                P.best[q] = none ? -1 : ci;
+                reinterpret_cast<float*>(P.best_cycles)[q] = e;
+                if (P.q_status) P.q_status[q] = st | (none ? KLR_Q_NONE_FEASIBLE : 0);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 
 // Re-decide FP32 near-ties: FP64 evaluation of the tied candidates (or of
 // every configuration) with the unspecialised program, lowest index on ties.
@@ -932,6 +1119,30 @@ klr_status klr_argmin_candidates(klr_ctx* ctx, const klr_program* prog, const kl
     P.q_status = q_status;
     P.cand = cand;
     P.kc = k;
+    if (k <= 32 && (k & (k - 1)) == 0) {
+        // one warp per kernel
+        const int NC = 2 * (P.degree + 1);
+        const size_t smem = align16(4 * (size_t)P.n_cfg * P.m) +
+                            kRerankWarps * rerank_warp_bytes(P.u, P.n_cfg, NC);
+        if (smem <= c->smem_optin) {
+            auto go = [&](auto kern) -> klr_status {
+                int per_sm = 0;
+                KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem));
+                KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
+                                                                             32 * kRerankWarps, smem));
+                const int grid = (int)std::min<int64_t>(
+                    ((int64_t)P.n_kernels + kRerankWarps - 1) / kRerankWarps,
+                    (int64_t)c->n_sm * std::max(per_sm, 1));
+                kern<<<grid, 32 * kRerankWarps, smem, stream>>>(P);
+                KLR_CHECK_CUDA(cudaGetLastError());
+                return KLR_OK;
+            };
+            if (P.degree == 1) return go(rerank_kernel<1>);
+            if (P.degree == 2) return go(rerank_kernel<2>);
+            return go(rerank_kernel<3>);
+        }
+    }
     return launch_eval(c, P, false, stream);
 }
 

@@ -130,14 +130,18 @@ def test_bad_arguments_return_einval(klr, ctx):
         ctx.eval(prog, hw, torch.zeros((300, 3), dtype=torch.int32).cuda(), qo, qn)
 
 
-def test_candidate_rerank_matches_oracle(klr, ctx):
+@pytest.mark.parametrize("kc,n_sizes", [(8, 64), (2, 8), (32, 16), (6, 64)])
+def test_candidate_rerank_matches_oracle(klr, ctx, kc, n_sizes):
     """klr_argmin_candidates: per query the least-cycles meaningful shape among
     its candidates (ties to the lowest index), against the oracle's cycles
-    table restricted to the same candidates."""
+    table restricted to the same candidates.  The cases cover a kernel whose
+    proposed shapes outnumber the specialised slots (8 x 64), all shapes
+    specialised (2 x 8), whole warps per query (32) and a candidate count that
+    is not a power of two (6: the block-per-kernel form)."""
     gt = G.make_program(6, 48)
     coef = gt.coef.astype(np.float32)
-    q = W.queries_per_kernel(48, W.log_spaced_sizes(64))
-    n_q, kc = len(q.sizes), 8
+    q = W.queries_per_kernel(48, W.log_spaced_sizes(n_sizes))
+    n_q = len(q.sizes)
     keys = W.stream_keys(41, (3,), np.arange(n_q, dtype=np.uint64))
     cand = (W.words(keys[:, None], np.arange(kc, dtype=np.uint64)[None, :]) % np.uint64(56))
     cand = cand.astype(np.int32) - 2          # -2..53: some skipped entries, some duplicates
