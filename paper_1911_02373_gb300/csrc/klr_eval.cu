@@ -66,6 +66,10 @@ struct EvalParams {
     int kc;
     const uint8_t* done;        // history mode: 1 for queries answered already, or NULL
     uint8_t exps[kMaxBasis][kMaxVars];
+    // terms grouped by their power of N (increasing term index within a
+    // group): group j is ord[jstart[j] .. jstart[j + 1])
+    uint8_t ord[kMaxBasis];
+    uint8_t jstart[8];
 };
 
 // Fig. 1 with the program's hardware limits.
@@ -379,30 +383,25 @@ eval_kernel(const __grid_constant__ EvalParams P) {
             xb[0] = (T)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
             xb[1] = (T)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
             xb[2] = (T)ldexp((double)P.cfg[3 * c + 2], -P.b_scale_log2);
-            T acc[2][D + 1];
-#pragma unroll
-            for (int s = 0; s < 2; ++s)
-#pragma unroll
-                for (int j = 0; j <= D; ++j) acc[s][j] = T(0);
-            for (int t = 0; t < m; ++t) {
-                T bm = T(1);
-                if (kMonoTable) {
-                    bm = bmon[c * m + t];
-                } else {
-                    for (int v = 1; v < P.n_vars; ++v)
-                        for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
-                }
-                const int j = P.exps[t][0];
-                const T a = coef_s[i * u + t] * bm, b = coef_s[i * u + m + t] * bm;
-#pragma unroll
-                for (int jj = 0; jj <= D; ++jj)
-                    if (jj == j) { acc[0][jj] += a; acc[1][jj] += b; }
-            }
             T* sp = spec + (size_t)idx * NC;
+            // coefficient of N^j: its terms in increasing index order
 #pragma unroll
             for (int j = 0; j <= D; ++j) {
-                sp[j] = acc[0][j];
-                sp[D + 1 + j] = acc[1][j];
+                T pa = T(0), qa = T(0);
+                for (int r = P.jstart[j]; r < P.jstart[j + 1]; ++r) {
+                    const int t = P.ord[r];
+                    T bm = T(1);
+                    if (kMonoTable) {
+                        bm = bmon[c * m + t];
+                    } else {
+                        for (int v = 1; v < P.n_vars; ++v)
+                            for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
+                    }
+                    pa = fma(coef_s[i * u + t], bm, pa);
+                    qa = fma(coef_s[i * u + m + t], bm, qa);
+                }
+                sp[j] = pa;
+                sp[D + 1 + j] = qa;
             }
         }
         __syncthreads();
@@ -628,24 +627,19 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
         }
         for (int idx = lane; idx < n_used * 8; idx += 32) {
             const int s = idx >> 3, i = idx & 7, c = slot_cfg[s];
-            float acc[2][D + 1];
-#pragma unroll
-            for (int a = 0; a < 2; ++a)
-#pragma unroll
-                for (int j = 0; j <= D; ++j) acc[a][j] = 0.f;
-            for (int t = 0; t < m; ++t) {
-                const float bm = bmon[c * m + t];
-                const int j = P.exps[t][0];
-                const float a = coef_s[i * u + t] * bm, b = coef_s[i * u + m + t] * bm;
-#pragma unroll
-                for (int jj = 0; jj <= D; ++jj)
-                    if (jj == j) { acc[0][jj] += a; acc[1][jj] += b; }
-            }
             float* sp = spec + (size_t)idx * NC;
+            // the same sums, in the same order, as the sweep's specialisation
 #pragma unroll
             for (int j = 0; j <= D; ++j) {
-                sp[j] = acc[0][j];
-                sp[D + 1 + j] = acc[1][j];
+                float pa = 0.f, qa = 0.f;
+                for (int r = P.jstart[j]; r < P.jstart[j + 1]; ++r) {
+                    const int t = P.ord[r];
+                    const float bm = bmon[c * m + t];
+                    pa = fmaf(coef_s[i * u + t], bm, pa);
+                    qa = fmaf(coef_s[i * u + m + t], bm, qa);
+                }
+                sp[j] = pa;
+                sp[D + 1 + j] = qa;
             }
         }
         __syncwarp();
@@ -827,6 +821,15 @@ klr_status prepare(Context* c, const klr_program* prog, const klr_hw* hw, const 
     P.n_q = q->n_queries;
     for (int t = 0; t < basis.m; ++t)
         for (int v = 0; v < kMaxVars; ++v) P.exps[t][v] = basis.exps[t][v];
+    if (P.degree > 6) return KLR_EINVAL;
+    int r = 0;
+    for (int j = 0; j <= P.degree; ++j) {
+        P.jstart[j] = (uint8_t)r;
+        for (int t = 0; t < basis.m; ++t)
+            if (basis.exps[t][0] == j) P.ord[r++] = (uint8_t)t;
+    }
+    P.jstart[P.degree + 1] = (uint8_t)r;
+    if (r != basis.m) return KLR_EINVAL;
     (void)c;
     return KLR_OK;
 }

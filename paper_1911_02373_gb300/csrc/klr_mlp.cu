@@ -23,6 +23,9 @@ namespace klr {
 namespace {
 
 constexpr int FEAT = 16, EMB = 64, IN = 80, H = 256;
+// per-kernel table row: the 64 embedding values, then (proposal, per-query
+// form) eight 32-bit occupancy words, bit c of word w for shape 32 w + c
+constexpr int kEmbLd = EMB + 16;
 constexpr int64_t kMaxRows = 262144;
 
 struct Offsets {
@@ -57,9 +60,44 @@ __device__ __forceinline__ float tanh_hw(float x) {
     asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
+// gelu(z) = z/2 (1 + tanh(u)), u = sqrt(2/pi) (z + 0.044715 z^3) written as
+// z (c + c3 z^2); the same operations, in the same order, as gelu2_bf16
+constexpr float kGeluC = 0.7978845608028654f;      // sqrt(2 / pi)
+constexpr float kGeluC3 = 0.035677408136300125f;   // sqrt(2 / pi) x 0.044715
 __device__ __forceinline__ float gelu(float z) {
-    const float c = 0.7978845608028654f;   // sqrt(2 / pi)
-    return 0.5f * z * (1.0f + tanh_hw(c * (z + 0.044715f * z * z * z)));
+    const float u = z * fmaf(z * z, kGeluC3, kGeluC);
+    const float h = 0.5f * z;
+    return fmaf(h, tanh_hw(u), h);
+}
+
+// two GELUs of (a + bias_a, b + bias_b) on packed FP32 pairs, rounded to a
+// BF16 pair (first value in the low half)
+__device__ __forceinline__ uint32_t gelu2_bf16(float a, float b, float bias_a, float bias_b) {
+    uint32_t out;
+    asm("{\n"
+        ".reg .b64 z, t, k, w;\n"
+        ".reg .f32 u0, u1, t0, t1;\n"
+        "mov.b64 z, {%1, %2};\n"
+        "mov.b64 t, {%3, %4};\n"
+        "add.rn.f32x2 z, z, t;\n"               // z
+        "mul.rn.f32x2 w, z, z;\n"               // z^2
+        "mov.b64 k, {%5, %5};\n"
+        "mov.b64 t, {%6, %6};\n"
+        "fma.rn.f32x2 w, w, k, t;\n"            // c + c3 z^2
+        "mul.rn.f32x2 w, z, w;\n"               // u
+        "mov.b64 {u0, u1}, w;\n"
+        "tanh.approx.f32 t0, u0;\n"
+        "tanh.approx.f32 t1, u1;\n"
+        "mov.b64 k, {%7, %7};\n"
+        "mul.rn.f32x2 z, z, k;\n"               // h = z / 2
+        "mov.b64 t, {t0, t1};\n"
+        "fma.rn.f32x2 z, z, t, z;\n"            // h tanh(u) + h
+        "mov.b64 {u0, u1}, z;\n"
+        "cvt.rn.bf16x2.f32 %0, u1, u0;\n"
+        "}\n"
+        : "=r"(out)
+        : "f"(a), "f"(b), "f"(bias_a), "f"(bias_b), "f"(kGeluC3), "f"(kGeluC), "f"(0.5f));
+    return out;
 }
 __device__ __forceinline__ float gelu_grad(float z) {
     const float c = 0.7978845608028654f;
@@ -309,7 +347,7 @@ __global__ void embed_rows_kernel(const int32_t* __restrict__ kernel, int64_t n,
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = i / EMB;
         const int j = (int)(i - r * EMB);
-        X0[r * IN + FEAT + j] = table[(int64_t)kernel[r] * EMB + j];
+        X0[r * IN + FEAT + j] = table[(int64_t)kernel[r] * kEmbLd + j];
     }
 }
 
@@ -494,7 +532,7 @@ size_t mlp_ws_bytes(int64_t n, int n_coef, int n_out, int64_t n_kernels_table, b
     b += align256(2 * (size_t)n * IN);                        // X0
     b += align256(2 * (size_t)n * H) * 3;                     // A1..A3
     b += align256(4 * (size_t)n * oc) * 2;                    // pred, dpred
-    b += align256(2 * (size_t)n_kernels_table * EMB);         // emb table
+    b += align256(2 * (size_t)n_kernels_table * kEmbLd);      // emb table
     if (train) {
         b += align256(2 * (size_t)n * n_coef);                // CR
         b += align256(4 * (size_t)n * H) * 3;                 // Z1..Z3
@@ -522,7 +560,7 @@ MlpWs carve(void* base, int64_t n, int n_coef, int n_out, int64_t n_kernels_tabl
     w.A3 = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n * H));
     w.pred = reinterpret_cast<float*>(take(4 * (size_t)n * oc));
     w.dpred = reinterpret_cast<float*>(take(4 * (size_t)n * oc));
-    w.emb_table = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n_kernels_table * EMB));
+    w.emb_table = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n_kernels_table * kEmbLd));
     if (train) {
         w.CR = reinterpret_cast<__nv_bfloat16*>(take(2 * (size_t)n * n_coef));
         w.Z1 = reinterpret_cast<float*>(take(4 * (size_t)n * H));
@@ -619,7 +657,6 @@ klr_status forward_hidden(const MlpWs& w, const float* params, const Offsets& o,
 // elements advances the start address by 32 bytes within a block.
 // ---------------------------------------------------------------------------
 constexpr int kTileRows = 128;
-constexpr int kFusedThreads = 256;
 constexpr int kKPad1 = 128;                 // layer-1 K (80) padded to whole blocks
 
 __host__ __device__ inline uint32_t swz_off(int r, int k, int rows) {
@@ -729,28 +766,25 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t ad, uint64_t b
                  :: "r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                   "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
-                   "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// two 16-column loads of this warp's 32 lanes (columns t0.., t1..) and one
+// wait, in one statement so that no register is read early; the warp is
+// reconverged first (the loads are .sync.aligned and may follow code that
+// only some lanes ran)
+__device__ __forceinline__ void tmem_ld16x2(uint32_t t0, uint32_t t1, float (&v)[32]) {
+    uint32_t r[32];
+    __syncwarp();
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
+                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%33];\n"
+                 "tcgen05.wait::ld.sync.aligned;\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+                   "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+                   "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(t0), "r"(t1)
+                 : "memory");
 #pragma unroll
-    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-}
-
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-                   "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+    for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 struct FusedArgs {
@@ -773,10 +807,9 @@ struct FusedArgs {
     const int64_t* q_off;
     const int64_t* q_N;
     int32_t n_kernels;
-    const __nv_bfloat16* emb_table;   // n_kernels x EMB
+    const __nv_bfloat16* emb_table;   // n_kernels x kEmbLd: embedding, then occupancy words
     float hw[7];
     const int32_t* cfg;
-    const uint8_t* occ;               // n_kernels x n_out: B_active > 0
     int k;                            // 1..16
     int32_t* cand;                    // n_queries x k
 };
@@ -791,9 +824,85 @@ __device__ int32_t kernel_of(const int64_t* off, int32_t nk, int64_t q) {
     return lo;
 }
 
-// Dynamic shared memory: 1 KB alignment slack + activations (128 x 256) +
-// weights (256 x 256).
-constexpr size_t kFusedSmem = 1024 + (size_t)kTileRows * H * 2 + (size_t)H * H * 2;
+// ---------------------------------------------------------------------------
+// Fused forward pass on the tensor cores, pipelined across layers.
+//
+// One CTA per SM, persistent over tiles of 128 rows; 16 epilogue warps, one
+// warp whose lane 0 issues the products and one whose lane 0 streams the
+// weights.  Tensor memory holds two 128 x 256 FP32 accumulators, so
+// a layer's products go to one while the previous layer's are read from the
+// other.  The epilogue of a layer hands the next layer's operand over one
+// 64-column K-block at a time (mbarrier act[g]: the 16 epilogue warps,
+// one arrival per warp once all its lanes have written and fenced their
+// part), and the issuing thread starts that K-block's products as soon as it
+// is complete, so the products of layer L + 1 overlap the epilogue of layer L.
+// Weights stream through four 32 KB slots, one K-block of one layer each
+// (mbarrier full[g]); the producer refills a slot with its next K-block as
+// soon as the products that read it have completed (free[g], by
+// tcgen05.commit), a whole layer ahead of its use.  In the last layer's epilogue one warp per lane
+// quadrant keeps each row's top-k over all columns (or writes the outputs)
+// while the other twelve build the next tile's input rows, whose first
+// products start at once (they use the other accumulator).
+//
+// Every wait is bounded and gives up when another thread has given up; the
+// issuer then drains the tensor pipe, the producer its outstanding copies, and
+// the CTA marks its rows (NaN outputs, -1 candidates) and sets the error flag.
+// ---------------------------------------------------------------------------
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kFusedThreads = kEpiThreads + 64;     // + the MMA issuer and the weight producer
+constexpr uint32_t kKBlockBytes = kTileRows * 128;        // one K-block of the activations
+constexpr uint32_t kSlotBytes = H * 128;                  // one K-block of a layer's weights
+// Dynamic shared memory, from a 1 KB boundary: activations (128 x 256 BF16),
+// four weight slots, and in proposal mode each row's occupancy words and size
+// for two tiles (by tile parity); every offset is a multiple of 1 KB.
+constexpr uint32_t kRowOccBytes = 2 * kTileRows * 8 * 4;
+constexpr uint32_t kRowNBytes = 2 * kTileRows * 8;
+constexpr size_t kFusedSmem = 1024 + (size_t)kTileRows * H * 2 + 4 * (size_t)kSlotBytes +
+                              kRowOccBytes + kRowNBytes;
+
+__device__ __forceinline__ bool mbar_try(uint64_t* mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 "selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok) : "r"(smem_addr(mbar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// bounded wait that also gives up once `abort` is set
+__device__ __forceinline__ bool mbar_wait_ab(uint64_t* mbar, uint32_t parity,
+                                             volatile int* abort) {
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try(mbar, parity)) return true;
+        if ((it & 15) == 15 && *abort) return false;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(mbar)) : "memory");
+}
+
+// the wait of every lane of a warp; true only when it ended for all of
+// them, so that the warp stays converged on the way out
+__device__ __forceinline__ bool warp_wait(uint64_t* mbar, uint32_t parity, volatile int* abort) {
+    const bool ok = mbar_wait_ab(mbar, parity, abort);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// every lane's shared-memory writes made visible to the tensor core (async
+// proxy) and ordered before one arrival for the warp
+__device__ __forceinline__ void warp_arrive_async(uint64_t* mbar, int lane) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) mbar_arrive(mbar);
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(smem_addr(mbar)) : "memory");
+}
 
 template <int KMAX>
 __global__ void __launch_bounds__(kFusedThreads, 1)
@@ -802,35 +911,38 @@ fused_forward_kernel(const __grid_constant__ FusedArgs a) {
     unsigned char* As = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(fsm_raw) + 1023) & ~(uintptr_t)1023);
     unsigned char* Bs = As + kTileRows * H * 2;
-    __shared__ uint64_t mbar_w, mbar_mma;
+    // proposal mode: row_occ[buf][row][w] and row_N[buf][row]
+    auto row_occ = reinterpret_cast<uint32_t (*)[kTileRows][8]>(Bs + 4 * kSlotBytes);
+    auto row_N = reinterpret_cast<long long (*)[kTileRows]>(Bs + 4 * kSlotBytes + kRowOccBytes);
+    __shared__ uint64_t mb_full[4], mb_free[4], mb_act[4], mb_mma, mb_rows, mb_final;
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
-    __shared__ int32_t tile_kernel[kTileRows];       // proposal mode: each row's kernel
     __shared__ float bias_s[4 * H];                  // b1, b2, b3, b4 (np <= 256)
     __shared__ int32_t cfg_max[H];                   // proposal mode: largest block dimension
+    volatile int* abort_v = &abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t n_tiles = (a.n + kTileRows - 1) / kTileRows;
     if ((int64_t)blockIdx.x >= n_tiles) return;
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar_w)));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mbar_mma)));
+        for (int g = 0; g < 4; ++g) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mb_full[g])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mb_free[g])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                         :: "r"(smem_addr(&mb_act[g])), "r"(kEpiWarps));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mb_mma)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                     :: "r"(smem_addr(&mb_rows)), "r"(kEpiWarps - 4));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mb_final)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
-    if (warp == 0) {
+    if (warp == kEpiWarps) {
+        // both accumulators: 512 columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_addr(&tmem_base)), "r"((uint32_t)H));
+                     :: "r"(smem_addr(&tmem_base)), "r"((uint32_t)(2 * H)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base;
-    uint32_t pw = 0, pm = 0;
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    const int row_in_tile = 32 * (warp & 3) + lane;
-    const int half = warp >> 2;
-    if (tid == 0) tma_load(Bs, a.img + a.pk.w1, (uint32_t)(H * kKPad1 * 2), &mbar_w);
     for (int i = tid; i < 4 * H; i += kFusedThreads) {
         const int l = i / H, c = i - l * H;
         const int64_t off = l == 0 ? a.o.b1 : l == 1 ? a.o.b2 : l == 2 ? a.o.b3 : a.o.b4;
@@ -839,192 +951,286 @@ fused_forward_kernel(const __grid_constant__ FusedArgs a) {
     if (a.propose)
         for (int c = tid; c < a.n_out; c += kFusedThreads)
             cfg_max[c] = max(a.cfg[3 * c], max(a.cfg[3 * c + 1], a.cfg[3 * c + 2]));
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const int64_t r0 = t * kTileRows;
-        if (a.propose) {
-            // rows are queries: features (log2 N / 23, shape features 0, the
-            // hardware vector) and the kernel's embedding
-            if (tid < kTileRows) {
-                const int64_t gr = r0 + tid;
-                tile_kernel[tid] = gr < a.n ? a.q_kernel[a.q0 + gr] : 0;
-            }
-            __syncthreads();
-            for (int c = tid; c < kTileRows * (IN / 8); c += kFusedThreads) {
-                const int r = c / (IN / 8), ch = c % (IN / 8);
-                const int64_t gr = r0 + r;
-                unsigned char* dst = As + swz_off(r, ch * 8, kTileRows);
-                if (ch < 2) {
-                    float f[8];
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) f[i] = 0.f;
-                    if (gr < a.n) {
-                        if (ch == 0) {
-                            f[0] = log2f((float)a.q_N[a.q0 + gr]) * (1.0f / 23.0f);
-                            for (int i = 0; i < 4; ++i) f[4 + i] = a.hw[i];
-                        } else {
-                            for (int i = 0; i < 3; ++i) f[i] = a.hw[4 + i];
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t sA = smem_addr(As), sB = smem_addr(Bs);
+
+    if (warp == kEpiWarps) {
+        // ------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t ph_full = 0, ph_act = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int L = 0; L < 4 && ok; ++L) {
+                    const int nkb = L == 0 ? 2 : 4;
+                    const uint32_t idesc = umma_idesc_bf16(kTileRows, L == 3 ? a.np : H);
+                    const uint32_t acc = tmem + (uint32_t)((L & 1) * H);
+                    for (int g = 0; g < nkb; ++g) {
+                        if (!mbar_wait_ab(&mb_full[g], (ph_full >> g) & 1u, abort_v) ||
+                            !mbar_wait_ab(&mb_act[g], (ph_act >> g) & 1u, abort_v)) {
+                            ok = false;
+                            break;
                         }
+                        ph_full ^= 1u << g;
+                        ph_act ^= 1u << g;
+                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                        const int steps = (L == 0 && g == 1) ? (IN - 64) / 16 : 4;
+                        for (int s = 0; s < steps; ++s)
+                            umma_bf16(acc, umma_desc(sA + g * kKBlockBytes + s * 32),
+                                      umma_desc(sB + g * kSlotBytes + s * 32), idesc, (g | s) != 0);
+                        umma_commit(&mb_free[g]);       // slot g and K-block g read
                     }
-                    uint32_t w[4];
+                    if (ok) umma_commit(&mb_mma);
+                }
+            }
+            if (!ok) *abort_v = 1;
+            // drain: every product issued has completed
+            umma_commit(&mb_final);
+            mbar_wait(&mb_final, 0);
+        }
+        __syncwarp();
+    } else if (warp == kEpiWarps + 1) {
+        // -------------------------------------------------- weight producer
+        // K-block g of each layer's weights into slot g, in the order the
+        // products use them; a slot is refilled once the products that read
+        // its previous K-block have completed (a layer ahead of its use)
+        if (lane == 0) {
+            uint32_t ph_free = 0, used = 0, n_issued[4] = {0u, 0u, 0u, 0u};
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x) {
+                for (int L = 0; L < 4 && ok; ++L) {
+                    const int nkb = L == 0 ? 2 : 4;
+                    const uint32_t bytes = (uint32_t)(L == 3 ? a.np : H) * 128u;
+                    const int64_t base = L == 0 ? a.pk.w1 : L == 1 ? a.pk.w2 : L == 2 ? a.pk.w3 : a.pk.w4;
+                    for (int g = 0; g < nkb; ++g) {
+                        if ((used >> g) & 1u) {
+                            if (!mbar_wait_ab(&mb_free[g], (ph_free >> g) & 1u, abort_v)) {
+                                ok = false;
+                                break;
+                            }
+                            ph_free ^= 1u << g;
+                        }
+                        used |= 1u << g;
+                        tma_load(Bs + g * kSlotBytes, a.img + base + (int64_t)g * bytes, bytes,
+                                 &mb_full[g]);
+                        ++n_issued[g];
+                    }
+                }
+            }
+            if (!ok) *abort_v = 1;
+            // drain: every copy issued has landed
+            for (int g = 0; g < 4; ++g)
+                if (n_issued[g]) mbar_wait(&mb_full[g], (n_issued[g] - 1) & 1u);
+        }
+        __syncwarp();
+    } else {
+        // ----------------------------------------------------------- epilogue
+        const int qd = warp & 3, cg = warp >> 2;       // lane quadrant, column group
+        const int row = 32 * qd + lane;                // row of the tile (TMEM lane)
+        const uint32_t lane_base = (uint32_t)(32 * qd) << 16;
+        // Column group 0 keeps the last layer's outputs (one thread per row,
+        // every column); groups 1-3 build the next tile's input meanwhile,
+        // three threads per row: input chunks (8 columns) 0-3, 4-6 and 7-9.
+        const int bj = cg - 1;
+        const int ch_lo = bj == 0 ? 0 : bj == 1 ? 4 : 7, ch_hi = bj == 0 ? 4 : bj == 1 ? 7 : 10;
+        // input row `row` of tile tt (columns 0-79: K-blocks 0 and 1), and in
+        // proposal mode the row's size and occupancy words (rows buffer `rb`)
+        auto build_input = [&](int64_t tt, int rb) {
+            const int64_t gr = tt * kTileRows + row;
+            const bool in = gr < a.n;
+            if (a.propose) {
+                // rows are queries: features (log2 N / 23, shape features 0,
+                // the hardware vector) and the kernel's embedding
+                const int64_t q = a.q0 + (in ? gr : 0);
+                const long long N = in ? a.q_N[q] : 1;
+                const int32_t kk = in ? a.q_kernel[q] : 0;
+                const __nv_bfloat16* erow = a.emb_table + (int64_t)kk * kEmbLd;
+                for (int ch = ch_lo; ch < ch_hi; ++ch) {
+                    unsigned char* dst = As + swz_off(row, ch * 8, kTileRows);
+                    if (ch < 2) {
+                        float f[8];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-                        w[i] = *reinterpret_cast<const uint32_t*>(&h2);
+                        for (int i = 0; i < 8; ++i) f[i] = 0.f;
+                        if (in) {
+                            if (ch == 0) {
+                                f[0] = log2f((float)N) * (1.0f / 23.0f);
+                                for (int i = 0; i < 4; ++i) f[4 + i] = a.hw[i];
+                            } else {
+                                for (int i = 0; i < 3; ++i) f[i] = a.hw[4 + i];
+                            }
+                        }
+                        uint32_t w[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const __nv_bfloat162 h2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+                            w[i] = *reinterpret_cast<const uint32_t*>(&h2);
+                        }
+                        *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+                    } else {
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                                     :: "r"(smem_addr(dst)), "l"(erow + (ch - 2) * 8),
+                                        "r"(in ? 16u : 0u)
+                                     : "memory");
                     }
-                    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
-                } else {
-                    const void* src = a.emb_table + (int64_t)tile_kernel[r] * EMB + (ch - 2) * 8;
+                }
+                if (bj == 0) row_N[rb][row] = N;
+                if (bj == 2) {
+                    // the occupancy words stored after the embedding
+                    for (int h = 0; h < 2; ++h)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                                     :: "r"(smem_addr(&row_occ[rb][row][4 * h])),
+                                        "l"(erow + EMB + 8 * h)
+                                     : "memory");
+                }
+            } else {
+                for (int ch = ch_lo; ch < ch_hi; ++ch) {
+                    const void* src = a.X0 + (in ? gr : 0) * IN + ch * 8;
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                                 :: "r"(smem_addr(dst)), "l"(src), "r"(gr < a.n ? 16u : 0u)
+                                 :: "r"(smem_addr(As + swz_off(row, ch * 8, kTileRows))), "l"(src),
+                                    "r"(in ? 16u : 0u)
                                  : "memory");
                 }
             }
-        } else
-        // input tile: 128 rows x 80 columns into blocks 0-1 of the operand image
-        for (int c = tid; c < kTileRows * (IN / 8); c += kFusedThreads) {
-            const int r = c / (IN / 8), k = (c % (IN / 8)) * 8;
-            const int64_t gr = r0 + r;
-            const void* src = a.X0 + (gr < a.n ? gr : 0) * IN + k;
-            const uint32_t dst = smem_addr(As + swz_off(r, k, kTileRows));
-            const uint32_t bytes = gr < a.n ? 16u : 0u;     // rows past n: zeros
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
-                         :: "r"(dst), "l"(src), "r"(bytes) : "memory");
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        // builders: copies done, both input K-blocks (and the rows) announced
+        auto input_ready = [&]() {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            warp_arrive_async(&mb_act[0], lane);
+            if (lane == 0) {
+                mbar_arrive(&mb_act[1]);
+                if (a.propose) mbar_arrive(&mb_rows);
+            }
+        };
+        // group 0: no writes of its own; its arrival only counts
+        auto input_count = [&]() {
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&mb_act[0]);
+                mbar_arrive(&mb_act[1]);
+            }
+        };
+        uint32_t ph_mma = 0, ph_rows = 0;
+        bool ok = true;
+        if (cg > 0) {
+            build_input(blockIdx.x, 0);
+            input_ready();
+        } else {
+            input_count();
         }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        for (int layer = 0; layer < 4; ++layer) {
-            const int K = layer == 0 ? IN : H;
-            const int N = layer == 3 ? a.np : H;
-            if (!mbar_wait(&mbar_w, pw)) abort_flag = 1;
-            pw ^= 1;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            __syncthreads();
-            if (abort_flag) break;
-            if (tid == 0) {
-                const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
-                const uint32_t idesc = umma_idesc_bf16(kTileRows, N);
-                for (int s = 0; s < K / 16; ++s) {
-                    const int kb = s >> 2, ks = s & 3;
-                    umma_bf16(tmem, umma_desc(a0 + kb * kTileRows * 128 + ks * 32),
-                              umma_desc(b0 + kb * N * 128 + ks * 32), idesc, s > 0);
-                }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(smem_addr(&mbar_mma)) : "memory");
+        int it = 0;
+        for (int64_t t = blockIdx.x; t < n_tiles && ok; t += gridDim.x, ++it) {
+            const int64_t r0 = t * kTileRows;
+            const bool more = t + gridDim.x < n_tiles;
+            const int rb = it & 1;
+            // group 0, proposal mode: this tile's rows are staged (waited
+            // here, before the next tile's builders can reuse the phase)
+            if (cg == 0 && a.propose) {
+                if (!warp_wait(&mb_rows, ph_rows, abort_v)) { ok = false; break; }
+                ph_rows ^= 1;
             }
-            if (!mbar_wait(&mbar_mma, pm)) abort_flag = 1;
-            pm ^= 1;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            // the weights buffer is free: copy the next layer's (or the next
-            // tile's first layer's) weights while the epilogue runs
-            if (tid == 0 && !abort_flag) {
-                if (layer == 0) tma_load(Bs, a.img + a.pk.w2, (uint32_t)(H * H * 2), &mbar_w);
-                else if (layer == 1) tma_load(Bs, a.img + a.pk.w3, (uint32_t)(H * H * 2), &mbar_w);
-                else if (layer == 2) tma_load(Bs, a.img + a.pk.w4, (uint32_t)(a.np * H * 2), &mbar_w);
-                else if (t + gridDim.x < n_tiles)
-                    tma_load(Bs, a.img + a.pk.w1, (uint32_t)(H * kKPad1 * 2), &mbar_w);
-            }
-            if (layer < 3) {
-                const float* bias = bias_s + layer * H;
-                for (int c0 = half * 128; c0 < half * 128 + 128; c0 += 16) {
-                    float v[16];
-                    tmem_ld16(tmem + lane_base + (uint32_t)c0, v);
+            // hidden layers: bias + GELU, BF16 operand of the next layer
+            for (int L = 0; L < 3; ++L) {
+                if (!warp_wait(&mb_mma, ph_mma, abort_v)) { ok = false; break; }
+                ph_mma ^= 1;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t tb = tmem + lane_base + (uint32_t)(L & 1) * H + (uint32_t)(cg * 16);
+                const float* bias = bias_s + L * H;
+                float v[32];                           // K-blocks two at a time
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    if ((g & 1) == 0) tmem_ld16x2(tb + 64 * g, tb + 64 * (g + 1), v);
+                    const int c0 = g * 64 + cg * 16;
                     uint32_t packed[8];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float x0 = gelu(v[2 * j] + bias[c0 + 2 * j]);
-                        const float x1 = gelu(v[2 * j + 1] + bias[c0 + 2 * j + 1]);
-                        const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
-                        packed[j] = *reinterpret_cast<const uint32_t*>(&h2);
-                    }
-                    *reinterpret_cast<uint4*>(As + swz_off(row_in_tile, c0, kTileRows)) =
+                    for (int j = 0; j < 8; ++j)
+                        packed[j] = gelu2_bf16(v[16 * (g & 1) + 2 * j], v[16 * (g & 1) + 2 * j + 1],
+                                               bias[c0 + 2 * j], bias[c0 + 2 * j + 1]);
+                    *reinterpret_cast<uint4*>(As + swz_off(row, c0, kTileRows)) =
                         make_uint4(packed[0], packed[1], packed[2], packed[3]);
-                    *reinterpret_cast<uint4*>(As + swz_off(row_in_tile, c0 + 8, kTileRows)) =
+                    *reinterpret_cast<uint4*>(As + swz_off(row, c0 + 8, kTileRows)) =
                         make_uint4(packed[4], packed[5], packed[6], packed[7]);
+                    warp_arrive_async(&mb_act[g], lane);
                 }
-            } else if (a.propose) {
+            }
+            if (!ok) break;
+            // output layer
+            if (!warp_wait(&mb_mma, ph_mma, abort_v)) { ok = false; break; }
+            ph_mma ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (cg > 0) {
+                // K-blocks 0-1 are free: the next tile's input
+                if (more) {
+                    build_input(t + gridDim.x, rb ^ 1);
+                    input_ready();
+                }
+                continue;
+            }
+            // group 0: the next tile's first products may start (they use
+            // the other accumulator)
+            if (more) input_count();
+            const int64_t gr = r0 + row;
+            const float* bias = bias_s + 3 * H;
+            const uint32_t tb = tmem + lane_base + (uint32_t)H;
+            if (a.propose) {
                 // the k least predictions among the meaningful shapes of the
-                // row's query: each half of the warps keeps a sorted list for
-                // its half of the columns, then half 0 merges the two
-                const int64_t gr = r0 + row_in_tile;
-                const int64_t q = a.q0 + (gr < a.n ? gr : 0);
-                const long long N = a.q_N[q];
-                const int32_t kk = tile_kernel[row_in_tile];
-                const uint8_t* occ = a.occ + (int64_t)kk * a.n_out;
-                const float* bias = bias_s + 3 * H;
+                // row's query, ties to the lower shape index
+                const long long qN = row_N[rb][row];
                 float bv[KMAX];
                 int bi[KMAX];
 #pragma unroll
                 for (int j = 0; j < KMAX; ++j) { bv[j] = INFINITY; bi[j] = -1; }
-                const int cols = a.np >> 1;
-                for (int c0 = half * cols; c0 < half * cols + cols; c0 += 8) {
-                    float v[8];
-                    tmem_ld8(tmem + lane_base + (uint32_t)c0, v);
+                for (int c0 = 0; c0 < a.np; c0 += 32) {
+                    float v[32];
+                    tmem_ld16x2(tb + c0, tb + c0 + 16, v);
+                    const uint32_t ob = row_occ[rb][row][c0 >> 5];
+                    // branch-free: a shape that is not meaningful enters as
+                    // +inf and never displaces an entry (nor does a NaN)
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
+                    for (int j = 0; j < 32; ++j) {
                         const int c = c0 + j;
-                        if (c >= a.n_out || cfg_max[c] > N || !occ[c]) continue;
-                        float x = v[j] + bias[c];
+                        if (c >= a.n_out) break;          // the same for every lane
+                        const bool use = cfg_max[c] <= qN && ((ob >> j) & 1u);
+                        float x = use ? v[j] + bias[c] : INFINITY;
                         int xi = c;
 #pragma unroll
                         for (int m = 0; m < KMAX; ++m) {
-                            if (x < bv[m]) {
-                                const float tv = bv[m]; const int ti = bi[m];
-                                bv[m] = x; bi[m] = xi;
-                                x = tv; xi = ti;
-                            }
+                            const bool sw = x < bv[m];
+                            const float tv = bv[m];
+                            const int ti = bi[m];
+                            bv[m] = sw ? x : tv;
+                            bi[m] = sw ? xi : ti;
+                            x = sw ? tv : x;
+                            xi = sw ? ti : xi;
                         }
                     }
                 }
-                // half 1 hands its list over through the (now free) operand buffer
-                float* sv = reinterpret_cast<float*>(As);
-                int* si = reinterpret_cast<int*>(As) + kTileRows * KMAX;
-                if (half == 1) {
+                if (gr < a.n) {
+                    const int64_t q = a.q0 + gr;
 #pragma unroll
-                    for (int m = 0; m < KMAX; ++m) {
-                        sv[row_in_tile * KMAX + m] = bv[m];
-                        si[row_in_tile * KMAX + m] = bi[m];
-                    }
-                }
-                __syncthreads();
-                if (half == 0 && gr < a.n) {
-                    // merge: equal values keep half 0's (lower) index first
-                    int ia = 0, ib = 0;
-                    for (int m = 0; m < a.k; ++m) {
-                        float va = INFINITY, vb = INFINITY;
-                        int xa = -1, xb = -1;
-#pragma unroll
-                        for (int j = 0; j < KMAX; ++j) if (j == ia) { va = bv[j]; xa = bi[j]; }
-                        if (ib < KMAX) { vb = sv[row_in_tile * KMAX + ib]; xb = si[row_in_tile * KMAX + ib]; }
-                        int pick;
-                        if (xb >= 0 && (xa < 0 || vb < va)) { pick = xb; ++ib; }
-                        else { pick = xa; if (xa >= 0) ++ia; }
-                        a.cand[q * a.k + m] = pick;
-                    }
+                    for (int m = 0; m < KMAX; ++m)
+                        if (m < a.k) a.cand[q * a.k + m] = bi[m];
                 }
             } else {
-                const int64_t gr = r0 + row_in_tile;
-                const float* bias = bias_s + 3 * H;
-                const int cols = a.np >> 1;
-                for (int c0 = half * cols; c0 < half * cols + cols; c0 += 8) {
-                    float v[8];
-                    tmem_ld8(tmem + lane_base + (uint32_t)c0, v);
+                for (int c0 = 0; c0 < a.np; c0 += 32) {
+                    float v[32];
+                    tmem_ld16x2(tb + c0, tb + c0 + 16, v);
                     if (gr < a.n) {
 #pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            if (c0 + j < a.n_out)
-                                a.pred[gr * a.n_out + c0 + j] = v[j] + bias[c0 + j];
+                        for (int j = 0; j < 32; ++j)
+                            if (c0 + j < a.n_out) a.pred[gr * a.n_out + c0 + j] = v[j] + bias[c0 + j];
                     }
                 }
             }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
         }
-        if (abort_flag) break;
+        if (!ok) *abort_v = 1;
+        asm volatile("cp.async.wait_all;" ::: "memory");
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
     if (abort_flag) {
         // a wait gave up: every prediction of this CTA's tiles NaN (proposal
         // mode: no candidates)
@@ -1040,11 +1246,11 @@ fused_forward_kernel(const __grid_constant__ FusedArgs a) {
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0)
+    if (warp == kEpiWarps) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
-                     :: "r"(tmem), "r"((uint32_t)H));
+                     :: "r"(tmem), "r"((uint32_t)(2 * H)));
+    }
 }
 
 // Packed weight images for the fused kernel, from the BF16 parameter copy;
@@ -1476,6 +1682,27 @@ __global__ void occupancy_table_kernel(const __grid_constant__ ProposeArgs a) {
     }
 }
 
+// the same facts as bits, stored after each kernel's embedding in the
+// table row: word w holds shapes 32 w .. 32 w + 31 (zero past the shapes)
+__global__ void occupancy_bits_kernel(const __grid_constant__ ProposeArgs a,
+                                      __nv_bfloat16* table) {
+    const int64_t total = (int64_t)a.n_kernels * 8;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t kk = (int32_t)(i >> 3);
+        const int w = (int)(i & 7);
+        uint32_t b = 0;
+        for (int j = 0; j < 32; ++j) {
+            const int c = 32 * w + j;
+            if (c >= a.n_cfg) break;
+            const long long T = (long long)a.cfg[3 * c] * a.cfg[3 * c + 1] * a.cfg[3 * c + 2];
+            if (occupancy_blocks(T, a.regs[kk], a.smem[kk], a.Bm, a.Wm, a.Rm, a.Zm, a.Tmax) > 0)
+                b |= 1u << j;
+        }
+        reinterpret_cast<uint32_t*>(table + (int64_t)kk * kEmbLd + EMB)[w] = b;
+    }
+}
+
 __global__ void propose_rows_kernel(const __grid_constant__ ProposeArgs a) {
     const int64_t total = a.nq * a.n_cfg;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < total;
@@ -1571,10 +1798,13 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
     // fused kernel builds its rows itself and needs no row buffers
     const int64_t qchunk = no > 0 ? kMaxRows : std::max<int64_t>(1, kMaxRows / n_cfg);
     const int64_t rows = no > 0 ? 0 : qchunk * n_cfg;
+    // occupancy per (kernel, shape): bytes here for the per-row form; the
+    // per-query form keeps bits in the embedding table's rows
+    const size_t occ_bytes = (size_t)n_cfg;
     // workspace: network buffers for `rows` rows + per-kernel embeddings + row tables
     const size_t base = mlp_ws_bytes(rows, nc, no, n_kernels, false);
     const size_t extra = align256(2 * (size_t)n_kernels * nc) + align256(4 * (size_t)rows) * 2 +
-                         align256(8 * (size_t)rows) * 2 + align256((size_t)n_kernels * n_cfg) +
+                         align256(8 * (size_t)rows) * 2 + align256((size_t)n_kernels * occ_bytes) +
                          kFusedScratch + (no > 0 ? align256(4 * (size_t)q->n_queries) : 0);
     if ((st = ensure_workspace(c, base + extra, s)) != KLR_OK) return st;
     MlpWs w = carve(c->ws, rows, nc, no, n_kernels, false);
@@ -1590,7 +1820,7 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
     int64_t* row_query = reinterpret_cast<int64_t*>(p);
     p += align256(8 * (size_t)rows);
     uint8_t* occ = reinterpret_cast<uint8_t*>(p);
-    p += align256((size_t)n_kernels * n_cfg);
+    p += align256((size_t)n_kernels * occ_bytes);
     unsigned char* img = reinterpret_cast<unsigned char*>(p);
     int* err = reinterpret_cast<int*>(img + kFusedScratch - 256);
     p += kFusedScratch;
@@ -1608,7 +1838,7 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
     g.B = w.pb + o.E;
     g.ldb = nc;
     g.Cb = w.emb_table;
-    g.ldcb = EMB;
+    g.ldcb = kEmbLd;
     if ((st = gemm<false, false, EPI_BF16>(g, s)) != KLR_OK) return st;
     {
         ProposeArgs ta{};
@@ -1623,7 +1853,11 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
         ta.Zm = hw->smem_per_sm;
         ta.Tmax = hw->max_threads_per_block;
         ta.occ = occ;
-        occupancy_table_kernel<<<blocks_for((int64_t)n_kernels * n_cfg, 256), 256, 0, s>>>(ta);
+        if (no > 0)
+            occupancy_bits_kernel<<<blocks_for((int64_t)n_kernels * 8, 256), 256, 0, s>>>(
+                ta, w.emb_table);
+        else
+            occupancy_table_kernel<<<blocks_for((int64_t)n_kernels * n_cfg, 256), 256, 0, s>>>(ta);
         KLR_CHECK_CUDA(cudaGetLastError());
     }
     if (no > 0) {
@@ -1641,7 +1875,6 @@ extern "C" klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float*
         fa.emb_table = w.emb_table;
         for (int i = 0; i < 7; ++i) fa.hw[i] = net->hw_feat[i];
         fa.cfg = cfg;
-        fa.occ = occ;
         fa.k = k;
         fa.cand = cand_out;
         fa.q0 = 0;

@@ -296,3 +296,43 @@ def test_trained_head_proposer_beats_random_candidates(klr, ctx):
     assert np.all(reg_s >= -1e-5)
     assert np.mean(reg_s) < 0.5 * np.mean(reg_r), (np.mean(reg_s), np.mean(reg_r))
     assert np.median(reg_s) < 0.05
+
+
+@pytest.mark.parametrize("dims,k", [(2, 8), (2, 16), (3, 5)])
+def test_proposal_is_topk_of_predictions(klr, ctx, dims, k):
+    """klr_propose's fused top-k against the network's own outputs: for every
+    query, the k meaningful shapes (B_active > 0 by Fig. 1, every block side
+    <= N) of least prediction, ties to the lower shape index, -1 past the
+    meaningful ones.  The proposal builds its input rows inside the kernel and
+    never writes the outputs; klr_mlp_predict writes them from the same
+    network, so the two agree exactly.  60,000 queries: several 128-row tiles
+    per CTA and a ragged last tile; 251 shapes (3D) put four 16-column chunks
+    in every column group."""
+    from oracle import occupancy as oocc
+    nk, per = 500, 120
+    gt = W.ground_truth(51, nk, 3, 2, 8, 23, 10)
+    n_coef = 8 * gt.coef.shape[-1]
+    cfg_np = klr.enumerate_configs(dims)
+    n_cfg = len(cfg_np)
+    t = lambda a: torch.tensor(a).cuda()
+    coef = t(gt.coef.astype(np.float32)).reshape(nk, n_coef)
+    regs, smem, cfg = t(gt.regs), t(gt.smem), t(cfg_np)
+    hw = klr.make_hw(W.HARDWARE)
+    q = W.queries_per_kernel(nk, W.log_spaced_sizes(per))
+    qo, qn = t(q.offsets), t(q.sizes)
+    sur = klr.Surrogate(ctx, n_coef, _init(klr, n_coef, 12 + dims, n_cfg), HW_FEAT, n_out=n_cfg)
+    cand = sur.propose(coef, regs, smem, hw, cfg, qo, qn, k)
+    kern = t(np.repeat(np.arange(nk, dtype=np.int32), per))
+    pred = sur.predict(coef, cfg, kern, qn, None)
+    torch.cuda.synchronize()
+    cand, pred = cand.cpu().numpy(), pred.cpu().numpy()
+    T = np.prod(cfg_np.astype(np.int64), axis=1)
+    occ = np.array([[oocc.active_blocks(int(T[c]), int(gt.regs[i]), int(gt.smem[i]), W.HARDWARE) > 0
+                     for c in range(n_cfg)] for i in range(nk)])
+    bmax = cfg_np.max(axis=1)
+    mask = occ[np.repeat(np.arange(nk), per)] & (bmax[None, :] <= q.sizes[:, None])
+    val = np.where(mask & np.isfinite(pred), pred, np.inf)
+    order = np.argsort(val, axis=1, kind="stable")[:, :k]      # value, then index
+    want = np.where(np.isfinite(np.take_along_axis(val, order, axis=1)), order, -1)
+    assert np.all(mask.sum(axis=1) > 0)
+    assert np.array_equal(cand, want), np.argwhere(cand != want)[:5]
