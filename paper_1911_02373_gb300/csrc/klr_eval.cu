@@ -65,6 +65,7 @@ struct EvalParams {
     const int32_t* cand;        // candidate mode: n_q x kc shape indices, or NULL
     int kc;
     const uint8_t* done;        // history mode: 1 for queries answered already, or NULL
+    int slots;                  // warp re-rank: shapes specialised per kernel
     uint8_t exps[kMaxBasis][kMaxVars];
     // terms grouped by their power of N (increasing term index within a
     // group): group j is ord[jstart[j] .. jstart[j + 1])
@@ -520,19 +521,18 @@ eval_kernel(const __grid_constant__ EvalParams P) {
 
 // ---------------------------------------------------------------------------
 // Candidate re-rank with one warp per kernel: the kernel's coefficients, the
-// union of the shapes proposed for its queries (at most kSlots specialised
+// union of the shapes proposed for its queries (at most P.slots specialised
 // per kernel; others are evaluated unspecialised) and their specialised
 // polynomials live in the warp's own shared memory, so warps never wait on
 // one another; lanes then take (query, candidate) pairs, kc lanes per query.
 // ---------------------------------------------------------------------------
-constexpr int kSlots = 48, kRerankWarps = 4;
+constexpr int kRerankWarps = 4;
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // bytes of one warp's region
-__host__ __device__ inline int rerank_slots(int n_cfg) { return n_cfg < kSlots ? n_cfg : kSlots; }
-__host__ __device__ inline size_t rerank_warp_bytes(int u, int n_cfg, int nc) {
-    const size_t ns = (size_t)rerank_slots(n_cfg);
+__host__ __device__ inline size_t rerank_warp_bytes(int u, int n_cfg, int nc, int slots) {
+    const size_t ns = (size_t)slots;
     return align16(4 * (size_t)8 * u) + align16(4 * ns * 8 * nc) + align16(sizeof(CfgInfo) * ns) +
            align16(4 * ns) + align16(4 * ns) + align16(2 * (size_t)n_cfg) + 32;
 }
@@ -542,12 +542,12 @@ __global__ void __launch_bounds__(32 * kRerankWarps)
 rerank_kernel(const __grid_constant__ EvalParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NC = 2 * (D + 1);
-    const int m = P.m, u = P.u, n_cfg = P.n_cfg, kc = P.kc, n_slot = rerank_slots(n_cfg);
+    const int m = P.m, u = P.u, n_cfg = P.n_cfg, kc = P.kc, n_slot = P.slots;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
     float* bmon = reinterpret_cast<float*>(smem_raw);                 // n_cfg x m
     unsigned char* wb = smem_raw + align16(4 * (size_t)n_cfg * m) +
-                        (size_t)w * rerank_warp_bytes(u, n_cfg, NC);
+                        (size_t)w * rerank_warp_bytes(u, n_cfg, NC, n_slot);
     float* coef_s = reinterpret_cast<float*>(wb);
     wb += align16(4 * (size_t)8 * u);
     float* spec = reinterpret_cast<float*>(wb);
@@ -1124,9 +1124,18 @@ klr_status klr_argmin_candidates(klr_ctx* ctx, const klr_program* prog, const kl
     P.kc = k;
     if (k <= 32 && (k & (k - 1)) == 0) {
         // one warp per kernel
+        // as many shapes specialised per kernel as keep three blocks per SM
+        // (every shape when they fit), at least 48 (or every shape)
         const int NC = 2 * (P.degree + 1);
-        const size_t smem = align16(4 * (size_t)P.n_cfg * P.m) +
-                            kRerankWarps * rerank_warp_bytes(P.u, P.n_cfg, NC);
+        auto smem_for = [&](int sl) {
+            return align16(4 * (size_t)P.n_cfg * P.m) +
+                   kRerankWarps * rerank_warp_bytes(P.u, P.n_cfg, NC, sl);
+        };
+        int slots = std::min(P.n_cfg, 48);
+        for (int sl = std::min(P.n_cfg, 256); sl > slots; sl -= 4)
+            if (3 * (smem_for(sl) + 1024) <= (size_t)c->smem_optin + 1024) { slots = sl; break; }
+        P.slots = slots;
+        const size_t smem = smem_for(slots);
         if (smem <= c->smem_optin) {
             auto go = [&](auto kern) -> klr_status {
                 int per_sm = 0;
