@@ -625,21 +625,30 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
             cinfo[s] = ci;
             wrcp[s] = 1.0f / (float)ci.wave;
         }
-        for (int idx = lane; idx < n_used * 8; idx += 32) {
-            const int s = idx >> 3, i = idx & 7, c = slot_cfg[s];
-            float* sp = spec + (size_t)idx * NC;
-            // the same sums, in the same order, as the sweep's specialisation
+        // two (shape, metric) items per lane at a time (four independent
+        // sums): the same sums, in the same order, as the sweep's
+        // specialisation
+        for (int idx = lane; idx < n_used * 8; idx += 64) {
+            const int idx2 = idx + 32 < n_used * 8 ? idx + 32 : idx;   // a repeat is harmless
+            const int c1 = slot_cfg[idx >> 3], i1 = idx & 7;
+            const int c2 = slot_cfg[idx2 >> 3], i2 = idx2 & 7;
+            float* sp1 = spec + (size_t)idx * NC;
+            float* sp2 = spec + (size_t)idx2 * NC;
 #pragma unroll
             for (int j = 0; j <= D; ++j) {
-                float pa = 0.f, qa = 0.f;
+                float pa1 = 0.f, qa1 = 0.f, pa2 = 0.f, qa2 = 0.f;
                 for (int r = P.jstart[j]; r < P.jstart[j + 1]; ++r) {
                     const int t = P.ord[r];
-                    const float bm = bmon[c * m + t];
-                    pa = fmaf(coef_s[i * u + t], bm, pa);
-                    qa = fmaf(coef_s[i * u + m + t], bm, qa);
+                    const float bm1 = bmon[c1 * m + t], bm2 = bmon[c2 * m + t];
+                    pa1 = fmaf(coef_s[i1 * u + t], bm1, pa1);
+                    qa1 = fmaf(coef_s[i1 * u + m + t], bm1, qa1);
+                    pa2 = fmaf(coef_s[i2 * u + t], bm2, pa2);
+                    qa2 = fmaf(coef_s[i2 * u + m + t], bm2, qa2);
                 }
-                sp[j] = pa;
-                sp[D + 1 + j] = qa;
+                sp1[j] = pa1;
+                sp1[D + 1 + j] = qa1;
+                sp2[j] = pa2;
+                sp2[D + 1 + j] = qa2;
             }
         }
         __syncwarp();

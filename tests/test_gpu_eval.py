@@ -175,6 +175,40 @@ def test_candidate_rerank_matches_oracle(klr, ctx, kc, n_sizes):
     assert strict > 0.9 * n_q
 
 
+@pytest.mark.parametrize("degree", [2, 3])
+def test_candidate_rerank_equals_table_minimum(klr, ctx, degree):
+    """The warp re-rank specialises the proposed shapes with the sweep's own
+    sums, in the same order, and evaluates them with the same code: its cycles
+    equal, bit for bit, the least entry of the sweep's FP32 cycles table over
+    each query's candidates (ties to the lower shape index), and its choice is
+    that entry's shape."""
+    gt = G.make_program(7, 64, degree=degree)
+    coef = gt.coef.astype(np.float32)
+    q = W.queries_per_kernel(64, W.log_spaced_sizes(32))
+    n_q, kc = len(q.sizes), 16
+    keys = W.stream_keys(43, (degree,), np.arange(n_q, dtype=np.uint64))
+    cand = (W.words(keys[:, None], np.arange(kc, dtype=np.uint64)[None, :]) % np.uint64(51))
+    cand = cand.astype(np.int32)
+    prog = G.gpu_program(klr, torch.tensor(coef).cuda(), gt, torch)
+    hw = klr.make_hw(W.HARDWARE)
+    cfg = torch.tensor(klr.enumerate_configs(2)).cuda()
+    qo, qn = torch.tensor(q.offsets).cuda(), torch.tensor(q.sizes).cuda()
+    table = ctx.eval(prog, hw, cfg, qo, qn, out_dtype=klr.F32)
+    best, cyc, st = klr.argmin_candidates(ctx, prog, hw, cfg, qo, qn, torch.tensor(cand).cuda())
+    torch.cuda.synchronize()
+    table, best, cyc = table.cpu().numpy(), best.cpu().numpy(), cyc.cpu().numpy()
+    vals = np.take_along_axis(table, cand.astype(np.int64), axis=1)      # (n_q, kc)
+    key = np.where(np.isfinite(vals), vals, np.inf)
+    # least value, then least shape index
+    order = np.lexsort((cand, key), axis=1)[:, 0]
+    want_v = key[np.arange(n_q), order]
+    want_c = np.where(np.isfinite(want_v), cand[np.arange(n_q), order], -1)
+    assert np.array_equal(best, want_c)
+    fin = np.isfinite(want_v)
+    assert np.array_equal(cyc[fin], want_v[fin].astype(np.float32))
+    assert fin.mean() > 0.9
+
+
 @pytest.mark.parametrize("eps", [0.0, 0.02, 0.2])
 def test_refined_choice_matches_oracle(klr, ctx, eps):
     """klr_argmin_refined on klr_eval's table against the oracle's refinement of
