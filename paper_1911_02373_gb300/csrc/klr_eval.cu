@@ -654,13 +654,13 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
         __syncwarp();
         const int64_t npairs = (qb - qa) * kc;
         const int64_t span = (npairs + 31) & ~(int64_t)31;
-        for (int64_t pi = lane; pi < span; pi += 32) {
-            const bool valid = pi < npairs;
-            const int64_t q = qa + (valid ? pi / kc : 0);
-            const int j = (int)(pi & (kc - 1));
-            const int c = valid ? P.cand[q * kc + j] : -1;
-            int st = 0;
-            float e = INFINITY;
+        // cycles of pair pi (query pi / kc, its candidate pi mod kc)
+        auto pair_eval = [&](int64_t pi, float& e, int& st, int& c, int64_t& q, bool& valid) {
+            valid = pi < npairs;
+            q = qa + (valid ? pi / kc : 0);
+            c = valid ? P.cand[q * kc + (int)(pi & (kc - 1))] : -1;
+            st = 0;
+            e = INFINITY;
             if (c >= 0 && c < n_cfg) {
                 const long long N = P.q_N[q];
                 const int s = slot_of[c];
@@ -681,6 +681,9 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
                     }
                 }
             }
+        };
+        // the least (cycles, shape) over the kc lanes of each query
+        auto pair_finish = [&](int64_t pi, float e, int st, int c, int64_t q, bool valid) {
             int ci = e < INFINITY ? c : 0x7fffffff;
             for (int o = 1; o < kc; o <<= 1) {
                 const float oe = __shfl_xor_sync(full, e, o);
@@ -688,12 +691,24 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
                 st |= __shfl_xor_sync(full, st, o);
                 if (oe < e || (oe == e && oc < ci)) { e = oe; ci = oc; }
             }
-            if (valid && j == 0) {
+            if (valid && (pi & (kc - 1)) == 0) {
                 const bool none = !(e < INFINITY);
                 P.best[q] = none ? -1 : ci;
                 reinterpret_cast<float*>(P.best_cycles)[q] = e;
                 if (P.q_status) P.q_status[q] = st | (none ? KLR_Q_NONE_FEASIBLE : 0);
             }
+        };
+        // two pairs per lane at a time (independent work for the scheduler);
+        // every lane runs the same number of iterations
+        for (int64_t pi = lane; pi < span; pi += 64) {
+            float e1, e2;
+            int s1, s2, c1, c2;
+            int64_t q1, q2;
+            bool v1, v2;
+            pair_eval(pi, e1, s1, c1, q1, v1);
+            pair_eval(pi + 32, e2, s2, c2, q2, v2);
+            pair_finish(pi, e1, s1, c1, q1, v1);
+            pair_finish(pi + 32, e2, s2, c2, q2, v2);
         }
         __syncwarp();
     }
