@@ -60,13 +60,16 @@ def parse():
     ap.add_argument("--sweep-check-kernels", type=int, default=1000,
                     help="kernels of the 3D sweep checked against the oracle")
     ap.add_argument("--sur-kernels", type=int, default=50000)
-    ap.add_argument("--sur-rows-per-kernel", type=int, default=400)
-    ap.add_argument("--sur-epochs", type=int, default=100)
+    ap.add_argument("--sur-rows-per-kernel", type=int, default=1632,
+                    help="training rows per kernel (per-query form: rows / 51 sizes)")
+    ap.add_argument("--sur-epochs", type=int, default=300)
     ap.add_argument("--sur-form", default="query", choices=["query", "row"],
                     help="surrogate output form: per (kernel, N) query or per (kernel, N, shape) row")
     ap.add_argument("--sur-lr", type=float, default=2e-3)
     ap.add_argument("--sur-queries-per-kernel", type=int, default=20)
     ap.add_argument("--sur-k", type=int, default=8)
+    ap.add_argument("--sur-k-list", default="4,8,16",
+                    help="candidate counts of the proposal/regret frontier (one training)")
     ap.add_argument("--prec-fits", type=int, default=4096)
     ap.add_argument("--prec-check-fits", type=int, default=64)
     ap.add_argument("--cpu-sample-kernels", type=int, default=0,
@@ -689,6 +692,16 @@ def run_surrogate(args):
     rreg = rb[1].cpu().numpy()[ok] / c_best[ok] - 1.0
     rreg = np.where(np.isfinite(rreg), rreg, np.inf)
     pct = lambda a, p: float(np.percentile(a, p))
+    # the frontier: other candidate counts with the same network
+    frontier = []
+    for kk in sorted({int(v) for v in args.sur_k_list.split(",") if v.strip()} | {args.sur_k}):
+        ms_k, res_k = timed(lambda: proposer.propose_and_rerank(ctx, sur, prog, hw, coef, regs,
+                                                                smem, cfg, qo, qn, kk))
+        rg = res_k[1].cpu().numpy().astype(np.float64)[ok] / c_best[ok] - 1.0
+        rg = np.where(np.isfinite(rg), rg, np.inf)
+        frontier.append({"k": kk, "ms": ms_k, "speedup_vs_plain": plain_ms / ms_k,
+                         "regret_mean": float(np.mean(np.minimum(rg, 10))),
+                         "regret_median": pct(rg, 50), "within_1pct": float(np.mean(rg <= 0.01))})
     return {"metric": "argmin queries/s (surrogate top-k proposal + exact re-rank)",
             "value": n_q / (sur_ms * 1e-3), "unit": "queries/s", "n_gpus": 1, "steps": K,
             "higher_is_better": True, "dtype": "bf16 (network), f32 (re-rank)",
@@ -708,6 +721,7 @@ def run_surrogate(args):
                             "median": pct(reg, 50), "p90": pct(reg, 90), "p99": pct(reg, 99),
                             "exact_fraction": float(np.mean(reg <= 1e-6)),
                             "within_1pct": float(np.mean(reg <= 0.01))},
+            "frontier": frontier,
             "random_k_regret": {"mean": float(np.mean(np.minimum(rreg, 10))),
                                 "median": pct(rreg, 50),
                                 "within_1pct": float(np.mean(rreg <= 0.01))}}
