@@ -678,6 +678,10 @@ def run_surrogate(args):
     ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=klr.F32, autotune=True)
     plain_tune = ctx.last_tune
     plain_ms, plain = timed(lambda: ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=klr.F32))
+    # the FP32 sweep alone (every cycle of every shape, no FP64 re-decision of
+    # near-ties), as the table kernel computes it
+    table_ms, _ = timed(lambda: ctx.eval(prog, hw, cfg, qo, qn, out_dtype=klr.F32))
+    tie_frac = float(((plain[3] & klr.Q_TIE_RESOLVED) != 0).float().mean())
     sur_ms, surr = timed(lambda: proposer.propose_and_rerank(ctx, sur, prog, hw, coef, regs, smem,
                                                              cfg, qo, qn, args.sur_k))
     prop_ms, _ = timed(lambda: sur.propose(coef, regs, smem, hw, cfg, qo, qn, args.sur_k))
@@ -711,6 +715,7 @@ def run_surrogate(args):
                        "epochs": args.sur_epochs, "batch": batch, "train_steps": steps,
                        "queries": n_q, "k": args.sur_k, "configs": 51},
             "plain_sweep": {"ms": plain_ms, "queries_per_s": n_q / (plain_ms * 1e-3),
+                            "fp64_redecided_fraction": tie_frac, "fp32_table_ms": table_ms,
                             "autotuned_threads": 32 << plain_tune[0]},
             "surrogate_path": {"ms": sur_ms, "propose_ms": prop_ms,
                                "speedup_vs_plain": plain_ms / sur_ms},

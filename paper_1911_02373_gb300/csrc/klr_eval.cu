@@ -717,36 +717,48 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
 
 // Re-decide FP32 near-ties: FP64 evaluation of the tied candidates (or of
 // every configuration) with the unspecialised program, lowest index on ties.
-__global__ void __launch_bounds__(128)
+// One warp per tie record, lanes over its configurations; the least (value,
+// index) and the runner-up value (the least over every other configuration)
+// by warp reductions.
+constexpr int kTieWarps = 4;
+__global__ void __launch_bounds__(32 * kTieWarps)
 tie_kernel(const __grid_constant__ EvalParams P) {
     const int64_t n = min((int64_t)*P.tie_count, P.tie_cap);
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
-         r += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const unsigned full = 0xffffffffu;
+    for (int64_t r = blockIdx.x * (int64_t)kTieWarps + (threadIdx.x >> 5); r < n;
+         r += (int64_t)gridDim.x * kTieWarps) {
         const TieRecord rec = P.ties[r];
         const long long N = P.q_N[rec.q];
-        double bv = INFINITY, sv = INFINITY;
-        int bj = -1;
         const int cnt = rec.n < 0 ? P.n_cfg : rec.n;
-        // candidates are visited in increasing configuration index
-        int order[kTopK];
-        if (rec.n >= 0) {
-            for (int j = 0; j < cnt; ++j) order[j] = rec.cand[j];
-            for (int a = 1; a < cnt; ++a)
-                for (int b = a; b > 0 && order[b] < order[b - 1]; --b) {
-                    int t = order[b]; order[b] = order[b - 1]; order[b - 1] = t;
-                }
-        }
-        for (int j = 0; j < cnt; ++j) {
-            const int c = rec.n < 0 ? j : order[j];
+        double bv = INFINITY, sv = INFINITY;     // this lane's least and runner-up
+        int bj = 0x7fffffff;
+        for (int j = lane; j < cnt; j += 32) {
+            const int c = rec.n < 0 ? j : rec.cand[j];
             bool us;
-            double v = eval_full_f64(P, rec.kernel, N, c, us);
-            if (v < bv) { sv = bv; bv = v; bj = c; }
+            const double v = eval_full_f64(P, rec.kernel, N, c, us);
+            if (v < bv || (v == bv && c < bj)) { sv = bv; bv = v; bj = c; }
             else if (v < sv) sv = v;
         }
-        P.best[rec.q] = bj;
-        reinterpret_cast<float*>(P.best_cycles)[rec.q] = (float)bv;
-        if (P.margin) P.margin[rec.q] = isfinite(sv) ? (float)((sv - bv) / bv) : INFINITY;
-        write_launch(P, rec.q, N, bj);
+        // the least (value, index) over the warp
+        double gv = bv;
+        int gj = bj;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(full, gv, o);
+            const int oj = __shfl_xor_sync(full, gj, o);
+            if (ov < gv || (ov == gv && oj < gj)) { gv = ov; gj = oj; }
+        }
+        // runner-up: every lane's least except the chosen one, and its own
+        // runner-up
+        double rv = (bj == gj) ? sv : fmin(bv, sv);
+        for (int o = 16; o > 0; o >>= 1) rv = fmin(rv, __shfl_xor_sync(full, rv, o));
+        if (lane == 0) {
+            const int best = (gv < INFINITY) ? gj : -1;
+            P.best[rec.q] = best;
+            reinterpret_cast<float*>(P.best_cycles)[rec.q] = (float)gv;
+            if (P.margin) P.margin[rec.q] = isfinite(rv) ? (float)((rv - gv) / gv) : INFINITY;
+            write_launch(P, rec.q, N, best);
+        }
     }
 }
 
@@ -1118,8 +1130,8 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
     }
     st = launch_eval(c, P, f64, stream);
     if (st != KLR_OK || f64) return st;
-    const int grid = (int)std::min<int64_t>((P.tie_cap + 127) / 128, (int64_t)c->n_sm * 4);
-    tie_kernel<<<grid, 128, 0, stream>>>(P);
+    const int grid = (int)std::min<int64_t>((P.tie_cap + kTieWarps - 1) / kTieWarps, (int64_t)c->n_sm * 8);
+    tie_kernel<<<grid, 32 * kTieWarps, 0, stream>>>(P);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
 }
@@ -1219,8 +1231,8 @@ klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw, const i
     KLR_CHECK_CUDA(cudaMemsetAsync(P.tie_count, 0, sizeof(int), stream));
     st = launch_eval(&c, P, false, stream);
     if (st != KLR_OK) return st;
-    const int grid = (int)std::min<int64_t>((P.tie_cap + 127) / 128, (int64_t)c.n_sm * 4);
-    tie_kernel<<<grid, 128, 0, stream>>>(P);
+    const int grid = (int)std::min<int64_t>((P.tie_cap + kTieWarps - 1) / kTieWarps, (int64_t)c.n_sm * 8);
+    tie_kernel<<<grid, 32 * kTieWarps, 0, stream>>>(P);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
 }
@@ -1326,8 +1338,8 @@ klr_status klr_argmin_history(klr_ctx* ctx, klr_history* hist, const klr_program
     KLR_CHECK_CUDA(cudaGetLastError());
     P.done = done;
     if ((st = launch_eval(c, P, false, stream)) != KLR_OK) return st;
-    const int tgrid = (int)std::min<int64_t>((P.tie_cap + 127) / 128, (int64_t)c->n_sm * 4);
-    tie_kernel<<<tgrid, 128, 0, stream>>>(P);
+    const int tgrid = (int)std::min<int64_t>((P.tie_cap + kTieWarps - 1) / kTieWarps, (int64_t)c->n_sm * 8);
+    tie_kernel<<<tgrid, 32 * kTieWarps, 0, stream>>>(P);
     KLR_CHECK_CUDA(cudaGetLastError());
     history_insert_kernel<<<grid, 256, 0, stream>>>(P, *h, done);
     KLR_CHECK_CUDA(cudaGetLastError());
