@@ -718,6 +718,8 @@ def run_surrogate(args):
                             "fp64_redecided_fraction": tie_frac, "fp32_table_ms": table_ms,
                             "autotuned_threads": 32 << plain_tune[0]},
             "surrogate_path": {"ms": sur_ms, "propose_ms": prop_ms,
+                               "fp64_redecided_fraction":
+                                   float(((surr[2] & klr.Q_TIE_RESOLVED) != 0).float().mean()),
                                "speedup_vs_plain": plain_ms / sur_ms},
             "train": {"ms": train_ms, "rows_per_s": n_rows * args.sur_epochs / (train_ms * 1e-3),
                       "tuples_per_s": n_tuples * args.sur_epochs / (train_ms * 1e-3),

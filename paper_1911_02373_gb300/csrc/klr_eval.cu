@@ -34,7 +34,8 @@ constexpr double kTieWindow = 5e-5;
 struct TieRecord {
     int64_t q;
     int32_t kernel;
-    int32_t n;                  // candidates, or -1 for a full FP64 sweep
+    int32_t n;                  // candidates, -1: every configuration, -2: every one of
+                                // the query's proposed candidates (candidate mode)
     int32_t cand[kTopK];
 };
 
@@ -217,6 +218,103 @@ __device__ __noinline__ void decide_f64_inplace(const EvalParams& P, int k, int6
     if (P.margin) P.margin[q] = isfinite(sv) ? (float)((sv - bv) / bv) : INFINITY;
     if (P.q_status) P.q_status[q] = st;
     write_launch(P, q, N, bj);
+}
+
+// Candidate mode, the rare case of a full tie list: the FP64 decision among
+// the query's own candidates, in place (out of line, as above).
+__device__ __noinline__ void decide_cand_f64_inplace(const EvalParams& P, int k, int64_t q,
+                                                     long long N, int st) {
+    double bv = INFINITY;
+    int bj = -1;
+    for (int j = 0; j < P.kc; ++j) {
+        const int c = P.cand[q * P.kc + j];
+        if (c < 0 || c >= P.n_cfg) continue;
+        bool us;
+        const double v = eval_full_f64(P, k, N, c, us);
+        if (v < bv || (v == bv && bj >= 0 && c < bj)) { bv = v; bj = c; }
+    }
+    P.best[q] = bj;
+    reinterpret_cast<float*>(P.best_cycles)[q] = (float)bv;
+    if (P.q_status) P.q_status[q] = st | (bj < 0 ? KLR_Q_NONE_FEASIBLE : 0);
+}
+
+// Candidate mode, after the FP32 decision of one query (by lane j == 0 of
+// its group): a near-tie (another candidate within the FP32 error window of
+// the best) goes to the FP64 re-decision among the tied candidates (`tied`
+// of them, listed in tc; more than kTopK: among all of the query's
+// candidates), as in the full sweep.
+__device__ __noinline__ void cand_write(const EvalParams& P, int k, int64_t q, long long N,
+                                        float e, int ci, int st, int tied, int tc0, int tc1,
+                                        int tc2, int tc3) {
+    static_assert(kTopK == 4, "four tied candidates per record");
+    const int tc[kTopK] = {tc0, tc1, tc2, tc3};
+    const bool none = !(e < INFINITY);
+    if (!none && tied >= 2) {
+        st |= KLR_Q_TIE_RESOLVED;
+        const int slot = atomicAdd(P.tie_count, 1);
+        if (slot < P.tie_cap) {
+            TieRecord r;
+            r.q = q;
+            r.kernel = k;
+            r.n = tied <= kTopK ? tied : -2;
+#pragma unroll
+            for (int m = 0; m < kTopK; ++m) r.cand[m] = tc[m];
+            P.ties[slot] = r;
+        } else {
+            decide_cand_f64_inplace(P, k, q, N, st);   // scratch full
+            return;
+        }
+    }
+    P.best[q] = none ? -1 : ci;
+    reinterpret_cast<float*>(P.best_cycles)[q] = e;
+    if (P.q_status) P.q_status[q] = st | (none ? KLR_Q_NONE_FEASIBLE : 0);
+}
+
+// Candidate mode, kc lanes per query (kc a power of two <= 32): from each
+// lane's own (cycles, shape), the query's least (ties to the lower shape),
+// the status bits, and the near-tied shapes; lane j == 0 writes the result.
+// Every lane of the warp calls it.
+__device__ __forceinline__ void cand_group_finish(const EvalParams& P, int k, int64_t q,
+                                                  long long N, bool valid, int j, int kc,
+                                                  float e, int c, int st) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float e_own = e;
+    const int c_own = e < INFINITY ? c : -1;
+    int ci = e < INFINITY ? c : 0x7fffffff;
+    for (int o = 1; o < kc; o <<= 1) {
+        const float oe = __shfl_xor_sync(full, e, o);
+        const int oc = __shfl_xor_sync(full, ci, o);
+        st |= __shfl_xor_sync(full, st, o);
+        if (oe < e || (oe == e && oc < ci)) { e = oe; ci = oc; }
+    }
+    // other shapes within the window of the least (a repeat of the chosen
+    // shape is no tie)
+    const bool near = c_own >= 0 && c_own != ci && (double)e_own <= (double)e * (1.0 + kTieWindow);
+    const unsigned bal = __ballot_sync(full, near);
+    if (bal == 0u) {
+        // no near-tie in the warp (the common case)
+        if (valid && j == 0) {
+            const bool none = !(e < INFINITY);
+            P.best[q] = none ? -1 : ci;
+            reinterpret_cast<float*>(P.best_cycles)[q] = e;
+            if (P.q_status) P.q_status[q] = st | (none ? KLR_Q_NONE_FEASIBLE : 0);
+        }
+        return;
+    }
+    const unsigned gmask = kc >= 32 ? full : (((1u << kc) - 1u) << (lane & ~(kc - 1)));
+    unsigned rest = bal & gmask;
+    const int others = __popc(rest);
+    int tc[kTopK];
+    tc[0] = ci;
+#pragma unroll
+    for (int m = 1; m < kTopK; ++m) {
+        const int src = rest ? __ffs(rest) - 1 : lane;
+        tc[m] = __shfl_sync(full, c_own, src);
+        rest = rest ? (rest & (rest - 1)) : 0u;
+    }
+    if (valid && j == 0)
+        cand_write(P, k, q, N, e, ci, st, others > 0 ? others + 1 : 1, tc[0], tc[1], tc[2], tc[3]);
 }
 
 // Per-configuration integer facts staged in shared memory.
@@ -425,19 +523,7 @@ eval_kernel(const __grid_constant__ EvalParams P) {
                     e = eval_cfg<T, D>(P, cinfo, wave_rcp, spec, lo, sc, n_sm, N, N < (1LL << 24),
                                        (T)N * n_scale, c, st);
                 }
-                int ci = e < (T)INFINITY ? c : 0x7fffffff;
-                for (int o = 1; o < kc; o <<= 1) {
-                    const T oe = __shfl_xor_sync(0xffffffffu, e, o);
-                    const int oc = __shfl_xor_sync(0xffffffffu, ci, o);
-                    st |= __shfl_xor_sync(0xffffffffu, st, o);
-                    if (oe < e || (oe == e && oc < ci)) { e = oe; ci = oc; }
-                }
-                if (valid && j == 0) {
-                    const bool none = !(e < (T)INFINITY);
-                    P.best[q] = none ? -1 : ci;
-                    reinterpret_cast<T*>(P.best_cycles)[q] = e;
-                    if (P.q_status) P.q_status[q] = st | (none ? KLR_Q_NONE_FEASIBLE : 0);
-                }
+                cand_group_finish(P, k, q, P.q_N[q], valid, j, kc, (float)e, c, st);
             }
             continue;
         }
@@ -451,8 +537,6 @@ eval_kernel(const __grid_constant__ EvalParams P) {
 #pragma unroll
             for (int j = 0; j < kTopK; ++j) { topv[j] = (T)INFINITY; topi[j] = -1; }
             int st = 0;
-            T cbv = (T)INFINITY;           // candidate mode: best value and index
-            int cbj = -1;
             const int n_it = P.cand ? P.kc : n_cfg;
 #pragma unroll 1
             for (int it = 0; it < n_it; ++it) {
@@ -460,8 +544,24 @@ eval_kernel(const __grid_constant__ EvalParams P) {
                 if (c < 0 || c >= n_cfg) continue;
                 T e = eval_cfg<T, D>(P, cinfo, wave_rcp, spec, lo, sc, n_sm, N, small, xN, c, st);
                 if (P.cand) {
-                    // lowest value, ties to the lowest shape index
-                    if (e < cbv || (e == cbv && e < (T)INFINITY && c < cbj)) { cbv = e; cbj = c; }
+                    // candidates come in any order: a sorted top-k by (value,
+                    // shape), a repeated shape entered once
+                    if (!(e < (T)INFINITY)) continue;
+                    bool seen = false;
+#pragma unroll
+                    for (int j = 0; j < kTopK; ++j) seen = seen || topi[j] == c;
+                    if (seen) continue;
+                    T ve = e;
+                    int vi = c;
+#pragma unroll
+                    for (int j = 0; j < kTopK; ++j) {
+                        if (topi[j] < 0 || ve < topv[j] || (ve == topv[j] && vi < topi[j])) {
+                            T tv = topv[j]; int ti = topi[j];
+                            topv[j] = ve; topi[j] = vi;
+                            ve = tv; vi = ti;
+                            if (vi < 0) break;
+                        }
+                    }
                 } else if (P.table) {
                     reinterpret_cast<T*>(P.cycles)[q * n_cfg + c] = e;
                 } else if (e < topv[kTopK - 1]) {
@@ -480,10 +580,16 @@ eval_kernel(const __grid_constant__ EvalParams P) {
             }
             if (P.table) continue;
             if (P.cand) {
-                if (cbj < 0) st |= KLR_Q_NONE_FEASIBLE;
-                P.best[q] = cbj;
-                reinterpret_cast<T*>(P.best_cycles)[q] = cbv;
-                if (P.q_status) P.q_status[q] = st;
+                // near-ties of the best go to the FP64 re-decision (all of the
+                // query's candidates when every kept entry is tied)
+                int tied = 0, tc[kTopK];
+#pragma unroll
+                for (int j = 0; j < kTopK; ++j) {
+                    tc[j] = topi[j];
+                    if (topi[j] >= 0 && (double)topv[j] <= (double)topv[0] * (1.0 + kTieWindow)) ++tied;
+                }
+                if (tied == kTopK) tied = kTopK + 1;
+                cand_write(P, k, q, N, (float)topv[0], topi[0], st, tied, tc[0], tc[1], tc[2], tc[3]);
                 continue;
             }
             const int bi = topi[0];
@@ -655,14 +761,15 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
         const int64_t npairs = (qb - qa) * kc;
         const int64_t span = (npairs + 31) & ~(int64_t)31;
         // cycles of pair pi (query pi / kc, its candidate pi mod kc)
-        auto pair_eval = [&](int64_t pi, float& e, int& st, int& c, int64_t& q, bool& valid) {
+        auto pair_eval = [&](int64_t pi, float& e, int& st, int& c, int64_t& q, bool& valid,
+                             long long& N) {
             valid = pi < npairs;
             q = qa + (valid ? pi / kc : 0);
             c = valid ? P.cand[q * kc + (int)(pi & (kc - 1))] : -1;
             st = 0;
             e = INFINITY;
+            N = P.q_N[q];
             if (c >= 0 && c < n_cfg) {
-                const long long N = P.q_N[q];
                 const int s = slot_of[c];
                 if (s >= 0) {
                     e = eval_cfg<float, D>(P, cinfo, wrcp, spec, lo, sc, n_sm, N, N < (1LL << 24),
@@ -682,33 +789,15 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
                 }
             }
         };
-        // the least (cycles, shape) over the kc lanes of each query
-        auto pair_finish = [&](int64_t pi, float e, int st, int c, int64_t q, bool valid) {
-            int ci = e < INFINITY ? c : 0x7fffffff;
-            for (int o = 1; o < kc; o <<= 1) {
-                const float oe = __shfl_xor_sync(full, e, o);
-                const int oc = __shfl_xor_sync(full, ci, o);
-                st |= __shfl_xor_sync(full, st, o);
-                if (oe < e || (oe == e && oc < ci)) { e = oe; ci = oc; }
-            }
-            if (valid && (pi & (kc - 1)) == 0) {
-                const bool none = !(e < INFINITY);
-                P.best[q] = none ? -1 : ci;
-                reinterpret_cast<float*>(P.best_cycles)[q] = e;
-                if (P.q_status) P.q_status[q] = st | (none ? KLR_Q_NONE_FEASIBLE : 0);
-            }
-        };
-        // two pairs per lane at a time (independent work for the scheduler);
         // every lane runs the same number of iterations
-        for (int64_t pi = lane; pi < span; pi += 64) {
-            float e1, e2;
-            int s1, s2, c1, c2;
-            int64_t q1, q2;
-            bool v1, v2;
-            pair_eval(pi, e1, s1, c1, q1, v1);
-            pair_eval(pi + 32, e2, s2, c2, q2, v2);
-            pair_finish(pi, e1, s1, c1, q1, v1);
-            pair_finish(pi + 32, e2, s2, c2, q2, v2);
+        for (int64_t pi = lane; pi < span; pi += 32) {
+            float e1;
+            int s1, c1;
+            int64_t q1;
+            bool v1;
+            long long N1;
+            pair_eval(pi, e1, s1, c1, q1, v1, N1);
+            cand_group_finish(P, (int)k, q1, N1, v1, (int)(pi & (kc - 1)), kc, e1, c1, s1);
         }
         __syncwarp();
     }
@@ -717,33 +806,47 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
 
 // Re-decide FP32 near-ties: FP64 evaluation of the tied candidates (or of
 // every configuration) with the unspecialised program, lowest index on ties.
-// One warp per tie record, lanes over its configurations; the least (value,
-// index) and the runner-up value (the least over every other configuration)
-// by warp reductions.
+// One group of G lanes per tie record (G = 32 for the sweep's records, the
+// candidate count rounded up to a power of two in candidate mode: FP64 issue
+// slots are scarce), lanes over its configurations; the least (value, index)
+// and the runner-up value (the least over every other configuration) by
+// shuffles within the group.
 constexpr int kTieWarps = 4;
 __global__ void __launch_bounds__(32 * kTieWarps)
-tie_kernel(const __grid_constant__ EvalParams P) {
+tie_kernel(const __grid_constant__ EvalParams P, int G) {
     const int64_t n = min((int64_t)*P.tie_count, P.tie_cap);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
     const unsigned full = 0xffffffffu;
-    for (int64_t r = blockIdx.x * (int64_t)kTieWarps + (threadIdx.x >> 5); r < n;
-         r += (int64_t)gridDim.x * kTieWarps) {
-        const TieRecord rec = P.ties[r];
-        const long long N = P.q_N[rec.q];
-        const int cnt = rec.n < 0 ? P.n_cfg : rec.n;
+    const int per_warp = 32 / G;
+    const int64_t groups = ((int64_t)gridDim.x * kTieWarps) * per_warp;
+    const int64_t first = ((int64_t)blockIdx.x * kTieWarps + (threadIdx.x >> 5)) * per_warp + lane / G;
+    // every lane of a warp runs the same number of iterations
+    const int64_t rounds = (n + groups - 1) / groups;
+    for (int64_t it = 0; it < rounds; ++it) {
+        const int64_t r = first + it * groups;
+        const bool live = r < n;
+        TieRecord rec;
+        rec.n = 0;
+        long long N = 1;
+        if (live) {
+            rec = P.ties[r];
+            N = P.q_N[rec.q];
+        }
+        const int cnt = !live ? 0 : rec.n == -2 ? P.kc : rec.n < 0 ? P.n_cfg : rec.n;
         double bv = INFINITY, sv = INFINITY;     // this lane's least and runner-up
         int bj = 0x7fffffff;
-        for (int j = lane; j < cnt; j += 32) {
-            const int c = rec.n < 0 ? j : rec.cand[j];
+        for (int j = gl; j < cnt; j += G) {
+            const int c = rec.n == -2 ? P.cand[rec.q * P.kc + j] : rec.n < 0 ? j : rec.cand[j];
+            if (c < 0 || c >= P.n_cfg) continue;
             bool us;
             const double v = eval_full_f64(P, rec.kernel, N, c, us);
             if (v < bv || (v == bv && c < bj)) { sv = bv; bv = v; bj = c; }
             else if (v < sv) sv = v;
         }
-        // the least (value, index) over the warp
+        // the least (value, index) over the group
         double gv = bv;
         int gj = bj;
-        for (int o = 16; o > 0; o >>= 1) {
+        for (int o = G >> 1; o > 0; o >>= 1) {
             const double ov = __shfl_xor_sync(full, gv, o);
             const int oj = __shfl_xor_sync(full, gj, o);
             if (ov < gv || (ov == gv && oj < gj)) { gv = ov; gj = oj; }
@@ -751,8 +854,8 @@ tie_kernel(const __grid_constant__ EvalParams P) {
         // runner-up: every lane's least except the chosen one, and its own
         // runner-up
         double rv = (bj == gj) ? sv : fmin(bv, sv);
-        for (int o = 16; o > 0; o >>= 1) rv = fmin(rv, __shfl_xor_sync(full, rv, o));
-        if (lane == 0) {
+        for (int o = G >> 1; o > 0; o >>= 1) rv = fmin(rv, __shfl_xor_sync(full, rv, o));
+        if (live && gl == 0) {
             const int best = (gv < INFINITY) ? gj : -1;
             P.best[rec.q] = best;
             reinterpret_cast<float*>(P.best_cycles)[rec.q] = (float)gv;
@@ -760,6 +863,27 @@ tie_kernel(const __grid_constant__ EvalParams P) {
             write_launch(P, rec.q, N, best);
         }
     }
+}
+
+// lanes per tie record: 32 for the sweep; in candidate mode the candidates
+// per query rounded up to a power of two (at least kTopK)
+inline int tie_group(const EvalParams& P) {
+    if (!P.cand) return 32;
+    int g = kTopK;
+    while (g < P.kc && g < 32) g <<= 1;
+    return g;
+}
+
+// the FP64 re-decision of the tie records (sized by the tie capacity; the
+// groups past the recorded count do nothing)
+klr_status launch_ties(const Context* c, const EvalParams& P, cudaStream_t stream) {
+    const int G = tie_group(P);
+    const int64_t per_block = (int64_t)kTieWarps * (32 / G);
+    const int grid = (int)std::min<int64_t>((P.tie_cap + per_block - 1) / per_block,
+                                            (int64_t)c->n_sm * 8);
+    tie_kernel<<<grid, 32 * kTieWarps, 0, stream>>>(P, G);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
 }
 
 int64_t tie_capacity(int64_t n_q) {
@@ -1059,6 +1183,45 @@ __global__ void history_insert_kernel(const __grid_constant__ EvalParams P, Hist
     }
 }
 
+// the FP32 decision of every query among its candidates
+klr_status launch_candidates(Context* c, EvalParams& P, cudaStream_t stream) {
+    const int k = P.kc;
+    if (k <= 32 && (k & (k - 1)) == 0) {
+        // one warp per kernel
+        // as many shapes specialised per kernel as keep three blocks per SM
+        // (every shape when they fit), at least 48 (or every shape)
+        const int NC = 2 * (P.degree + 1);
+        auto smem_for = [&](int sl) {
+            return align16(4 * (size_t)P.n_cfg * P.m) +
+                   kRerankWarps * rerank_warp_bytes(P.u, P.n_cfg, NC, sl);
+        };
+        int slots = std::min(P.n_cfg, 48);
+        for (int sl = std::min(P.n_cfg, 256); sl > slots; sl -= 4)
+            if (3 * (smem_for(sl) + 1024) <= (size_t)c->smem_optin + 1024) { slots = sl; break; }
+        P.slots = slots;
+        const size_t smem = smem_for(slots);
+        if (smem <= c->smem_optin) {
+            auto go = [&](auto kern) -> klr_status {
+                int per_sm = 0;
+                KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)smem));
+                KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
+                                                                             32 * kRerankWarps, smem));
+                const int grid = (int)std::min<int64_t>(
+                    ((int64_t)P.n_kernels + kRerankWarps - 1) / kRerankWarps,
+                    (int64_t)c->n_sm * std::max(per_sm, 1));
+                kern<<<grid, 32 * kRerankWarps, smem, stream>>>(P);
+                KLR_CHECK_CUDA(cudaGetLastError());
+                return KLR_OK;
+            };
+            if (P.degree == 1) return go(rerank_kernel<1>);
+            if (P.degree == 2) return go(rerank_kernel<2>);
+            return go(rerank_kernel<3>);
+        }
+    }
+    return launch_eval(c, P, false, stream);
+}
+
 }  // namespace
 
 size_t fit_workspace_bytes(int64_t n_fits, int n_mom);
@@ -1130,10 +1293,7 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
     }
     st = launch_eval(c, P, f64, stream);
     if (st != KLR_OK || f64) return st;
-    const int grid = (int)std::min<int64_t>((P.tie_cap + kTieWarps - 1) / kTieWarps, (int64_t)c->n_sm * 8);
-    tie_kernel<<<grid, 32 * kTieWarps, 0, stream>>>(P);
-    KLR_CHECK_CUDA(cudaGetLastError());
-    return KLR_OK;
+    return launch_ties(c, P, stream);
 }
 
 klr_status klr_argmin_candidates(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
@@ -1158,41 +1318,18 @@ klr_status klr_argmin_candidates(klr_ctx* ctx, const klr_program* prog, const kl
     P.q_status = q_status;
     P.cand = cand;
     P.kc = k;
-    if (k <= 32 && (k & (k - 1)) == 0) {
-        // one warp per kernel
-        // as many shapes specialised per kernel as keep three blocks per SM
-        // (every shape when they fit), at least 48 (or every shape)
-        const int NC = 2 * (P.degree + 1);
-        auto smem_for = [&](int sl) {
-            return align16(4 * (size_t)P.n_cfg * P.m) +
-                   kRerankWarps * rerank_warp_bytes(P.u, P.n_cfg, NC, sl);
-        };
-        int slots = std::min(P.n_cfg, 48);
-        for (int sl = std::min(P.n_cfg, 256); sl > slots; sl -= 4)
-            if (3 * (smem_for(sl) + 1024) <= (size_t)c->smem_optin + 1024) { slots = sl; break; }
-        P.slots = slots;
-        const size_t smem = smem_for(slots);
-        if (smem <= c->smem_optin) {
-            auto go = [&](auto kern) -> klr_status {
-                int per_sm = 0;
-                KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                    (int)smem));
-                KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern,
-                                                                             32 * kRerankWarps, smem));
-                const int grid = (int)std::min<int64_t>(
-                    ((int64_t)P.n_kernels + kRerankWarps - 1) / kRerankWarps,
-                    (int64_t)c->n_sm * std::max(per_sm, 1));
-                kern<<<grid, 32 * kRerankWarps, smem, stream>>>(P);
-                KLR_CHECK_CUDA(cudaGetLastError());
-                return KLR_OK;
-            };
-            if (P.degree == 1) return go(rerank_kernel<1>);
-            if (P.degree == 2) return go(rerank_kernel<2>);
-            return go(rerank_kernel<3>);
-        }
-    }
-    return launch_eval(c, P, false, stream);
+    // near-ties among the candidates are re-decided in FP64, as in the sweep
+    st = ensure_workspace(c, workspace_bytes(0, P.n_q), stream);
+    if (st != KLR_OK) return st;
+    P.tie_count = reinterpret_cast<int*>(c->ws);
+    P.ties = reinterpret_cast<TieRecord*>(reinterpret_cast<char*>(c->ws) + 256);
+    P.tie_cap = tie_capacity(P.n_q);
+    KLR_CHECK_CUDA(cudaMemsetAsync(P.tie_count, 0, sizeof(int), stream));
+    st = launch_candidates(c, P, stream);
+    if (st != KLR_OK) return st;
+    return launch_ties(c, P, stream);
 }
+
 
 klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw, const int32_t* cfg,
                               int n_cfg, const klr_queries* q, int32_t* best_idx,
@@ -1231,8 +1368,10 @@ klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw, const i
     KLR_CHECK_CUDA(cudaMemsetAsync(P.tie_count, 0, sizeof(int), stream));
     st = launch_eval(&c, P, false, stream);
     if (st != KLR_OK) return st;
-    const int grid = (int)std::min<int64_t>((P.tie_cap + kTieWarps - 1) / kTieWarps, (int64_t)c.n_sm * 8);
-    tie_kernel<<<grid, 32 * kTieWarps, 0, stream>>>(P);
+    {
+        const klr_status ts = launch_ties(&c, P, stream);
+        if (ts != KLR_OK) return ts;
+    }
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
 }
@@ -1338,8 +1477,10 @@ klr_status klr_argmin_history(klr_ctx* ctx, klr_history* hist, const klr_program
     KLR_CHECK_CUDA(cudaGetLastError());
     P.done = done;
     if ((st = launch_eval(c, P, false, stream)) != KLR_OK) return st;
-    const int tgrid = (int)std::min<int64_t>((P.tie_cap + kTieWarps - 1) / kTieWarps, (int64_t)c->n_sm * 8);
-    tie_kernel<<<tgrid, 32 * kTieWarps, 0, stream>>>(P);
+    {
+        const klr_status ts = launch_ties(c, P, stream);
+        if (ts != KLR_OK) return ts;
+    }
     KLR_CHECK_CUDA(cudaGetLastError());
     history_insert_kernel<<<grid, 256, 0, stream>>>(P, *h, done);
     KLR_CHECK_CUDA(cudaGetLastError());
