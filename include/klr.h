@@ -443,9 +443,13 @@ klr_status klr_propose(klr_ctx* ctx, const klr_mlp* net, const float* coef,
  * the meaningful candidate of least cycles by the FP32 rational program as
  * klr_argmin's sweep evaluates it (per kernel, only the proposed shapes are
  * specialised); ties go to the lowest shape index; no meaningful candidate:
- * -1 and KLR_Q_NONE_FEASIBLE.  cand: device int32 [n_queries x k] shape
- * indices (entries outside 0..n_cfg-1 are skipped).  best_cycles: device
- * float [n_queries]; q_status: device int32 [n_queries] or NULL. */
+ * -1 and KLR_Q_NONE_FEASIBLE.  As in klr_argmin, a query whose FP32 least has
+ * another candidate shape within the FP32 error window is re-decided by FP64
+ * evaluation of the tied candidates (KLR_Q_TIE_RESOLVED; best_cycles then
+ * holds the FP64 value rounded to FP32).  cand: device int32 [n_queries x k]
+ * shape indices (entries outside 0..n_cfg-1 are skipped; a repeated shape
+ * counts once).  best_cycles: device float [n_queries]; q_status: device int32
+ * [n_queries] or NULL.  Uses the context's scratch memory (tie records). */
 klr_status klr_argmin_candidates(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
                                  const int32_t* cfg, int n_cfg, const klr_queries* q,
                                  const int32_t* cand, int k, int32_t* best_idx,
