@@ -68,10 +68,6 @@ struct EvalParams {
     const uint8_t* done;        // history mode: 1 for queries answered already, or NULL
     int slots;                  // warp re-rank: shapes specialised per kernel
     uint8_t exps[kMaxBasis][kMaxVars];
-    // terms grouped by their power of N (increasing term index within a
-    // group): group j is ord[jstart[j] .. jstart[j + 1])
-    uint8_t ord[kMaxBasis];
-    uint8_t jstart[8];
 };
 
 // Fig. 1 with the program's hardware limits.
@@ -79,6 +75,15 @@ __device__ __forceinline__ int active_blocks(long long T, long long R, long long
                                              const EvalParams& P) {
     return occupancy_blocks(T, R, Z, P.B_max, P.W_max, P.R_max, P.Z_max, P.T_max);
 }
+
+// Products and sums of the per-shape specialisation, rounded one by one
+// (never fused), so that every kernel that specialises gets the same bits.
+template <typename T> __device__ __forceinline__ T mul_rn(T a, T b);
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <typename T> __device__ __forceinline__ T add_rn(T a, T b);
+template <> __device__ __forceinline__ float add_rn<float>(float a, float b) { return __fadd_rn(a, b); }
+template <> __device__ __forceinline__ double add_rn<double>(double a, double b) { return __dadd_rn(a, b); }
 
 // a / b: the fast approximate quotient in FP32 (2 ulp), IEEE in FP64
 template <typename T> __device__ __forceinline__ T qdiv(T a, T b) { return a / b; }
@@ -482,25 +487,31 @@ eval_kernel(const __grid_constant__ EvalParams P) {
             xb[0] = (T)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
             xb[1] = (T)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
             xb[2] = (T)ldexp((double)P.cfg[3 * c + 2], -P.b_scale_log2);
-            T* sp = spec + (size_t)idx * NC;
             // coefficient of N^j: its terms in increasing index order
+            T acc[2][D + 1];
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+                for (int j = 0; j <= D; ++j) acc[s2][j] = T(0);
+            for (int t = 0; t < m; ++t) {
+                T bm = T(1);
+                if (kMonoTable) {
+                    bm = bmon[c * m + t];
+                } else {
+                    for (int v = 1; v < P.n_vars; ++v)
+                        for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
+                }
+                const int j = P.exps[t][0];
+                const T pa = mul_rn(coef_s[i * u + t], bm), qa = mul_rn(coef_s[i * u + m + t], bm);
+#pragma unroll
+                for (int jj = 0; jj <= D; ++jj)
+                    if (jj == j) { acc[0][jj] = add_rn(acc[0][jj], pa); acc[1][jj] = add_rn(acc[1][jj], qa); }
+            }
+            T* sp = spec + (size_t)idx * NC;
 #pragma unroll
             for (int j = 0; j <= D; ++j) {
-                T pa = T(0), qa = T(0);
-                for (int r = P.jstart[j]; r < P.jstart[j + 1]; ++r) {
-                    const int t = P.ord[r];
-                    T bm = T(1);
-                    if (kMonoTable) {
-                        bm = bmon[c * m + t];
-                    } else {
-                        for (int v = 1; v < P.n_vars; ++v)
-                            for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
-                    }
-                    pa = fma(coef_s[i * u + t], bm, pa);
-                    qa = fma(coef_s[i * u + m + t], bm, qa);
-                }
-                sp[j] = pa;
-                sp[D + 1 + j] = qa;
+                sp[j] = acc[0][j];
+                sp[D + 1 + j] = acc[1][j];
             }
         }
         __syncthreads();
@@ -527,25 +538,24 @@ eval_kernel(const __grid_constant__ EvalParams P) {
             }
             continue;
         }
-        for (int64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) {
-            if (P.done && P.done[q]) continue;
-            const long long N = P.q_N[q];
-            const bool small = N < (1LL << 24);   // 32-bit wave counts exact
-            const T xN = (T)N * n_scale;
-            T topv[kTopK];
-            int topi[kTopK];
+        if (P.cand) {
+            // candidate mode, one thread per query (kc not a power of two or
+            // above 32): a sorted top-k by (value, shape) over the candidates,
+            // which come in any order, a repeated shape entered once
+            for (int64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) {
+                const long long N = P.q_N[q];
+                const bool small = N < (1LL << 24);
+                const T xN = (T)N * n_scale;
+                T topv[kTopK];
+                int topi[kTopK];
 #pragma unroll
-            for (int j = 0; j < kTopK; ++j) { topv[j] = (T)INFINITY; topi[j] = -1; }
-            int st = 0;
-            const int n_it = P.cand ? P.kc : n_cfg;
+                for (int j = 0; j < kTopK; ++j) { topv[j] = (T)INFINITY; topi[j] = -1; }
+                int st = 0;
 #pragma unroll 1
-            for (int it = 0; it < n_it; ++it) {
-                const int c = P.cand ? P.cand[q * P.kc + it] : it;
-                if (c < 0 || c >= n_cfg) continue;
-                T e = eval_cfg<T, D>(P, cinfo, wave_rcp, spec, lo, sc, n_sm, N, small, xN, c, st);
-                if (P.cand) {
-                    // candidates come in any order: a sorted top-k by (value,
-                    // shape), a repeated shape entered once
+                for (int it = 0; it < P.kc; ++it) {
+                    const int c = P.cand[q * P.kc + it];
+                    if (c < 0 || c >= n_cfg) continue;
+                    T e = eval_cfg<T, D>(P, cinfo, wave_rcp, spec, lo, sc, n_sm, N, small, xN, c, st);
                     if (!(e < (T)INFINITY)) continue;
                     bool seen = false;
 #pragma unroll
@@ -562,7 +572,34 @@ eval_kernel(const __grid_constant__ EvalParams P) {
                             if (vi < 0) break;
                         }
                     }
-                } else if (P.table) {
+                }
+                // near-ties of the best go to the FP64 re-decision (all of the
+                // query's candidates when every kept entry is tied)
+                int tied = 0, tc[kTopK];
+#pragma unroll
+                for (int j = 0; j < kTopK; ++j) {
+                    tc[j] = topi[j];
+                    if (topi[j] >= 0 && (double)topv[j] <= (double)topv[0] * (1.0 + kTieWindow)) ++tied;
+                }
+                if (tied == kTopK) tied = kTopK + 1;
+                cand_write(P, k, q, N, (float)topv[0], topi[0], st, tied, tc[0], tc[1], tc[2], tc[3]);
+            }
+            continue;
+        }
+        for (int64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) {
+            if (P.done && P.done[q]) continue;
+            const long long N = P.q_N[q];
+            const bool small = N < (1LL << 24);   // 32-bit wave counts exact
+            const T xN = (T)N * n_scale;
+            T topv[kTopK];
+            int topi[kTopK];
+#pragma unroll
+            for (int j = 0; j < kTopK; ++j) { topv[j] = (T)INFINITY; topi[j] = -1; }
+            int st = 0;
+#pragma unroll 1
+            for (int c = 0; c < n_cfg; ++c) {
+                T e = eval_cfg<T, D>(P, cinfo, wave_rcp, spec, lo, sc, n_sm, N, small, xN, c, st);
+                if (P.table) {
                     reinterpret_cast<T*>(P.cycles)[q * n_cfg + c] = e;
                 } else if (e < topv[kTopK - 1]) {
                     // insert into the sorted top-k; ties keep the lower index first
@@ -579,19 +616,6 @@ eval_kernel(const __grid_constant__ EvalParams P) {
                 }
             }
             if (P.table) continue;
-            if (P.cand) {
-                // near-ties of the best go to the FP64 re-decision (all of the
-                // query's candidates when every kept entry is tied)
-                int tied = 0, tc[kTopK];
-#pragma unroll
-                for (int j = 0; j < kTopK; ++j) {
-                    tc[j] = topi[j];
-                    if (topi[j] >= 0 && (double)topv[j] <= (double)topv[0] * (1.0 + kTieWindow)) ++tied;
-                }
-                if (tied == kTopK) tied = kTopK + 1;
-                cand_write(P, k, q, N, (float)topv[0], topi[0], st, tied, tc[0], tc[1], tc[2], tc[3]);
-                continue;
-            }
             const int bi = topi[0];
             if (bi < 0) st |= KLR_Q_NONE_FEASIBLE;
             float mg = 0.f;
@@ -731,30 +755,39 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
             cinfo[s] = ci;
             wrcp[s] = 1.0f / (float)ci.wave;
         }
-        // two (shape, metric) items per lane at a time (four independent
-        // sums): the same sums, in the same order, as the sweep's
-        // specialisation
+        // two (shape, metric) items per lane at a time: the same products
+        // and sums, in the same order, as the sweep's specialisation
         for (int idx = lane; idx < n_used * 8; idx += 64) {
             const int idx2 = idx + 32 < n_used * 8 ? idx + 32 : idx;   // a repeat is harmless
             const int c1 = slot_cfg[idx >> 3], i1 = idx & 7;
             const int c2 = slot_cfg[idx2 >> 3], i2 = idx2 & 7;
+            float acc1[2][D + 1], acc2[2][D + 1];
+#pragma unroll
+            for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+                for (int j = 0; j <= D; ++j) { acc1[s2][j] = 0.f; acc2[s2][j] = 0.f; }
+            for (int t = 0; t < m; ++t) {
+                const float bm1 = bmon[c1 * m + t], bm2 = bmon[c2 * m + t];
+                const int j = P.exps[t][0];
+                const float pa1 = mul_rn(coef_s[i1 * u + t], bm1), qa1 = mul_rn(coef_s[i1 * u + m + t], bm1);
+                const float pa2 = mul_rn(coef_s[i2 * u + t], bm2), qa2 = mul_rn(coef_s[i2 * u + m + t], bm2);
+#pragma unroll
+                for (int jj = 0; jj <= D; ++jj)
+                    if (jj == j) {
+                        acc1[0][jj] = add_rn(acc1[0][jj], pa1);
+                        acc1[1][jj] = add_rn(acc1[1][jj], qa1);
+                        acc2[0][jj] = add_rn(acc2[0][jj], pa2);
+                        acc2[1][jj] = add_rn(acc2[1][jj], qa2);
+                    }
+            }
             float* sp1 = spec + (size_t)idx * NC;
             float* sp2 = spec + (size_t)idx2 * NC;
 #pragma unroll
             for (int j = 0; j <= D; ++j) {
-                float pa1 = 0.f, qa1 = 0.f, pa2 = 0.f, qa2 = 0.f;
-                for (int r = P.jstart[j]; r < P.jstart[j + 1]; ++r) {
-                    const int t = P.ord[r];
-                    const float bm1 = bmon[c1 * m + t], bm2 = bmon[c2 * m + t];
-                    pa1 = fmaf(coef_s[i1 * u + t], bm1, pa1);
-                    qa1 = fmaf(coef_s[i1 * u + m + t], bm1, qa1);
-                    pa2 = fmaf(coef_s[i2 * u + t], bm2, pa2);
-                    qa2 = fmaf(coef_s[i2 * u + m + t], bm2, qa2);
-                }
-                sp1[j] = pa1;
-                sp1[D + 1 + j] = qa1;
-                sp2[j] = pa2;
-                sp2[D + 1 + j] = qa2;
+                sp1[j] = acc1[0][j];
+                sp1[D + 1 + j] = acc1[1][j];
+                sp2[j] = acc2[0][j];
+                sp2[D + 1 + j] = acc2[1][j];
             }
         }
         __syncwarp();
@@ -806,14 +839,16 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
 
 // Re-decide FP32 near-ties: FP64 evaluation of the tied candidates (or of
 // every configuration) with the unspecialised program, lowest index on ties.
-// One group of G lanes per tie record (G = 32 for the sweep's records, the
-// candidate count rounded up to a power of two in candidate mode: FP64 issue
-// slots are scarce), lanes over its configurations; the least (value, index)
-// and the runner-up value (the least over every other configuration) by
-// shuffles within the group.
+// One group of G lanes per tie record, lanes over its configurations: one
+// pass takes the records that list their tied configurations (G = kTopK, or
+// the candidate count rounded up to a power of two in candidate mode), the
+// other those that re-sweep every configuration (G = 32), so that the scarce
+// FP64 issue slots run with every lane busy.  The least (value, index) and
+// the runner-up value (the least over every other configuration) by shuffles
+// within the group.
 constexpr int kTieWarps = 4;
 __global__ void __launch_bounds__(32 * kTieWarps)
-tie_kernel(const __grid_constant__ EvalParams P, int G) {
+tie_kernel(const __grid_constant__ EvalParams P, int G, int full_sweeps) {
     const int64_t n = min((int64_t)*P.tie_count, P.tie_cap);
     const int lane = threadIdx.x & 31, gl = lane & (G - 1);
     const unsigned full = 0xffffffffu;
@@ -824,14 +859,11 @@ tie_kernel(const __grid_constant__ EvalParams P, int G) {
     const int64_t rounds = (n + groups - 1) / groups;
     for (int64_t it = 0; it < rounds; ++it) {
         const int64_t r = first + it * groups;
-        const bool live = r < n;
         TieRecord rec;
         rec.n = 0;
-        long long N = 1;
-        if (live) {
-            rec = P.ties[r];
-            N = P.q_N[rec.q];
-        }
+        if (r < n) rec = P.ties[r];
+        const bool live = r < n && ((rec.n == -1) == (full_sweeps != 0));
+        const long long N = live ? P.q_N[rec.q] : 1;
         const int cnt = !live ? 0 : rec.n == -2 ? P.kc : rec.n < 0 ? P.n_cfg : rec.n;
         double bv = INFINITY, sv = INFINITY;     // this lane's least and runner-up
         int bj = 0x7fffffff;
@@ -865,24 +897,27 @@ tie_kernel(const __grid_constant__ EvalParams P, int G) {
     }
 }
 
-// lanes per tie record: 32 for the sweep; in candidate mode the candidates
-// per query rounded up to a power of two (at least kTopK)
+// lanes per listed tie record: kTopK for the sweep; in candidate mode the
+// candidates per query rounded up to a power of two (at least kTopK)
 inline int tie_group(const EvalParams& P) {
-    if (!P.cand) return 32;
+    if (!P.cand) return kTopK;
     int g = kTopK;
     while (g < P.kc && g < 32) g <<= 1;
     return g;
 }
 
-// the FP64 re-decision of the tie records (sized by the tie capacity; the
-// groups past the recorded count do nothing)
+// the FP64 re-decision of the tie records (grids sized by the tie capacity;
+// the groups past the recorded count do nothing): listed records, then (the
+// sweep only) the full re-sweeps
 klr_status launch_ties(const Context* c, const EvalParams& P, cudaStream_t stream) {
-    const int G = tie_group(P);
-    const int64_t per_block = (int64_t)kTieWarps * (32 / G);
-    const int grid = (int)std::min<int64_t>((P.tie_cap + per_block - 1) / per_block,
-                                            (int64_t)c->n_sm * 8);
-    tie_kernel<<<grid, 32 * kTieWarps, 0, stream>>>(P, G);
-    KLR_CHECK_CUDA(cudaGetLastError());
+    for (int pass = 0; pass < (P.cand ? 1 : 2); ++pass) {
+        const int G = pass == 0 ? tie_group(P) : 32;
+        const int64_t per_block = (int64_t)kTieWarps * (32 / G);
+        const int grid = (int)std::min<int64_t>((P.tie_cap + per_block - 1) / per_block,
+                                                (int64_t)c->n_sm * 8);
+        tie_kernel<<<grid, 32 * kTieWarps, 0, stream>>>(P, G, pass);
+        KLR_CHECK_CUDA(cudaGetLastError());
+    }
     return KLR_OK;
 }
 
@@ -981,15 +1016,6 @@ klr_status prepare(Context* c, const klr_program* prog, const klr_hw* hw, const 
     P.n_q = q->n_queries;
     for (int t = 0; t < basis.m; ++t)
         for (int v = 0; v < kMaxVars; ++v) P.exps[t][v] = basis.exps[t][v];
-    if (P.degree > 6) return KLR_EINVAL;
-    int r = 0;
-    for (int j = 0; j <= P.degree; ++j) {
-        P.jstart[j] = (uint8_t)r;
-        for (int t = 0; t < basis.m; ++t)
-            if (basis.exps[t][0] == j) P.ord[r++] = (uint8_t)t;
-    }
-    P.jstart[P.degree + 1] = (uint8_t)r;
-    if (r != basis.m) return KLR_EINVAL;
     (void)c;
     return KLR_OK;
 }
