@@ -354,7 +354,7 @@ klr_status klr_tune_import(klr_ctx* ctx, const uint64_t* keys, const int32_t* ch
  * The paper has no learned component; these calls add a surrogate of the
  * rational program that proposes candidate block shapes, which the exact
  * program then re-ranks (klr_argmin_candidates), so the rational program is
- * both the fallback and the judge of the surrogate.
+ * both the fallback and the arbiter of the surrogate.
  *
  * Network (FP32 master parameters, BF16 operands, FP32 accumulation; every
  * dense layer y = x W^T + b with W stored out x in, row-major):

@@ -1641,7 +1641,7 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
     const float ladder[7] = {1.0f - 1.0f / 64, 1.0f - 1.0f / 32, 1.0f - 1.0f / 16,
                              1.0f - 1.0f / 8, 1.0f - 1.0f / 4, 0.5f, 0.25f};
     for (int round = 0; round < 3 && __any_sync(full, !done); ++round) {
-        bool need = !done;      // this group still needs a factor this round
+        bool need = !done;      // this group still needs a factor in this pass
         bool have = false;
         for (int k = 0; k < 8 && __any_sync(full, need && !have); ++k) {
             const bool try_ = need && !have;

@@ -7,7 +7,7 @@ query at once (per-query form).  Its training targets come from the rational
 program itself (klr_eval, then klr_mlp_query_targets).  At query time the
 network proposes the k most promising meaningful shapes (klr_propose) and the
 exact rational program re-ranks them (klr_argmin_candidates), so the plain
-method remains the judge.  Random numbers (initial weights, training rows,
+method remains the arbiter.  Random numbers (initial weights, training rows,
 batch order) are inputs drawn by the caller.
 """
 from __future__ import annotations
