@@ -330,14 +330,15 @@ struct CfgInfo {
 };
 
 // Cycles of configuration c for one query (N, its scaled xN) from the
-// specialised per-kernel tables; +inf when c is not meaningful or its metrics
-// are invalid (then KLR_Q_BAD_METRIC is added to st).
+// specialised per-kernel tables (configuration c's 8 x NC coefficients at
+// spec + c * sstride); +inf when c is not meaningful or its metrics are
+// invalid (then KLR_Q_BAD_METRIC is added to st).
 template <typename T, int D>
 __device__ __forceinline__ T eval_cfg(const EvalParams& P, const CfgInfo* __restrict__ cinfo,
                                       const float* __restrict__ wave_rcp,
                                       const T* __restrict__ spec, const T* lo, const T* sc,
                                       unsigned n_sm, long long N, bool small, T xN, int c,
-                                      int& st) {
+                                      int& st, int sstride = 8 * 2 * (D + 1)) {
     constexpr int NC = 2 * (D + 1);
     const CfgInfo ci = cinfo[c];
     const int B = ci.B;
@@ -345,7 +346,7 @@ __device__ __forceinline__ T eval_cfg(const EvalParams& P, const CfgInfo* __rest
     T e = (T)INFINITY;
     if (meaningful) {
         T a[8 * NC];
-        const T* sp = spec + (size_t)c * 8 * NC;
+        const T* sp = spec + (size_t)c * sstride;
         if constexpr (sizeof(T) == 4) {
 #pragma unroll
             for (int t = 0; t < 2 * NC; ++t) {
@@ -661,9 +662,13 @@ constexpr int kRerankWarps = 4;
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
 
 // bytes of one warp's region
+// specialised coefficients of one slot, padded by 16 bytes: lanes that read
+// different slots at once then fall in different banks
+__host__ __device__ inline int rerank_slot_stride(int nc) { return 8 * nc + 4; }
 __host__ __device__ inline size_t rerank_warp_bytes(int u, int n_cfg, int nc, int slots) {
     const size_t ns = (size_t)slots;
-    return align16(4 * (size_t)8 * u) + align16(4 * ns * 8 * nc) + align16(sizeof(CfgInfo) * ns) +
+    return align16(4 * (size_t)8 * u) + align16(4 * ns * rerank_slot_stride(nc)) +
+           align16(sizeof(CfgInfo) * ns) +
            align16(4 * ns) + align16(4 * ns) + align16(2 * (size_t)n_cfg) + 32;
 }
 
@@ -681,7 +686,8 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
     float* coef_s = reinterpret_cast<float*>(wb);
     wb += align16(4 * (size_t)8 * u);
     float* spec = reinterpret_cast<float*>(wb);
-    wb += align16(4 * (size_t)n_slot * 8 * NC);
+    constexpr int SS = 8 * NC + 4;                                     // rerank_slot_stride
+    wb += align16(4 * (size_t)n_slot * SS);
     CfgInfo* cinfo = reinterpret_cast<CfgInfo*>(wb);
     wb += align16(sizeof(CfgInfo) * (size_t)n_slot);
     float* wrcp = reinterpret_cast<float*>(wb);
@@ -780,8 +786,8 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
                         acc2[1][jj] = add_rn(acc2[1][jj], qa2);
                     }
             }
-            float* sp1 = spec + (size_t)idx * NC;
-            float* sp2 = spec + (size_t)idx2 * NC;
+            float* sp1 = spec + (size_t)(idx >> 3) * SS + (idx & 7) * NC;
+            float* sp2 = spec + (size_t)(idx2 >> 3) * SS + (idx2 & 7) * NC;
 #pragma unroll
             for (int j = 0; j <= D; ++j) {
                 sp1[j] = acc1[0][j];
@@ -806,7 +812,7 @@ rerank_kernel(const __grid_constant__ EvalParams P) {
                 const int s = slot_of[c];
                 if (s >= 0) {
                     e = eval_cfg<float, D>(P, cinfo, wrcp, spec, lo, sc, n_sm, N, N < (1LL << 24),
-                                           (float)N * n_scale, s, st);
+                                           (float)N * n_scale, s, st, SS);
                 } else {
                     // beyond the specialised slots: the unspecialised form
                     bool us;
