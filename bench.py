@@ -59,6 +59,12 @@ def parse():
     ap.add_argument("--sweep-kernels", type=int, default=100000)
     ap.add_argument("--sweep-check-kernels", type=int, default=1000,
                     help="kernels of the 3D sweep checked against the oracle")
+    ap.add_argument("--sweep-sur-kernels", type=int, default=100000,
+                    help="3D sweep's surrogate arm: kernels it is trained on (0: no surrogate arm)")
+    ap.add_argument("--sweep-sur-sizes", type=int, default=4,
+                    help="3D sweep's surrogate arm: training sizes per kernel (of the 256)")
+    ap.add_argument("--sweep-sur-epochs", type=int, default=100)
+    ap.add_argument("--sweep-sur-k", type=int, default=8)
     ap.add_argument("--sur-kernels", type=int, default=50000)
     ap.add_argument("--sur-rows-per-kernel", type=int, default=1632,
                     help="training rows per kernel (per-query form: rows / 51 sizes)")
@@ -539,6 +545,12 @@ def run_sweep3d(args):
                      "config_evals_per_s": n_q * SWEEP["n_cfg"] / (ms * 1e-3),
                      "hbm_gbs": moved / (ms * 1e-3) / 1e9}
         results[name] = [b.cpu().numpy() for b in bufs[:2]]
+        if name == "f32":
+            prog32, coef32 = prog, coef
+    sur_out = None
+    if args.sweep_sur_kernels > 0:
+        sur_out = sweep3d_surrogate(args, klr, W, ctx, gt, prog32, coef32, regs, smem, cfg, hw,
+                                    sizes, qo, qn, results["f32"], out["f32"]["ms"])
     # oracle on a seeded subsample of kernels, in spawned worker processes
     import multiprocessing as mp
     t_or = time.time()
@@ -574,9 +586,85 @@ def run_sweep3d(args):
                        "configs": SWEEP["n_cfg"], "queries": n_q,
                        "check_kernels": int(len(ks)), "check_queries": int(len(rows)),
                        "oracle_s": oracle_s, "oracle_workers": n_workers},
-            "fp32": out["f32"], "fp64": out["f64"],
+            "fp32": out["f32"], "fp64": out["f64"], "surrogate": sur_out,
             "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)),
             "agreement_vs_oracle": agree}
+
+
+def sweep3d_surrogate(args, klr, W, ctx, gt, prog, coef, regs, smem, cfg, hw, sizes, qo, qn,
+                      plain, plain_ms):
+    """The 3D sweep's surrogate arm: a per-query network (251 outputs) trained
+    on a seeded subset of the kernels (by default all of them) at a few of the
+    256 sizes, then top-k proposal + exact re-rank over every query, against
+    the FP32 sweep's choices (same decision rule: FP32 cycles, FP64
+    near-ties)."""
+    import torch
+    from paper_1911_02373_gb300 import proposer
+    dev = coef.device
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    nk = coef.shape[0]
+    n_cfg = cfg.shape[0]
+    n_coef = coef[0].numel()
+    coef2 = coef.reshape(nk, n_coef)
+    t0 = time.time()
+    ks = np.sort(W.subsample_kernels(args.seed + 21, nk, min(nk, args.sweep_sur_kernels)))
+    nsz = max(1, min(len(sizes), args.sweep_sur_sizes))
+    tr_sizes = sizes[np.linspace(0, len(sizes) - 1, nsz).round().astype(np.int64)]
+    tq = W.queries_per_kernel(len(ks), tr_sizes)
+    sub = klr.Context.program(coef[t(ks)].contiguous(), regs[t(ks)].contiguous(),
+                              smem[t(ks)].contiguous(), n_vars=4, degree=2, n_scale_log2=23,
+                              b_scale_log2=10, metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+    target = proposer.query_table(ctx, sub, hw, cfg, t(tq.offsets), t(tq.sizes))
+    keep = torch.isfinite(target).any(dim=1)
+    rows = torch.nonzero(keep)[:, 0]
+    kern = t(ks.astype(np.int32))[(rows // nsz)].int().contiguous()
+    N = t(tq.sizes)[rows].contiguous()
+    target = target[rows].contiguous()
+    n_rows = kern.numel()
+    z = W.normal(W.stream_key(args.seed, 95),
+                 np.arange(klr.mlp_param_count(n_coef, n_cfg), dtype=np.uint64))
+    sur = klr.Surrogate(ctx, n_coef, proposer.init_params(n_coef, z, n_cfg), np.ones(7),
+                        n_out=n_cfg)
+    okeys = W.stream_keys(args.seed, (96,), np.arange(args.sweep_sur_epochs, dtype=np.uint64))
+    order = lambda ep: torch.argsort(t(W.words(okeys[ep], np.arange(n_rows, dtype=np.uint64))
+                                       .view(np.int64)))
+    prep_s = time.time() - t0
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    losses = proposer.train(sur, coef2, cfg, kern, N, None, target, batch=4096,
+                            epochs=args.sweep_sur_epochs, lr=args.sur_lr, order=order,
+                            log_every=100)
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    k = args.sweep_sur_k
+    run = lambda: proposer.propose_and_rerank(ctx, sur, prog, hw, coef2, regs, smem, cfg, qo, qn, k)
+    res = run()
+    torch.cuda.synchronize()
+    K = max(1, args.steps)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(K):
+        res = run()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / K
+    c_best = plain[1].astype(np.float64)
+    ok = np.isfinite(c_best)
+    reg = res[1].cpu().numpy().astype(np.float64)[ok] / c_best[ok] - 1.0
+    reg = np.where(np.isfinite(reg), reg, np.inf)
+    n_q = qn.numel()
+    return {"ms": ms, "queries_per_s": n_q / (ms * 1e-3), "speedup_vs_fp32_sweep": plain_ms / ms,
+            "k": k, "train_kernels": int(len(ks)), "train_sizes_per_kernel": nsz,
+            "train_rows": n_rows, "epochs": args.sweep_sur_epochs, "train_ms": train_ms,
+            "prep_s": prep_s, "loss_first": losses[0], "loss_last": losses[-1],
+            "regret_top1": {"mean": float(np.mean(np.minimum(reg, 10))),
+                            "median": float(np.percentile(reg, 50)),
+                            "p90": float(np.percentile(reg, 90)),
+                            "within_1pct": float(np.mean(reg <= 0.01)),
+                            "exact_fraction": float(np.mean(reg <= 1e-6))},
+            "fp64_redecided_fraction": float(((res[2] & klr.Q_TIE_RESOLVED) != 0).float().mean())}
 
 
 def run_surrogate(args):
