@@ -100,6 +100,36 @@ def test_argmin_matches_oracle(klr, ctx, name, seed, nk, nv, sizes, dtype):
         assert list(launch[r]) == g + [int(v) for v in b]
 
 
+def test_argmin_degree3_near_ties_match_oracle(klr, ctx):
+    """Degree-3 programs put more queries within the FP32 window of a tie
+    (among them, all four best shapes tied: the whole sweep redone in FP64).
+    The usual bars hold, and every query re-decided in FP64 gets the oracle's
+    choice wherever the oracle's margin is above 1e-9 (FP64 against FP64)."""
+    gt = G.make_program(19, 96, degree=3)
+    coef = gt.coef.astype(np.float32)
+    q = W.queries_per_kernel(96, W.log_spaced_sizes(64))
+    best, cyc, margin, status, launch = _run(klr, ctx, gt, coef, q.offsets, q.sizes, klr.F32, False)
+    ref = G.oracle_choose(coef, gt, q.offsets, q.sizes)
+    table = ref["cycles"].reshape(len(q.sizes), -1)
+    bnd = ref["boundary"].reshape(len(q.sizes), -1)
+    ref = dict(ref, cycles=table, boundary=bnd)
+    strict, loose = G.compare_argmin(best, cyc, ref, 1e-4, 1e-6, 1e-5)
+    assert strict > 0
+    tie = np.nonzero((status & klr.Q_TIE_RESOLVED) != 0)[0]
+    assert len(tie) > 0
+    checked = 0
+    for r in tie:
+        row = np.where(np.isfinite(table[r]), table[r], np.inf)
+        order = np.argsort(row, kind="stable")
+        bv = row[order[0]]
+        m = (row[order[1]] - bv) / bv
+        if m > 1e-9 and bnd[r, order[0]] > 1e-9:
+            checked += 1
+            assert best[r] == order[0], (r, best[r], order[0], m)
+            assert abs(cyc[r] - bv) <= 1e-6 * bv
+    assert checked > 0
+
+
 def test_all_infeasible_and_empty_kernels(klr, ctx):
     gt = G.make_program(9, 3)
     gt.regs[:] = np.array([4096, 32, 64], dtype=np.int32)   # kernel 0: no block fits
