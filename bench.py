@@ -61,9 +61,9 @@ def parse():
                     help="kernels of the 3D sweep checked against the oracle")
     ap.add_argument("--sweep-sur-kernels", type=int, default=100000,
                     help="3D sweep's surrogate arm: kernels it is trained on (0: no surrogate arm)")
-    ap.add_argument("--sweep-sur-sizes", type=int, default=4,
+    ap.add_argument("--sweep-sur-sizes", type=int, default=8,
                     help="3D sweep's surrogate arm: training sizes per kernel (of the 256)")
-    ap.add_argument("--sweep-sur-epochs", type=int, default=100)
+    ap.add_argument("--sweep-sur-epochs", type=int, default=200)
     ap.add_argument("--sweep-sur-k", type=int, default=8)
     ap.add_argument("--sur-kernels", type=int, default=50000)
     ap.add_argument("--sur-rows-per-kernel", type=int, default=1632,
