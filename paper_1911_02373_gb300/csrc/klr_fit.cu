@@ -72,7 +72,9 @@ struct FitParams {
     double gram_eps;  // unit roundoff of the Gram entries (sets shifts and thresholds)
     double f_jit, f_null, f_rank;   // shift, noise and rank levels as multiples of
                                     // gram_eps * trace
-    int32_t* flags;// scratch: n_fits, bit 0 non-finite sample, bit 1 inexact DF32
+    int32_t* flags;// scratch: n_fits, bit 0 non-finite sample, bit 1 inexact DF32,
+                   // bit 2 left to the per-sample moments kernel by the binned one
+    int fallback_only;  // moments_fast_kernel: only the fits with flag bit 2
     uint8_t exps[kMaxMoments][kMaxVars];
     uint8_t pair[kMaxBasis][kMaxBasis];
 };
@@ -225,6 +227,7 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
     const int wib = threadIdx.x >> 5;
     const int f = blockIdx.x * (blockDim.x >> 5) + wib;
     if (f >= P.n_fits) return;
+    if (P.fallback_only && (P.flags[f] & 4) == 0) return;   // done by the binned kernel
     TC* stage = reinterpret_cast<TC*>(smem_raw + (size_t)wib * P.warp_smem);
     const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
     const TS* X = reinterpret_cast<const TS*>(P.x);
@@ -365,6 +368,241 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
         }
     }
     if (lane == 0) P.flags[f] = (bad ? 1 : 0) | (inexact ? 2 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Moments through per-cell sums (degree 2 in (N, b0, b1), double-FP32, FP32
+// samples whose coordinates are powers of two).
+//
+// With x_N = N 2^-ns = 2^-t and b = (2^e0, 2^e1), the monomial x^mu of a
+// sample, mu = (a, i, j), is the power of two 2^(-a t + i (e0 - bs) + j (e1 - bs)).
+// Samples that share a cell (t, e0, e1) therefore contribute
+//     M_k[mu] = sum_cells 2^(-a t + i (e0 - bs) + j (e1 - bs)) S_k[cell],
+//     S_k[cell] = sum_{s in cell} y_s^k   (k = 0, 1, 2).
+// A warp owns one fit at a time (a persistent grid strides over the fits).
+// It streams the samples once, adding (1, y, y^2) into its cell's
+// double-FP32 sums in shared memory (2 double-word additions per sample
+// instead of 105 moment updates), then folds: over t for each block shape,
+//     F_k[shape][a] = sum_t 2^-at S_k[t][shape],
+// then over the shapes for each moment.  Every scaling is by a power of two
+// (exact), so the roundings are those of double-word sums, as in the direct
+// accumulation.  Cells: 16 octaves of N, t = ns - log2 N in 0..15, times the
+// 51 block shapes of 32..1024 threads.  A fit with any sample outside that
+// set (another N or shape, a coordinate that is not a power of two, a
+// non-finite value) is marked with flag bit 4 and left to moments_fast_kernel,
+// which then runs over the marked fits only.
+// ---------------------------------------------------------------------------
+constexpr int kBinT = 16;                 // octaves of N per fit
+constexpr int kBinS = 51;                 // block shapes (b0, b1), 5 <= log2 b0 b1 <= 10
+constexpr int kBinC = kBinT * kBinS;      // cells
+static_assert(kBinS % 3 == 0, "the shape fold runs three partial sums");
+constexpr int kBinU = 4;                  // 32-sample tiles per load batch
+constexpr size_t kBinWarpSmem = (size_t)kBinC * (sizeof(float4) + sizeof(float));
+
+struct BinShapes {   // exponents (log2 b0, log2 b1), by thread count, then decreasing b0
+    int8_t e[kBinS][2];
+    __host__ __device__ constexpr BinShapes() : e{} {
+        int idx = 0;
+        for (int s = 5; s <= 10; ++s)
+            for (int e0 = s; e0 >= 0; --e0) {
+                e[idx][0] = (int8_t)e0;
+                e[idx][1] = (int8_t)(s - e0);
+                ++idx;
+            }
+    }
+};
+__constant__ BinShapes c_bin_shapes{};
+__constant__ MonoTable<3, 4> c_mono34{};
+
+// index of shape (2^e0, 2^e1) in BinShapes, for 5 <= e0 + e1 <= 10, e0, e1 >= 0
+__device__ __forceinline__ int bin_shape_index(int e0, int e1) {
+    const int T = e0 + e1;
+    return T * (T + 1) / 2 - 15 + (T - e0);
+}
+
+__device__ __forceinline__ float pow2f(int e) {   // 2^e for -126 <= e <= 127
+    return __int_as_float((127 + e) << 23);
+}
+
+// (h, l) += v * p for a power of two p (exact product), TwoSum on the high part
+__device__ __forceinline__ void dw_acc_scaled(float& h, float& l, float vh, float vl, float p) {
+    float s, e;
+    two_sum(h, __fmul_rn(vh, p), s, e);
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(e, __fmul_rn(vl, p)));
+}
+
+__global__ void __launch_bounds__(32)
+moments_binned_kernel(const __grid_constant__ FitParams P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = lane_id();
+    const unsigned full = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+    // per warp: float4 (sum y hi, lo, sum y^2 hi, lo) and the count per cell;
+    // after the first fold the float4 region holds F as float2 [3][5][51]
+    float4* cv = reinterpret_cast<float4*>(smem_raw);
+    float* cn = reinterpret_cast<float*>(cv + kBinC);
+    float2* Fs = reinterpret_cast<float2*>(cv);
+    const float* X = reinterpret_cast<const float*>(P.x);
+    const float* Y = reinterpret_cast<const float*>(P.y);
+    const int ns = P.n_scale_log2, bs = P.b_scale_log2;
+    for (int f = blockIdx.x; f < P.n_fits; f += gridDim.x) {
+        const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
+        for (int c = lane; c < kBinC; c += 32) {
+            cv[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            cn[c] = 0.f;
+        }
+        __syncwarp();
+        bool fallback = false;
+        // ---- stream: two batches of kBinU tiles in flight ----------------------
+        float nb[kBinU][4] = {};
+        auto load = [&](int64_t base, float (&b)[kBinU][4]) {
+#pragma unroll
+            for (int u = 0; u < kBinU; ++u) {
+                const int64_t s = base + u * 32 + lane;
+                if (s < s1) {
+                    b[u][0] = X[s];
+                    b[u][1] = X[P.x_stride + s];
+                    b[u][2] = X[2 * P.x_stride + s];
+                    b[u][3] = Y[s];
+                }
+            }
+        };
+        load(s0, nb);
+        for (int64_t base = s0; base < s1; base += 32 * kBinU) {
+            float cb[kBinU][4];
+#pragma unroll
+            for (int u = 0; u < kBinU; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) cb[u][v] = nb[u][v];
+            if (base + 32 * kBinU < s1) load(base + 32 * kBinU, nb);
+#pragma unroll
+            for (int u = 0; u < kBinU; ++u) {
+                const int64_t s = base + u * 32 + lane;
+                const bool live = s < s1;
+                if (!__any_sync(full, live)) break;
+                int cell = -1 - lane;   // distinct for idle lanes
+                bool ok = true;
+                if (live) {
+                    const unsigned un = __float_as_uint(cb[u][0]);
+                    const unsigned u0 = __float_as_uint(cb[u][1]);
+                    const unsigned u1 = __float_as_uint(cb[u][2]);
+                    // positive powers of two: sign and mantissa bits clear (zero
+                    // and infinity fail the range tests below)
+                    const bool p2 = ((un | u0 | u1) & 0x807FFFFFu) == 0u;
+                    const int t = ns - ((int)(un >> 23) - 127);
+                    const int e0 = (int)(u0 >> 23) - 127, e1 = (int)(u1 >> 23) - 127;
+                    const int T = e0 + e1;
+                    ok = p2 && t >= 0 && t < kBinT && e0 >= 0 && e1 >= 0 && T >= 5 && T <= 10 &&
+                         isfinite(cb[u][3]);
+                    if (ok) cell = t * kBinS + bin_shape_index(e0, e1);
+                }
+                if (__any_sync(full, !ok)) {
+                    fallback = true;
+                    break;
+                }
+                // lanes with the same cell add one after the other
+                const unsigned peers = __match_any_sync(full, cell);
+                const unsigned rank = __popc(peers & lt);
+                const unsigned rounds = __reduce_max_sync(full, rank) + 1u;
+                const float y = cb[u][3];
+                const float y2h = __fmul_rn(y, y);
+                const float y2l = fmaf(y, y, -y2h);
+                for (unsigned r = 0; r < rounds; ++r) {
+                    if (live && rank == r) {
+                        float4 v = cv[cell];
+                        float hs, e;
+                        two_sum(v.x, y, hs, e);
+                        v.x = hs;
+                        v.y = __fadd_rn(v.y, e);
+                        two_sum(v.z, y2h, hs, e);
+                        v.z = hs;
+                        v.w = __fadd_rn(v.w, __fadd_rn(e, y2l));
+                        cv[cell] = v;
+                        cn[cell] = __fadd_rn(cn[cell], 1.f);
+                    }
+                    __syncwarp();
+                }
+            }
+            if (fallback) break;
+        }
+        if (fallback) {
+            if (lane == 0) P.flags[f] = 4;
+            __syncwarp();
+            continue;
+        }
+        __syncwarp();
+        // ---- fold over the octaves of N: items (k, shape) -------------------------
+        constexpr int R1 = (3 * kBinS + 31) / 32;
+        float fh[R1][5], fl[R1][5];
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+            const int it = r * 32 + lane;
+            const int k = it / kBinS, sh = it - k * kBinS;
+#pragma unroll
+            for (int a = 0; a < 5; ++a) fh[r][a] = fl[r][a] = 0.f;
+            if (it < 3 * kBinS) {
+#pragma unroll 1
+                for (int t = 0; t < kBinT; ++t) {
+                    const int c = t * kBinS + sh;
+                    float vh, vl;
+                    if (k == 0) {
+                        vh = cn[c];
+                        vl = 0.f;
+                    } else {
+                        const float4 v = cv[c];
+                        vh = k == 1 ? v.x : v.z;
+                        vl = k == 1 ? v.y : v.w;
+                    }
+                    const float pt = pow2f(-t);
+                    float p = 1.f;
+#pragma unroll
+                    for (int a = 0; a < 5; ++a) {
+                        dw_acc_scaled(fh[r][a], fl[r][a], vh, vl, p);
+                        p = __fmul_rn(p, pt);
+                    }
+                }
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < R1; ++r) {
+            const int it = r * 32 + lane;
+            const int k = it / kBinS, sh = it - k * kBinS;
+            if (it < 3 * kBinS) {
+#pragma unroll
+                for (int a = 0; a < 5; ++a)
+                    Fs[(k * 5 + a) * kBinS + sh] = make_float2(fh[r][a], fl[r][a]);
+            }
+        }
+        __syncwarp();
+        // ---- fold over the block shapes: items (k, moment) ------------------------
+        // three partial sums over interleaved shapes (independent chains)
+        float2* mom = reinterpret_cast<float2*>(P.mom) + (int64_t)f * 3 * 35;
+#pragma unroll 1
+        for (int it = lane; it < 3 * 35; it += 32) {
+            const int k = it / 35, mu = it - k * 35;
+            const int a = c_mono34.e[mu][0], i = c_mono34.e[mu][1], j = c_mono34.e[mu][2];
+            const float2* Fk = Fs + (k * 5 + a) * kBinS;
+            float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+#pragma unroll 1
+            for (int sh = 0; sh < kBinS; sh += 3) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const int ex = i * (c_bin_shapes.e[sh + q][0] - bs) +
+                                   j * (c_bin_shapes.e[sh + q][1] - bs);
+                    const float2 v = Fk[sh + q];
+                    dw_acc_scaled(h[q], l[q], v.x, v.y, pow2f(ex));
+                }
+            }
+            dw_acc_scaled(h[0], l[0], h[1], l[1], 1.f);
+            dw_acc_scaled(h[0], l[0], h[2], l[2], 1.f);
+            const dw q = dw_2sum(h[0], l[0]);
+            mom[it] = make_float2(q.h, q.l);
+        }
+        if (lane == 0) P.flags[f] = 0;
+        __syncwarp();
+    }
 }
 
 template <typename TS, int ACC, int MG, int MAXT>
@@ -1964,6 +2202,26 @@ klr_status launch_moments(const FitParams& P, int n_mom, int rec, int wpb, cudaS
     return KLR_OK;
 }
 
+// DF32 degree-2 fits in (N, b0, b1): the binned moments kernel on a
+// persistent grid (one warp per fit at a time), then the per-sample kernel
+// over the fits it left (flag bit 4).
+klr_status launch_moments_binned(const FitParams& P, int n_sm, int rec, int wpb,
+                                 cudaStream_t stream) {
+    const size_t smem = kBinWarpSmem;
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(moments_binned_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, moments_binned_kernel,
+                                                                 32, smem));
+    const int64_t slots = (int64_t)std::max(1, per_sm) * std::max(1, n_sm);
+    const int grid = (int)std::min<int64_t>(P.n_fits, slots);
+    moments_binned_kernel<<<grid, 32, smem, stream>>>(P);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    FitParams Q = P;
+    Q.fallback_only = 1;
+    return launch_moments<float, ACC_DF32>(Q, 35, rec, wpb, stream);
+}
+
 template <typename TS>
 klr_status launch_solve_warp(const FitParams& P, size_t smem_optin, cudaStream_t stream) {
     size_t per_warp = sizeof(double) * (3 * (size_t)P.n_mom + (size_t)P.u * P.ld + 6 * (size_t)P.u);
@@ -2173,6 +2431,7 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     P.status = fit_status;
     P.diag = fit_diag;
     P.refine = b->refine_iters;
+    P.fallback_only = 0;
     P.ld = (u % 2) ? u : u + 1;
     memcpy(P.exps, basis.exps, sizeof(P.exps));
     memcpy(P.pair, basis.pair, sizeof(P.pair));
@@ -2235,7 +2494,13 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
                      : launch_moments<float, ACC_FP64>(P, basis.n_mom, rec, wpb, stream);
             break;
         case KLR_FIT_DF32:
-            st = launch_moments<float, ACC_DF32>(P, basis.n_mom, rec, wpb, stream);
+            // binned moments where they apply (degree 2 in (N, b0, b1); the
+            // block-size scale keeps every monomial's power of two normal)
+            if (!box && b->n_vars == 3 && b->degree == 2 && b->b_scale_log2 >= 5 &&
+                b->b_scale_log2 <= 15)
+                st = launch_moments_binned(P, c->n_sm, rec, wpb, stream);
+            else
+                st = launch_moments<float, ACC_DF32>(P, basis.n_mom, rec, wpb, stream);
             break;
         case KLR_FIT_FP32:
             st = s64 ? launch_moments<double, ACC_FP32>(P, basis.n_mom, rec, wpb, stream)

@@ -113,6 +113,36 @@ def test_batched_noisy_ragged(klr, ctx, mode):
         assert err <= bound(mode, 20, gap, 0) + 2.0 ** -24, (f, err, gap)
 
 
+def test_df32_binned_and_per_sample_fits_in_one_batch(klr, ctx):
+    """DF32 degree-2 fits go through per-cell sums when every sample is a
+    power of two inside the 16 octaves of N below the N scale and has one of
+    the 51 block shapes of 32..1024 threads; any other fit is left to the
+    per-sample moments kernel.  One batch with both kinds, and the statuses
+    of an empty fit and a fit with a NaN sample."""
+    from types import SimpleNamespace
+    fb = W.fit_batch(25, 3, (50, 600), noise=0.01, dtype=np.float32)
+    xs = [fb.x[:, fb.offsets[f]:fb.offsets[f + 1]].copy() for f in range(fb.n_fits)]
+    ys = [fb.y[fb.offsets[f]:fb.offsets[f + 1]].copy() for f in range(fb.n_fits)]
+    xs[1][0, 0] = 2.0 ** 7                 # one octave below the window
+    xs[3][1:, 0] = (4.0, 4.0)              # a 16-thread block shape
+    xs[5][0, 0] = 2.0 ** 24                # above the N scale
+    ys[7][3] = np.nan                      # non-finite sample
+    xs[9], ys[9] = xs[9][:, :0], ys[9][:0]  # empty fit
+    xs[11][0, -1] = 2.0 ** 8               # edge of the window (t = 15): binned
+    xs[11][1:, -1] = (1024.0, 1.0)         # edge shape: binned
+    off = np.concatenate([[0], np.cumsum([len(v) for v in ys])]).astype(np.int64)
+    b = SimpleNamespace(offsets=off, x=np.concatenate(xs, axis=1).astype(np.float32),
+                        y=np.concatenate(ys).astype(np.float32), n_vars=3, degree=2,
+                        n_scale_log2=23, b_scale_log2=10)
+    coef, st, _ = gpu_fit(klr, ctx, b, klr.FIT_DF32, 0)
+    assert st[9] == rational.FIT_EMPTY and st[7] == rational.FIT_NONFINITE
+    assert np.all(coef[9] == 0) and np.all(coef[7] == 0)
+    check(b, coef, st, "df32", 0)
+    # the same batch twice: the binned path is deterministic
+    coef2, st2, _ = gpu_fit(klr, ctx, b, klr.FIT_DF32, 0)
+    assert np.array_equal(coef, coef2) and np.array_equal(st, st2)
+
+
 def test_degree3_refinement(klr, ctx):
     fb = W.fit_batch(24, 2, 1500, degree=3, n_hi_log2=30, dtype=np.float64)
     ref = rational.fit_batch(fb.offsets, fb.x, fb.y, 3, 3, 30, 10)
