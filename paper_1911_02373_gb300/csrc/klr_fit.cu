@@ -46,6 +46,7 @@ namespace {
 
 constexpr int kRefineMaxU = 40;         // unknowns supported by refinement passes
 constexpr int kLaneMaxU = 30;           // unknowns supported by the lane-per-fit solver
+constexpr int kLanczosSteps = 6;        // Lanczos steps of the group solver's first phase
 
 enum { ACC_FP64 = 0, ACC_DF32 = 1, ACC_FP32 = 2 };
 
@@ -1722,6 +1723,70 @@ __device__ __noinline__ void group_tri_solve(float2* wv, const float2* Lf, const
 
 #undef GLF
 
+// Largest eigenpair of the K x K symmetric tridiagonal matrix (a on the
+// diagonal, b beside it), in FP32.  Newton's method on the characteristic
+// polynomial from Gershgorin's upper bound: for a polynomial with real roots
+// it decreases monotonically to the largest root.  The pivots r_i of
+// T - x I (all negative above the largest eigenvalue) give p'/p =
+// sum_i r_i'/r_i.  The eigenvector comes from two steps of inverse iteration
+// with x I - T (positive definite for x just above the root), solved by the
+// Thomas recurrence without pivoting.  s is normalised to unit length.
+template <int K>
+__device__ float tridiag_top_eigen(const float (&a)[K], const float (&b)[K], float (&s)[K]) {
+    float x = -FLT_MAX;
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const float r = (i > 0 ? fabsf(b[i - 1]) : 0.f) + (i + 1 < K ? fabsf(b[i]) : 0.f);
+        x = fmaxf(x, a[i] + r);
+    }
+    x = x + 1e-6f * fabsf(x) + FLT_MIN;
+#pragma unroll 1
+    for (int it = 0; it < 40; ++it) {
+        float r = a[0] - x, dr = -1.f, sum = dr / r;
+#pragma unroll
+        for (int i = 1; i < K; ++i) {
+            const float bb = b[i - 1] * b[i - 1];
+            const float rn = (a[i] - x) - bb / r;
+            dr = -1.f + bb * dr / (r * r);
+            r = rn;
+            sum += dr / r;
+        }
+        // p / p' = 1 / sum; the step is negative above the root
+        const float dx = 1.f / sum;
+        const float xn = x - dx;
+        if (!(xn < x) || !(xn == xn)) break;
+        x = xn;
+        if (fabsf(dx) <= 1e-7f * fabsf(x)) break;
+    }
+    const float xs = x + 2e-6f * fabsf(x) + FLT_MIN;   // above the root: x I - T is definite
+#pragma unroll
+    for (int i = 0; i < K; ++i) s[i] = 1.f;
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+        // (xs I - T) z = s by the Thomas recurrence
+        float c[K], d[K];
+        float den = xs - a[0];
+        c[0] = -b[0] / den;
+        d[0] = s[0] / den;
+#pragma unroll
+        for (int i = 1; i < K; ++i) {
+            den = (xs - a[i]) + b[i - 1] * c[i - 1];
+            c[i] = i + 1 < K ? -b[i] / den : 0.f;
+            d[i] = (s[i] + b[i - 1] * d[i - 1]) / den;
+        }
+        s[K - 1] = d[K - 1];
+#pragma unroll
+        for (int i = K - 2; i >= 0; --i) s[i] = d[i] - c[i] * s[i + 1];
+        float nn = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) nn += s[i] * s[i];
+        const float inv = rsqrtf(nn);
+#pragma unroll
+        for (int i = 0; i < K; ++i) s[i] *= inv;
+    }
+    return x;
+}
+
 // The double-word solver with Q lanes per fit (32 / Q fits per warp).  Each
 // fit's factor lives in shared memory (packed lower triangle, 8-byte pairs);
 // row i of the factor is computed by lane i % Q of the fit's group, so a fit's
@@ -1859,35 +1924,93 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
         for (int i = q; i < u; i += Q) vv[i] = st2(dw_mul(ld2(vv[i]), inv));
         __syncwarp();
     }
+    // Phase 1: Lanczos on T = (Ghat - shift I)^-1 from v (every group runs the
+    // same kLanczosSteps solves).  Each new direction T q_j is orthogonalised
+    // against every earlier basis vector (modified Gram-Schmidt); the
+    // coefficients give the tridiagonal projection (alpha_j = q_j . T q_j,
+    // beta_j the norm of what remains).  Its largest eigenvalue mu gives the
+    // Ritz value theta = shift + 1/mu >= lambda_1 and its eigenvector the Ritz
+    // vector.  Per solve this converges like a Chebyshev-accelerated inverse
+    // iteration: about 0.12 per step at lambda_1/lambda_2 = 0.4 instead of 0.4.
+    {
+        float2* Qv = Dv + u;        // kLanczosSteps basis vectors of u
+        float la[kLanczosSteps], lb[kLanczosSteps];
+        for (int i = q; i < u; i += Q) Qv[i] = vv[i];
+        __syncwarp();
+#pragma unroll 1
+        for (int j = 0; j < kLanczosSteps; ++j) {
+            for (int i = q; i < u; i += Q) wv[i] = Qv[j * u + i];
+            __syncwarp();
+            solve(ok);
+            dw aj{0.f, 0.f};
+#pragma unroll 1
+            for (int k = j; k >= 0; --k) {      // latest first: the large coefficients
+                const dw c = gdot(Qv + k * u, wv);
+                if (k == j) aj = c;
+                for (int i = q; i < u; i += Q)
+                    if (ok) wv[i] = st2(dw_sub(ld2(wv[i]), dw_mul(c, ld2(Qv[k * u + i]))));
+                __syncwarp();
+            }
+            const dw bj = dw_sqrt(gdot(wv, wv));
+            la[j] = aj.h + aj.l;
+            lb[j] = bj.h + bj.l;
+            if (j + 1 < kLanczosSteps) {
+                const dw inv = dw_div(dw{1.f, 0.f}, bj.h > 0.f ? bj : dw{FLT_MIN, 0.f});
+                for (int i = q; i < u; i += Q)
+                    if (ok) Qv[(j + 1) * u + i] = st2(dw_mul(ld2(wv[i]), inv));
+                __syncwarp();
+            }
+        }
+        float sv[kLanczosSteps];
+        const float mu = tridiag_top_eigen<kLanczosSteps>(la, lb, sv);
+        // Ritz vector sum_j s_j q_j, normalised
+        for (int i = q; i < u; i += Q) {
+            dw_acc y;
+            y.init(dw{0.f, 0.f});
+#pragma unroll
+            for (int j = 0; j < kLanczosSteps; ++j) y.add_prod(ld2(Qv[j * u + i]), dw{sv[j], 0.f});
+            if (ok) wv[i] = st2(y.value());
+        }
+        __syncwarp();
+        const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(gdot(wv, wv)));
+        for (int i = q; i < u; i += Q)
+            if (ok) vv[i] = st2(dw_mul(ld2(wv[i]), inv));
+        __syncwarp();
+        if (ok) theta = dw_add(shift, dw_div(dw{1.f, 0.f}, dw{mu > 0.f ? mu : FLT_MIN, 0.f}));
+    }
     bool active = ok;
     float dv2 = 1.f, prev = 1.f;
-    for (int it = 0; it < 6 && __any_sync(full, active); ++it) {
-        const dw th = step(shift, active, dv2);
-        if (active) {
-            // a noisy fit leaves as soon as its Rayleigh quotient has settled
-            // (to 1/128): it only seeds the shifts below
-            const bool settled = it >= 1 && dw_gt(th, null_level) &&
-                                 fabsf(th.h - theta.h) <= 0.0078125f * th.h;
-            theta = th;
-            if (converged(dv2, prev) || settled) active = false;
-            prev = dv2;
+    // noisy fits: rounds of re-factoring on a ladder of shifts below theta
+    // (the Ritz value is accurate to far better than its first rung)
+    bool noisy = ok && dw_gt(theta, null_level);
+    // fits whose lambda_1 is at the rounding level: polish v at the first
+    // shift (the next eigenvalue is far above, a step gains lambda_2 / jitter)
+    {
+        bool act = active && !noisy;
+        for (int it = 0; it < 4 && __any_sync(full, act); ++it) {
+            const dw th = step(shift, act, dv2);
+            if (act) {
+                theta = th;
+                if (converged(dv2, prev)) act = false;
+                prev = dv2;
+            }
         }
     }
-    // noisy fits: rounds of re-factoring on a ladder of shifts below theta
-    bool noisy = ok && dw_gt(theta, null_level);
     bool done = !noisy;
-    const float ladder[7] = {1.0f - 1.0f / 64, 1.0f - 1.0f / 32, 1.0f - 1.0f / 16,
-                             1.0f - 1.0f / 8, 1.0f - 1.0f / 4, 0.5f, 0.25f};
+    const float ladder[8] = {1.0f - 1.0f / 4096, 1.0f - 1.0f / 64, 1.0f - 1.0f / 16,
+                             1.0f - 1.0f / 8, 1.0f - 1.0f / 4, 0.5f, 0.25f, 0.0625f};
     for (int round = 0; round < 3 && __any_sync(full, !done); ++round) {
         bool need = !done;      // this group still needs a factor in this pass
         bool have = false;
-        for (int k = 0; k < 8 && __any_sync(full, need && !have); ++k) {
+        int rung = 9;
+        for (int k = 0; k < 9 && __any_sync(full, need && !have); ++k) {
             const bool try_ = need && !have;
-            const dw sh = k < 7 ? dw_mul_f(theta, ladder[k]) : dw_neg(jitter);
+            const dw sh = k < 8 ? dw_mul_f(theta, ladder[k]) : dw_neg(jitter);
             const bool good = cholesky(sh, try_);
             if (try_ && good) {
                 have = true;
                 shift = sh;
+                rung = k;
             }
         }
         if (need && !have) {
@@ -1901,7 +2024,13 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
             const dw th = step(shift, act, dv2);
             if (act) {
                 theta = th;
-                if (converged(dv2, prev)) { act = false; done = true; }
+                // on the first two rungs a step leaves at most about 1/64 of
+                // the error (1/4096 on the first): a change below 1e-8 leaves
+                // an error below 2e-10
+                if ((rung <= 1 && dv2 <= 1e-16f) || converged(dv2, prev)) {
+                    act = false;
+                    done = true;
+                }
                 prev = dv2;
             }
         }
@@ -2259,7 +2388,8 @@ klr_status launch_solve_group_dw_q(const FitParams& P, cudaStream_t stream) {
         return KLR_ENOTSUP;
     }
     FitParams Q_ = P;
-    int stride = P.u * (P.u + 1) / 2 + 4 * P.u;   // L, 1/L_jj, v, w, D
+    // L, 1/L_jj, v, w, D and the Lanczos basis
+    int stride = P.u * (P.u + 1) / 2 + (4 + kLanczosSteps) * P.u;
     if (stride % 2 == 0) ++stride;          // spread the groups over the banks
     Q_.ld = stride;
     const size_t smem = sizeof(float2) * (size_t)stride * GPW;
