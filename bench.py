@@ -31,11 +31,12 @@ import numpy as np  # noqa: E402
 WORKLOAD = dict(name="batched_fit_eval_fp32", kernels=10000, metrics=8, counts=(50, 2000),
                 noise=0.01, degree=2, n_vars=3, n_hi_log2=23, sizes_per_kernel=64, n_cfg=51)
 METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
-# DRAM bytes (read + write) per sample of the moments kernel, from one ncu
-# capture of the 3,000-kernel copy of this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum over its samples); the traffic of a full launch scales
-# with the sample count.  Summary: profiles/moments_fast_kernel_batched_3000k.md
-MOMENTS_DRAM_BYTES_PER_SAMPLE = 16.79
+# DRAM bytes (read + write) per sample of the binned moments kernel, from one
+# ncu capture of the 1,000-kernel copy of this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum = 136.53 MB over 8,240,324 samples); the traffic of a
+# full launch scales with the sample count.
+# Summary: profiles/moments_binned_kernel_batched_1000k.md
+MOMENTS_DRAM_BYTES_PER_SAMPLE = 16.569
 
 
 def parse():
@@ -79,7 +80,13 @@ def parse():
     ap.add_argument("--prec-fits", type=int, default=4096)
     ap.add_argument("--prec-check-fits", type=int, default=64)
     ap.add_argument("--cpu-sample-kernels", type=int, default=0,
-                    help="kernels in the bounded oracle sample (0: auto)")
+                    help="oracle kernels per worker process and step (0: auto)")
+    ap.add_argument("--parity-kernels", type=int, default=32,
+                    help="kernels of the oracle sample whose outputs the library's are checked against")
+    ap.add_argument("--line-sur-kernels", type=int, default=10000,
+                    help="learned-proposer leg of the default line: kernels (0: no leg)")
+    ap.add_argument("--line-sur-epochs", type=int, default=100)
+    ap.add_argument("--line-sur-queries-per-kernel", type=int, default=20)
     return ap.parse_args()
 
 
@@ -166,11 +173,26 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# oracle baseline (bounded sample, one host thread)
+# oracle baseline: one single-threaded oracle process per host core
 # ---------------------------------------------------------------------------
-def oracle_worker(seed, groups):
-    """Time the oracle on groups of kernels (one group per step); prints JSON.
-    Runs in a child process with one BLAS/OpenMP thread."""
+def _oracle_proc(seed, groups, keep, barrier, out_q, wid):
+    """Worker entry: runs _oracle_work and reports an exception instead of
+    leaving the others waiting at the barrier."""
+    try:
+        _oracle_work(seed, groups, keep, barrier, out_q, wid)
+    except BaseException as e:  # noqa: BLE001 - reported to the parent
+        try:
+            barrier.abort()
+        finally:
+            out_q.put((wid, None, repr(e)[-500:]))
+
+
+def _oracle_work(seed, groups, keep, barrier, out_q, wid):
+    """One worker: its inputs for every step are drawn first (untimed); then,
+    step by step, all workers start together at a barrier and time the oracle
+    (fit every metric of the step's kernels, then choose for their queries).
+    The first `keep` kernels' coefficients and choices are returned too (the
+    parity check of the library's outputs on the same kernels)."""
     import workloads as W
     from oracle import configs as ocfg
     from oracle import program as oprog
@@ -178,64 +200,155 @@ def oracle_worker(seed, groups):
     wl = WORKLOAD
     cfgs = ocfg.enumerate_configs(wl["n_vars"] - 1)
     sizes = W.log_spaced_sizes(wl["sizes_per_kernel"])
-    out = []
-    for kernels in groups:
-        fb = W.fit_batch(seed, wl["kernels"], wl["counts"], n_vars=wl["n_vars"],
-                         degree=wl["degree"], n_hi_log2=wl["n_hi_log2"], noise=wl["noise"],
-                         dtype=np.float32, kernels=kernels)
-        t0 = time.perf_counter()
+    inputs = [W.fit_batch(seed, wl["kernels"], wl["counts"], n_vars=wl["n_vars"],
+                          degree=wl["degree"], n_hi_log2=wl["n_hi_log2"], noise=wl["noise"],
+                          dtype=np.float32, kernels=k) for k in groups]
+    recs, kept = [], []
+    for kernels, fb in zip(groups, inputs):
+        barrier.wait(timeout=900)
+        t0 = time.time()
         coef, _, _ = rational.fit_batch(fb.offsets, fb.x.astype(np.float64),
                                         fb.y.astype(np.float64), wl["n_vars"], wl["degree"],
                                         wl["n_hi_log2"], 10)
-        t1 = time.perf_counter()
         q = W.queries_per_kernel(len(kernels), sizes)
         prog = dict(coef=coef.reshape(len(kernels), 8, -1), regs=fb.truth.regs,
                     smem=fb.truth.smem, n_vars=wl["n_vars"], degree=wl["degree"],
                     n_scale_log2=wl["n_hi_log2"], b_scale_log2=10, metric_lo=W.METRIC_LO,
                     metric_scale=W.METRIC_SCALE)
-        oprog.choose(prog, W.HARDWARE, cfgs, q.offsets, q.sizes)
-        t2 = time.perf_counter()
-        out.append(dict(fit_s=t1 - t0, eval_s=t2 - t1, kernels=len(kernels),
-                        samples=int(fb.offsets[-1]), n_queries=int(len(q.sizes))))
-    print(json.dumps(out))
+        ref = oprog.choose(prog, W.HARDWARE, cfgs, q.offsets, q.sizes)
+        t1 = time.time()
+        recs.append(dict(t0=t0, t1=t1, kernels=len(kernels), samples=int(fb.offsets[-1]),
+                         n_queries=int(len(q.sizes))))
+        if len(kept) < keep:
+            n = min(keep - len(kept), len(kernels))
+            nq = n * len(sizes)
+            rows = np.arange(nq)
+            bnd = np.where(ref["best"][:nq] >= 0,
+                           ref["boundary"][rows, np.maximum(ref["best"][:nq], 0)], np.inf)
+            kept.append(dict(kernels=list(kernels[:n]), coef=coef[:n * 8].tolist(),
+                             best=ref["best"][:nq].tolist(), margin=ref["margin"][:nq].tolist(),
+                             best_cycles=ref["best_cycles"][:nq].tolist(),
+                             boundary=bnd.tolist()))
+    out_q.put((wid, recs, kept))
 
 
-def oracle_steps(seed, n_groups, per_group):
-    """Run oracle_worker in a fresh single-threaded process; list of step records."""
+def oracle_parallel(seed, n_steps, per_worker, n_workers=None, keep=0):
+    """The oracle on `n_workers` host cores (default: all), `per_worker`
+    kernels per worker and step, `n_steps` steps.  Returns (steps, kept,
+    workers): per step the wall time from the common start to the last
+    worker's end and the work done."""
+    import multiprocessing as mp
     import workloads as W
-    ids = W.subsample_kernels(seed + 7, WORKLOAD["kernels"], n_groups * per_group)
-    groups = [ids[i * per_group:(i + 1) * per_group].tolist() for i in range(n_groups)]
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = (f"import sys; sys.path.insert(0, {ROOT!r}); import bench; "
-            f"bench.oracle_worker({seed}, {groups!r})")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
-    if r.returncode:
-        raise RuntimeError("oracle worker failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    n_workers = n_workers or (os.cpu_count() or 1)
+    total = n_steps * n_workers * per_worker
+    ids = W.subsample_kernels(seed + 7, WORKLOAD["kernels"], min(total, WORKLOAD["kernels"]))
+    ids = np.resize(ids, total)     # a sample larger than the workload repeats kernels
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(n_workers)
+    out_q = ctx.Queue()
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                             "MKL_NUM_THREADS")}
+    os.environ.update(OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    procs = []
+    try:
+        for w in range(n_workers):
+            groups = [ids[(st * n_workers + w) * per_worker:(st * n_workers + w + 1) * per_worker]
+                      .tolist() for st in range(n_steps)]
+            per_keep = keep // n_workers + (1 if w < keep % n_workers else 0)
+            pr = ctx.Process(target=_oracle_proc, args=(seed, groups, per_keep, barrier, out_q, w))
+            pr.start()
+            procs.append(pr)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    import queue as _queue
+    res, err = [], None
+    t_end = time.time() + 1800
+    while len(res) < len(procs) and err is None:
+        try:
+            r = out_q.get(timeout=2)
+        except _queue.Empty:
+            # a worker that died before reporting (e.g. at import) never will
+            dead = [i for i, pr in enumerate(procs) if pr.exitcode not in (None, 0)]
+            if dead:
+                err = f"oracle worker {dead[0]} exited with {procs[dead[0]].exitcode}"
+            elif time.time() > t_end:
+                err = "oracle workers gave no result within 30 minutes"
+            continue
+        if r[1] is None:
+            err = f"oracle worker {r[0]} failed: {r[2]}"
+        else:
+            res.append(r)
+    if err is not None:
+        for pr in procs:
+            pr.terminate()
+        for pr in procs:
+            pr.join(timeout=10)
+        raise RuntimeError(err)
+    for pr in procs:
+        pr.join()
+        if pr.exitcode:
+            raise RuntimeError(f"oracle worker exited with {pr.exitcode}")
+    res.sort(key=lambda r: r[0])
+    steps = []
+    for st in range(n_steps):
+        rr = [r[1][st] for r in res]
+        steps.append(dict(wall_s=max(x["t1"] for x in rr) - min(x["t0"] for x in rr),
+                          busy_s=sum(x["t1"] - x["t0"] for x in rr),
+                          kernels=sum(x["kernels"] for x in rr),
+                          samples=sum(x["samples"] for x in rr),
+                          n_queries=sum(x["n_queries"] for x in rr)))
+    kept = [k for r in res for k in r[2]]
+    return steps, kept, n_workers
 
 
-def whole_step_seconds(rec):
-    """A whole step at the oracle's measured per-kernel cost (fits and queries
-    scale with the number of kernels)."""
-    return (rec["fit_s"] + rec["eval_s"]) * WORKLOAD["kernels"] / rec["kernels"]
-
-
-def oracle_baseline(seed, n_kernels_sample):
-    rec = oracle_steps(seed, 1, n_kernels_sample)[0]
-    n_q = WORKLOAD["kernels"] * WORKLOAD["sizes_per_kernel"]
-    step_s = whole_step_seconds(rec)
-    return dict(value=n_q / step_s, unit="queries/s", cores=1, kind="oracle",
-                sample=(f"{rec['kernels']} of {WORKLOAD['kernels']} kernels "
-                        f"({8 * rec['kernels']} fits, {rec['samples']} samples, "
-                        f"{rec['n_queries']} queries): fit {rec['fit_s']:.2f} s + evaluate "
-                        f"{rec['eval_s']:.2f} s on 1 host thread, scaled by kernel count"),
-                step_s=step_s)
+def oracle_baseline(seed, per_worker, keep=32):
+    """cpu_baseline of the default line: one step of `per_worker` kernels on
+    every host core (a bounded sample of the workload), plus the oracle's
+    coefficients and choices of `keep` of those kernels."""
+    steps, kept, nw = oracle_parallel(seed, 1, per_worker, keep=keep)
+    st = steps[0]
+    value = st["n_queries"] / st["wall_s"]
+    cb = dict(value=value, unit="queries/s", cores=nw, kind="oracle",
+              sample=(f"{st['kernels']} of {WORKLOAD['kernels']} kernels ({8 * st['kernels']} "
+                      f"fits, {st['samples']} samples, {st['n_queries']} queries: fit + "
+                      f"evaluate + argmin), {per_worker} per worker on {nw} single-threaded "
+                      f"worker processes, wall time from a common start; the rate scales "
+                      f"with kernel count"),
+              single_thread_value=st["n_queries"] / (st["busy_s"] / nw) / nw,
+              wall_s=st["wall_s"])
+    return cb, kept
 
 
 # ---------------------------------------------------------------------------
 # the library arm
 # ---------------------------------------------------------------------------
-def run_klr(args):
+# Launches per step of the batched path (fit: binned moments, the per-sample
+# moments kernel over the fits the binned one left, the group solver;
+# argmin: the sweep and the two FP64 tie passes) and the per-unit work of
+# each stage used by the rooflines (SURVEY-style per-unit figures, stated in
+# DESIGN): the moments stage reads 16 B per sample and writes 3 x 35
+# double-word moment sums and a flag per fit; its contraction is u^2 = 420
+# flop per sample; the null-vector solve is u^3 = 8000 FP64-class flop per
+# fit; an evaluation is about 70 flop plus the 8 divides of the metric map.
+LAUNCHES_PER_STEP = {"fit_moments": 2, "fit_solve": 1, "argmin": 3}
+FLOP_PER_SAMPLE = 420
+FLOP_PER_FIT = 8000
+FLOP_PER_EVAL = 70
+FP64_PEAK_TFLOPS = 1.25      # GB300 nominal FP64 (the solver's precision class)
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "of measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "of fallback"
+
+
+def run_klr(args, cb_kept=None):
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -251,6 +364,8 @@ def run_klr(args):
     wl = WORKLOAD
     n_fits, n_q = fb.n_fits, len(q.sizes)
     dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    n_sm = props.multi_processor_count
     ctx = klr.Context(local)
     ctx.reserve(n_fits, n_q)
     off_h = torch.from_numpy(fb.offsets).pin_memory()
@@ -276,11 +391,11 @@ def run_klr(args):
     prog = klr.Context.program(coef.view(wl["kernels"], 8, 2 * m), regs, smem, n_vars=3,
                                degree=2, n_scale_log2=23, b_scale_log2=10,
                                metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+    fit_kw = dict(n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10, precision=klr.FIT_DF32,
+                  refine_iters=0, coef_dtype=klr.F32, out=(coef, fst, fdg))
 
     def fit(xx, yy, oo, autotune=False):
-        ctx.fit(oo, xx, yy, n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10,
-                precision=klr.FIT_DF32, refine_iters=0, coef_dtype=klr.F32,
-                out=(coef, fst, fdg), autotune=autotune)
+        ctx.fit(oo, xx, yy, autotune=autotune, **fit_kw)
 
     def choose(qoo, qnn, autotune=False):
         ctx.argmin(prog, hw, cfg, qoo, qnn, out_dtype=klr.F32, out=(best, cyc, mrg, qst, lp),
@@ -299,37 +414,35 @@ def run_klr(args):
         fit(x, y, off)
         choose(qo, qn)
     torch.cuda.synchronize()
-    # the step captured as three CUDA graphs (fit stage F1-F2: moment sums;
-    # fit stage F3: null-vector solve; argmin E1-E5) replayed back to back;
-    # events recorded between the replays time each kernel on its stream
-    def gram():
-        ctx.fit(off, x, y, n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10,
-                precision=klr.FIT_DF32, refine_iters=0, coef_dtype=klr.F32,
-                out=(coef, fst, fdg), stage="gram")
+    # stage functions: fit F1-F2 (moment sums), fit F3 (null-vector solve),
+    # argmin E1-E5
+    parts = [lambda: ctx.fit(off, x, y, stage="gram", **fit_kw),
+             lambda: ctx.fit(off, x, y, stage="solve", **fit_kw),
+             lambda: choose(qo, qn)]
+    names = ["fit_moments", "fit_solve", "argmin"]
 
-    def solve():
-        ctx.fit(off, x, y, n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10,
-                precision=klr.FIT_DF32, refine_iters=0, coef_dtype=klr.F32,
-                out=(coef, fst, fdg), stage="solve")
-
-    parts = [gram, solve, lambda: choose(qo, qn)]
-    graphs = None
+    def step():
+        for fn in parts:
+            fn()
+    graph, stage_graphs = None, None
     if not args.no_graph:
         try:
-            gs = [torch.cuda.CUDAGraph() for _ in parts]
-            for g_, fn in zip(gs, parts):
+            # the whole step as one CUDA graph (the timed replay), and each
+            # stage as its own graph (for the per-stage breakdown)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                step()
+            stage_graphs = [torch.cuda.CUDAGraph() for _ in parts]
+            for g_, fn in zip(stage_graphs, parts):
                 with torch.cuda.graph(g_):
                     fn()
             for _ in range(args.warmup):
-                for g_ in gs:
-                    g_.replay()
+                graph.replay()
             torch.cuda.synchronize()
-            graphs = gs
         except Exception as e:  # report and fall back to eager launches
             print(f"graph capture failed: {e}", file=sys.stderr)
-            graphs = None
+            graph, stage_graphs = None, None
     K = args.steps
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)] for _ in range(K)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
@@ -338,26 +451,52 @@ def run_klr(args):
         dist.barrier()
     torch.cuda.synchronize()
     start.record(stream)
-    for k in range(K):
-        for i, fn in enumerate(parts):
-            ev[k][i].record(stream)
-            if graphs is not None:
-                graphs[i].replay()
-            else:
-                fn()
-        ev[k][len(parts)].record(stream)
+    for _ in range(K):
+        if graph is not None:
+            graph.replay()
+        else:
+            step()
     stop.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     ck = clocks.stop()
     total_ms = start.elapsed_time(stop)
-    part_ms = [float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev])) for i in range(len(parts))]
-    gram_ms, solve_ms, eval_ms = part_ms
-    fit_ms = gram_ms + solve_ms
     ms_step, units = whole_job(total_ms / K, n_q, dist, dev)
+    # per-stage breakdown (outside the timed region): each stage's graph
+    # replayed with events between stages on the launching stream
+    KB = max(3, min(K, 50))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(parts) + 1)] for _ in range(KB)]
+    for k in range(KB):
+        for i, fn in enumerate(parts):
+            ev[k][i].record(stream)
+            if stage_graphs is not None:
+                stage_graphs[i].replay()
+            else:
+                fn()
+        ev[k][len(parts)].record(stream)
+    torch.cuda.synchronize()
+    part_ms = {nm: float(np.mean([e[i].elapsed_time(e[i + 1]) for e in ev]))
+               for i, nm in enumerate(names)}
     fit_status = fst.cpu().numpy()
     q_status = qst.cpu().numpy()
+    best_np, cyc_np = best.cpu().numpy(), cyc.cpu().numpy()
+    coef_np = coef.cpu().numpy()
+
+    # table mode: the full cycles table of the fitted program (FP32),
+    # 640,000 x 51 values written to HBM
+    table = torch.empty((n_q, cfg.shape[0]), device=dev, dtype=torch.float32)
+    ctx.eval(prog, hw, cfg, qo, qn, out_dtype=klr.F32, out=table)
+    torch.cuda.synchronize()
+    ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    KT = max(3, min(K, 50))
+    ta.record(stream)
+    for _ in range(KT):
+        ctx.eval(prog, hw, cfg, qo, qn, out_dtype=klr.F32, out=table)
+    tb.record(stream)
+    torch.cuda.synchronize()
+    table_ms = ta.elapsed_time(tb) / KT
+    del table
 
     # end to end through the public API: pinned host inputs in, results out,
     # every step.  The inputs of step i+1 are copied on a second stream into
@@ -368,11 +507,8 @@ def run_klr(args):
     bufs = [(off, x, y, qo, qn),
             tuple(torch.empty_like(t_) for t_ in (off, x, y, qo, qn))]
     hosts = (off_h, x_h, y_h, qo_h, qn_h)
-    # the copies of a step are split into chunks over several streams (the
-    # host link is not saturated by a single copy)
     n_cs = args.e2e_copy_streams
     copy_streams = [torch.cuda.Stream(device=dev) for _ in range(n_cs)]
-    copy_stream = copy_streams[0]
     h2d_done = [[torch.cuda.Event() for _ in range(n_cs)] for _ in range(2)]
     used = [torch.cuda.Event() for _ in range(2)]
     pieces = []
@@ -412,28 +548,51 @@ def run_klr(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms, e2e_units = whole_job(e0.elapsed_time(e1) / E, n_q, dist, dev)
-    h2d = sum(t.numel() * t.element_size() for t in (off_h, x_h, y_h, qo_h, qn_h))
-    d2h = best_h.numel() * 4 + cyc_h.numel() * 4
+    h2d_b = sum(t.numel() * t.element_size() for t in (off_h, x_h, y_h, qo_h, qn_h))
+    d2h_b = best_h.numel() * 4 + cyc_h.numel() * 4
+
+    sur = None
+    if rank == 0 and args.line_sur_kernels > 0:
+        sur = surrogate_study(args, args.line_sur_kernels, args.line_sur_epochs,
+                              args.sur_rows_per_kernel, args.line_sur_queries_per_kernel,
+                              args.sur_k_list, args.sur_k, reps=5)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return None
     n_samples = int(fb.offsets[-1])
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
-        pass
+    peaks, peak_src = load_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    # moments stage: samples and offsets in, 3 x 35 double-FP32 sums + a flag out
-    fit_bytes = n_samples * 16 + (n_fits + 1) * 8 + n_fits * (3 * 35 * 8 + 4)
-    sm_max = (ck or {}).get("sm_max_mhz") or 2070.0
-    # double-FP32 moment accumulation: per sample and moment, three error-free
-    # sums (6 FP32 ops + 1 compensation add each), two products and one FMA
-    n_mom = 35
-    fit_ops = n_samples * n_mom * (3 * 7 + 3)
-    alu_peak = 152 * 128 * sm_max * 1e6   # FP32 lanes x clock: lane-ops/s
+    sm_mhz = (ck or {}).get("sm_max_mhz") or 2070.0
+    fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s (FMA = 2 flop)
+    # stage rooflines from the per-unit work above
+    mom_bytes = n_samples * 16 + (n_fits + 1) * 8 + n_fits * (3 * 35 * 8 + 4)
+    t_mom, t_sol, t_arg = (part_ms[k] * 1e-3 for k in names)
+    evals = n_q * wl["n_cfg"]
+    moments_rf = {"bound": "hbm", "achieved": mom_bytes / t_mom / 1e9, "peak": hbm_peak,
+                  "unit": "GB/s", "frac": mom_bytes / t_mom / 1e9 / hbm_peak,
+                  "traffic": MOMENTS_DRAM_BYTES_PER_SAMPLE * n_samples,
+                  "kernel": "moments_binned_kernel (+ moments_fast_kernel over left fits)",
+                  "algorithmic_bytes": mom_bytes,
+                  "flop_tflops": FLOP_PER_SAMPLE * n_samples / t_mom / 1e12,
+                  "flop_peak_tflops": fp32_peak,
+                  "flop_frac": FLOP_PER_SAMPLE * n_samples / t_mom / 1e12 / fp32_peak,
+                  "peak_source": f"hbm {peak_src}; FP32 FMA lanes x {n_sm} SMs x max clock"}
+    solve_rf = {"bound": "alu", "achieved": FLOP_PER_FIT * n_fits / t_sol / 1e12,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": FLOP_PER_FIT * n_fits / t_sol / 1e12 / FP64_PEAK_TFLOPS,
+                "traffic": None, "kernel": "solve_group_dw_kernel (double-word FP32)",
+                "frac_of_fp32_peak": FLOP_PER_FIT * n_fits / t_sol / 1e12 / fp32_peak,
+                "peak_source": "nominal FP64 (the solve's precision class); u^3 per fit"}
+    argmin_rf = {"bound": "alu", "achieved": FLOP_PER_EVAL * evals / t_arg / 1e12,
+                 "peak": fp32_peak, "unit": "TFLOP/s",
+                 "frac": FLOP_PER_EVAL * evals / t_arg / 1e12 / fp32_peak, "traffic": None,
+                 "kernel": "eval_kernel<float, 2> + tie_kernel (2 passes)",
+                 "peak_source": f"FP32 FMA lanes x {n_sm} SMs x max clock"}
+    rooflines = {"fit_moments": moments_rf, "fit_solve": solve_rf, "argmin": argmin_rf}
+    dominant = max(names, key=lambda k: part_ms[k])
+    table_bytes = evals * 4 + n_q * 8 + (wl["kernels"] + 1) * 8 + wl["kernels"] * 8 * 2 * m * 4
     out = {
         "metric": METRIC,
         "value": units / (ms_step * 1e-3),
@@ -449,34 +608,98 @@ def run_klr(args):
         "data": "synthetic (seeded rational ground truth, 1% noise)",
         "config": {"workload": WORKLOAD["name"], "kernels": wl["kernels"], "fits": n_fits,
                    "samples": n_samples, "queries": n_q, "configs": wl["n_cfg"],
-                   "evals": n_q * wl["n_cfg"], "fit_precision": "df32", "refine_iters": 0,
+                   "evals": evals, "fit_precision": "df32", "refine_iters": 0,
                    "l2": "inputs larger than L2 (1.31 GB of samples per step)",
-                   "launch": ("CUDA graphs (fit moments, fit solve, argmin)" if graphs is not None
-                              else "eager"),
+                   "launch": ("one CUDA graph per step (fit moments, fit solve, argmin)"
+                              if graph is not None else "eager"),
                    "autotuned": {k: {"choice": v[0], "ms": v[1]} for k, v in tuned.items()},
                    "parallelism": f"replicas x{ws}"},
         "fits_per_s": units / n_q * n_fits / (ms_step * 1e-3),
         "config_evals_per_s": units * wl["n_cfg"] / (ms_step * 1e-3),
-        "kernel_ms": {"fit_moments": gram_ms, "fit_solve": solve_ms, "argmin": eval_ms},
-        "roofline": {"bound": "alu", "achieved": fit_ops / (gram_ms * 1e-3) / 1e12,
-                     "peak": alu_peak / 1e12, "unit": "Tops/s (FP32 lane-ops)",
-                     "frac": fit_ops / (gram_ms * 1e-3) / alu_peak,
-                     "traffic": MOMENTS_DRAM_BYTES_PER_SAMPLE * n_samples,
-                     "traffic_algorithmic": fit_bytes,
-                     "kernel": "moments_fast_kernel (double-FP32 moment sums, F1-F2)",
-                     "hbm_gbs": fit_bytes / (gram_ms * 1e-3) / 1e9, "hbm_peak_gbs": hbm_peak,
-                     "hbm_frac": fit_bytes / (gram_ms * 1e-3) / 1e9 / hbm_peak,
-                     "peak_source": "FP32 lanes x max SM clock (unit counts)"},
+        "kernel_ms": part_ms,
+        "roofline": dict(rooflines[dominant], stage=dominant),
+        "rooflines": rooflines,
+        "table": {"ms": table_ms, "evals_per_s": evals / (table_ms * 1e-3),
+                  "bytes": table_bytes, "gbs": table_bytes / (table_ms * 1e-3) / 1e9,
+                  "hbm_frac": table_bytes / (table_ms * 1e-3) / 1e9 / hbm_peak,
+                  "flop_frac": FLOP_PER_EVAL * evals / (table_ms * 1e-3) / 1e12 / fp32_peak,
+                  "note": "klr_eval FP32 cycles table of the fitted program, 4 B per evaluation"},
         "e2e": {"value": e2e_units / (e2e_ms * 1e-3), "unit": "queries/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": 4 * K,
+                "h2d_bytes_per_step": int(h2d_b), "d2h_bytes_per_step": int(d2h_b)},
+        "gpu_launches": sum(LAUNCHES_PER_STEP.values()) * K,
         "clocks": ck,
         "fit_status_nonzero": int(np.count_nonzero(fit_status & ~8)),
         "ties_resolved": int(np.count_nonzero(q_status & 4)),
+        "surrogate": sur,
     }
+    if cb_kept:
+        out["parity"] = parity_vs_oracle(cb_kept, coef_np, best_np, cyc_np, fb, q)
     if dist:
         dist.destroy_process_group()
     return out
+
+
+def parity_vs_oracle(kept, coef, best, cyc, fb, q):
+    """The library's outputs on the kernels whose oracle results the CPU
+    baseline returned: coefficients (max-abs of the unit-norm vectors),
+    predictions of the fitted metrics on the query grid (max difference over
+    the fit's largest |p/q| on the grid; points where the oracle's denominator
+    is below 1% of its largest value, near a pole of the noisy fit, are
+    counted instead), and the
+    argmin of the whole fitted program (the oracle chooses with its own fits,
+    the library with its own)."""
+    import workloads as W
+    wl = WORKLOAD
+    sizes = W.log_spaced_sizes(wl["sizes_per_kernel"])
+    shapes = np.ldexp(1.0, W.block_shape_exponents(2))
+    exps = W.term_exponents(3, 2)
+    xs = np.empty((len(sizes), len(shapes), 3))
+    xs[..., 0] = sizes[:, None] * 2.0 ** -wl["n_hi_log2"]
+    xs[..., 1:] = shapes[None, :, :] * 2.0 ** -10
+    phi = np.ones(xs.shape[:-1] + (len(exps),))
+    for t, e in enumerate(exps):
+        for v in range(3):
+            phi[..., t] *= xs[..., v] ** e[v]
+    cerr, perr, n_strict, n_eq, n_all_eq, crel, n_pole = [], [], 0, 0, 0, [], 0
+    for rec in kept:
+        oc = np.array(rec["coef"])
+        for i, k in enumerate(rec["kernels"]):
+            for mtr in range(8):
+                a, g = oc[i * 8 + mtr], coef[k * 8 + mtr].astype(np.float64)
+                cerr.append(float(np.max(np.abs(a - g))))
+                qa = phi @ a[len(exps):]
+                # grid points near a pole of the noisy fit (a pole-zero pair
+                # of the least-squares rational fit) are counted, not compared
+                away = np.abs(qa) >= 1e-2 * np.max(np.abs(qa))
+                n_pole += int((~away).sum())
+                pa = (phi @ a[:len(exps)])[away] / qa[away]
+                pg = ((phi @ g[:len(exps)]) / (phi @ g[len(exps):]))[away]
+                perr.append(float(np.max(np.abs(pg - pa)) / np.max(np.abs(pa))))
+            r0 = int(q.offsets[k])
+            ob = np.array(rec["best"][i * len(sizes):(i + 1) * len(sizes)])
+            om = np.array(rec["margin"][i * len(sizes):(i + 1) * len(sizes)])
+            obd = np.array(rec["boundary"][i * len(sizes):(i + 1) * len(sizes)])
+            oc_ = np.array(rec["best_cycles"][i * len(sizes):(i + 1) * len(sizes)])
+            gb = best[r0:r0 + len(sizes)]
+            strict = (om > 1e-4) & (obd > 1e-4)
+            n_strict += int(strict.sum())
+            n_eq += int((gb[strict] == ob[strict]).sum())
+            n_all_eq += int((gb == ob).sum())
+            same = (gb == ob) & np.isfinite(oc_)
+            crel += list(np.abs(cyc[r0:r0 + len(sizes)][same] - oc_[same]) / oc_[same])
+    n_k = sum(len(r["kernels"]) for r in kept)
+    return {"kernels": n_k, "fits": 8 * n_k,
+            "coef_err_max": max(cerr), "coef_err_median": float(np.median(cerr)),
+            "pred_rel_err_max": max(perr) if perr else 0.0,
+            "pred_rel_err_median": float(np.median(perr)) if perr else 0.0,
+            "pred_points": 8 * sum(len(r["kernels"]) for r in kept) * phi.shape[0] * phi.shape[1],
+            "pred_points_near_pole": n_pole,
+            "argmin_checked": n_k * len(sizes), "argmin_equal": n_all_eq,
+            "argmin_strict_checked": n_strict, "argmin_strict_equal": n_eq,
+            "best_cycles_rel_err_max": float(max(crel)) if crel else 0.0,
+            "note": ("library (DF32 fit, FP32 program) against the FP64 oracle, each fitting "
+                     "the same FP32 samples and choosing with its own fit; strict = oracle "
+                     "margin and branch distance > 1e-4")}
 
 
 SWEEP = dict(name="sweep3d_fp32_fp64", n_vars=4, degree=2, n_hi_log2=23, sizes=256, n_cfg=251)
@@ -668,14 +891,22 @@ def sweep3d_surrogate(args, klr, W, ctx, gt, prog, coef, regs, smem, cfg, hw, si
 
 
 def run_surrogate(args):
-    """Learned proposer at scale: train the surrogate on rows labelled by the
-    rational program, then resolve argmin queries by top-k proposal + exact
-    re-ranking and compare with the plain sweep (time and top-1 regret)."""
+    """Learned proposer at scale (--workload surrogate)."""
+    return surrogate_study(args, args.sur_kernels, args.sur_epochs, args.sur_rows_per_kernel,
+                           args.sur_queries_per_kernel, args.sur_k_list, args.sur_k,
+                           reps=max(1, args.steps // 10))
+
+
+def surrogate_study(args, nk, epochs, rows_per_kernel, queries_per_kernel, k_list, k_main, reps):
+    """Train the surrogate on rows labelled by the rational program (degree-3
+    programs of nk seeded kernels), then resolve argmin queries at sizes off
+    the training grid by top-k proposal + exact re-ranking, against the plain
+    sweep with the same decision rule (time and top-1 regret, per k)."""
     import torch
     import paper_1911_02373_gb300 as klr
     from paper_1911_02373_gb300 import proposer
     import workloads as W
-    nk, seed = args.sur_kernels, args.seed
+    seed = args.seed
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
     t0 = time.time()
     gt = W.ground_truth(seed, nk, 3, 3, 8, 23, 10)
@@ -692,7 +923,7 @@ def run_surrogate(args):
     # centred log2 cycles of the FP32 rational program
     sizes = W.log_spaced_sizes(64)
     q = W.queries_per_kernel(nk, sizes)
-    R = args.sur_rows_per_kernel
+    R = rows_per_kernel
     keys = W.stream_keys(seed, (90,), np.arange(nk, dtype=np.uint64))
     per_query = args.sur_form == "query"
     if per_query:
@@ -727,7 +958,7 @@ def run_surrogate(args):
                  np.arange(klr.mlp_param_count(n_coef, n_out), dtype=np.uint64))
     sur = klr.Surrogate(ctx, n_coef, proposer.init_params(n_coef, z, n_out), np.ones(7),
                         n_out=n_out)
-    okeys = W.stream_keys(seed, (92,), np.arange(args.sur_epochs, dtype=np.uint64))
+    okeys = W.stream_keys(seed, (92,), np.arange(epochs, dtype=np.uint64))
     order = lambda ep: torch.argsort(t(W.words(okeys[ep], np.arange(n_rows, dtype=np.uint64))
                                        .view(np.int64)))
     prep_s = time.time() - t0
@@ -735,13 +966,13 @@ def run_surrogate(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     losses = proposer.train(sur, coef, cfg, kern, N, ci, target, batch=batch,
-                            epochs=args.sur_epochs, lr=args.sur_lr, order=order, log_every=50)
+                            epochs=epochs, lr=args.sur_lr, order=order, log_every=50)
     e1.record()
     torch.cuda.synchronize()
     train_ms = e0.elapsed_time(e1)
-    steps = args.sur_epochs * ((n_rows + batch - 1) // batch)
+    steps = epochs * ((n_rows + batch - 1) // batch)
     # evaluation queries: sizes off the training grid
-    qk = args.sur_queries_per_kernel
+    qk = queries_per_kernel
     ek = W.stream_keys(seed, (93,), np.arange(nk, dtype=np.uint64))
     u = (W.words(ek[:, None], np.arange(qk, dtype=np.uint64)[None, :]) >> np.uint64(11)).astype(
         np.float64) * 2.0 ** -53
@@ -750,7 +981,7 @@ def run_surrogate(args):
     qn = t(ev_sizes)
     n_q = qn.numel()
     ctx.reserve(0, n_q)
-    K = max(1, args.steps // 10)
+    K = max(1, reps)
 
     def timed(fn):
         fn()
@@ -771,22 +1002,22 @@ def run_surrogate(args):
     table_ms, _ = timed(lambda: ctx.eval(prog, hw, cfg, qo, qn, out_dtype=klr.F32))
     tie_frac = float(((plain[3] & klr.Q_TIE_RESOLVED) != 0).float().mean())
     sur_ms, surr = timed(lambda: proposer.propose_and_rerank(ctx, sur, prog, hw, coef, regs, smem,
-                                                             cfg, qo, qn, args.sur_k))
-    prop_ms, _ = timed(lambda: sur.propose(coef, regs, smem, hw, cfg, qo, qn, args.sur_k))
+                                                             cfg, qo, qn, k_main))
+    prop_ms, _ = timed(lambda: sur.propose(coef, regs, smem, hw, cfg, qo, qn, k_main))
     c_best = plain[1].cpu().numpy().astype(np.float64)
     c_sur = surr[1].cpu().numpy().astype(np.float64)
     ok = np.isfinite(c_best)
     reg = c_sur[ok] / c_best[ok] - 1.0
     reg = np.where(np.isfinite(reg), reg, np.inf)
     rk = W.stream_keys(seed, (94,), np.arange(n_q, dtype=np.uint64))
-    rnd = (W.words(rk[:, None], np.arange(args.sur_k, dtype=np.uint64)[None, :]) % np.uint64(51))
+    rnd = (W.words(rk[:, None], np.arange(k_main, dtype=np.uint64)[None, :]) % np.uint64(51))
     rb = klr.argmin_candidates(ctx, prog, hw, cfg, qo, qn, t(rnd.astype(np.int32)))
     rreg = rb[1].cpu().numpy()[ok] / c_best[ok] - 1.0
     rreg = np.where(np.isfinite(rreg), rreg, np.inf)
     pct = lambda a, p: float(np.percentile(a, p))
     # the frontier: other candidate counts with the same network
     frontier = []
-    for kk in sorted({int(v) for v in args.sur_k_list.split(",") if v.strip()} | {args.sur_k}):
+    for kk in sorted({int(v) for v in k_list.split(",") if v.strip()} | {k_main}):
         ms_k, res_k = timed(lambda: proposer.propose_and_rerank(ctx, sur, prog, hw, coef, regs,
                                                                 smem, cfg, qo, qn, kk))
         rg = res_k[1].cpu().numpy().astype(np.float64)[ok] / c_best[ok] - 1.0
@@ -800,8 +1031,8 @@ def run_surrogate(args):
             "data": "synthetic (seeded rational ground truth)",
             "config": {"workload": "learned_proposer", "form": args.sur_form, "kernels": nk,
                        "degree": 3, "train_rows": n_rows, "train_tuples": n_tuples,
-                       "epochs": args.sur_epochs, "batch": batch, "train_steps": steps,
-                       "queries": n_q, "k": args.sur_k, "configs": 51},
+                       "epochs": epochs, "batch": batch, "train_steps": steps,
+                       "queries": n_q, "k": k_main, "configs": 51},
             "plain_sweep": {"ms": plain_ms, "queries_per_s": n_q / (plain_ms * 1e-3),
                             "fp64_redecided_fraction": tie_frac, "fp32_table_ms": table_ms,
                             "autotuned_threads": 32 << plain_tune[0]},
@@ -809,8 +1040,8 @@ def run_surrogate(args):
                                "fp64_redecided_fraction":
                                    float(((surr[2] & klr.Q_TIE_RESOLVED) != 0).float().mean()),
                                "speedup_vs_plain": plain_ms / sur_ms},
-            "train": {"ms": train_ms, "rows_per_s": n_rows * args.sur_epochs / (train_ms * 1e-3),
-                      "tuples_per_s": n_tuples * args.sur_epochs / (train_ms * 1e-3),
+            "train": {"ms": train_ms, "rows_per_s": n_rows * epochs / (train_ms * 1e-3),
+                      "tuples_per_s": n_tuples * epochs / (train_ms * 1e-3),
                       "loss_first": losses[0], "loss_last": losses[-1], "prep_s": prep_s},
             "regret_top1": {"mean": float(np.mean(np.minimum(reg, 10))),
                             "median": pct(reg, 50), "p90": pct(reg, 90), "p99": pct(reg, 99),
@@ -964,24 +1195,35 @@ def run_precision(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on every host core (one
+    single-threaded process per core), each step a bounded sample of the
+    batched workload (--cpu-sample-kernels kernels per worker, default 4),
+    its time extrapolated to the whole step by kernel count."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return None
-    per = args.cpu_sample_kernels or 1
-    recs = oracle_steps(args.seed, args.warmup + args.steps, per)[args.warmup:]
-    step_s = float(np.mean([whole_step_seconds(r) for r in recs]))
+    per = args.cpu_sample_kernels or 4
+    steps, _, nw = oracle_parallel(args.seed, args.warmup + args.steps, per)
+    steps = steps[args.warmup:]
+    n_q_sample = steps[0]["n_queries"]
+    wall = float(np.mean([st["wall_s"] for st in steps]))
+    value = n_q_sample / wall
     n_q = WORKLOAD["kernels"] * WORKLOAD["sizes_per_kernel"]
-    value = n_q / step_s
-    cb = dict(value=value, unit="queries/s", cores=1, kind="oracle",
-              sample=(f"{per} kernel(s) per step ({8 * per} fits and {64 * per} queries of "
-                      f"{WORKLOAD['kernels']} kernels), {len(recs)} timed steps on 1 host "
-                      f"thread, scaled by kernel count"))
+    step_s = n_q / value
+    cb = dict(value=value, unit="queries/s", cores=nw, kind="oracle",
+              sample=(f"{steps[0]['kernels']} kernel(s) per step ({per} per worker; "
+                      f"{8 * steps[0]['kernels']} fits and {n_q_sample} queries of "
+                      f"{WORKLOAD['kernels']} kernels) on {nw} single-threaded worker "
+                      f"processes, {len(steps)} timed steps, wall time per step from a common "
+                      f"start"))
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded rational ground truth, 1% noise)",
         "config": {"workload": WORKLOAD["name"], "kernels": WORKLOAD["kernels"]},
+        "extrapolated": True, "sampled_kernels_per_step": steps[0]["kernels"],
+        "measured_ms_per_sampled_step": wall * 1e3,
         "cpu_baseline": cb,
         "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -1012,15 +1254,15 @@ def main():
         print(json.dumps(run_history(args)))
         return
     ws, rank, _ = dist_env()
-    cb = None
+    cb, kept = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        # before the first CUDA call: the oracle runs in a fresh process
+        # before the first CUDA call: the oracle runs in spawned processes
         try:
-            cb = oracle_baseline(args.seed, args.cpu_sample_kernels or 1200)
-            cb.pop("step_s")
+            per = args.cpu_sample_kernels or max(1, 3200 // (os.cpu_count() or 1))
+            cb, kept = oracle_baseline(args.seed, per, keep=args.parity_kernels)
         except Exception as e:  # report, do not hide
             cb = {"error": str(e)[-300:]}
-    out = run_klr(args)
+    out = run_klr(args, kept)
     if out is not None:
         out["cpu_baseline"] = cb
         print(json.dumps(out))

@@ -189,6 +189,24 @@ klr_status klr_fit_solve(klr_ctx* ctx, const klr_fit_batch* batch, void* coef_ou
 klr_status klr_fit_heldout(klr_ctx* ctx, const klr_fit_batch* batch, const void* coef,
                            int32_t coef_dtype, double* err_out, void* stream);
 
+/* Choice of a basis per fit from held-out errors (Section V-E bounds each
+ * variable's degree separately and leaves the bounds to be chosen).  This
+ * library's rule: among the candidates whose error is finite and at most
+ * (1 + tol) times the fit's least error plus floor, the one with the fewest
+ * monomials; ties go to the lower column.  The threshold is computed in FP64
+ * as (least * (1 + tol)) + floor, rounded after each operation.
+ * errors: device, n_fits x n_cand doubles, row-major (e.g. one klr_fit_heldout
+ *   output per column).
+ * sizes: HOST, n_cand int32, the monomials of each candidate basis (> 0).
+ * choice_out: device, n_fits int32: the chosen column, -1 when no error of the
+ *   fit is finite.
+ * 1 <= n_cand <= KLR_CHOOSE_BASIS_MAX_CAND, tol >= 0 and floor >= 0 (finite),
+ * else KLR_EINVAL before anything is enqueued. */
+#define KLR_CHOOSE_BASIS_MAX_CAND 64
+klr_status klr_choose_basis(klr_ctx* ctx, const double* errors, const int32_t* sizes,
+                            int64_t n_fits, int32_t n_cand, double tol, double floor,
+                            int32_t* choice_out, void* stream);
+
 /* ---- E2-E5: the rational program ----------------------------------------- */
 
 /* Hardware parameters H.  Integer limits per SM feed the occupancy program of

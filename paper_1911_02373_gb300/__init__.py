@@ -36,9 +36,10 @@ ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last
                "klr_autotune_argmin", "klr_tune_export", "klr_tune_import", "klr_fit_gram",
                "klr_fit_solve", "klr_mlp_query_targets", "klr_history_create",
                "klr_history_clear", "klr_history_destroy", "klr_argmin_history",
-               "klr_argmin_refined", "klr_fit_heldout")
+               "klr_argmin_refined", "klr_fit_heldout", "klr_choose_basis")
 #: largest query count klr_argmin_noalloc accepts
 ARGMIN_NOALLOC_MAX_QUERIES = 65536
+ARGMIN_NOALLOC_TIE_RECORDS = 16384   # FP32 near-ties it lists; more are decided in place
 
 
 class KlrError(RuntimeError):
@@ -115,6 +116,8 @@ for _name, _args in {
                             ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float), _vp],
     "klr_fit_gram": [_vp, ctypes.POINTER(FitBatch), _vp],
     "klr_fit_heldout": [_vp, ctypes.POINTER(FitBatch), _vp, ctypes.c_int32, _vp, _vp],
+    "klr_choose_basis": [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                         ctypes.c_double, _vp, _vp],
     "klr_history_create": [_vp, ctypes.c_int32, ctypes.POINTER(_vp)],
     "klr_history_clear": [_vp, _vp],
     "klr_argmin_refined": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
@@ -269,6 +272,21 @@ class Context:
         _set_var_degree(b, var_degree)
         _check("klr_fit_heldout", _lib.klr_fit_heldout(self._h, ctypes.byref(b), _ptr(coef), cdt,
                                                        _ptr(out), _stream(stream)))
+        return out
+
+    def choose_basis(self, errors, sizes, tol=0.05, floor=1e-6, out=None, stream=None):
+        """klr_choose_basis: per fit (row of the float64 device tensor errors,
+        one column per candidate basis of sizes[j] monomials) the chosen
+        column, -1 when no error is finite; an int32 device tensor."""
+        import torch
+        n_fits, n_cand = errors.shape
+        errors = errors.contiguous()
+        sz = np.ascontiguousarray(np.asarray(sizes, dtype=np.int32))
+        if out is None:
+            out = torch.empty(n_fits, device=errors.device, dtype=torch.int32)
+        _check("klr_choose_basis", _lib.klr_choose_basis(self._h, _ptr(errors), sz.ctypes.data_as(_vp),
+                                                         n_fits, n_cand, tol, floor, _ptr(out),
+                                                         _stream(stream)))
         return out
 
     # -- tuned launch shapes -------------------------------------------------

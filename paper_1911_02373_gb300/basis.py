@@ -18,9 +18,9 @@ def select_basis(ctx: Context, train, heldout, candidates, *, n_vars, n_scale_lo
                  b_scale_log2, precision=FIT_DF32, refine_iters=0, tol=0.05, floor=1e-6):
     """train, heldout: (offsets, x, y) CSR sample sets of the same fits.
     candidates: per-variable bound tuples, or ints (total degree).
-    Returns (choice (n_fits,) int64 device tensor, -1 where no candidate has a
-    finite error; errors (n_fits, n_cand) float64; coefficients per
-    candidate)."""
+    Returns (choice (n_fits,) int32 device tensor from klr_choose_basis, -1
+    where no candidate has a finite error; errors (n_fits, n_cand) float64;
+    coefficients per candidate)."""
     import torch
     errs, coefs, sizes = [], [], []
     for cand in candidates:
@@ -33,13 +33,6 @@ def select_basis(ctx: Context, train, heldout, candidates, *, n_vars, n_scale_lo
                                     b_scale_log2=b_scale_log2, **kw))
         coefs.append(coef)
         sizes.append(_n_monomials(n_vars, kw["degree"], kw["var_degree"]))
-    E = torch.stack(errs, dim=1)
-    fin = torch.isfinite(E)
-    best = torch.where(fin, E, torch.full_like(E, float("inf"))).min(dim=1).values
-    ok = fin & (E <= best[:, None] * (1.0 + tol) + floor)
-    # rank candidates by (size, order); the first eligible in that ranking
-    order = sorted(range(len(candidates)), key=lambda j: (sizes[j], j))
-    choice = torch.full((E.shape[0],), -1, dtype=torch.int64, device=E.device)
-    for j in reversed(order):
-        choice = torch.where(ok[:, j], torch.full_like(choice, j), choice)
+    E = torch.stack(errs, dim=1).contiguous()
+    choice = ctx.choose_basis(E, sizes, tol=tol, floor=floor)
     return choice, E, coefs

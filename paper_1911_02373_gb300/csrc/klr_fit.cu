@@ -2465,6 +2465,35 @@ heldout_kernel(const __grid_constant__ FitParams P, double* __restrict__ out) {
     if (lane == 0) out[f] = s1 > s0 ? sqrt(acc / (double)(s1 - s0)) : 0.0;
 }
 
+// The basis choice of klr_choose_basis, one thread per fit, in FP64: the
+// least finite error, the threshold (least (1 + tol)) + floor with each
+// operation rounded on its own, then the eligible column with the fewest
+// monomials (the lower column on ties).
+struct ChooseBasisParams {
+    int32_t sizes[KLR_CHOOSE_BASIS_MAX_CAND];
+    int n_cand;
+    double tol1, floor;
+};
+
+__global__ void __launch_bounds__(256)
+choose_basis_kernel(const double* __restrict__ err, int64_t n_fits,
+                    const __grid_constant__ ChooseBasisParams P, int32_t* __restrict__ out) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= n_fits) return;
+    const double* e = err + f * P.n_cand;
+    double lo = INFINITY;
+    for (int j = 0; j < P.n_cand; ++j)
+        if (isfinite(e[j]) && e[j] < lo) lo = e[j];
+    int pick = -1;
+    if (lo < INFINITY) {
+        const double lim = __dadd_rn(__dmul_rn(lo, P.tol1), P.floor);
+        for (int j = 0; j < P.n_cand; ++j)
+            if (isfinite(e[j]) && e[j] <= lim && (pick < 0 || P.sizes[j] < P.sizes[pick]))
+                pick = j;
+    }
+    out[f] = pick;
+}
+
 }  // namespace
 
 size_t fit_workspace_bytes(int64_t n_fits, int n_mom) {
@@ -2746,3 +2775,32 @@ extern "C" klr_status klr_fit_heldout(klr_ctx* ctx, const klr_fit_batch* b, cons
     return KLR_OK;
 }
 
+
+extern "C" klr_status klr_choose_basis(klr_ctx* ctx, const double* errors, const int32_t* sizes,
+                                       int64_t n_fits, int32_t n_cand, double tol, double floor,
+                                       int32_t* choice_out, void* stream_) {
+    KLR_REQUIRE(ctx, "klr_choose_basis: NULL context");
+    Context* c = reinterpret_cast<Context*>(ctx);
+    KLR_REQUIRE(n_fits >= 0, "klr_choose_basis: n_fits < 0");
+    KLR_REQUIRE(n_cand >= 1 && n_cand <= KLR_CHOOSE_BASIS_MAX_CAND,
+                "klr_choose_basis: n_cand %d not in 1..%d", n_cand, KLR_CHOOSE_BASIS_MAX_CAND);
+    KLR_REQUIRE(std::isfinite(tol) && tol >= 0 && std::isfinite(floor) && floor >= 0,
+                "klr_choose_basis: tol and floor must be finite and >= 0");
+    KLR_REQUIRE(sizes, "klr_choose_basis: NULL sizes");
+    ChooseBasisParams P{};
+    for (int j = 0; j < n_cand; ++j) {
+        KLR_REQUIRE(sizes[j] > 0, "klr_choose_basis: sizes[%d] = %d not > 0", j, sizes[j]);
+        P.sizes[j] = sizes[j];
+    }
+    P.n_cand = n_cand;
+    P.tol1 = 1.0 + tol;
+    P.floor = floor;
+    if (n_fits == 0) return KLR_OK;
+    KLR_REQUIRE(errors && choice_out, "klr_choose_basis: NULL device array");
+    KLR_CHECK_CUDA(cudaSetDevice(c->device));
+    const int grid = (int)((n_fits + 255) / 256);
+    choose_basis_kernel<<<grid, 256, 0, reinterpret_cast<cudaStream_t>(stream_)>>>(
+        errors, n_fits, P, choice_out);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}

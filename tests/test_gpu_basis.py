@@ -146,3 +146,34 @@ def test_basis_selection_matches_oracle(klr, ctx):
     choice0, E0, _ = basis.select_basis(ctx, (d(to), d(tx), d(ty)), (d(ho), d(hx), d(hy)), cands,
                                         n_vars=3, n_scale_log2=23, b_scale_log2=10)
     assert np.mean(choice0.cpu().numpy() == 1) > 0.9
+
+
+def test_choose_basis_kernel_matches_the_oracle_rule(klr, ctx):
+    """klr_choose_basis against oracle.rational.choose_basis on error tables
+    with exact ties at the threshold (binary fractions: least * (1 + tol) +
+    floor is exact), NaN and infinite errors, rows with nothing finite,
+    candidates of equal size and errors within the floor of each other."""
+    rng = np.random.default_rng(7)
+    n_fits, n_cand = 4000, 6
+    sizes = [10, 8, 16, 8, 20, 35]
+    tol, floor = 0.25, 2.0 ** -20
+    E = rng.uniform(0.5, 1.0, (n_fits, n_cand))
+    E[rng.random(E.shape) < 0.3] *= 1.2
+    lo = E.min(axis=1)
+    lim = lo * (1 + tol) + floor
+    hit = rng.random(E.shape) < 0.2                 # exactly at the threshold
+    E[hit] = np.broadcast_to(lim[:, None], E.shape)[hit]
+    E[:200] = np.round(E[:200] * 64) / 64           # many exact ties
+    E[rng.random(E.shape) < 0.05] = np.nan
+    E[rng.random(E.shape) < 0.05] = np.inf
+    E[300:310] = np.nan                            # nothing finite
+    E[310:320] = 1e-7 * rng.random((10, n_cand))   # all within the floor
+    got = ctx.choose_basis(torch.tensor(E).cuda(), sizes, tol=tol, floor=floor).cpu().numpy()
+    want = rational.choose_basis(E, sizes, tol=tol, floor=floor)
+    assert np.array_equal(got, want)
+    assert np.all(got[300:310] == -1)
+    # bad arguments fail before anything runs
+    with pytest.raises(klr.KlrError):
+        ctx.choose_basis(torch.tensor(E).cuda(), sizes[:5] + [0], tol=tol, floor=floor)
+    with pytest.raises(klr.KlrError):
+        ctx.choose_basis(torch.tensor(E).cuda(), sizes, tol=-1.0, floor=floor)

@@ -133,6 +133,28 @@ def test_full_size_argmin_matches_oracle(run):
     assert np.array_equal((status[rows] & klr.Q_NONE_FEASIBLE) != 0, ref["best"] < 0)
 
 
+def test_full_size_fitted_program_argmin_matches_oracle(run):
+    """The whole chain at full size: the oracle's rational program evaluated
+    on the library's own fitted FP32 coefficients (the table the argmin of
+    the step used) for the checked kernels' 2,048 queries, against the
+    library's choices of that step."""
+    fb, q, coef = run["fb"], run["q"], run["coef"]
+    best, cyc, margin, status, launch = run["fit_out"]
+    ks = _kernels()
+    rows = G.query_rows(q.offsets, ks)
+    fitted = coef.astype(np.float32).reshape(-1, 8, 20)
+    ref = G.oracle_choose(fitted, fb.truth, q.offsets, q.sizes, kernels=ks)
+    ref["cycles"] = np.asarray(ref["cycles"]).reshape(len(rows), -1)
+    ref["boundary"] = np.asarray(ref["boundary"]).reshape(len(rows), -1)
+    ref["best"] = np.asarray(ref["best"])
+    ref["best_cycles"] = np.asarray(ref["best_cycles"], dtype=np.float64)
+    ref["margin"] = np.asarray(ref["margin"], dtype=np.float64)
+    strict, loose = G.compare_argmin(best[rows], cyc[rows], ref, 1e-4, 1e-6, 1e-5)
+    assert strict > 0.9 * len(rows)
+    klr = run["klr"]
+    assert np.array_equal((status[rows] & klr.Q_NONE_FEASIBLE) != 0, ref["best"] < 0)
+
+
 def test_full_size_pipeline_properties(run):
     """On the whole output of the fitted program: every choice is feasible,
     its cycles are the evaluator's table minimum (within the FP32 near-tie

@@ -73,3 +73,52 @@ def test_noalloc_matches_context_argmin_twice():
         klr.argmin_noalloc(prog, hw, cfg, qo, qn, out)
     assert e.value.status == klr.EINVAL and "maximum" in str(e.value)
     ctx.close()
+
+
+def test_noalloc_more_near_ties_than_its_tie_records():
+    """More FP32 near-ties than the static array holds tie records for: the
+    queries past its KLR_ARGMIN_NOALLOC_TIE_RECORDS are re-decided in FP64
+    in place by the sweep instead of by the tie passes.  Both routes must
+    give what klr_argmin (whose context scratch lists every one of them)
+    gives, bit for bit.  The program's metrics do not depend on the block
+    shape, so every shape of a thread count has the same cycles and every
+    query is a near-tie."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import json
+    import os
+    import paper_1911_02373_gb300 as klr
+    with open(os.path.join(os.path.dirname(__file__), "golden", "chain_cases.json")) as f:
+        g = json.load(f)
+    k = g["kernels"]["B"]           # constant metrics
+    coef = torch.tensor(np.array(k["coef"], dtype=np.float32)[None]).cuda()
+    prog = klr.Context.program(coef, torch.tensor([k["regs"]], dtype=torch.int32).cuda(),
+                               torch.tensor([k["smem"]], dtype=torch.int32).cuda(), n_vars=3,
+                               degree=2, n_scale_log2=23, b_scale_log2=10,
+                               metric_lo=g["metric_lo"], metric_scale=g["metric_scale"])
+    n = klr.ARGMIN_NOALLOC_TIE_RECORDS + 7616
+    u = W.uniform(W.stream_key(44, 1), np.arange(n, dtype=np.uint64))
+    sizes = np.floor(np.exp2(10 + 12 * u)).astype(np.int64)
+    qo = torch.tensor([0, n], dtype=torch.int64).cuda()
+    qn = torch.tensor(sizes).cuda()
+    cfg = torch.tensor(klr.enumerate_configs(2)).cuda()
+    hw = klr.make_hw(g["hw"])
+    ctx = klr.Context(0)
+    out = (torch.full((n,), -7, dtype=torch.int32, device="cuda"),
+           torch.full((n,), -1.0, dtype=torch.float32, device="cuda"),
+           torch.full((n,), -1.0, dtype=torch.float32, device="cuda"),
+           torch.full((n,), -1, dtype=torch.int32, device="cuda"),
+           torch.full((n, 6), -1, dtype=torch.int32, device="cuda"))
+    klr.argmin_noalloc(prog, hw, cfg, qo, qn, out)
+    ref = ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=klr.F32)
+    torch.cuda.synchronize()
+    got = [t.cpu().numpy() for t in out]
+    want = [t.cpu().numpy() for t in ref]
+    tied = (want[3] & klr.Q_TIE_RESOLVED) != 0
+    assert tied.sum() > klr.ARGMIN_NOALLOC_TIE_RECORDS, tied.sum()
+    assert np.array_equal(got[3], want[3])
+    assert np.array_equal(got[0], want[0]) and np.all(got[0] >= 0)
+    assert np.array_equal(got[1].view(np.int32), want[1].view(np.int32))
+    assert np.array_equal(got[2].view(np.int32), want[2].view(np.int32))
+    assert np.array_equal(got[4], want[4])
+    ctx.close()
