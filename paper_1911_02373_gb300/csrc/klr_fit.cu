@@ -390,15 +390,17 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
 // accumulation.  Cells: 16 octaves of N, t = ns - log2 N in 0..15, times the
 // 51 block shapes of 32..1024 threads.  A fit with any sample outside that
 // set (another N or shape, a coordinate that is not a power of two, a
-// non-finite value) is marked with flag bit 4 and left to moments_fast_kernel,
-// which then runs over the marked fits only.
+// non-finite value) or with more than 65,535 samples (the cell counts are 16
+// bits) is marked with flag bit 4 and left to moments_fast_kernel, which then
+// runs over the marked fits only.
 // ---------------------------------------------------------------------------
 constexpr int kBinT = 16;                 // octaves of N per fit
 constexpr int kBinS = 51;                 // block shapes (b0, b1), 5 <= log2 b0 b1 <= 10
 constexpr int kBinC = kBinT * kBinS;      // cells
 static_assert(kBinS % 3 == 0, "the shape fold runs three partial sums");
 constexpr int kBinU = 4;                  // 32-sample tiles per load batch
-constexpr size_t kBinWarpSmem = (size_t)kBinC * (sizeof(float4) + sizeof(float));
+constexpr size_t kBinWarpSmem = (size_t)kBinC * (sizeof(float4) + sizeof(uint16_t));
+constexpr int64_t kBinMaxSamples = 65535;   // per fit: a cell count fits in 16 bits
 
 struct BinShapes {   // exponents (log2 b0, log2 b1), by thread count, then decreasing b0
     int8_t e[kBinS][2];
@@ -439,10 +441,10 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
     const int lane = lane_id();
     const unsigned full = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
-    // per warp: float4 (sum y hi, lo, sum y^2 hi, lo) and the count per cell;
-    // after the first fold the float4 region holds F as float2 [3][5][51]
+    // per warp: float4 (sum y hi, lo, sum y^2 hi, lo) and the 16-bit count per
+    // cell; after the first fold the float4 region holds F as float2 [3][5][51]
     float4* cv = reinterpret_cast<float4*>(smem_raw);
-    float* cn = reinterpret_cast<float*>(cv + kBinC);
+    uint16_t* cn = reinterpret_cast<uint16_t*>(cv + kBinC);
     float2* Fs = reinterpret_cast<float2*>(cv);
     const float* X = reinterpret_cast<const float*>(P.x);
     const float* Y = reinterpret_cast<const float*>(P.y);
@@ -451,10 +453,10 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
         const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
         for (int c = lane; c < kBinC; c += 32) {
             cv[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-            cn[c] = 0.f;
+            cn[c] = 0;
         }
         __syncwarp();
-        bool fallback = false;
+        bool fallback = s1 - s0 > kBinMaxSamples;
         // ---- stream: two batches of kBinU tiles in flight ----------------------
         float nb[kBinU][4] = {};
         auto load = [&](int64_t base, float (&b)[kBinU][4]) {
@@ -469,8 +471,8 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
                 }
             }
         };
-        load(s0, nb);
-        for (int64_t base = s0; base < s1; base += 32 * kBinU) {
+        if (!fallback) load(s0, nb);
+        for (int64_t base = s0; base < s1 && !fallback; base += 32 * kBinU) {
             float cb[kBinU][4];
 #pragma unroll
             for (int u = 0; u < kBinU; ++u)
@@ -520,7 +522,7 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
                         v.z = hs;
                         v.w = __fadd_rn(v.w, __fadd_rn(e, y2l));
                         cv[cell] = v;
-                        cn[cell] = __fadd_rn(cn[cell], 1.f);
+                        cn[cell] = (uint16_t)(cn[cell] + 1);
                     }
                     __syncwarp();
                 }
@@ -548,7 +550,7 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
                     const int c = t * kBinS + sh;
                     float vh, vl;
                     if (k == 0) {
-                        vh = cn[c];
+                        vh = (float)cn[c];
                         vl = 0.f;
                     } else {
                         const float4 v = cv[c];

@@ -143,6 +143,25 @@ def test_df32_binned_and_per_sample_fits_in_one_batch(klr, ctx):
     assert np.array_equal(coef, coef2) and np.array_equal(st, st2)
 
 
+def test_df32_fits_beyond_the_binned_sample_limit(klr, ctx):
+    """Fits with more samples than a 16-bit cell count holds (65,535) take
+    the per-sample moments kernel; a batch mixing them with binned fits."""
+    from types import SimpleNamespace
+    big = W.fit_batch(26, 1, 70000, noise=0.01, dtype=np.float32)
+    small = W.fit_batch(27, 1, 400, noise=0.01, dtype=np.float32)
+    pick = [0, 3]                          # two big fits, then the small batch
+    xs = [big.x[:, big.offsets[f]:big.offsets[f + 1]] for f in pick]
+    ys = [big.y[big.offsets[f]:big.offsets[f + 1]] for f in pick]
+    xs += [small.x[:, small.offsets[f]:small.offsets[f + 1]] for f in range(small.n_fits)]
+    ys += [small.y[small.offsets[f]:small.offsets[f + 1]] for f in range(small.n_fits)]
+    off = np.concatenate([[0], np.cumsum([len(v) for v in ys])]).astype(np.int64)
+    b = SimpleNamespace(offsets=off, x=np.concatenate(xs, axis=1).astype(np.float32),
+                        y=np.concatenate(ys).astype(np.float32), n_vars=3, degree=2,
+                        n_scale_log2=23, b_scale_log2=10)
+    coef, st, _ = gpu_fit(klr, ctx, b, klr.FIT_DF32, 0)
+    check(b, coef, st, "df32", 0)
+
+
 def test_degree3_refinement(klr, ctx):
     fb = W.fit_batch(24, 2, 1500, degree=3, n_hi_log2=30, dtype=np.float64)
     ref = rational.fit_batch(fb.offsets, fb.x, fb.y, 3, 3, 30, 10)
