@@ -1732,8 +1732,9 @@ __device__ __noinline__ void group_tri_solve(float2* wv, const float2* Lf, const
 // T - x I (all negative above the largest eigenvalue) give p'/p =
 // sum_i r_i'/r_i.  The eigenvector comes from two steps of inverse iteration
 // with x I - T (positive definite for x just above the root), solved by the
-// Thomas recurrence without pivoting.  s is normalised to unit length.
-template <int K>
+// Thomas recurrence without pivoting, when VEC.  s is normalised to unit
+// length.
+template <int K, bool VEC>
 __device__ float tridiag_top_eigen(const float (&a)[K], const float (&b)[K], float (&s)[K]) {
     float x = -FLT_MAX;
 #pragma unroll
@@ -1760,6 +1761,7 @@ __device__ float tridiag_top_eigen(const float (&a)[K], const float (&b)[K], flo
         x = xn;
         if (fabsf(dx) <= 1e-7f * fabsf(x)) break;
     }
+    if (!VEC) return x;
     const float xs = x + 2e-6f * fabsf(x) + FLT_MIN;   // above the root: x I - T is definite
 #pragma unroll
     for (int i = 0; i < K; ++i) s[i] = 1.f;
@@ -1918,75 +1920,73 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
         status |= KLR_FIT_SOLVE_FAILED;
     }
     dw theta{0.f, 0.f}, theta2{0.f, 0.f};
-    for (int i = q; i < u; i += Q) vv[i] = make_float2(1.0f + 0.0625f * (float)((i * 7) % 11), 0.f);
-    __syncwarp();
-    {
+    // the start vector (a fixed pattern), normalised
+    auto start_vector = [&]() {
+        for (int i = q; i < u; i += Q)
+            vv[i] = make_float2(1.0f + 0.0625f * (float)((i * 7) % 11), 0.f);
+        __syncwarp();
         const dw nn = gdot(vv, vv);
         const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(nn));
         for (int i = q; i < u; i += Q) vv[i] = st2(dw_mul(ld2(vv[i]), inv));
         __syncwarp();
-    }
-    // Phase 1: Lanczos on T = (Ghat - shift I)^-1 from v (every group runs the
-    // same kLanczosSteps solves).  Each new direction T q_j is orthogonalised
-    // against every earlier basis vector (modified Gram-Schmidt); the
-    // coefficients give the tridiagonal projection (alpha_j = q_j . T q_j,
-    // beta_j the norm of what remains).  Its largest eigenvalue mu gives the
-    // Ritz value theta = shift + 1/mu >= lambda_1 and its eigenvector the Ritz
-    // vector.  Per solve this converges like a Chebyshev-accelerated inverse
-    // iteration: about 0.12 per step at lambda_1/lambda_2 = 0.4 instead of 0.4.
+    };
+    start_vector();
+    // Phase 1: Lanczos on T = (Ghat - shift I)^-1 from the start vector, by
+    // its three-term recurrence (every group runs the same kLanczosSteps
+    // solves): alpha_j = q_j . T q_j, r = T q_j - alpha_j q_j - beta_{j-1}
+    // q_{j-1}, beta_j = |r|, q_{j+1} = r / beta_j.  The largest eigenvalue mu
+    // of the tridiagonal projection gives the Ritz value theta = shift + 1/mu
+    // >= lambda_1, which places the next shift.  Its accuracy grows like that
+    // of a Chebyshev-accelerated inverse iteration (about 0.12 per solve at
+    // lambda_1/lambda_2 = 0.4); over six steps the basis keeps its
+    // orthogonality in double-word arithmetic (a Ritz vector converges to
+    // about 1e-5, far from the square root of the rounding where Lanczos
+    // loses it), so no basis is stored and no reorthogonalisation is needed.
     {
-        float2* Qv = Dv + u;        // kLanczosSteps basis vectors of u
+        float2* pv = Dv + u;        // the previous Lanczos vector
         float la[kLanczosSteps], lb[kLanczosSteps];
-        for (int i = q; i < u; i += Q) Qv[i] = vv[i];
-        __syncwarp();
+        dw bprev{0.f, 0.f};
 #pragma unroll 1
         for (int j = 0; j < kLanczosSteps; ++j) {
-            for (int i = q; i < u; i += Q) wv[i] = Qv[j * u + i];
+            for (int i = q; i < u; i += Q) wv[i] = vv[i];
             __syncwarp();
             solve(ok);
-            dw aj{0.f, 0.f};
-#pragma unroll 1
-            for (int k = j; k >= 0; --k) {      // latest first: the large coefficients
-                const dw c = gdot(Qv + k * u, wv);
-                if (k == j) aj = c;
-                for (int i = q; i < u; i += Q)
-                    if (ok) wv[i] = st2(dw_sub(ld2(wv[i]), dw_mul(c, ld2(Qv[k * u + i]))));
-                __syncwarp();
+            const dw aj = gdot(vv, wv);
+            for (int i = q; i < u; i += Q) {
+                dw r = dw_sub(ld2(wv[i]), dw_mul(aj, ld2(vv[i])));
+                if (j > 0) r = dw_sub(r, dw_mul(bprev, ld2(pv[i])));
+                if (ok) wv[i] = st2(r);
             }
+            __syncwarp();
             const dw bj = dw_sqrt(gdot(wv, wv));
             la[j] = aj.h + aj.l;
             lb[j] = bj.h + bj.l;
             if (j + 1 < kLanczosSteps) {
                 const dw inv = dw_div(dw{1.f, 0.f}, bj.h > 0.f ? bj : dw{FLT_MIN, 0.f});
-                for (int i = q; i < u; i += Q)
-                    if (ok) Qv[(j + 1) * u + i] = st2(dw_mul(ld2(wv[i]), inv));
+                for (int i = q; i < u; i += Q) {
+                    if (ok) {
+                        pv[i] = vv[i];
+                        vv[i] = st2(dw_mul(ld2(wv[i]), inv));
+                    }
+                }
                 __syncwarp();
             }
+            bprev = bj;
         }
         float sv[kLanczosSteps];
-        const float mu = tridiag_top_eigen<kLanczosSteps>(la, lb, sv);
-        // Ritz vector sum_j s_j q_j, normalised
-        for (int i = q; i < u; i += Q) {
-            dw_acc y;
-            y.init(dw{0.f, 0.f});
-#pragma unroll
-            for (int j = 0; j < kLanczosSteps; ++j) y.add_prod(ld2(Qv[j * u + i]), dw{sv[j], 0.f});
-            if (ok) wv[i] = st2(y.value());
-        }
-        __syncwarp();
-        const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(gdot(wv, wv)));
-        for (int i = q; i < u; i += Q)
-            if (ok) vv[i] = st2(dw_mul(ld2(wv[i]), inv));
-        __syncwarp();
+        const float mu = tridiag_top_eigen<kLanczosSteps, false>(la, lb, sv);
         if (ok) theta = dw_add(shift, dw_div(dw{1.f, 0.f}, dw{mu > 0.f ? mu : FLT_MIN, 0.f}));
     }
+    // the iterations below start again from the start vector
+    start_vector();
     bool active = ok;
     float dv2 = 1.f, prev = 1.f;
     // noisy fits: rounds of re-factoring on a ladder of shifts below theta
     // (the Ritz value is accurate to far better than its first rung)
     bool noisy = ok && dw_gt(theta, null_level);
-    // fits whose lambda_1 is at the rounding level: polish v at the first
-    // shift (the next eigenvalue is far above, a step gains lambda_2 / jitter)
+    // fits whose lambda_1 is at the rounding level: inverse iteration at the
+    // first shift (the next eigenvalue is far above, a step gains about
+    // lambda_2 / jitter)
     {
         bool act = active && !noisy;
         for (int it = 0; it < 4 && __any_sync(full, act); ++it) {
@@ -2390,8 +2390,8 @@ klr_status launch_solve_group_dw_q(const FitParams& P, cudaStream_t stream) {
         return KLR_ENOTSUP;
     }
     FitParams Q_ = P;
-    // L, 1/L_jj, v, w, D and the Lanczos basis
-    int stride = P.u * (P.u + 1) / 2 + (4 + kLanczosSteps) * P.u;
+    // L, 1/L_jj, v, w, D and the previous Lanczos vector
+    int stride = P.u * (P.u + 1) / 2 + 5 * P.u;
     if (stride % 2 == 0) ++stride;          // spread the groups over the banks
     Q_.ld = stride;
     const size_t smem = sizeof(float2) * (size_t)stride * GPW;
