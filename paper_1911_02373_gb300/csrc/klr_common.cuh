@@ -206,6 +206,18 @@ __device__ __forceinline__ dw dw_from_double(double v) {
     return {h, (float)(v - (double)h)};
 }
 __device__ __forceinline__ double dw_to_double(dw x) { return (double)x.h + (double)x.l; }
+// 1/sqrt(x) for x > 0: the FP32 estimate r0, then one correction from the
+// residual e = 1 - x r0^2, formed from exact products: 1/sqrt(x) =
+// r0 (1 - e)^(-1/2) = r0 (1 + e/2 + 3e^2/8 + O(e^3)) (binomial series; |e| is
+// about 2^-22, so the truncation is far below the double-word rounding)
+__device__ __forceinline__ dw dw_rsqrt(dw x) {
+    const float r0 = rsqrtf(x.h);
+    const dw t = dw_mul_f(x, r0);
+    const dw w = dw_mul_f(t, r0);
+    const float e = __fsub_rn(__fsub_rn(1.f, w.h), w.l);
+    const float c = __fmul_rn(e, fmaf(0.375f, e, 0.5f));
+    return dw_fast2sum(r0, __fmul_rn(r0, c));
+}
 // x > y, x and y normalised
 __device__ __forceinline__ bool dw_gt(dw x, dw y) { return x.h > y.h || (x.h == y.h && x.l > y.l); }
 

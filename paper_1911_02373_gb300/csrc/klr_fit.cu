@@ -545,7 +545,7 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
 #pragma unroll
             for (int a = 0; a < 5; ++a) fh[r][a] = fl[r][a] = 0.f;
             if (it < 3 * kBinS) {
-#pragma unroll 1
+#pragma unroll 2
                 for (int t = 0; t < kBinT; ++t) {
                     const int c = t * kBinS + sh;
                     float vh, vl;
@@ -1636,7 +1636,7 @@ __device__ __noinline__ bool group_cholesky(float2* Lf, float2* rinv, const floa
         }
         const dw sjj = dw_sub(dw_sub(gh(j, j), shift), sum);
         good = good && (sjj.h > 0.f);
-        const dw r = good ? dw_div(dw{1.f, 0.f}, dw_sqrt(sjj)) : dw{1.f, 0.f};
+        const dw r = good ? dw_rsqrt(sjj) : dw{1.f, 0.f};
         if (good && q == 0) rinv[j] = st2(r);
         for (int i = j + 1 + ((q - (j + 1) % Q) + Q) % Q; i < u; i += Q) {
             dw_acc t0, t1;
@@ -1881,7 +1881,7 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
         __syncwarp();
         solve(write);
         const dw vw = gdot(vv, wv), ww = gdot(wv, wv);
-        const dw inv = dw_div(dw{1.f, 0.f}, dw_sqrt(ww));
+        const dw inv = dw_rsqrt(ww);
         float part = 0.f;
         for (int i = q; i < u; i += Q) {
             const dw nvi = dw_mul(ld2(wv[i]), inv);
@@ -1958,11 +1958,12 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
                 if (ok) wv[i] = st2(r);
             }
             __syncwarp();
-            const dw bj = dw_sqrt(gdot(wv, wv));
+            const dw bb = gdot(wv, wv);
+            const dw inv = dw_rsqrt(bb.h > 0.f ? bb : dw{FLT_MIN, 0.f});
+            const dw bj = dw_mul(bb, inv);
             la[j] = aj.h + aj.l;
             lb[j] = bj.h + bj.l;
             if (j + 1 < kLanczosSteps) {
-                const dw inv = dw_div(dw{1.f, 0.f}, bj.h > 0.f ? bj : dw{FLT_MIN, 0.f});
                 for (int i = q; i < u; i += Q) {
                     if (ok) {
                         pv[i] = vv[i];
