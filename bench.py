@@ -2,7 +2,8 @@
 
 A step is one pass of the whole path over the batched workload: fit all
 10,000 kernels x 8 metrics (80,000 rational fits, 50-2000 noisy samples each,
-about 82 M samples, 1.31 GB of FP32 samples in HBM), then evaluate the fitted
+about 82 M samples: 574 MB in HBM as uint8 base-2 logarithms of the
+power-of-two coordinates and FP32 values), then evaluate the fitted
 rational program for 64 data sizes x 51 block shapes per kernel and choose the
 argmin (640,000 queries, 32.6 M evaluations).  The metric is argmin queries
 per second of whole steps.
@@ -31,12 +32,12 @@ import numpy as np  # noqa: E402
 WORKLOAD = dict(name="batched_fit_eval_fp32", kernels=10000, metrics=8, counts=(50, 2000),
                 noise=0.01, degree=2, n_vars=3, n_hi_log2=23, sizes_per_kernel=64, n_cfg=51)
 METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
-# DRAM bytes (read + write) per sample of the binned moments kernel, from one
-# ncu capture of the 1,000-kernel copy of this workload (dram__bytes_read.sum +
-# dram__bytes_write.sum = 136.53 MB over 8,240,324 samples); the traffic of a
-# full launch scales with the sample count.
-# Summary: profiles/moments_binned_kernel_batched_1000k.md
-MOMENTS_DRAM_BYTES_PER_SAMPLE = 16.569
+# DRAM bytes (read + write) per sample of the binned moments kernel on this
+# workload's KLR_EXP8 samples, from one ncu capture of its 1,000-kernel copy
+# (dram__bytes_read.sum + dram__bytes_write.sum over its samples); the
+# traffic of a full launch scales with the sample count.  None: not captured
+# since the kernel last changed.
+MOMENTS_DRAM_BYTES_PER_SAMPLE = None
 
 
 def parse():
@@ -371,7 +372,12 @@ def run_klr(args, cb_kept=None):
     ctx = klr.Context(local)
     ctx.reserve(n_fits, n_q)
     off_h = torch.from_numpy(fb.offsets).pin_memory()
-    x_h = torch.from_numpy(np.ascontiguousarray(fb.x)).pin_memory()
+    # the coordinates are powers of two: uint8 base-2 logarithms (KLR_EXP8),
+    # 7 bytes per sample with the FP32 values instead of 16
+    x8 = np.round(np.log2(fb.x)).astype(np.uint8)
+    assert np.array_equal(np.ldexp(np.float32(1), x8.astype(np.int32)), fb.x)
+    x_h = torch.from_numpy(x8).pin_memory()
+    x32_h = torch.from_numpy(np.ascontiguousarray(fb.x)).pin_memory()
     y_h = torch.from_numpy(fb.y).pin_memory()
     qo_h = torch.from_numpy(q.offsets).pin_memory()
     qn_h = torch.from_numpy(q.sizes).pin_memory()
@@ -552,6 +558,41 @@ def run_klr(args, cb_kept=None):
     e2e_ms, e2e_units = whole_job(e0.elapsed_time(e1) / E, n_q, dist, dev)
     h2d_b = sum(t.numel() * t.element_size() for t in (off_h, x_h, y_h, qo_h, qn_h))
     d2h_b = best_h.numel() * 4 + cyc_h.numel() * 4
+    # the same with FP32 coordinates (16 bytes per sample) for comparison
+    del bufs
+    x32 = torch.empty(x32_h.shape, dtype=torch.float32, device=dev)
+    x32b = torch.empty_like(x32)
+    bufs = [(off, x32, y, qo, qn),
+            (torch.empty_like(off), x32b, torch.empty_like(y), torch.empty_like(qo),
+             torch.empty_like(qn))]
+    hosts = (off_h, x32_h, y_h, qo_h, qn_h)
+    pieces = []
+    for j, (d_, h_) in enumerate(zip(bufs[0], hosts)):
+        n = h_.numel()
+        cuts = np.linspace(0, n, n_cs + 1).astype(np.int64) if n > (1 << 20) else np.array([0, n])
+        for c in range(len(cuts) - 1):
+            pieces.append((j, int(cuts[c]), int(cuts[c + 1])))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for cs in copy_streams:
+        cs.wait_event(e0)
+    h2d(0)
+    for i in range(E):
+        if i + 1 < E:
+            h2d(i + 1)
+        for ev_ in h2d_done[i % 2]:
+            stream.wait_event(ev_)
+        o_, x_, y_, qo_, qn_ = bufs[i % 2]
+        fit(x_, y_, o_)
+        choose(qo_, qn_)
+        used[i % 2].record(stream)
+        best_h.copy_(best, non_blocking=True)
+        cyc_h.copy_(cyc, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e32_ms, _ = whole_job(e0.elapsed_time(e1) / E, n_q, dist, dev)
+    h2d32_b = sum(t.numel() * t.element_size() for t in hosts)
+    del bufs, x32, x32b
 
     sur = None
     if rank == 0 and args.line_sur_kernels > 0:
@@ -569,12 +610,13 @@ def run_klr(args, cb_kept=None):
     sm_mhz = (ck or {}).get("sm_max_mhz") or 2070.0
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s (FMA = 2 flop)
     # stage rooflines from the per-unit work above
-    mom_bytes = n_samples * 16 + (n_fits + 1) * 8 + n_fits * (3 * 35 * 8 + 4)
+    mom_bytes = n_samples * 7 + (n_fits + 1) * 8 + n_fits * (3 * 35 * 8 + 4)
     t_mom, t_sol, t_arg = (part_ms[k] * 1e-3 for k in names)
     evals = n_q * wl["n_cfg"]
     moments_rf = {"bound": "hbm", "achieved": mom_bytes / t_mom / 1e9, "peak": hbm_peak,
                   "unit": "GB/s", "frac": mom_bytes / t_mom / 1e9 / hbm_peak,
-                  "traffic": MOMENTS_DRAM_BYTES_PER_SAMPLE * n_samples,
+                  "traffic": (MOMENTS_DRAM_BYTES_PER_SAMPLE * n_samples
+                              if MOMENTS_DRAM_BYTES_PER_SAMPLE else None),
                   "kernel": "moments_binned_kernel (+ moments_fast_kernel over left fits)",
                   "algorithmic_bytes": mom_bytes,
                   "flop_tflops": FLOP_PER_SAMPLE * n_samples / t_mom / 1e12,
@@ -611,7 +653,9 @@ def run_klr(args, cb_kept=None):
         "config": {"workload": WORKLOAD["name"], "kernels": wl["kernels"], "fits": n_fits,
                    "samples": n_samples, "queries": n_q, "configs": wl["n_cfg"],
                    "evals": evals, "fit_precision": "df32", "refine_iters": 0,
-                   "l2": "inputs larger than L2 (1.31 GB of samples per step)",
+                   "sample_format": ("uint8 base-2 logarithms of (N, b0, b1) + FP32 values "
+                                     "(KLR_EXP8, 7 B per sample)"),
+                   "l2": "inputs larger than L2 (574 MB of samples per step)",
                    "launch": ("one CUDA graph per step (fit moments, fit solve, argmin)"
                               if graph is not None else "eager"),
                    "autotuned": {k: {"choice": v[0], "ms": v[1]} for k, v in tuned.items()},
@@ -628,6 +672,9 @@ def run_klr(args, cb_kept=None):
                   "note": "klr_eval FP32 cycles table of the fitted program, 4 B per evaluation"},
         "e2e": {"value": e2e_units / (e2e_ms * 1e-3), "unit": "queries/s",
                 "h2d_bytes_per_step": int(h2d_b), "d2h_bytes_per_step": int(d2h_b)},
+        "e2e_fp32_samples": {"value": e2e_units / (e2e32_ms * 1e-3), "unit": "queries/s",
+                             "h2d_bytes_per_step": int(h2d32_b),
+                             "d2h_bytes_per_step": int(d2h_b)},
         "gpu_launches": sum(LAUNCHES_PER_STEP.values()) * K,
         "clocks": ck,
         "fit_status_nonzero": int(np.count_nonzero(fit_status & ~8)),

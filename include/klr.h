@@ -54,6 +54,11 @@ typedef int32_t klr_status;
 /* ---- element types ----------------------------------------------------- */
 #define KLR_F32 0
 #define KLR_F64 1
+/* Sample coordinates as 8-bit base-2 logarithms (klr_fit_batch.sample_dtype):
+ * x holds uint8 e, the coordinate is 2^e exactly (e > 127 is not finite), and
+ * y is FP32.  7 bytes per sample at n_vars = 3 instead of 16 for FP32: the
+ * paper's data sizes and block dimensions are powers of two. */
+#define KLR_EXP8 2
 
 /* ---- fit precision modes (how the Gram matrix is accumulated) ------------
  * The Gram matrix G = A^T A of the design matrix A = [Phi | -y Phi] is built
@@ -142,7 +147,10 @@ typedef struct klr_fit_batch {
     int32_t degree;        /* total degree, 1..3                             */
     int32_t n_scale_log2;  /* N is scaled by 2^-n_scale_log2                  */
     int32_t b_scale_log2;  /* block dimensions are scaled by 2^-b_scale_log2  */
-    int32_t sample_dtype;  /* KLR_F32 or KLR_F64: element type of x and y    */
+    int32_t sample_dtype;  /* KLR_F32 or KLR_F64: element type of x and y;
+                            * KLR_EXP8: x uint8 log2, y FP32 (supported with
+                            * KLR_FIT_DF32, the degree-2 basis in (N, b0, b1)
+                            * and no refinement; else KLR_ENOTSUP)          */
     const int64_t* offsets;/* device, n_fits + 1, non-decreasing, >= 0        */
     const void* x;         /* device, n_vars rows, row stride x_stride        */
     int64_t x_stride;      /* elements between rows of x, >= offsets[n_fits]  */

@@ -76,9 +76,33 @@ struct FitParams {
     int32_t* flags;// scratch: n_fits, bit 0 non-finite sample, bit 1 inexact DF32,
                    // bit 2 left to the per-sample moments kernel by the binned one
     int fallback_only;  // moments_fast_kernel: only the fits with flag bit 2
+    int x_exp8;    // x holds uint8 base-2 logarithms (KLR_EXP8)
     uint8_t exps[kMaxMoments][kMaxVars];
     uint8_t pair[kMaxBasis][kMaxBasis];
 };
+
+// coordinate of a KLR_EXP8 sample: 2^e exactly, +inf above 127
+__device__ __forceinline__ float exp8_value(uint8_t e) {
+    return e <= 127 ? __int_as_float((int)(e + 127u) << 23) : __int_as_float(0x7f800000);
+}
+
+// Coordinate v of sample s in two steps, so that a prefetched load is not
+// waited for until its value is used: load_coord gives the raw element (a
+// KLR_EXP8 byte carried in the bits of a float), coord_value the coordinate.
+template <typename TS, bool E8>
+__device__ __forceinline__ TS load_coord(const FitParams& P, int v, int64_t s) {
+    if constexpr (E8) {
+        static_assert(sizeof(TS) == 4, "KLR_EXP8 samples come with FP32 values");
+        return __uint_as_float((unsigned)reinterpret_cast<const uint8_t*>(P.x)[(int64_t)v * P.x_stride + s]);
+    } else {
+        return reinterpret_cast<const TS*>(P.x)[(int64_t)v * P.x_stride + s];
+    }
+}
+template <typename TS, bool E8>
+__device__ __forceinline__ TS coord_value(TS raw) {
+    if constexpr (E8) return exp8_value((uint8_t)__float_as_uint(raw));
+    else return raw;
+}
 
 __device__ __forceinline__ bool is_pow2_positive(float v) {
     unsigned b = __float_as_uint(v);
@@ -214,7 +238,7 @@ struct MonoTable {
 // moments_kernel specialised on the basis: the staging lane computes all
 // n_mom monomials of its sample once (compile-time exponents, registers
 // only), and each accumulating lane reads its monomial with one load.
-template <typename TS, int ACC, int NV, int D2, int MG, int MAXT>
+template <typename TS, int ACC, int NV, int D2, int MG, int MAXT, bool E8 = false>
 __global__ void __launch_bounds__(128, 4)
 moments_fast_kernel(const __grid_constant__ FitParams P) {
     constexpr MonoTable<NV, D2> tab{};
@@ -231,7 +255,6 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
     if (P.fallback_only && (P.flags[f] & 4) == 0) return;   // done by the binned kernel
     TC* stage = reinterpret_cast<TC*>(smem_raw + (size_t)wib * P.warp_smem);
     const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
-    const TS* X = reinterpret_cast<const TS*>(P.x);
     const TS* Y = reinterpret_cast<const TS*>(P.y);
     const TC sN = (TC)ldexpf(1.0f, -P.n_scale_log2), sB = (TC)ldexpf(1.0f, -P.b_scale_log2);
     const int mg = lane % MG, sg = lane / MG;
@@ -248,7 +271,7 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
     for (int v = 0; v < NV; ++v) cx[v] = nx[v] = TS(1);
     if (s0 + lane < s1) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) cx[v] = X[(int64_t)v * P.x_stride + s0 + lane];
+        for (int v = 0; v < NV; ++v) cx[v] = load_coord<TS, E8>(P, v, s0 + lane);
         cy = Y[s0 + lane];
     }
     for (int64_t base = s0; base < s1; base += 32) {
@@ -256,14 +279,14 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
         const int64_t sn = s + 32;
         if (sn < s1) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) nx[v] = X[(int64_t)v * P.x_stride + sn];
+            for (int v = 0; v < NV; ++v) nx[v] = load_coord<TS, E8>(P, v, sn);
             ny = Y[sn];
         }
         if (s < s1) {
             TC pw[NV][D2 + 1];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const TS raw = cx[v];
+                const TS raw = coord_value<TS, E8>(cx[v]);
                 bad |= !isfinite(raw);
                 if constexpr (ACC == ACC_DF32) inexact |= !is_pow2_positive(raw);
                 const TC xv = (TC)raw * (v == 0 ? sN : sB);
@@ -435,6 +458,7 @@ __device__ __forceinline__ void dw_acc_scaled(float& h, float& l, float vh, floa
     l = __fadd_rn(l, __fadd_rn(e, __fmul_rn(vl, p)));
 }
 
+template <bool E8>
 __global__ void __launch_bounds__(32)
 moments_binned_kernel(const __grid_constant__ FitParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -446,7 +470,6 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
     float4* cv = reinterpret_cast<float4*>(smem_raw);
     uint16_t* cn = reinterpret_cast<uint16_t*>(cv + kBinC);
     float2* Fs = reinterpret_cast<float2*>(cv);
-    const float* X = reinterpret_cast<const float*>(P.x);
     const float* Y = reinterpret_cast<const float*>(P.y);
     const int ns = P.n_scale_log2, bs = P.b_scale_log2;
     for (int f = blockIdx.x; f < P.n_fits; f += gridDim.x) {
@@ -464,9 +487,9 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
             for (int u = 0; u < kBinU; ++u) {
                 const int64_t s = base + u * 32 + lane;
                 if (s < s1) {
-                    b[u][0] = X[s];
-                    b[u][1] = X[P.x_stride + s];
-                    b[u][2] = X[2 * P.x_stride + s];
+                    b[u][0] = load_coord<float, E8>(P, 0, s);
+                    b[u][1] = load_coord<float, E8>(P, 1, s);
+                    b[u][2] = load_coord<float, E8>(P, 2, s);
                     b[u][3] = Y[s];
                 }
             }
@@ -475,9 +498,11 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
         for (int64_t base = s0; base < s1 && !fallback; base += 32 * kBinU) {
             float cb[kBinU][4];
 #pragma unroll
-            for (int u = 0; u < kBinU; ++u)
+            for (int u = 0; u < kBinU; ++u) {
 #pragma unroll
-                for (int v = 0; v < 4; ++v) cb[u][v] = nb[u][v];
+                for (int v = 0; v < 3; ++v) cb[u][v] = coord_value<float, E8>(nb[u][v]);
+                cb[u][3] = nb[u][3];
+            }
             if (base + 32 * kBinU < s1) load(base + 32 * kBinU, nb);
 #pragma unroll
             for (int u = 0; u < kBinU; ++u) {
@@ -2337,21 +2362,44 @@ klr_status launch_moments(const FitParams& P, int n_mom, int rec, int wpb, cudaS
 // DF32 degree-2 fits in (N, b0, b1): the binned moments kernel on a
 // persistent grid (one warp per fit at a time), then the per-sample kernel
 // over the fits it left (flag bit 4).
-klr_status launch_moments_binned(const FitParams& P, int n_sm, int rec, int wpb,
-                                 cudaStream_t stream) {
+// moments_fast_kernel for the degree-2 basis in (N, b0, b1), DF32, FP32 or
+// KLR_EXP8 samples (the binned path's per-sample kernel)
+template <bool E8>
+klr_status launch_moments_fast_e8(const FitParams& P, int wpb, cudaStream_t stream) {
+    auto kern = moments_fast_kernel<float, ACC_DF32, 3, 4, 4, 9, E8>;
+    FitParams R = P;
+    const int rec_ = 35 + 3 + ((35 + 3) % 2 == 0 ? 1 : 0);
+    R.warp_smem = (int)((32 * rec_ * 4 + 15) & ~(size_t)15);
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        R.warp_smem * wpb));
+    kern<<<(P.n_fits + wpb - 1) / wpb, wpb * 32, (size_t)R.warp_smem * wpb, stream>>>(R);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
+}
+
+template <bool E8>
+klr_status launch_moments_binned_t(const FitParams& P, int n_sm, int wpb, cudaStream_t stream) {
     const size_t smem = kBinWarpSmem;
-    KLR_CHECK_CUDA(cudaFuncSetAttribute(moments_binned_kernel,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = moments_binned_kernel<E8>;
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
     int per_sm = 0;
-    KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, moments_binned_kernel,
-                                                                 32, smem));
+    KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32, smem));
     const int64_t slots = (int64_t)std::max(1, per_sm) * std::max(1, n_sm);
     const int grid = (int)std::min<int64_t>(P.n_fits, slots);
-    moments_binned_kernel<<<grid, 32, smem, stream>>>(P);
+    kern<<<grid, 32, smem, stream>>>(P);
     KLR_CHECK_CUDA(cudaGetLastError());
+    // the per-sample kernel over the fits left (flag bit 4)
     FitParams Q = P;
     Q.fallback_only = 1;
-    return launch_moments<float, ACC_DF32>(Q, 35, rec, wpb, stream);
+    return launch_moments_fast_e8<E8>(Q, wpb, stream);
+}
+
+klr_status launch_moments_binned(const FitParams& P, int n_sm, int rec, int wpb,
+                                 cudaStream_t stream) {
+    (void)rec;
+    return P.x_exp8 ? launch_moments_binned_t<true>(P, n_sm, wpb, stream)
+                    : launch_moments_binned_t<false>(P, n_sm, wpb, stream);
 }
 
 template <typename TS>
@@ -2537,8 +2585,8 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     const bool box = b->var_degree[0] > 0;
     KLR_REQUIRE(box || (b->degree >= 1 && b->degree <= 3), "klr_fit: degree %d not in 1..3",
                 b->degree);
-    KLR_REQUIRE(b->sample_dtype == KLR_F32 || b->sample_dtype == KLR_F64,
-                "klr_fit: bad sample_dtype");
+    KLR_REQUIRE(b->sample_dtype == KLR_F32 || b->sample_dtype == KLR_F64 ||
+                b->sample_dtype == KLR_EXP8, "klr_fit: bad sample_dtype");
     KLR_REQUIRE(!(stages & STAGE_SOLVE) || coef_dtype == KLR_F32 || coef_dtype == KLR_F64,
                 "klr_fit: bad coef_dtype");
     KLR_REQUIRE(b->precision >= KLR_FIT_FP64 && b->precision <= KLR_FIT_BF16,
@@ -2552,7 +2600,15 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
                 "klr_fit: NULL coef_out or fit_status");
     KLR_REQUIRE(b->x_stride >= 0, "klr_fit: x_stride < 0");
     if (b->precision == KLR_FIT_DF32)
-        KLR_REQUIRE(b->sample_dtype == KLR_F32, "klr_fit: DF32 needs KLR_F32 samples");
+        KLR_REQUIRE(b->sample_dtype == KLR_F32 || b->sample_dtype == KLR_EXP8,
+                    "klr_fit: DF32 needs KLR_F32 or KLR_EXP8 samples");
+    if (b->sample_dtype == KLR_EXP8 &&
+        !(b->precision == KLR_FIT_DF32 && b->n_vars == 3 && !box && b->degree == 2 &&
+          b->refine_iters == 0)) {
+        set_error("klr_fit: KLR_EXP8 samples need KLR_FIT_DF32, the degree-2 basis in "
+                  "(N, b0, b1) and no refinement");
+        return KLR_ENOTSUP;
+    }
     Basis basis;
     KLR_REQUIRE(make_basis(b->n_vars, b->degree, b->var_degree, &basis),
                 "klr_fit: no basis (per-variable bounds must be 0..3, at most %d monomials)",
@@ -2594,6 +2650,7 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     P.diag = fit_diag;
     P.refine = b->refine_iters;
     P.fallback_only = 0;
+    P.x_exp8 = b->sample_dtype == KLR_EXP8;
     P.ld = (u % 2) ? u : u + 1;
     memcpy(P.exps, basis.exps, sizeof(P.exps));
     memcpy(P.pair, basis.pair, sizeof(P.pair));
@@ -2661,6 +2718,8 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
             if (!box && b->n_vars == 3 && b->degree == 2 && b->b_scale_log2 >= 5 &&
                 b->b_scale_log2 <= 15)
                 st = launch_moments_binned(P, c->n_sm, rec, wpb, stream);
+            else if (P.x_exp8)   // (KLR_EXP8 is only accepted with this basis)
+                st = launch_moments_fast_e8<true>(P, wpb, stream);
             else
                 st = launch_moments<float, ACC_DF32>(P, basis.n_mom, rec, wpb, stream);
             break;

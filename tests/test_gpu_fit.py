@@ -162,6 +162,53 @@ def test_df32_fits_beyond_the_binned_sample_limit(klr, ctx):
     check(b, coef, st, "df32", 0)
 
 
+def test_exp8_samples_equal_float32_samples(klr, ctx):
+    """KLR_EXP8 (uint8 base-2 logarithms of the coordinates) carries the same
+    power-of-two samples in 7 bytes instead of 16: every output equals the
+    FP32-input fit's bit for bit, the per-sample route included (a fit with
+    an N outside the 16 binned octaves, one with a coordinate of 2^200, which
+    is not finite, and an empty one)."""
+    fb = W.fit_batch(28, 3, (50, 900), noise=0.01, dtype=np.float32)
+    e = np.round(np.log2(fb.x.astype(np.float64))).astype(np.int64)
+    assert np.array_equal(np.ldexp(1.0, e), fb.x)
+    e[0, fb.offsets[2]] = 6                       # N = 64: per-sample route
+    e[1, fb.offsets[5] + 1] = 200                 # 2^200: not finite
+    x8 = e.astype(np.uint8)
+    x32 = np.where(e <= 127, np.ldexp(1.0, np.minimum(e, 127)), np.inf).astype(np.float32)
+    off = fb.offsets.copy()
+    off[9:] = off[9:] - (off[9] - off[8])         # fit 8 empty
+    n = int(off[-1])
+    keep = np.r_[0:fb.offsets[8], fb.offsets[9]:fb.offsets[-1]]
+    x8, x32, y = x8[:, keep], x32[:, keep], fb.y[keep]
+    assert x8.shape[1] == n
+    t = lambda a: torch.tensor(np.ascontiguousarray(a)).cuda()
+    kw = dict(n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10, precision=klr.FIT_DF32,
+              refine_iters=0, coef_dtype=klr.F32)
+    c8, s8, d8 = ctx.fit(t(off), t(x8), t(y), **kw)
+    c32, s32, d32 = ctx.fit(t(off), t(x32), t(y), **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(c8, c32) and torch.equal(s8, s32) and torch.equal(d8, d32)
+    st = s8.cpu().numpy()
+    assert st[5] == rational.FIT_NONFINITE and st[8] == rational.FIT_EMPTY
+    # other fits against the oracle on the decoded FP32 samples
+    from types import SimpleNamespace
+    b = SimpleNamespace(offsets=off, x=x32, y=y, n_vars=3, degree=2, n_scale_log2=23,
+                        b_scale_log2=10)
+    check(b, c8.cpu().numpy().astype(np.float64), st, "df32", 0)
+    # a block-size scale outside the binned kernel's range: the per-sample
+    # kernel reads the same bytes (both scalings are exact)
+    kw11 = dict(kw, b_scale_log2=16)
+    c8b, s8b, _ = ctx.fit(t(off), t(x8), t(y), **kw11)
+    c32b, s32b, _ = ctx.fit(t(off), t(x32), t(y), **kw11)
+    torch.cuda.synchronize()
+    assert torch.equal(c8b, c32b) and torch.equal(s8b, s32b)
+    # unsupported combinations are refused before anything runs
+    for bad in (dict(kw, precision=klr.FIT_FP64), dict(kw, refine_iters=1), dict(kw, degree=3)):
+        with pytest.raises(klr.KlrError) as e_:
+            ctx.fit(t(off), t(x8), t(y), **bad)
+        assert e_.value.status == klr.ENOTSUP
+
+
 def test_degree3_refinement(klr, ctx):
     fb = W.fit_batch(24, 2, 1500, degree=3, n_hi_log2=30, dtype=np.float64)
     ref = rational.fit_batch(fb.offsets, fb.x, fb.y, 3, 3, 30, 10)
