@@ -33,11 +33,11 @@ WORKLOAD = dict(name="batched_fit_eval_fp32", kernels=10000, metrics=8, counts=(
                 noise=0.01, degree=2, n_vars=3, n_hi_log2=23, sizes_per_kernel=64, n_cfg=51)
 METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
 # DRAM bytes (read + write) per sample of the binned moments kernel on this
-# workload's KLR_EXP8 samples, from one ncu capture of its 1,000-kernel copy
-# (dram__bytes_read.sum + dram__bytes_write.sum over its samples); the
-# traffic of a full launch scales with the sample count.  None: not captured
-# since the kernel last changed.
-MOMENTS_DRAM_BYTES_PER_SAMPLE = None
+# workload's KLR_EXP8 samples, from one ncu capture of the kernel on its
+# 1,000-kernel copy (dram__bytes_read.sum + dram__bytes_write.sum = 57.78 +
+# 0.38 MB over 8,240,324 samples); the traffic of a full launch scales with
+# the sample count.  Summary: profiles/moments_binned_kernel_batched_1000k.md
+MOMENTS_DRAM_BYTES_PER_SAMPLE = 7.058
 
 
 def parse():
@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="built-in launch shapes instead of the autotuned ones")
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "sweep3d", "surrogate", "precision", "history"],
+                    choices=["batched", "sweep3d", "surrogate", "precision", "history",
+                             "fit_formats"],
                     help="batched: fit + argmin (default metric); sweep3d: 3D evaluator sweep")
     ap.add_argument("--sweep-kernels", type=int, default=100000)
     ap.add_argument("--sweep-check-kernels", type=int, default=1000,
@@ -613,16 +614,21 @@ def run_klr(args, cb_kept=None):
     mom_bytes = n_samples * 7 + (n_fits + 1) * 8 + n_fits * (3 * 35 * 8 + 4)
     t_mom, t_sol, t_arg = (part_ms[k] * 1e-3 for k in names)
     evals = n_q * wl["n_cfg"]
-    moments_rf = {"bound": "hbm", "achieved": mom_bytes / t_mom / 1e9, "peak": hbm_peak,
-                  "unit": "GB/s", "frac": mom_bytes / t_mom / 1e9 / hbm_peak,
+    # the fit's contraction is u^2 = 420 flop per 7-byte sample (60 flop/B,
+    # above the FP32 ridge of ~12 flop/B): its roofline is the FP32 FMA peak;
+    # the HBM fraction of its algorithmic bytes is reported beside it
+    mom_flops = FLOP_PER_SAMPLE * n_samples / t_mom / 1e12
+    moments_rf = {"bound": "alu", "achieved": mom_flops, "peak": fp32_peak,
+                  "unit": "TFLOP/s", "frac": mom_flops / fp32_peak,
                   "traffic": (MOMENTS_DRAM_BYTES_PER_SAMPLE * n_samples
                               if MOMENTS_DRAM_BYTES_PER_SAMPLE else None),
                   "kernel": "moments_binned_kernel (+ moments_fast_kernel over left fits)",
                   "algorithmic_bytes": mom_bytes,
-                  "flop_tflops": FLOP_PER_SAMPLE * n_samples / t_mom / 1e12,
-                  "flop_peak_tflops": fp32_peak,
-                  "flop_frac": FLOP_PER_SAMPLE * n_samples / t_mom / 1e12 / fp32_peak,
-                  "peak_source": f"hbm {peak_src}; FP32 FMA lanes x {n_sm} SMs x max clock"}
+                  "hbm_gbs": mom_bytes / t_mom / 1e9, "hbm_peak_gbs": hbm_peak,
+                  "hbm_frac": mom_bytes / t_mom / 1e9 / hbm_peak,
+                  "arithmetic_intensity_flop_per_byte": FLOP_PER_SAMPLE * n_samples / mom_bytes,
+                  "peak_source": (f"FP32 FMA lanes x {n_sm} SMs x 2 flop x max clock; "
+                                  f"hbm {peak_src}")}
     solve_rf = {"bound": "alu", "achieved": FLOP_PER_FIT * n_fits / t_sol / 1e12,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": FLOP_PER_FIT * n_fits / t_sol / 1e12 / FP64_PEAK_TFLOPS,
@@ -1126,6 +1132,44 @@ def surrogate_study(args, nk, epochs, rows_per_kernel, queries_per_kernel, k_lis
                                 "within_1pct": float(np.mean(rreg <= 0.01))}}
 
 
+def run_fit_formats(args):
+    """The fit's first stage (klr_fit_gram: the moment sums) on the batched
+    workload with FP32 coordinates and with KLR_EXP8 coordinates (uint8
+    base-2 logarithms, the default line's format): the same samples, 16 and
+    7 bytes per sample."""
+    import torch
+    import paper_1911_02373_gb300 as klr
+    fb, _ = make_inputs(args.seed)
+    dev = torch.device("cuda", 0)
+    off, y = torch.from_numpy(fb.offsets).to(dev), torch.from_numpy(fb.y).to(dev)
+    xs = {"f32": torch.from_numpy(np.ascontiguousarray(fb.x)).to(dev),
+          "exp8": torch.from_numpy(np.round(np.log2(fb.x)).astype(np.uint8)).to(dev)}
+    ctx = klr.Context(0)
+    ctx.reserve(fb.n_fits, 0)
+    kw = dict(n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10, precision=klr.FIT_DF32,
+              refine_iters=0, coef_dtype=klr.F32, stage="gram")
+    out = {}
+    K = max(1, args.steps)
+    for name, x in xs.items():
+        for _ in range(max(3, args.warmup)):
+            ctx.fit(off, x, y, **kw)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            ctx.fit(off, x, y, **kw)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / K
+        n_s = int(fb.offsets[-1])
+        out[name] = {"ms": ms, "samples_per_s": n_s / (ms * 1e-3),
+                     "bytes_per_sample": 16 if name == "f32" else 7}
+    ctx.close()
+    return {"metric": "fit moments stage (klr_fit_gram) by sample format",
+            "config": {"workload": WORKLOAD["name"], "fits": fb.n_fits,
+                       "samples": int(fb.offsets[-1])}, "results": out}
+
+
 def run_history(args):
     """Runtime history: the batched workload's 640,000 queries against its
     ground-truth programs, answered by the plain FP32 argmin, then through the
@@ -1325,6 +1369,9 @@ def main():
         return
     if args.workload == "history":
         print(json.dumps(run_history(args)))
+        return
+    if args.workload == "fit_formats":
+        print(json.dumps(run_fit_formats(args)))
         return
     ws, rank, _ = dist_env()
     cb, kept = None, None
