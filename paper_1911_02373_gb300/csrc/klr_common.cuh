@@ -130,6 +130,43 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
+// Two FP32 values in one 64-bit register (the first in the low half), for
+// the packed FP32x2 instructions of this architecture: one instruction
+// computes both halves, each rounded as its scalar form is (round to nearest,
+// no contraction).
+typedef unsigned long long f2p;
+__device__ __forceinline__ f2p f2p_make(float lo, float hi) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ float2 f2p_get(f2p v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ f2p f2p_add(f2p a, f2p b) {
+    f2p d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p f2p_sub(f2p a, f2p b) {
+    f2p d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p f2p_mul(f2p a, f2p b) {
+    f2p d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// TwoSum (Knuth) of both halves at once: a + b = s + e exactly, per half
+__device__ __forceinline__ void two_sum2(f2p a, f2p b, f2p& s, f2p& e) {
+    s = f2p_add(a, b);
+    const f2p bp = f2p_sub(s, a);
+    e = f2p_add(f2p_sub(a, f2p_sub(s, bp)), f2p_sub(b, bp));
+}
+
 // Double-FP32 accumulator (hi, lo) += t with an error-free TwoSum.
 __device__ __forceinline__ void df_add(float& hi, float& lo, float t) {
     float s, e;

@@ -458,6 +458,14 @@ __device__ __forceinline__ void dw_acc_scaled(float& h, float& l, float vh, floa
     l = __fadd_rn(l, __fadd_rn(e, __fmul_rn(vl, p)));
 }
 
+// dw_acc_scaled on packed pairs
+__device__ __forceinline__ void dw_acc_scaled2(f2p& h, f2p& l, f2p vh, f2p vl, f2p p) {
+    f2p s, e;
+    two_sum2(h, f2p_mul(vh, p), s, e);
+    h = s;
+    l = f2p_add(l, f2p_add(e, f2p_mul(vl, p)));
+}
+
 template <bool E8>
 __global__ void __launch_bounds__(32)
 moments_binned_kernel(const __grid_constant__ FitParams P) {
@@ -561,14 +569,16 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
         }
         __syncwarp();
         // ---- fold over the octaves of N: items (k, shape) -------------------------
+        // the powers a = (0, 1) and (2, 3) as packed pairs, a = 4 alone
         constexpr int R1 = (3 * kBinS + 31) / 32;
-        float fh[R1][5], fl[R1][5];
+        f2p ph[R1][2], pl[R1][2];
+        float fh4[R1], fl4[R1];
 #pragma unroll
         for (int r = 0; r < R1; ++r) {
             const int it = r * 32 + lane;
             const int k = it / kBinS, sh = it - k * kBinS;
-#pragma unroll
-            for (int a = 0; a < 5; ++a) fh[r][a] = fl[r][a] = 0.f;
+            ph[r][0] = ph[r][1] = pl[r][0] = pl[r][1] = 0ull;
+            fh4[r] = fl4[r] = 0.f;
             if (it < 3 * kBinS) {
 #pragma unroll 2
                 for (int t = 0; t < kBinT; ++t) {
@@ -582,13 +592,12 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
                         vh = k == 1 ? v.x : v.z;
                         vl = k == 1 ? v.y : v.w;
                     }
-                    const float pt = pow2f(-t);
-                    float p = 1.f;
-#pragma unroll
-                    for (int a = 0; a < 5; ++a) {
-                        dw_acc_scaled(fh[r][a], fl[r][a], vh, vl, p);
-                        p = __fmul_rn(p, pt);
-                    }
+                    const float pt = pow2f(-t), pt2 = pow2f(-2 * t);
+                    const f2p vh2 = f2p_make(vh, vh), vl2 = f2p_make(vl, vl);
+                    const f2p p01 = f2p_make(1.f, pt), p23 = f2p_mul(p01, f2p_make(pt2, pt2));
+                    dw_acc_scaled2(ph[r][0], pl[r][0], vh2, vl2, p01);
+                    dw_acc_scaled2(ph[r][1], pl[r][1], vh2, vl2, p23);
+                    dw_acc_scaled(fh4[r], fl4[r], vh, vl, pow2f(-4 * t));
                 }
             }
         }
@@ -598,35 +607,61 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
             const int it = r * 32 + lane;
             const int k = it / kBinS, sh = it - k * kBinS;
             if (it < 3 * kBinS) {
+                float2* Fk = Fs + (k * 5) * kBinS + sh;
 #pragma unroll
-                for (int a = 0; a < 5; ++a)
-                    Fs[(k * 5 + a) * kBinS + sh] = make_float2(fh[r][a], fl[r][a]);
+                for (int g = 0; g < 2; ++g) {
+                    const float2 h = f2p_get(ph[r][g]), l = f2p_get(pl[r][g]);
+                    Fk[(2 * g) * kBinS] = make_float2(h.x, l.x);
+                    Fk[(2 * g + 1) * kBinS] = make_float2(h.y, l.y);
+                }
+                Fk[4 * kBinS] = make_float2(fh4[r], fl4[r]);
             }
         }
         __syncwarp();
         // ---- fold over the block shapes: items (k, moment) ------------------------
-        // three partial sums over interleaved shapes (independent chains)
+        // the shape fold with two moments per lane as a packed pair (items it
+        // and it + 53 of 105), two interleaved partial sums over the shapes
         float2* mom = reinterpret_cast<float2*>(P.mom) + (int64_t)f * 3 * 35;
 #pragma unroll 1
-        for (int it = lane; it < 3 * 35; it += 32) {
-            const int k = it / 35, mu = it - k * 35;
-            const int a = c_mono34.e[mu][0], i = c_mono34.e[mu][1], j = c_mono34.e[mu][2];
-            const float2* Fk = Fs + (k * 5 + a) * kBinS;
-            float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
-#pragma unroll 1
-            for (int sh = 0; sh < kBinS; sh += 3) {
+        for (int it = lane; it < 53; it += 32) {
+            const int i2 = it + 53;                 // item 105 does not exist
+            const bool two = i2 < 3 * 35;
+            int kk[2], aa[2], ii[2], jj[2];
+            const int items[2] = {it, two ? i2 : it};
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    const int ex = i * (c_bin_shapes.e[sh + q][0] - bs) +
-                                   j * (c_bin_shapes.e[sh + q][1] - bs);
-                    const float2 v = Fk[sh + q];
-                    dw_acc_scaled(h[q], l[q], v.x, v.y, pow2f(ex));
+            for (int g = 0; g < 2; ++g) {
+                kk[g] = items[g] / 35;
+                const int mu = items[g] - kk[g] * 35;
+                aa[g] = c_mono34.e[mu][0]; ii[g] = c_mono34.e[mu][1]; jj[g] = c_mono34.e[mu][2];
+            }
+            const float2* F0 = Fs + (kk[0] * 5 + aa[0]) * kBinS;
+            const float2* F1 = Fs + (kk[1] * 5 + aa[1]) * kBinS;
+            f2p h[2] = {0ull, 0ull}, l[2] = {0ull, 0ull};
+#pragma unroll 1
+            for (int sh = 0; sh < kBinS - 1; sh += 2) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int e0 = c_bin_shapes.e[sh + q][0] - bs, e1 = c_bin_shapes.e[sh + q][1] - bs;
+                    const float2 v0 = F0[sh + q], v1 = F1[sh + q];
+                    const f2p p = f2p_make(pow2f(ii[0] * e0 + jj[0] * e1), pow2f(ii[1] * e0 + jj[1] * e1));
+                    dw_acc_scaled2(h[q], l[q], f2p_make(v0.x, v1.x), f2p_make(v0.y, v1.y), p);
                 }
             }
-            dw_acc_scaled(h[0], l[0], h[1], l[1], 1.f);
-            dw_acc_scaled(h[0], l[0], h[2], l[2], 1.f);
-            const dw q = dw_2sum(h[0], l[0]);
-            mom[it] = make_float2(q.h, q.l);
+            {   // the last shape (51 is odd)
+                const int sh = kBinS - 1;
+                const int e0 = c_bin_shapes.e[sh][0] - bs, e1 = c_bin_shapes.e[sh][1] - bs;
+                const float2 v0 = F0[sh], v1 = F1[sh];
+                const f2p p = f2p_make(pow2f(ii[0] * e0 + jj[0] * e1), pow2f(ii[1] * e0 + jj[1] * e1));
+                dw_acc_scaled2(h[0], l[0], f2p_make(v0.x, v1.x), f2p_make(v0.y, v1.y), p);
+            }
+            dw_acc_scaled2(h[0], l[0], h[1], l[1], f2p_make(1.f, 1.f));
+            const float2 hh = f2p_get(h[0]), ll = f2p_get(l[0]);
+            const dw q0 = dw_2sum(hh.x, ll.x);
+            mom[it] = make_float2(q0.h, q0.l);
+            if (two) {
+                const dw q1 = dw_2sum(hh.y, ll.y);
+                mom[i2] = make_float2(q1.h, q1.l);
+            }
         }
         if (lane == 0) P.flags[f] = 0;
         __syncwarp();
