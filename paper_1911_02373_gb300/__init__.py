@@ -168,8 +168,18 @@ def enumerate_configs(dims: int, min_threads: int = 32, max_threads: int = 1024)
     return out
 
 
+def _dptr(t):
+    """Device address of a CUDA tensor.  The library's kernels read and write
+    the addresses they are given, so a tensor in host memory is refused here
+    (on a GPU that reaches host memory through a coherent link it would
+    otherwise be read or written in place instead of failing)."""
+    if not t.is_cuda:
+        raise ValueError(f"expected a CUDA tensor, got one on {t.device}")
+    return t.data_ptr()
+
+
 def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+    return None if t is None else ctypes.c_void_p(_dptr(t))
 
 
 def _stream(stream):
@@ -237,7 +247,7 @@ class Context:
         else:
             coef, status, diag = out
         b = FitBatch(n_fits, n_vars, degree, n_scale_log2, b_scale_log2, sdt,
-                     offsets.data_ptr(), x.data_ptr(), x.stride(0), y.data_ptr(),
+                     _dptr(offsets), _dptr(x), x.stride(0), _dptr(y),
                      precision, refine_iters)
         _set_var_degree(b, var_degree)
         if stage == "gram":
@@ -270,7 +280,7 @@ class Context:
         if out is None:
             out = torch.empty(n_fits, device=x.device, dtype=torch.float64)
         b = FitBatch(n_fits, n_vars, degree, n_scale_log2, b_scale_log2, sdt,
-                     offsets.data_ptr(), x.data_ptr(), x.stride(0), y.data_ptr(), FIT_FP64, 0)
+                     _dptr(offsets), _dptr(x), x.stride(0), _dptr(y), FIT_FP64, 0)
         _set_var_degree(b, var_degree)
         _check("klr_fit_heldout", _lib.klr_fit_heldout(self._h, ctypes.byref(b), _ptr(coef), cdt,
                                                        _ptr(out), _stream(stream)))
@@ -320,7 +330,7 @@ class Context:
         import torch
         p = Program(regs.numel(), n_vars, degree, n_scale_log2, b_scale_log2,
                     F64 if coef.dtype == torch.float64 else F32,
-                    coef.data_ptr(), regs.data_ptr(), smem.data_ptr())
+                    _dptr(coef), _dptr(regs), _dptr(smem))
         _set_var_degree(p, var_degree)
         for i in range(8):
             p.metric_lo[i] = float(metric_lo[i])
@@ -336,7 +346,7 @@ class Context:
         if out is None:
             out = torch.empty((n_q, cfg.shape[0]), device=q_N.device,
                               dtype=torch.float64 if out_dtype == F64 else torch.float32)
-        q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+        q = Queries(_dptr(q_offsets), _dptr(q_N), n_q)
         _check("klr_eval", _lib.klr_eval(self._h, ctypes.byref(prog), ctypes.byref(hw),
                                          _ptr(cfg), cfg.shape[0], ctypes.byref(q), _ptr(out),
                                          out_dtype, _stream(stream)))
@@ -359,7 +369,7 @@ class Context:
             lp = torch.empty((n_q, 6), device=dev, dtype=torch.int32) if launch else None
         else:
             best, cyc, margin, status, lp = out
-        q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+        q = Queries(_dptr(q_offsets), _dptr(q_N), n_q)
         if autotune:
             ch, ms = ctypes.c_int32(-1), ctypes.c_float(0.0)
             _check("klr_autotune_argmin",
@@ -416,7 +426,7 @@ def argmin_history(ctx: "Context", hist: History, prog: Program, hw: Hw, cfg, q_
                torch.empty(n_q, device=dev, dtype=torch.int32),
                torch.empty((n_q, 6), device=dev, dtype=torch.int32))
     best, cyc, margin, status, lp = out
-    q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+    q = Queries(_dptr(q_offsets), _dptr(q_N), n_q)
     _check("klr_argmin_history",
            _lib.klr_argmin_history(ctx._h, hist._h, ctypes.byref(prog), ctypes.byref(hw), _ptr(cfg),
                                    cfg.shape[0], ctypes.byref(q), _ptr(best), _ptr(cyc),
@@ -436,7 +446,7 @@ def argmin_refined(ctx: "Context", prog: Program, hw: Hw, cfg, q_offsets, q_N, c
                torch.empty(n_q, dtype=torch.float32, device=q_N.device),
                torch.empty(n_q, dtype=torch.int32, device=q_N.device))
     best, cyc, st = out
-    q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+    q = Queries(_dptr(q_offsets), _dptr(q_N), n_q)
     _check("klr_argmin_refined",
            _lib.klr_argmin_refined(ctx._h, ctypes.byref(prog), ctypes.byref(hw), _ptr(cfg),
                                    cfg.shape[0], ctypes.byref(q), _ptr(cycles_table), float(eps),
@@ -469,16 +479,16 @@ class Surrogate:
         self.params = init.cuda().contiguous()
         self.m = torch.zeros_like(self.params)
         self.v = torch.zeros_like(self.params)
-        self.net = MlpNet(n_coef, n_out, self.params.data_ptr(), self.m.data_ptr(),
-                          self.v.data_ptr(), 0)
+        self.net = MlpNet(n_coef, n_out, _dptr(self.params), _dptr(self.m),
+                          _dptr(self.v), 0)
         for i in range(7):
             self.net.hw_feat[i] = float(hw_feat[i])
 
     @staticmethod
     def _rows(kernel, N, cfg_idx, target=None):
-        return MlpRows(kernel.numel(), kernel.data_ptr(), N.data_ptr(),
-                       None if cfg_idx is None else cfg_idx.data_ptr(),
-                       None if target is None else target.data_ptr())
+        return MlpRows(kernel.numel(), _dptr(kernel), _dptr(N),
+                       None if cfg_idx is None else _dptr(cfg_idx),
+                       None if target is None else _dptr(target))
 
     def train_step(self, coef, cfg, kernel, N, cfg_idx, target, lr, weight_decay=0.0,
                    apply_update=True, loss=None, grads=None, stream=None):
@@ -508,7 +518,7 @@ class Surrogate:
         import torch
         if out is None:
             out = torch.empty((q_N.numel(), k), dtype=torch.int32, device=coef.device)
-        q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), q_N.numel())
+        q = Queries(_dptr(q_offsets), _dptr(q_N), q_N.numel())
         _check("klr_propose",
                _lib.klr_propose(self.ctx._h, ctypes.byref(self.net), _ptr(coef), _ptr(regs),
                                 _ptr(smem), regs.numel(), ctypes.byref(hw), _ptr(cfg),
@@ -538,7 +548,7 @@ def argmin_candidates(ctx: "Context", prog: Program, hw: Hw, cfg, q_offsets, q_N
                torch.empty(n_q, dtype=torch.float32, device=q_N.device),
                torch.empty(n_q, dtype=torch.int32, device=q_N.device))
     best, cyc, st = out
-    q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), n_q)
+    q = Queries(_dptr(q_offsets), _dptr(q_N), n_q)
     _check("klr_argmin_candidates",
            _lib.klr_argmin_candidates(ctx._h, ctypes.byref(prog), ctypes.byref(hw), _ptr(cfg),
                                       cfg.shape[0], ctypes.byref(q), _ptr(cand), cand.shape[1],
@@ -552,7 +562,7 @@ def argmin_noalloc(prog: Program, hw: Hw, cfg, q_offsets, q_N, out, stream=None)
     memory.  ``out`` = (best int32, cycles float32, margin float32 or None,
     status int32 or None, launch int32 (n, 6) or None), all preallocated."""
     best, cyc, margin, status, lp = out
-    q = Queries(q_offsets.data_ptr(), q_N.data_ptr(), q_N.numel())
+    q = Queries(_dptr(q_offsets), _dptr(q_N), q_N.numel())
     _check("klr_argmin_noalloc",
            _lib.klr_argmin_noalloc(ctypes.byref(prog), ctypes.byref(hw), _ptr(cfg), cfg.shape[0],
                                    ctypes.byref(q), _ptr(best), _ptr(cyc), _ptr(margin),

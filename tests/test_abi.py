@@ -74,3 +74,16 @@ def test_argument_errors_before_any_device_work():
     assert klr._lib.klr_argmin(None, None, None, None, 0, None, None, None, 0, None, None,
                                None, None) == klr.EINVAL
     assert klr.version() == 1
+
+
+def test_binding_refuses_host_tensors_for_device_arguments():
+    """Every address the binding hands the library comes from a CUDA tensor;
+    a host tensor is refused before any call (the GPU could otherwise read
+    or write host memory in place)."""
+    torch = pytest.importorskip("torch")
+    klr = _lib_or_skip()
+    with pytest.raises(ValueError):
+        klr._dptr(torch.zeros(4))
+    with pytest.raises(ValueError):
+        klr._ptr(torch.zeros(4, dtype=torch.int32))
+    assert klr._ptr(None) is None
