@@ -57,7 +57,7 @@ def parse():
                     help="built-in launch shapes instead of the autotuned ones")
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "sweep3d", "surrogate", "precision", "history",
-                             "fit_formats"],
+                             "fit_formats", "single"],
                     help="batched: fit + argmin (default metric); sweep3d: 3D evaluator sweep")
     ap.add_argument("--sweep-kernels", type=int, default=100000)
     ap.add_argument("--sweep-check-kernels", type=int, default=1000,
@@ -1132,6 +1132,69 @@ def surrogate_study(args, nk, epochs, rows_per_kernel, queries_per_kernel, k_lis
                                 "within_1pct": float(np.mean(rreg <= 0.01))}}
 
 
+def run_single(args):
+    """The single-kernel FP64 workload as a latency: one kernel's 8 metrics
+    fitted from 200 noiseless samples each (FP64 moments and solve, one
+    refinement pass), then the FP64 argmin over 16 data sizes x 51 block
+    shapes, each call and the whole chain captured as a CUDA graph and
+    replayed; microseconds per replay."""
+    import torch
+    import paper_1911_02373_gb300 as klr
+    import workloads as W
+    dev = torch.device("cuda", 0)
+    fb = W.fit_batch(args.seed, 1, 200, dtype=np.float64)
+    q = W.queries_per_kernel(1, W.query_sizes("pow2", 16))
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    off, x, y = t(fb.offsets), t(fb.x), t(fb.y)
+    qo, qn = t(q.offsets), t(q.sizes)
+    ctx = klr.Context(0)
+    ctx.reserve(8, 16)
+    coef = torch.empty((8, 20), device=dev, dtype=torch.float64)
+    fst = torch.empty(8, device=dev, dtype=torch.int32)
+    fdg = torch.empty((8, 4), device=dev, dtype=torch.float64)
+    prog = klr.Context.program(coef.view(1, 8, 20), t(fb.truth.regs), t(fb.truth.smem), n_vars=3,
+                               degree=2, n_scale_log2=23, b_scale_log2=10,
+                               metric_lo=W.METRIC_LO, metric_scale=W.METRIC_SCALE)
+    cfg = t(klr.enumerate_configs(2))
+    hw = klr.make_hw(W.HARDWARE)
+    outs = (torch.empty(16, dtype=torch.int32, device=dev),
+            torch.empty(16, dtype=torch.float64, device=dev),
+            torch.empty(16, dtype=torch.float32, device=dev),
+            torch.empty(16, dtype=torch.int32, device=dev),
+            torch.empty((16, 6), dtype=torch.int32, device=dev))
+    fit = lambda: ctx.fit(off, x, y, n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10,
+                          precision=klr.FIT_FP64, refine_iters=1, coef_dtype=klr.F64,
+                          out=(coef, fst, fdg))
+    choose = lambda: ctx.argmin(prog, hw, cfg, qo, qn, out_dtype=klr.F64, out=outs)
+    res = {}
+    for name, fns in (("fit", [fit]), ("argmin", [choose]), ("fit_and_argmin", [fit, choose])):
+        for fn in fns:
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for fn in fns:
+                fn()
+        for _ in range(max(3, args.warmup)):
+            g.replay()
+        torch.cuda.synchronize()
+        K = max(10, args.steps)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            g.replay()
+        b.record()
+        torch.cuda.synchronize()
+        res[name] = {"us": a.elapsed_time(b) / K * 1e3}
+    st = fst.cpu().numpy()
+    ctx.close()
+    return {"metric": "latency of the single-kernel FP64 workload (us per graph replay)",
+            "unit": "us", "higher_is_better": False, "dtype": "f64",
+            "config": {"workload": "single_kernel_fp64", "fits": 8, "samples_per_fit": 200,
+                       "queries": 16, "configs": 51, "refine_iters": 1},
+            "results": res, "fit_status_nonzero": int(np.count_nonzero(st))}
+
+
 def run_fit_formats(args):
     """The fit's first stage (klr_fit_gram: the moment sums) on the batched
     workload with FP32 coordinates and with KLR_EXP8 coordinates (uint8
@@ -1372,6 +1435,9 @@ def main():
         return
     if args.workload == "fit_formats":
         print(json.dumps(run_fit_formats(args)))
+        return
+    if args.workload == "single":
+        print(json.dumps(run_single(args)))
         return
     ws, rank, _ = dist_env()
     cb, kept = None, None

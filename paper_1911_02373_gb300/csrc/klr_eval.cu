@@ -403,6 +403,90 @@ __device__ __forceinline__ T eval_cfg(const EvalParams& P, const CfgInfo* __rest
     return e;
 }
 
+// Per-kernel tables of the sweep, by the threads of one block: the kernel's
+// coefficients, the per-shape integer facts (occupancy, warps, wave size)
+// and the specialised polynomials in N of every shape (of the proposed ones
+// in candidate mode).  Ends with the block synchronised.
+template <typename T, int D>
+__device__ __forceinline__ void eval_setup(const EvalParams& P, int k, T* coef_s, T* spec,
+                                           const T* bmon, CfgInfo* cinfo, float* wave_rcp,
+                                           unsigned* cmask, unsigned n_sm) {
+    constexpr int NC = 2 * (D + 1);
+    constexpr bool kMonoTable = sizeof(T) == 4;
+    const int m = P.m, u = P.u, n_cfg = P.n_cfg;
+    const int64_t qa = P.q_off[k], qb = P.q_off[k + 1];
+    __syncthreads();   // previous kernel's tables no longer in use
+    for (int i = threadIdx.x; i < 8 * u; i += blockDim.x) {
+        if (P.coef_f64) coef_s[i] = (T)reinterpret_cast<const double*>(P.coef)[(int64_t)k * 8 * u + i];
+        else coef_s[i] = (T)reinterpret_cast<const float*>(P.coef)[(int64_t)k * 8 * u + i];
+    }
+    // candidate mode: the shapes proposed for any of this kernel's queries
+    if (P.cand) {
+        for (int i = threadIdx.x; i < 8; i += blockDim.x) cmask[i] = 0u;
+        __syncthreads();
+        for (int64_t i = qa * P.kc + threadIdx.x; i < qb * P.kc; i += blockDim.x) {
+            const int c = P.cand[i];
+            if (c >= 0 && c < n_cfg) atomicOr(&cmask[c >> 5], 1u << (c & 31));
+        }
+    }
+    const int R = P.regs[k], Z = P.smem[k];
+    for (int c = threadIdx.x; c < n_cfg; c += blockDim.x) {
+        const long long b0 = P.cfg[3 * c], b1 = P.cfg[3 * c + 1], b2 = P.cfg[3 * c + 2];
+        const long long Tt = b0 * b1 * b2;
+        int B = active_blocks(Tt, R, Z, P);
+        if (Tt > P.T_max) B = 0;
+        const int W = (int)min((long long)B * Tt / 32, (long long)P.W_max);
+        CfgInfo ci;
+        ci.T = (int)Tt;
+        ci.B = B;
+        ci.W = W;
+        ci.b0 = (int)b0;
+        ci.b1 = P.dims >= 2 ? (int)b1 : 1;
+        ci.b2 = P.dims >= 3 ? (int)b2 : 1;
+        ci.t_shift = (Tt > 0 && (Tt & (Tt - 1)) == 0) ? __ffsll(Tt) - 1 : -1;
+        ci.wave = (unsigned)max(B, 1) * n_sm;
+        cinfo[c] = ci;
+        wave_rcp[c] = 1.0f / (float)ci.wave;
+    }
+    __syncthreads();
+    // fold the block shape into univariate polynomials in the scaled N
+    for (int idx = threadIdx.x; idx < n_cfg * 8; idx += blockDim.x) {
+        const int c = idx >> 3, i = idx & 7;
+        if (P.cand && !((cmask[c >> 5] >> (c & 31)) & 1u)) continue;
+        T xb[3];
+        xb[0] = (T)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
+        xb[1] = (T)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
+        xb[2] = (T)ldexp((double)P.cfg[3 * c + 2], -P.b_scale_log2);
+        // coefficient of N^j: its terms in increasing index order
+        T acc[2][D + 1];
+#pragma unroll
+        for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+            for (int j = 0; j <= D; ++j) acc[s2][j] = T(0);
+        for (int t = 0; t < m; ++t) {
+            T bm = T(1);
+            if (kMonoTable) {
+                bm = bmon[c * m + t];
+            } else {
+                for (int v = 1; v < P.n_vars; ++v)
+                    for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
+            }
+            const int j = P.exps[t][0];
+            const T pa = mul_rn(coef_s[i * u + t], bm), qa = mul_rn(coef_s[i * u + m + t], bm);
+#pragma unroll
+            for (int jj = 0; jj <= D; ++jj)
+                if (jj == j) { acc[0][jj] = add_rn(acc[0][jj], pa); acc[1][jj] = add_rn(acc[1][jj], qa); }
+        }
+        T* sp = spec + (size_t)idx * NC;
+#pragma unroll
+        for (int j = 0; j <= D; ++j) {
+            sp[j] = acc[0][j];
+            sp[D + 1 + j] = acc[1][j];
+        }
+    }
+    __syncthreads();
+}
+
 template <typename T, int D>
 __global__ void __launch_bounds__(256)
 eval_kernel(const __grid_constant__ EvalParams P) {
@@ -446,76 +530,7 @@ eval_kernel(const __grid_constant__ EvalParams P) {
             for (int64_t q = qa + threadIdx.x; q < qb; q += blockDim.x) open |= !P.done[q];
             if (!__syncthreads_or(open)) continue;
         }
-        __syncthreads();   // previous kernel's tables no longer in use
-        for (int i = threadIdx.x; i < 8 * u; i += blockDim.x) {
-            if (P.coef_f64) coef_s[i] = (T)reinterpret_cast<const double*>(P.coef)[(int64_t)k * 8 * u + i];
-            else coef_s[i] = (T)reinterpret_cast<const float*>(P.coef)[(int64_t)k * 8 * u + i];
-        }
-        // candidate mode: the shapes proposed for any of this kernel's queries
-        if (P.cand) {
-            for (int i = threadIdx.x; i < 8; i += blockDim.x) cmask[i] = 0u;
-            __syncthreads();
-            for (int64_t i = qa * P.kc + threadIdx.x; i < qb * P.kc; i += blockDim.x) {
-                const int c = P.cand[i];
-                if (c >= 0 && c < n_cfg) atomicOr(&cmask[c >> 5], 1u << (c & 31));
-            }
-        }
-        const int R = P.regs[k], Z = P.smem[k];
-        for (int c = threadIdx.x; c < n_cfg; c += blockDim.x) {
-            const long long b0 = P.cfg[3 * c], b1 = P.cfg[3 * c + 1], b2 = P.cfg[3 * c + 2];
-            const long long Tt = b0 * b1 * b2;
-            int B = active_blocks(Tt, R, Z, P);
-            if (Tt > P.T_max) B = 0;
-            const int W = (int)min((long long)B * Tt / 32, (long long)P.W_max);
-            CfgInfo ci;
-            ci.T = (int)Tt;
-            ci.B = B;
-            ci.W = W;
-            ci.b0 = (int)b0;
-            ci.b1 = P.dims >= 2 ? (int)b1 : 1;
-            ci.b2 = P.dims >= 3 ? (int)b2 : 1;
-            ci.t_shift = (Tt > 0 && (Tt & (Tt - 1)) == 0) ? __ffsll(Tt) - 1 : -1;
-            ci.wave = (unsigned)max(B, 1) * n_sm;
-            cinfo[c] = ci;
-            wave_rcp[c] = 1.0f / (float)ci.wave;
-        }
-        __syncthreads();
-        // fold the block shape into univariate polynomials in the scaled N
-        for (int idx = threadIdx.x; idx < n_cfg * 8; idx += blockDim.x) {
-            const int c = idx >> 3, i = idx & 7;
-            if (P.cand && !((cmask[c >> 5] >> (c & 31)) & 1u)) continue;
-            T xb[3];
-            xb[0] = (T)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
-            xb[1] = (T)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
-            xb[2] = (T)ldexp((double)P.cfg[3 * c + 2], -P.b_scale_log2);
-            // coefficient of N^j: its terms in increasing index order
-            T acc[2][D + 1];
-#pragma unroll
-            for (int s2 = 0; s2 < 2; ++s2)
-#pragma unroll
-                for (int j = 0; j <= D; ++j) acc[s2][j] = T(0);
-            for (int t = 0; t < m; ++t) {
-                T bm = T(1);
-                if (kMonoTable) {
-                    bm = bmon[c * m + t];
-                } else {
-                    for (int v = 1; v < P.n_vars; ++v)
-                        for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
-                }
-                const int j = P.exps[t][0];
-                const T pa = mul_rn(coef_s[i * u + t], bm), qa = mul_rn(coef_s[i * u + m + t], bm);
-#pragma unroll
-                for (int jj = 0; jj <= D; ++jj)
-                    if (jj == j) { acc[0][jj] = add_rn(acc[0][jj], pa); acc[1][jj] = add_rn(acc[1][jj], qa); }
-            }
-            T* sp = spec + (size_t)idx * NC;
-#pragma unroll
-            for (int j = 0; j <= D; ++j) {
-                sp[j] = acc[0][j];
-                sp[D + 1 + j] = acc[1][j];
-            }
-        }
-        __syncthreads();
+        eval_setup<T, D>(P, k, coef_s, spec, bmon, cinfo, wave_rcp, cmask, n_sm);
 
         if (P.cand && P.kc <= 32 && (P.kc & (P.kc - 1)) == 0) {
             // candidate mode: one (query, candidate) pair per lane, kc lanes
@@ -647,6 +662,83 @@ eval_kernel(const __grid_constant__ EvalParams P) {
             if (P.q_status) P.q_status[q] = st;
             write_launch(P, q, N, bi);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Latency mode of the FP64 argmin (a few queries, e.g. one kernel's sizes at
+// launch time): one one-warp block per query, so that the queries spread over
+// the SMs instead of sharing one block per kernel.  The warp builds its
+// query's kernel tables as the block-per-kernel sweep does (eval_setup), each
+// lane evaluates every 32nd shape with the sweep's eval_cfg, and shuffles
+// reduce the query to its least (cycles, shape), lowest shape on ties, and
+// the runner-up: the outputs are bitwise those of the block-per-kernel sweep.
+// ---------------------------------------------------------------------------
+constexpr int64_t kLatencyMaxQueries = 1024;
+
+template <int D>
+__global__ void __launch_bounds__(32)
+eval_query_warp_kernel(const __grid_constant__ EvalParams P) {
+    using T = double;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ unsigned cmask[8];
+    constexpr int NC = 2 * (D + 1);
+    const int n_cfg = P.n_cfg;
+    T* coef_s = reinterpret_cast<T*>(smem_raw);                 // 8 x u
+    T* spec = coef_s + 8 * P.u;                                 // n_cfg x 8 x NC
+    CfgInfo* cinfo = reinterpret_cast<CfgInfo*>(spec + (size_t)n_cfg * 8 * NC);
+    float* wave_rcp = reinterpret_cast<float*>(cinfo + n_cfg);
+    const int64_t q = blockIdx.x;
+    if (q >= P.n_q) return;
+    const int lane = threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    // the query's kernel: the last k with q_off[k] <= q
+    int kl = 0, kh = P.n_kernels - 1;
+    while (kl < kh) {
+        const int mid = (kl + kh + 1) >> 1;
+        if (P.q_off[mid] <= q) kl = mid;
+        else kh = mid - 1;
+    }
+    const int k = kl;
+    const unsigned n_sm = (unsigned)P.n_sm;
+    eval_setup<T, D>(P, k, coef_s, spec, nullptr, cinfo, wave_rcp, cmask, n_sm);
+    T lo[8], sc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) { lo[i] = (T)P.lo[i]; sc[i] = (T)P.sc[i]; }
+    const long long N = P.q_N[q];
+    const bool small = N < (1LL << 24);
+    const T xN = (T)N * (T)ldexp(1.0, -P.n_scale_log2);
+    int st = 0;
+    T bv = (T)INFINITY, sv = (T)INFINITY;
+    int bj = 0x7fffffff;
+    for (int c = lane; c < n_cfg; c += 32) {
+        const T e = eval_cfg<T, D>(P, cinfo, wave_rcp, spec, lo, sc, n_sm, N, small, xN, c, st);
+        if (e < bv) { sv = bv; bv = e; bj = c; }
+        else if (e < sv) sv = e;
+    }
+    T gv = bv;
+    int gj = bj;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(full, gv, o);
+        const int oj = __shfl_xor_sync(full, gj, o);
+        if (ov < gv || (ov == gv && oj < gj)) { gv = ov; gj = oj; }
+    }
+    T rv = (bj == gj) ? sv : fmin(bv, sv);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rv = fmin(rv, __shfl_xor_sync(full, rv, o));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) st |= __shfl_xor_sync(full, st, o);
+    if (lane == 0) {
+        const int best = gv < (T)INFINITY ? gj : -1;
+        if (best < 0) st |= KLR_Q_NONE_FEASIBLE;
+        float mg = 0.f;
+        if (best >= 0) mg = isfinite((float)rv) ? (float)((rv - gv) / gv) : INFINITY;
+        P.best[q] = best;
+        reinterpret_cast<T*>(P.best_cycles)[q] = gv;
+        if (P.margin) P.margin[q] = mg;
+        if (P.q_status) P.q_status[q] = st;
+        write_launch(P, q, N, best);
     }
 }
 
@@ -1322,6 +1414,21 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
         P.ties = reinterpret_cast<TieRecord*>(reinterpret_cast<char*>(c->ws) + 256);
         P.tie_cap = tie_capacity(P.n_q);
         KLR_CHECK_CUDA(cudaMemsetAsync(P.tie_count, 0, sizeof(int), stream));
+    }
+    if (f64 && P.n_q <= kLatencyMaxQueries) {
+        // a few FP64 queries: one warp each, spread over the SMs
+        const size_t smem = eval_smem_bytes(P, 8);
+        if (smem > c->smem_optin) {
+            set_error("evaluator needs %zu bytes of shared memory", smem);
+            return KLR_ENOTSUP;
+        }
+        auto kern = P.degree == 1 ? eval_query_warp_kernel<1>
+                  : P.degree == 2 ? eval_query_warp_kernel<2> : eval_query_warp_kernel<3>;
+        KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+        kern<<<(unsigned)P.n_q, 32, smem, stream>>>(P);
+        KLR_CHECK_CUDA(cudaGetLastError());
+        return KLR_OK;
     }
     st = launch_eval(c, P, f64, stream);
     if (st != KLR_OK || f64) return st;

@@ -312,3 +312,34 @@ def test_refined_choice_matches_oracle(klr, ctx, eps):
                     first = int(np.argmin(np.where(fin, row, np.inf)))
                     assert bool(st[r] & klr.Q_REFINED) == (want != first)
     assert strict > 0.8 * len(q.sizes)
+
+
+@pytest.mark.parametrize("seed,nv,degree", [(31, 3, 2), (32, 3, 1), (33, 4, 3), (34, 4, 2)])
+def test_fp64_latency_mode_equals_the_kernel_sweep(klr, ctx, seed, nv, degree):
+    """An FP64 argmin of at most 1024 queries runs one warp per query; a larger
+    one runs a block per kernel.  The same queries asked both ways (a batch of
+    1200, then slices of it) give bitwise equal outputs: index, cycles,
+    margin, status bits and launch geometry.  Kernel 1 has no queries, kernel
+    0 fits no block, and the sizes include N below every shape."""
+    nk = 12
+    gt = G.make_program(seed, nk, n_vars=nv, degree=degree)
+    gt.regs[0] = 4096
+    coef = gt.coef.astype(np.float64)
+    rng = np.random.default_rng(seed)
+    per = np.full(nk, 1200 // (nk - 1), dtype=np.int64)
+    per[1] = 0
+    per[-1] += 1200 - per.sum()
+    q_off = np.concatenate([[0], np.cumsum(per)]).astype(np.int64)
+    sizes = np.exp2(rng.uniform(0, 26, size=1200)).astype(np.int64)
+    sizes[::97] = 1
+    sizes[5::89] = 7
+    full = _run(klr, ctx, gt, coef, q_off, sizes, klr.F64, False)
+    for lo_q, hi_q in ((0, 1024), (300, 301), (513, 1200)):
+        # the slice's queries, with each kernel's offsets clipped to it
+        off = np.clip(q_off, lo_q, hi_q) - lo_q
+        part = _run(klr, ctx, gt, coef, off, sizes[lo_q:hi_q], klr.F64, False)
+        for a, b in zip(full, part):
+            assert np.array_equal(a[lo_q:hi_q].view(np.uint8), b.view(np.uint8)), (lo_q, hi_q)
+    best, cyc, status = full[0], full[1], full[3]
+    assert np.all(best[:q_off[1]] == -1) and np.all(status[:q_off[1]] & klr.Q_NONE_FEASIBLE)
+    assert np.any(best >= 0) and np.all(np.isfinite(cyc[best >= 0]))
