@@ -407,12 +407,11 @@ __device__ __forceinline__ T eval_cfg(const EvalParams& P, const CfgInfo* __rest
 // coefficients, the per-shape integer facts (occupancy, warps, wave size)
 // and the specialised polynomials in N of every shape (of the proposed ones
 // in candidate mode).  Ends with the block synchronised.
-template <typename T, int D>
+template <typename T, int D, bool kMonoTable = (sizeof(T) == 4)>
 __device__ __forceinline__ void eval_setup(const EvalParams& P, int k, T* coef_s, T* spec,
                                            const T* bmon, CfgInfo* cinfo, float* wave_rcp,
                                            unsigned* cmask, unsigned n_sm) {
     constexpr int NC = 2 * (D + 1);
-    constexpr bool kMonoTable = sizeof(T) == 4;
     const int m = P.m, u = P.u, n_cfg = P.n_cfg;
     const int64_t qa = P.q_off[k], qb = P.q_off[k + 1];
     __syncthreads();   // previous kernel's tables no longer in use
@@ -667,30 +666,44 @@ eval_kernel(const __grid_constant__ EvalParams P) {
 
 // ---------------------------------------------------------------------------
 // Latency mode of the FP64 argmin (a few queries, e.g. one kernel's sizes at
-// launch time): one one-warp block per query, so that the queries spread over
-// the SMs instead of sharing one block per kernel.  The warp builds its
-// query's kernel tables as the block-per-kernel sweep does (eval_setup), each
-// lane evaluates every 32nd shape with the sweep's eval_cfg, and shuffles
-// reduce the query to its least (cycles, shape), lowest shape on ties, and
-// the runner-up: the outputs are bitwise those of the block-per-kernel sweep.
+// launch time): one block per query, so that the queries spread over the SMs
+// instead of sharing one block per kernel.  The block builds its query's
+// kernel tables as the per-kernel sweep does (eval_setup, with the
+// block-shape monomials first put in a table: the same products in the same
+// order), each thread evaluates its shapes with the sweep's eval_cfg, and
+// shuffles then shared memory reduce the query to its least (cycles, shape),
+// lowest shape on ties, and the runner-up: the outputs are bitwise those of
+// the per-kernel sweep.  FP64 issues at 1/64 of the FP32 rate on GB300, so
+// the block's 8 warps are there to occupy every scheduler's FP64 unit.
 // ---------------------------------------------------------------------------
 constexpr int64_t kLatencyMaxQueries = 1024;
+constexpr int kLatencyThreads = 256;
+
+size_t latency_smem_bytes(const EvalParams& P) {
+    const int NC = 2 * (P.degree + 1);
+    size_t b = sizeof(double) * (8 * (size_t)P.u + (size_t)P.n_cfg * 8 * NC + (size_t)P.n_cfg * P.m);
+    b = (b + 15) & ~(size_t)15;
+    return b + (sizeof(CfgInfo) + sizeof(float)) * (size_t)P.n_cfg;
+}
 
 template <int D>
-__global__ void __launch_bounds__(32)
-eval_query_warp_kernel(const __grid_constant__ EvalParams P) {
+__global__ void __launch_bounds__(kLatencyThreads)
+eval_query_block_kernel(const __grid_constant__ EvalParams P) {
     using T = double;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned cmask[8];
+    __shared__ T red_v[kLatencyThreads / 32], red_r[kLatencyThreads / 32];
+    __shared__ int red_j[kLatencyThreads / 32], red_s[kLatencyThreads / 32];
     constexpr int NC = 2 * (D + 1);
-    const int n_cfg = P.n_cfg;
+    const int n_cfg = P.n_cfg, m = P.m;
     T* coef_s = reinterpret_cast<T*>(smem_raw);                 // 8 x u
     T* spec = coef_s + 8 * P.u;                                 // n_cfg x 8 x NC
-    CfgInfo* cinfo = reinterpret_cast<CfgInfo*>(spec + (size_t)n_cfg * 8 * NC);
+    T* bmon = spec + (size_t)n_cfg * 8 * NC;                    // n_cfg x m
+    CfgInfo* cinfo = reinterpret_cast<CfgInfo*>(bmon + (size_t)n_cfg * m);
     float* wave_rcp = reinterpret_cast<float*>(cinfo + n_cfg);
     const int64_t q = blockIdx.x;
     if (q >= P.n_q) return;
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned full = 0xffffffffu;
     // the query's kernel: the last k with q_off[k] <= q
     int kl = 0, kh = P.n_kernels - 1;
@@ -701,7 +714,18 @@ eval_query_warp_kernel(const __grid_constant__ EvalParams P) {
     }
     const int k = kl;
     const unsigned n_sm = (unsigned)P.n_sm;
-    eval_setup<T, D>(P, k, coef_s, spec, nullptr, cinfo, wave_rcp, cmask, n_sm);
+    for (int idx = threadIdx.x; idx < n_cfg * m; idx += blockDim.x) {
+        const int c = idx / m, t = idx - c * m;
+        T xb[3];
+        xb[0] = (T)ldexp((double)P.cfg[3 * c], -P.b_scale_log2);
+        xb[1] = (T)ldexp((double)P.cfg[3 * c + 1], -P.b_scale_log2);
+        xb[2] = (T)ldexp((double)P.cfg[3 * c + 2], -P.b_scale_log2);
+        T bm = T(1);
+        for (int v = 1; v < P.n_vars; ++v)
+            for (int e = 0; e < P.exps[t][v]; ++e) bm *= xb[v - 1];
+        bmon[idx] = bm;
+    }
+    eval_setup<T, D, true>(P, k, coef_s, spec, bmon, cinfo, wave_rcp, cmask, n_sm);
     T lo[8], sc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) { lo[i] = (T)P.lo[i]; sc[i] = (T)P.sc[i]; }
@@ -711,11 +735,12 @@ eval_query_warp_kernel(const __grid_constant__ EvalParams P) {
     int st = 0;
     T bv = (T)INFINITY, sv = (T)INFINITY;
     int bj = 0x7fffffff;
-    for (int c = lane; c < n_cfg; c += 32) {
+    for (int c = threadIdx.x; c < n_cfg; c += blockDim.x) {
         const T e = eval_cfg<T, D>(P, cinfo, wave_rcp, spec, lo, sc, n_sm, N, small, xN, c, st);
         if (e < bv) { sv = bv; bv = e; bj = c; }
         else if (e < sv) sv = e;
     }
+    // least (value, index) of the warp, then its runner-up value
     T gv = bv;
     int gj = bj;
 #pragma unroll
@@ -729,7 +754,21 @@ eval_query_warp_kernel(const __grid_constant__ EvalParams P) {
     for (int o = 16; o > 0; o >>= 1) rv = fmin(rv, __shfl_xor_sync(full, rv, o));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) st |= __shfl_xor_sync(full, st, o);
-    if (lane == 0) {
+    if (lane == 0) { red_v[wid] = gv; red_j[wid] = gj; red_r[wid] = rv; red_s[wid] = st; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = blockDim.x >> 5;
+        int w0 = 0;
+        for (int w = 1; w < nw; ++w)
+            if (red_v[w] < red_v[w0] || (red_v[w] == red_v[w0] && red_j[w] < red_j[w0])) w0 = w;
+        gv = red_v[w0];
+        gj = red_j[w0];
+        rv = red_r[w0];
+        st = 0;
+        for (int w = 0; w < nw; ++w) {
+            st |= red_s[w];
+            if (w != w0) rv = fmin(rv, red_v[w]);   // another warp's least: at most its runner-up
+        }
         const int best = gv < (T)INFINITY ? gj : -1;
         if (best < 0) st |= KLR_Q_NONE_FEASIBLE;
         float mg = 0.f;
@@ -1416,17 +1455,17 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
         KLR_CHECK_CUDA(cudaMemsetAsync(P.tie_count, 0, sizeof(int), stream));
     }
     if (f64 && P.n_q <= kLatencyMaxQueries) {
-        // a few FP64 queries: one warp each, spread over the SMs
-        const size_t smem = eval_smem_bytes(P, 8);
+        // a few FP64 queries: one block each, spread over the SMs
+        const size_t smem = latency_smem_bytes(P);
         if (smem > c->smem_optin) {
             set_error("evaluator needs %zu bytes of shared memory", smem);
             return KLR_ENOTSUP;
         }
-        auto kern = P.degree == 1 ? eval_query_warp_kernel<1>
-                  : P.degree == 2 ? eval_query_warp_kernel<2> : eval_query_warp_kernel<3>;
+        auto kern = P.degree == 1 ? eval_query_block_kernel<1>
+                  : P.degree == 2 ? eval_query_block_kernel<2> : eval_query_block_kernel<3>;
         KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)smem));
-        kern<<<(unsigned)P.n_q, 32, smem, stream>>>(P);
+        kern<<<(unsigned)P.n_q, kLatencyThreads, smem, stream>>>(P);
         KLR_CHECK_CUDA(cudaGetLastError());
         return KLR_OK;
     }

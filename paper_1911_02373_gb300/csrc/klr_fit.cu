@@ -120,8 +120,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Cholesky of (Ghat - shift I) into the lower triangle of G (leading dim ld);
-// the strict upper triangle keeps Ghat, gdiag its diagonal.  Warp-cooperative.
-__device__ bool warp_cholesky(double* G, const double* gdiag, int u, int ld, double shift) {
+// the strict upper triangle keeps Ghat, gdiag its diagonal, rinv receives the
+// reciprocals of the factor's diagonal.  Warp-cooperative.  GB300 issues FP64
+// at 1/64 of the FP32 rate, so the count of FP64 warp instructions on the
+// chain decides the time: one reciprocal square root per column, the column
+// scaled by it, and the trailing update spread over the lanes pair by pair
+// (about n^2 / 64 instructions for an n x n trailing block, not n).
+__device__ bool warp_cholesky(double* G, const double* gdiag, double* rinv, int u, int ld,
+                              double shift) {
     const int lane = lane_id();
     for (int idx = lane; idx < u * u; idx += 32) {
         int i = idx / u, j = idx % u;
@@ -130,33 +136,42 @@ __device__ bool warp_cholesky(double* G, const double* gdiag, int u, int ld, dou
     }
     __syncwarp();
     for (int k = 0; k < u; ++k) {
-        double akk = G[k * ld + k];
+        const double akk = G[k * ld + k];
         if (!(akk > 0.0)) return false;   // uniform across the warp
-        double lkk = sqrt(akk);
-        for (int i = k + 1 + lane; i < u; i += 32) G[i * ld + k] /= lkk;
+        const double r = rsqrt(akk);
+        for (int i = k + 1 + lane; i < u; i += 32) G[i * ld + k] *= r;
         __syncwarp();
-        if (lane == 0) G[k * ld + k] = lkk;
-        for (int i = k + 1 + lane; i < u; i += 32) {
-            double lik = G[i * ld + k];
-            for (int j = k + 1; j <= i; ++j) G[i * ld + j] -= lik * G[j * ld + k];
+        if (lane == 0) {
+            G[k * ld + k] = akk * r;
+            rinv[k] = r;
+        }
+        // trailing update G[i][j] -= L[i][k] L[j][k], k < j <= i: pair p of
+        // the n x n lower triangle is row rr, column p - rr (rr + 1) / 2
+        const int n = u - k - 1;
+        for (int p = lane; p < n * (n + 1) / 2; p += 32) {
+            int rr = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+            while ((rr + 1) * (rr + 2) / 2 <= p) ++rr;
+            while (rr * (rr + 1) / 2 > p) --rr;
+            const int i = k + 1 + rr, j = k + 1 + (p - rr * (rr + 1) / 2);
+            G[i * ld + j] -= G[i * ld + k] * G[j * ld + k];
         }
         __syncwarp();
     }
     return true;
 }
 
-// Solve (L L^T) w = b in place (w holds b on entry).
-__device__ void warp_chol_solve(const double* G, int u, int ld, double* w) {
+// Solve (L L^T) w = b in place (w holds b on entry; rinv = 1 / diag L).
+__device__ void warp_chol_solve(const double* G, const double* rinv, int u, int ld, double* w) {
     const int lane = lane_id();
     for (int k = 0; k < u; ++k) {
-        double yk = w[k] / G[k * ld + k];
+        const double yk = w[k] * rinv[k];
         __syncwarp();
         for (int i = k + 1 + lane; i < u; i += 32) w[i] -= G[i * ld + k] * yk;
         if (lane == 0) w[k] = yk;
         __syncwarp();
     }
     for (int k = u - 1; k >= 0; --k) {
-        double xk = w[k] / G[k * ld + k];
+        const double xk = w[k] * rinv[k];
         __syncwarp();
         for (int i = lane; i < k; i += 32) w[i] -= G[k * ld + i] * xk;
         if (lane == 0) w[k] = xk;
@@ -195,8 +210,13 @@ __device__ double warp_orth_normalise(double* w, const double* v, int u, bool or
         for (int i = lane_id(); i < u; i += 32) w[i] -= c * v[i];
         __syncwarp();
     }
-    double n = sqrt(warp_dot(w, w, u));
-    if (n > 0.0) warp_scale(w, u, 1.0 / n);
+    const double n2 = warp_dot(w, w, u);
+    double n = 0.0;
+    if (n2 > 0.0) {
+        const double rn = rsqrt(n2);
+        n = n2 * rn;
+        warp_scale(w, u, rn);
+    }
     __syncwarp();
     return n;
 }
@@ -864,6 +884,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     double* v = D + u;
     double* w = v + u;
     double* t = w + u;
+    double* rinv = t + u;
     const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
     const TS* X = reinterpret_cast<const TS*>(P.x);
     const TS* Y = reinterpret_cast<const TS*>(P.y);
@@ -941,10 +962,10 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     const double eps = P.gram_eps;
     const double jitter = P.f_jit * eps * trace;
     double shift = -jitter;                       // factor Ghat + jitter I
-    bool ok = warp_cholesky(G, gdiag, u, ld, shift);
+    bool ok = warp_cholesky(G, gdiag, rinv, u, ld, shift);
     if (!ok) {
         shift = -1024.0 * jitter;
-        ok = warp_cholesky(G, gdiag, u, ld, shift);
+        ok = warp_cholesky(G, gdiag, rinv, u, ld, shift);
     }
     if (!ok) {
         status |= KLR_FIT_SOLVE_FAILED;
@@ -960,7 +981,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
         double prev = 1.0;
         for (int it = 0; it < 32; ++it) {
             warp_copy(w, v, u);
-            warp_chol_solve(G, u, ld, v);
+            warp_chol_solve(G, rinv, u, ld, v);
             warp_orth_normalise(v, v, u, false);
             double dv2 = 0.0;
             for (int i = lane; i < u; i += 32) dv2 += (v[i] - w[i]) * (v[i] - w[i]);
@@ -982,7 +1003,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
                 bool ok2 = false;
                 for (int k = 0; k < 8 && !ok2; ++k) {
                     shift = k < 7 ? theta * ladder[k] : -jitter;
-                    ok2 = warp_cholesky(G, gdiag, u, ld, shift);
+                    ok2 = warp_cholesky(G, gdiag, rinv, u, ld, shift);
                 }
                 if (!ok2) {
                     status |= KLR_FIT_SOLVE_FAILED;
@@ -990,7 +1011,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
                     break;
                 }
                 for (int it = 0; it < 4; ++it) {
-                    warp_chol_solve(G, u, ld, v);
+                    warp_chol_solve(G, rinv, u, ld, v);
                     warp_orth_normalise(v, v, u, false);
                 }
                 warp_gram_matvec(G, gdiag, u, ld, v, t);
@@ -1005,7 +1026,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
         __syncwarp();
         warp_orth_normalise(w, v, u, true);
         for (int it = 0; it < 3; ++it) {
-            warp_chol_solve(G, u, ld, w);
+            warp_chol_solve(G, rinv, u, ld, w);
             warp_orth_normalise(w, v, u, true);
         }
         warp_gram_matvec(G, gdiag, u, ld, w, t);
@@ -1018,6 +1039,11 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     if (ok && P.refine > 0 && u <= kRefineMaxU) {
         for (int pass = 0; pass < P.refine; ++pass) {
             constexpr int HM = kRefineMaxU / 2;
+            // with w = D v (D: powers of two, so every scaling below is exact):
+            // r = (A D v)_s = sum_j p_j w_j - (y_s p_j) w_{m+j}, summed term by term,
+            // t_j = D_j sum_s r p_j and t_{m+j} = -D_{m+j} sum_s r (y_s p_j)
+            for (int i = lane; i < u; i += 32) w[i] = D[i] * v[i];
+            __syncwarp();
             double gp[HM], gq[HM];
 #pragma unroll
             for (int j = 0; j < HM; ++j) gp[j] = gq[j] = 0.0;
@@ -1026,25 +1052,27 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
                 for (int vv = 0; vv < nv; ++vv)
                     xs[vv] = (double)X[(int64_t)vv * P.x_stride + s] * (vv == 0 ? n_scale : b_scale);
                 const double ys = (double)Y[s];
-                double ap[HM], aq[HM];
+                double pm[HM], qm[HM];
                 double r = 0.0;
 #pragma unroll
                 for (int j = 0; j < HM; ++j) {
-                    ap[j] = aq[j] = 0.0;
+                    pm[j] = qm[j] = 0.0;
                     if (j < m) {
                         double p = 1.0;
                         for (int vv = 0; vv < nv; ++vv)
                             for (int e = 0; e < P.exps[j][vv]; ++e) p *= xs[vv];
-                        ap[j] = D[j] * p;               // equilibrated row of A
-                        aq[j] = -D[m + j] * ys * p;
-                        r = fma(ap[j], v[j], r);
-                        r = fma(aq[j], v[m + j], r);
+                        pm[j] = p;
+                        qm[j] = ys * p;
+                        r = fma(p, w[j], r);
+                        r = fma(-qm[j], w[m + j], r);
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < HM; ++j) {
-                    gp[j] = fma(r, ap[j], gp[j]);
-                    gq[j] = fma(r, aq[j], gq[j]);
+                    if (j < m) {
+                        gp[j] = fma(r, pm[j], gp[j]);
+                        gq[j] = fma(r, qm[j], gq[j]);
+                    }
                 }
             }
             // reduce across lanes; lane 0 writes t = (A D)^T (A D) v
@@ -1054,8 +1082,8 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
                     double sp = warp_sum(gp[j]);
                     double sq = warp_sum(gq[j]);
                     if (lane == 0) {
-                        t[j] = sp;
-                        t[m + j] = sq;
+                        t[j] = D[j] * sp;
+                        t[m + j] = -D[m + j] * sq;
                     }
                 }
             }
@@ -1064,7 +1092,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
             // residual r = A^T A v - theta v; correction w = (Ghat - shift)^-1 r, orthogonal to v
             for (int i = lane; i < u; i += 32) w[i] = t[i] - theta * v[i];
             __syncwarp();
-            warp_chol_solve(G, u, ld, w);
+            warp_chol_solve(G, rinv, u, ld, w);
             double c = warp_dot(w, v, u);
             for (int i = lane; i < u; i += 32) v[i] -= w[i] - c * v[i];
             __syncwarp();
@@ -2438,10 +2466,11 @@ klr_status launch_moments_binned(const FitParams& P, int n_sm, int rec, int wpb,
 }
 
 template <typename TS>
-klr_status launch_solve_warp(const FitParams& P, size_t smem_optin, cudaStream_t stream) {
+klr_status launch_solve_warp(const FitParams& P, size_t smem_optin, int n_sm, cudaStream_t stream) {
     size_t per_warp = sizeof(double) * (3 * (size_t)P.n_mom + (size_t)P.u * P.ld + 6 * (size_t)P.u);
     per_warp = (per_warp + 15) & ~(size_t)15;
-    int wpb = 4;
+    // a few fits (a latency): one warp per block, so each has an SM's FP64 units
+    int wpb = P.n_fits <= (int64_t)n_sm ? 1 : 4;
     while (wpb > 1 && per_warp * wpb > 96 * 1024) wpb >>= 1;
     if (per_warp * wpb > smem_optin) {
         set_error("klr_fit: %zu bytes of shared memory per fit exceed the device limit", per_warp);
@@ -2731,8 +2760,8 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
             if (st != KLR_OK) return st;
         }
         if (!(stages & STAGE_SOLVE)) return KLR_OK;
-        return s64 ? launch_solve_warp<double>(P, c->smem_optin, stream)
-                   : launch_solve_warp<float>(P, c->smem_optin, stream);
+        return s64 ? launch_solve_warp<double>(P, c->smem_optin, c->n_sm, stream)
+                   : launch_solve_warp<float>(P, c->smem_optin, c->n_sm, stream);
     }
     P.gram_direct = 0;
     klr_status st = ensure_workspace(c, fit_workspace_bytes(b->n_fits, basis.n_mom), stream);
@@ -2775,8 +2804,8 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     if (!(stages & STAGE_SOLVE)) return KLR_OK;
     if (b->refine_iters == 0 && u <= kLaneMaxU)
         return P.mom_dw ? launch_solve_group_dw(P, q_lanes, stream) : launch_solve_lane(P, stream);
-    return s64 ? launch_solve_warp<double>(P, c->smem_optin, stream)
-               : launch_solve_warp<float>(P, c->smem_optin, stream);
+    return s64 ? launch_solve_warp<double>(P, c->smem_optin, c->n_sm, stream)
+               : launch_solve_warp<float>(P, c->smem_optin, c->n_sm, stream);
 }
 
 }  // namespace

@@ -316,8 +316,8 @@ def test_refined_choice_matches_oracle(klr, ctx, eps):
 
 @pytest.mark.parametrize("seed,nv,degree", [(31, 3, 2), (32, 3, 1), (33, 4, 3), (34, 4, 2)])
 def test_fp64_latency_mode_equals_the_kernel_sweep(klr, ctx, seed, nv, degree):
-    """An FP64 argmin of at most 1024 queries runs one warp per query; a larger
-    one runs a block per kernel.  The same queries asked both ways (a batch of
+    """An FP64 argmin of at most 1024 queries runs one block per query; a
+    larger one runs a block per kernel.  The same queries asked both ways (a batch of
     1200, then slices of it) give bitwise equal outputs: index, cycles,
     margin, status bits and launch geometry.  Kernel 1 has no queries, kernel
     0 fits no block, and the sizes include N below every shape."""
