@@ -77,6 +77,10 @@ struct FitParams {
                    // bit 2 left to the per-sample moments kernel by the binned one
     int fallback_only;  // moments_fast_kernel: only the fits with flag bit 2
     int x_exp8;    // x holds uint8 base-2 logarithms (KLR_EXP8)
+    int fit_warps; // solve_warp_kernel: warps per fit (> 1: one fit per block, the
+                   // others join the refinement passes)
+    int mom_warps; // moments_fast_kernel with FP64 sums: warps per fit (> 1: one fit
+                   // per block, the warps over its samples)
     uint8_t exps[kMaxMoments][kMaxVars];
     uint8_t pair[kMaxBasis][kMaxBasis];
 };
@@ -119,13 +123,14 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Cholesky of (Ghat - shift I) into the lower triangle of G (leading dim ld);
-// the strict upper triangle keeps Ghat, gdiag its diagonal, rinv receives the
-// reciprocals of the factor's diagonal.  Warp-cooperative.  GB300 issues FP64
-// at 1/64 of the FP32 rate, so the count of FP64 warp instructions on the
-// chain decides the time: one reciprocal square root per column, the column
-// scaled by it, and the trailing update spread over the lanes pair by pair
-// (about n^2 / 64 instructions for an n x n trailing block, not n).
+// Cholesky of (Ghat - shift I), Ghat = L L^T, kept as the unit lower factor
+// Lt = L diag(L)^-1 in the strict lower triangle of G (leading dim ld) and
+// rinv = 1 / diag(L); the strict upper triangle keeps Ghat, gdiag its
+// diagonal.  Warp-cooperative.  GB300 issues FP64 at 1/64 of the FP32 rate,
+// so the count of FP64 warp instructions on the chain decides the time: one
+// reciprocal square root per column, the column scaled by it, and the
+// trailing update spread over the lanes pair by pair (about n^2 / 64
+// instructions for an n x n trailing block, not n).
 __device__ bool warp_cholesky(double* G, const double* gdiag, double* rinv, int u, int ld,
                               double shift) {
     const int lane = lane_id();
@@ -157,26 +162,76 @@ __device__ bool warp_cholesky(double* G, const double* gdiag, double* rinv, int 
         }
         __syncwarp();
     }
+    // L -> Lt: column k divided by L[k][k]
+    for (int idx = lane; idx < u * u; idx += 32) {
+        const int i = idx / u, j = idx % u;
+        if (i > j) G[i * ld + j] *= rinv[j];
+    }
+    __syncwarp();
     return true;
 }
 
-// Solve (L L^T) w = b in place (w holds b on entry; rinv = 1 / diag L).
-__device__ void warp_chol_solve(const double* G, const double* rinv, int u, int ld, double* w) {
+// Solve Lt diag(rinv)^-2 Lt^T w = b in place (w holds b on entry), with the
+// vector in registers, row i in lane i % 32: a step is one shuffle of the
+// pivot and one fused multiply-add.
+template <int R>
+__device__ void warp_chol_solve_r(const double* G, const double* rinv, int u, int ld, double* w) {
+    const unsigned full = 0xffffffffu;
     const int lane = lane_id();
+    double x[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+        x[r] = i < u ? w[i] : 0.0;
+    }
+#pragma unroll 4
     for (int k = 0; k < u; ++k) {
-        const double yk = w[k] * rinv[k];
-        __syncwarp();
-        for (int i = k + 1 + lane; i < u; i += 32) w[i] -= G[i * ld + k] * yk;
-        if (lane == 0) w[k] = yk;
-        __syncwarp();
+        const int kr = k >> 5;
+        double src = x[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) if (kr == r) src = x[r];
+        const double xk = __shfl_sync(full, src, k & 31);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = lane + 32 * r;
+            if (i > k && i < u) x[r] = fma(-G[i * ld + k], xk, x[r]);
+        }
     }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+        if (i < u) {
+            const double ri = rinv[i];
+            x[r] *= ri * ri;
+        }
+    }
+#pragma unroll 4
     for (int k = u - 1; k >= 0; --k) {
-        const double xk = w[k] * rinv[k];
-        __syncwarp();
-        for (int i = lane; i < k; i += 32) w[i] -= G[k * ld + i] * xk;
-        if (lane == 0) w[k] = xk;
-        __syncwarp();
+        const int kr = k >> 5;
+        double src = x[0];
+#pragma unroll
+        for (int r = 1; r < R; ++r) if (kr == r) src = x[r];
+        const double xk = __shfl_sync(full, src, k & 31);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = lane + 32 * r;
+            if (i < k) x[r] = fma(-G[k * ld + i], xk, x[r]);
+        }
     }
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int i = lane + 32 * r;
+        if (i < u) w[i] = x[r];
+    }
+    __syncwarp();
+}
+
+__device__ void warp_chol_solve(const double* G, const double* rinv, int u, int ld, double* w) {
+    static_assert(2 * kMaxBasis <= 96, "three rows per lane at most");
+    if (u <= 32) warp_chol_solve_r<1>(G, rinv, u, ld, w);
+    else if (u <= 64) warp_chol_solve_r<2>(G, rinv, u, ld, w);
+    else warp_chol_solve_r<3>(G, rinv, u, ld, w);
 }
 
 // y = Ghat v (Ghat in the strict upper triangle + gdiag).
@@ -268,13 +323,17 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
     static_assert(MG * MAXT >= NM, "too few lanes for the moments");
     using TC = typename std::conditional<ACC == ACC_FP64, double, float>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int flag_w[8];
     const int lane = lane_id();
     const int wib = threadIdx.x >> 5;
-    const int f = blockIdx.x * (blockDim.x >> 5) + wib;
+    // W > 1 (FP64 sums only): one fit per block, warp hw takes every W-th tile
+    const int W = ACC == ACC_FP64 ? P.mom_warps : 1;
+    const int hw = W > 1 ? wib : 0;
+    const int f = W > 1 ? (int)blockIdx.x : blockIdx.x * (blockDim.x >> 5) + wib;
     if (f >= P.n_fits) return;
     if (P.fallback_only && (P.flags[f] & 4) == 0) return;   // done by the binned kernel
     TC* stage = reinterpret_cast<TC*>(smem_raw + (size_t)wib * P.warp_smem);
-    const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
+    const int64_t s0 = P.offsets[f] + 32 * hw, s1 = P.offsets[f + 1];
     const TS* Y = reinterpret_cast<const TS*>(P.y);
     const TC sN = (TC)ldexpf(1.0f, -P.n_scale_log2), sB = (TC)ldexpf(1.0f, -P.b_scale_log2);
     const int mg = lane % MG, sg = lane / MG;
@@ -294,9 +353,9 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
         for (int v = 0; v < NV; ++v) cx[v] = load_coord<TS, E8>(P, v, s0 + lane);
         cy = Y[s0 + lane];
     }
-    for (int64_t base = s0; base < s1; base += 32) {
+    for (int64_t base = s0; base < s1; base += 32 * W) {
         const int64_t s = base + lane;
-        const int64_t sn = s + 32;
+        const int64_t sn = s + 32 * W;
         if (sn < s1) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) nx[v] = load_coord<TS, E8>(P, v, sn);
@@ -390,6 +449,38 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
     }
     bad = __any_sync(0xffffffffu, bad);
     inexact = __any_sync(0xffffffffu, inexact);
+    if constexpr (ACC == ACC_FP64) {
+        if (W > 1) {
+            // the warps' sums, added by warp 0 in warp order
+            double* part = reinterpret_cast<double*>(smem_raw + (size_t)W * P.warp_smem);
+            if (sg == 0) {
+#pragma unroll
+                for (int i = 0; i < MAXT; ++i) {
+                    const int mu = mg + MG * i;
+                    if (mu < NM) {
+                        part[hw * 3 * NM + mu] = a0[i];
+                        part[hw * 3 * NM + NM + mu] = a1[i];
+                        part[hw * 3 * NM + 2 * NM + mu] = a2[i];
+                    }
+                }
+            }
+            if (lane == 0) flag_w[hw] = (bad ? 1 : 0) | (inexact ? 2 : 0);
+            __syncthreads();
+            if (hw != 0) return;
+            double* mom = P.mom + (int64_t)f * 3 * NM;
+            for (int idx = lane; idx < 3 * NM; idx += 32) {
+                double acc = part[idx];
+                for (int g = 1; g < W; ++g) acc += part[g * 3 * NM + idx];
+                mom[idx] = acc;
+            }
+            if (lane == 0) {
+                int fl = 0;
+                for (int g = 0; g < W; ++g) fl |= flag_w[g];
+                P.flags[f] = fl;
+            }
+            return;
+        }
+    }
     if (sg == 0) {
         double* mom = P.mom + (int64_t)f * 3 * NM;
 #pragma unroll
@@ -868,16 +959,40 @@ moments_kernel(const __grid_constant__ FitParams P) {
     if (lane == 0) P.flags[f] = (bad ? 1 : 0) | (inexact ? 2 : 0);
 }
 
+// Sums of K values over the 32 lanes (K = 32 or 64): halve the values at
+// each of the five exchange distances, each lane keeping the half its lane
+// bit selects, so that K - K/32 additions replace 5 K of one warp_sum per
+// value.  On return a[i], i < K/32, holds the sum of value (K/32) lane + i.
+template <int K>
+__device__ __forceinline__ void warp_reduce_scatter(double (&a)[K]) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int lvl = 0; lvl < 5; ++lvl) {
+        const int o = 16 >> lvl, half = K >> (lvl + 1);
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const double keep = hi ? a[i + half] : a[i];
+            const double send = hi ? a[i] : a[i + half];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+}
+
 template <typename TS>
 __global__ void __launch_bounds__(128)
 solve_warp_kernel(const __grid_constant__ FitParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = lane_id();
     const int wib = threadIdx.x >> 5;
-    const int f = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int H = P.fit_warps;                  // warps per fit
+    const int h = H > 1 ? wib : 0;              // this warp's rank within its fit
+    const int f = H > 1 ? (int)blockIdx.x : blockIdx.x * (blockDim.x >> 5) + wib;
     if (f >= P.n_fits) return;
     const int nv = P.n_vars, m = P.m, u = P.u, n_mom = P.n_mom, ld = P.ld;
-    double* mom = reinterpret_cast<double*>(smem_raw + (size_t)wib * P.warp_smem);
+    double* mom = reinterpret_cast<double*>(smem_raw + (size_t)(H > 1 ? 0 : wib) * P.warp_smem);
+    double* part = reinterpret_cast<double*>(smem_raw + P.warp_smem);   // H x 64 (H > 1)
+    __shared__ int ok_s;
     double* G = mom + 3 * n_mom;
     double* gdiag = G + u * ld;
     double* D = gdiag + u;
@@ -890,7 +1005,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     const TS* Y = reinterpret_cast<const TS*>(P.y);
     const double n_scale = ldexp(1.0, -P.n_scale_log2);
     const double b_scale = ldexp(1.0, -P.b_scale_log2);
-    for (int i = lane; i < 3 * n_mom && !P.gram_direct; i += 32) {
+    for (int i = lane; i < 3 * n_mom && !P.gram_direct && h == 0; i += 32) {
         if (P.mom_dw) {
             const float2 g = reinterpret_cast<const float2*>(P.mom)[(int64_t)f * 3 * n_mom + i];
             mom[i] = (double)g.x + (double)g.y;
@@ -907,6 +1022,7 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     if (S == 0) status = KLR_FIT_EMPTY;
     else if (bad) status = KLR_FIT_NONFINITE;
     if (status) {
+        if (h != 0) return;
         for (int j = lane; j < u; j += 32) {
             if (P.coef_f64) reinterpret_cast<double*>(P.coef)[(int64_t)f * u + j] = 0.0;
             else reinterpret_cast<float*>(P.coef)[(int64_t)f * u + j] = 0.f;
@@ -919,122 +1035,131 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
     }
     if (inexact) status |= KLR_FIT_INEXACT;
 
-    // ---- assemble the Gram matrix (upper triangle + diagonal) ---------------
-    for (int idx = lane; idx < u * u; idx += 32) {
-        int i = idx / u, j = idx % u;
-        if (j < i) continue;
-        double val;
-        if (P.gram_direct) {
-            val = P.mom[((int64_t)f * u + i) * u + j];
-        } else {
-            int bi = i >= m, bj = j >= m;
-            val = mom[(bi + bj) * n_mom + P.pair[i - bi * m][j - bj * m]];
-            if (bi != bj) val = -val;
+    bool ok = false;
+    double trace = 0.0, theta = 0.0, theta2 = 0.0;
+    if (h == 0) {
+        // ---- assemble the Gram matrix (upper triangle + diagonal) ---------------
+        for (int idx = lane; idx < u * u; idx += 32) {
+            int i = idx / u, j = idx % u;
+            if (j < i) continue;
+            double val;
+            if (P.gram_direct) {
+                val = P.mom[((int64_t)f * u + i) * u + j];
+            } else {
+                int bi = i >= m, bj = j >= m;
+                val = mom[(bi + bj) * n_mom + P.pair[i - bi * m][j - bj * m]];
+                if (bi != bj) val = -val;
+            }
+            if (i == j) gdiag[i] = val;
+            else G[i * ld + j] = val;
         }
-        if (i == j) gdiag[i] = val;
-        else G[i * ld + j] = val;
-    }
-    __syncwarp();
-    // power-of-two equilibration: D_j = 2^-floor(e_j / 2), e_j = frexp exponent of G_jj
-    for (int j = lane; j < u; j += 32) {
-        double g = gdiag[j];
-        double dj = 1.0;
-        if (g > 0.0) {
-            int e;
-            frexp(g, &e);
-            dj = ldexp(1.0, -(e >> 1));
+        __syncwarp();
+        // power-of-two equilibration: D_j = 2^-floor(e_j / 2), e_j = frexp exponent of G_jj
+        for (int j = lane; j < u; j += 32) {
+            double g = gdiag[j];
+            double dj = 1.0;
+            if (g > 0.0) {
+                int e;
+                frexp(g, &e);
+                dj = ldexp(1.0, -(e >> 1));
+            }
+            D[j] = dj;
         }
-        D[j] = dj;
-    }
-    __syncwarp();
-    for (int idx = lane; idx < u * u; idx += 32) {
-        int i = idx / u, j = idx % u;
-        if (j < i) continue;
-        if (i == j) gdiag[i] *= D[i] * D[i];
-        else G[i * ld + j] *= D[i] * D[j];
-    }
-    __syncwarp();
-    double trace = 0.0;
-    for (int i = lane; i < u; i += 32) trace += gdiag[i];
-    trace = warp_sum(trace);
+        __syncwarp();
+        for (int idx = lane; idx < u * u; idx += 32) {
+            int i = idx / u, j = idx % u;
+            if (j < i) continue;
+            if (i == j) gdiag[i] *= D[i] * D[i];
+            else G[i * ld + j] *= D[i] * D[j];
+        }
+        __syncwarp();
+        trace = 0.0;
+        for (int i = lane; i < u; i += 32) trace += gdiag[i];
+        trace = warp_sum(trace);
 
-    // ---- F3: smallest eigenpair by shifted inverse iteration ----------------
-    const double eps = P.gram_eps;
-    const double jitter = P.f_jit * eps * trace;
-    double shift = -jitter;                       // factor Ghat + jitter I
-    bool ok = warp_cholesky(G, gdiag, rinv, u, ld, shift);
-    if (!ok) {
-        shift = -1024.0 * jitter;
+        // ---- F3: smallest eigenpair by shifted inverse iteration ----------------
+        const double eps = P.gram_eps;
+        const double jitter = P.f_jit * eps * trace;
+        double shift = -jitter;                       // factor Ghat + jitter I
         ok = warp_cholesky(G, gdiag, rinv, u, ld, shift);
-    }
-    if (!ok) {
-        status |= KLR_FIT_SOLVE_FAILED;
-    }
-    for (int i = lane; i < u; i += 32) v[i] = 1.0 + 0.0625 * (double)((i * 7) % 11);
-    __syncwarp();
-    warp_orth_normalise(v, v, u, false);
-    double theta = 0.0;
-    if (ok) {
-        // iterate until v stops moving (a large shift, as for the low-precision
-        // Gram matrices, converges slowly): change below 1e-11, or a stall
-        // (rate above 1/2) below 1e-8, at most 32 steps
-        double prev = 1.0;
-        for (int it = 0; it < 32; ++it) {
-            warp_copy(w, v, u);
-            warp_chol_solve(G, rinv, u, ld, v);
-            warp_orth_normalise(v, v, u, false);
-            double dv2 = 0.0;
-            for (int i = lane; i < u; i += 32) dv2 += (v[i] - w[i]) * (v[i] - w[i]);
-            dv2 = warp_sum(dv2);
-            if (it >= 2 && (dv2 <= 1e-22 || (dv2 <= 1e-16 && dv2 >= 0.25 * prev))) break;
-            prev = dv2;
+        if (!ok) {
+            shift = -1024.0 * jitter;
+            ok = warp_cholesky(G, gdiag, rinv, u, ld, shift);
         }
-        warp_gram_matvec(G, gdiag, u, ld, v, t);
-        theta = warp_dot(v, t, u);
-        if (theta > P.f_null * eps * trace) {
-            // A noisy fit: the smallest eigenvalue is well above round-off.  Each
-            // round factors Ghat - sigma I for the largest sigma of a ladder
-            // below the Rayleigh quotient that keeps the matrix positive
-            // definite (so sigma < lambda_min), then iterates; the quotient
-            // moves down toward lambda_min and the next round's shift closer.
-            const double ladder[8] = {1.0 - 1.0 / 64, 1.0 - 1.0 / 32, 1.0 - 1.0 / 16,
-                                      1.0 - 1.0 / 8, 1.0 - 1.0 / 4, 0.5, 0.25, 0.0};
-            for (int round = 0; round < 3 && ok; ++round) {
-                bool ok2 = false;
-                for (int k = 0; k < 8 && !ok2; ++k) {
-                    shift = k < 7 ? theta * ladder[k] : -jitter;
-                    ok2 = warp_cholesky(G, gdiag, rinv, u, ld, shift);
+        if (!ok) {
+            status |= KLR_FIT_SOLVE_FAILED;
+        }
+        for (int i = lane; i < u; i += 32) v[i] = 1.0 + 0.0625 * (double)((i * 7) % 11);
+        __syncwarp();
+        warp_orth_normalise(v, v, u, false);
+        if (ok) {
+            // iterate until v stops moving (a large shift, as for the low-precision
+            // Gram matrices, converges slowly): change below 1e-11, or a stall
+            // (rate above 1/2) below 1e-8, at most 32 steps
+            double prev = 1.0;
+            for (int it = 0; it < 32; ++it) {
+                warp_copy(w, v, u);
+                warp_chol_solve(G, rinv, u, ld, v);
+                warp_orth_normalise(v, v, u, false);
+                double dv2 = 0.0;
+                for (int i = lane; i < u; i += 32) dv2 += (v[i] - w[i]) * (v[i] - w[i]);
+                dv2 = warp_sum(dv2);
+                if (it >= 2 && (dv2 <= 1e-22 || (dv2 <= 1e-16 && dv2 >= 0.25 * prev))) break;
+                prev = dv2;
+            }
+            warp_gram_matvec(G, gdiag, u, ld, v, t);
+            theta = warp_dot(v, t, u);
+            if (theta > P.f_null * eps * trace) {
+                // A noisy fit: the smallest eigenvalue is well above round-off.  Each
+                // round factors Ghat - sigma I for the largest sigma of a ladder
+                // below the Rayleigh quotient that keeps the matrix positive
+                // definite (so sigma < lambda_min), then iterates; the quotient
+                // moves down toward lambda_min and the next round's shift closer.
+                const double ladder[8] = {1.0 - 1.0 / 64, 1.0 - 1.0 / 32, 1.0 - 1.0 / 16,
+                                          1.0 - 1.0 / 8, 1.0 - 1.0 / 4, 0.5, 0.25, 0.0};
+                for (int round = 0; round < 3 && ok; ++round) {
+                    bool ok2 = false;
+                    for (int k = 0; k < 8 && !ok2; ++k) {
+                        shift = k < 7 ? theta * ladder[k] : -jitter;
+                        ok2 = warp_cholesky(G, gdiag, rinv, u, ld, shift);
+                    }
+                    if (!ok2) {
+                        status |= KLR_FIT_SOLVE_FAILED;
+                        ok = false;
+                        break;
+                    }
+                    for (int it = 0; it < 4; ++it) {
+                        warp_chol_solve(G, rinv, u, ld, v);
+                        warp_orth_normalise(v, v, u, false);
+                    }
+                    warp_gram_matvec(G, gdiag, u, ld, v, t);
+                    theta = warp_dot(v, t, u);
                 }
-                if (!ok2) {
-                    status |= KLR_FIT_SOLVE_FAILED;
-                    ok = false;
-                    break;
-                }
-                for (int it = 0; it < 4; ++it) {
-                    warp_chol_solve(G, rinv, u, ld, v);
-                    warp_orth_normalise(v, v, u, false);
-                }
-                warp_gram_matvec(G, gdiag, u, ld, v, t);
-                theta = warp_dot(v, t, u);
             }
         }
-    }
-    // next-smallest eigenvalue: deflated inverse iteration (rank test)
-    double theta2 = 0.0;
-    if (ok) {
-        for (int i = lane; i < u; i += 32) w[i] = 1.0 + 0.03125 * (double)((i * 5) % 13) - 0.5 * (i & 1);
-        __syncwarp();
-        warp_orth_normalise(w, v, u, true);
-        for (int it = 0; it < 3; ++it) {
-            warp_chol_solve(G, rinv, u, ld, w);
+        // next-smallest eigenvalue: deflated inverse iteration (rank test)
+        if (ok) {
+            for (int i = lane; i < u; i += 32) w[i] = 1.0 + 0.03125 * (double)((i * 5) % 13) - 0.5 * (i & 1);
+            __syncwarp();
             warp_orth_normalise(w, v, u, true);
+            for (int it = 0; it < 3; ++it) {
+                warp_chol_solve(G, rinv, u, ld, w);
+                warp_orth_normalise(w, v, u, true);
+            }
+            warp_gram_matvec(G, gdiag, u, ld, w, t);
+            theta2 = warp_dot(w, t, u);
+            if (theta2 <= P.f_rank * eps * trace) status |= KLR_FIT_RANK_DEFICIENT;
         }
-        warp_gram_matvec(G, gdiag, u, ld, w, t);
-        theta2 = warp_dot(w, t, u);
-        if (theta2 <= P.f_rank * eps * trace) status |= KLR_FIT_RANK_DEFICIENT;
     }
 
     // ---- F4: FP64 refinement passes over the samples --------------------------
+    // With H > 1 warps per fit the other warps join here: warp h takes every
+    // H-th group of 32 samples, and warp 0 adds the warps' sums in warp order.
+    if (H > 1) {
+        if (threadIdx.x == 0) ok_s = ok;
+        __syncthreads();
+        ok = ok_s;
+    }
     int passes = 0;
     if (ok && P.refine > 0 && u <= kRefineMaxU) {
         for (int pass = 0; pass < P.refine; ++pass) {
@@ -1042,12 +1167,13 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
             // with w = D v (D: powers of two, so every scaling below is exact):
             // r = (A D v)_s = sum_j p_j w_j - (y_s p_j) w_{m+j}, summed term by term,
             // t_j = D_j sum_s r p_j and t_{m+j} = -D_{m+j} sum_s r (y_s p_j)
-            for (int i = lane; i < u; i += 32) w[i] = D[i] * v[i];
-            __syncwarp();
+            if (h == 0) for (int i = lane; i < u; i += 32) w[i] = D[i] * v[i];
+            if (H > 1) __syncthreads();
+            else __syncwarp();
             double gp[HM], gq[HM];
 #pragma unroll
             for (int j = 0; j < HM; ++j) gp[j] = gq[j] = 0.0;
-            for (int64_t s = s0 + lane; s < s1; s += 32) {
+            for (int64_t s = s0 + 32 * h + lane; s < s1; s += 32 * H) {
                 double xs[kMaxVars];
                 for (int vv = 0; vv < nv; ++vv)
                     xs[vv] = (double)X[(int64_t)vv * P.x_stride + s] * (vv == 0 ? n_scale : b_scale);
@@ -1075,31 +1201,67 @@ solve_warp_kernel(const __grid_constant__ FitParams P) {
                     }
                 }
             }
-            // reduce across lanes; lane 0 writes t = (A D)^T (A D) v
+            // sums over the lanes: value j of gp at slot j, of gq at slot OFF + j;
+            // this lane ends with slots NL lane + i, i < NL
+            double red[2];
+            int NL, OFF;
+            if (m <= 16) {
+                double a32[32];
 #pragma unroll
-            for (int j = 0; j < HM; ++j) {
-                if (j < m) {
-                    double sp = warp_sum(gp[j]);
-                    double sq = warp_sum(gq[j]);
-                    if (lane == 0) {
-                        t[j] = D[j] * sp;
-                        t[m + j] = -D[m + j] * sq;
+                for (int j = 0; j < 16; ++j) { a32[j] = gp[j]; a32[16 + j] = gq[j]; }
+                warp_reduce_scatter<32>(a32);
+                red[0] = a32[0];
+                red[1] = 0.0;
+                NL = 1;
+                OFF = 16;
+            } else {
+                double a64[64];
+#pragma unroll
+                for (int j = 0; j < HM; ++j) { a64[j] = gp[j]; a64[HM + j] = gq[j]; }
+#pragma unroll
+                for (int j = 2 * HM; j < 64; ++j) a64[j] = 0.0;
+                warp_reduce_scatter<64>(a64);
+                red[0] = a64[0];
+                red[1] = a64[1];
+                NL = 2;
+                OFF = HM;
+            }
+            if (H > 1) {
+                for (int i = 0; i < NL; ++i) part[h * 64 + NL * lane + i] = red[i];
+                __syncthreads();
+                if (h == 0)
+                    for (int i = 0; i < NL; ++i) {
+                        double acc = part[NL * lane + i];
+                        for (int g = 1; g < H; ++g) acc += part[g * 64 + NL * lane + i];
+                        red[i] = acc;
+                    }
+            }
+            if (h == 0) {
+                // t = (A D)^T (A D) v
+                for (int i = 0; i < NL; ++i) {
+                    const int slot = NL * lane + i;
+                    if (slot < OFF) {
+                        if (slot < m) t[slot] = D[slot] * red[i];
+                    } else if (slot - OFF < m) {
+                        t[m + slot - OFF] = -D[m + slot - OFF] * red[i];
                     }
                 }
+                __syncwarp();
+                theta = warp_dot(v, t, u);
+                // residual r = A^T A v - theta v; correction w = (Ghat - shift)^-1 r,
+                // orthogonal to v
+                for (int i = lane; i < u; i += 32) w[i] = t[i] - theta * v[i];
+                __syncwarp();
+                warp_chol_solve(G, rinv, u, ld, w);
+                double c = warp_dot(w, v, u);
+                for (int i = lane; i < u; i += 32) v[i] -= w[i] - c * v[i];
+                __syncwarp();
+                warp_orth_normalise(v, v, u, false);
             }
-            __syncwarp();
-            theta = warp_dot(v, t, u);
-            // residual r = A^T A v - theta v; correction w = (Ghat - shift)^-1 r, orthogonal to v
-            for (int i = lane; i < u; i += 32) w[i] = t[i] - theta * v[i];
-            __syncwarp();
-            warp_chol_solve(G, rinv, u, ld, w);
-            double c = warp_dot(w, v, u);
-            for (int i = lane; i < u; i += 32) v[i] -= w[i] - c * v[i];
-            __syncwarp();
-            warp_orth_normalise(v, v, u, false);
             ++passes;
         }
     }
+    if (h != 0) return;
 
     // ---- coefficients: c = D v, unit norm, sign rule --------------------------
     for (int i = lane; i < u; i += 32) w[i] = D[i] * v[i];
@@ -2394,9 +2556,18 @@ klr_status launch_moments(const FitParams& P, int n_mom, int rec, int wpb, cudaS
         FitParams R = P;
         const int rec_ = nm + 3 + ((nm + 3) % 2 == 0 ? 1 : 0);
         R.warp_smem = (int)((32 * rec_ * tc + 15) & ~(size_t)15);
+        int nb = blocks, nw = wpb;
+        size_t smem = (size_t)R.warp_smem * wpb;
+        if (ACC == ACC_FP64 && P.mom_warps > 1) {
+            nb = P.n_fits;
+            nw = P.mom_warps;
+            smem = (size_t)R.warp_smem * nw + sizeof(double) * 3 * nm * nw;
+        } else {
+            R.mom_warps = 1;
+        }
         KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            R.warp_smem * wpb));
-        kern<<<blocks, wpb * 32, (size_t)R.warp_smem * wpb, stream>>>(R);
+                                            (int)smem));
+        kern<<<nb, nw * 32, smem, stream>>>(R);
         KLR_CHECK_CUDA(cudaGetLastError());
         return KLR_OK;
     };
@@ -2469,19 +2640,28 @@ template <typename TS>
 klr_status launch_solve_warp(const FitParams& P, size_t smem_optin, int n_sm, cudaStream_t stream) {
     size_t per_warp = sizeof(double) * (3 * (size_t)P.n_mom + (size_t)P.u * P.ld + 6 * (size_t)P.u);
     per_warp = (per_warp + 15) & ~(size_t)15;
-    // a few fits (a latency): one warp per block, so each has an SM's FP64 units
-    int wpb = P.n_fits <= (int64_t)n_sm ? 1 : 4;
+    FitParams Q = P;
+    Q.warp_smem = (int)per_warp;
+    Q.fit_warps = 1;
+    int wpb = 4;
     while (wpb > 1 && per_warp * wpb > 96 * 1024) wpb >>= 1;
-    if (per_warp * wpb > smem_optin) {
+    size_t smem = per_warp * wpb;
+    int blocks = (P.n_fits + wpb - 1) / wpb;
+    if (P.n_fits <= (int64_t)n_sm) {
+        // a few fits (a latency): a block per fit, and with refinement passes
+        // one warp per scheduler for the passes over the samples
+        Q.fit_warps = P.refine > 0 ? 4 : 1;
+        wpb = Q.fit_warps;
+        smem = per_warp + (Q.fit_warps > 1 ? sizeof(double) * 64 * Q.fit_warps : 0);
+        blocks = P.n_fits;
+    }
+    if (smem > smem_optin) {
         set_error("klr_fit: %zu bytes of shared memory per fit exceed the device limit", per_warp);
         return KLR_ENOTSUP;
     }
-    FitParams Q = P;
-    Q.warp_smem = (int)per_warp;
-    const size_t smem = per_warp * wpb;
     KLR_CHECK_CUDA(cudaFuncSetAttribute(solve_warp_kernel<TS>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    solve_warp_kernel<TS><<<(P.n_fits + wpb - 1) / wpb, wpb * 32, smem, stream>>>(Q);
+    solve_warp_kernel<TS><<<blocks, wpb * 32, smem, stream>>>(Q);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
 }
@@ -2685,11 +2865,15 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     KLR_CHECK_CUDA(cudaSetDevice(c->device));
     // launch shapes: moments warps per block (bits 4-7: 1, 2, 4) and lanes
     // per fit of the group solver (bits 0-3: 2, 4, 8)
-    const int32_t choice = tune_choice(c, fit_tune_key(b), kFitDefaultChoice);
+    // (a batch of at most one fit per SM: one moments warp per block, so the
+    // fits spread over the SMs)
+    const int32_t choice = tune_choice(c, fit_tune_key(b),
+                                       b->n_fits <= (int64_t)c->n_sm ? (kFitDefaultChoice & ~0xF0)
+                                                                     : kFitDefaultChoice);
     const int wpb = 1 << std::min(2, (choice >> 4) & 15);
     const int q_lanes = 2 << std::min(2, choice & 15);
 
-    FitParams P;
+    FitParams P{};
     P.n_fits = b->n_fits;
     P.n_vars = b->n_vars;
     // the moments kernel tabulates powers up to twice the largest bound
@@ -2715,6 +2899,8 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     P.refine = b->refine_iters;
     P.fallback_only = 0;
     P.x_exp8 = b->sample_dtype == KLR_EXP8;
+    // a few FP64 fits (a latency): each fit's samples over one warp per scheduler
+    P.mom_warps = b->precision == KLR_FIT_FP64 && b->n_fits <= (int64_t)c->n_sm ? 4 : 1;
     P.ld = (u % 2) ? u : u + 1;
     memcpy(P.exps, basis.exps, sizeof(P.exps));
     memcpy(P.pair, basis.pair, sizeof(P.pair));
