@@ -35,9 +35,9 @@ METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
 # DRAM bytes (read + write) per sample of the binned moments kernel on this
 # workload's KLR_EXP8 samples, from one ncu capture of the kernel on its
 # 1,000-kernel copy (dram__bytes_read.sum + dram__bytes_write.sum = 57.78 +
-# 0.38 MB over 8,240,324 samples); the traffic of a full launch scales with
-# the sample count.  Summary: profiles/moments_binned_kernel_batched_1000k.md
-MOMENTS_DRAM_BYTES_PER_SAMPLE = 7.058
+# 0.34 MB over 8,240,324 samples); the traffic of a full launch scales with
+# the sample count.
+MOMENTS_DRAM_BYTES_PER_SAMPLE = 7.054
 
 
 def parse():
@@ -333,9 +333,9 @@ def oracle_baseline(seed, per_worker, keep=32):
 # Launches per step of the batched path (fit: binned moments, the per-sample
 # moments kernel over the fits the binned one left, the group solver;
 # argmin: the sweep and the two FP64 tie passes) and the per-unit work of
-# each stage used by the rooflines (SURVEY-style per-unit figures, stated in
-# DESIGN): the moments stage reads 16 B per sample and writes 3 x 35
-# double-word moment sums and a flag per fit; its contraction is u^2 = 420
+# each stage used by the rooflines: the moments stage reads 7 B per sample
+# (KLR_EXP8; 16 B with FP32 coordinates) and writes 3 x 35 double-word
+# moment sums and a flag per fit; its contraction is u^2 = 420
 # flop per sample; the null-vector solve is u^3 = 8000 FP64-class flop per
 # fit; an evaluation is about 70 flop plus the 8 divides of the metric map.
 LAUNCHES_PER_STEP = {"fit_moments": 2, "fit_solve": 1, "argmin": 3}
