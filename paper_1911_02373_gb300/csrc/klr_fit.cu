@@ -531,7 +531,6 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
 constexpr int kBinT = 16;                 // octaves of N per fit
 constexpr int kBinS = 51;                 // block shapes (b0, b1), 5 <= log2 b0 b1 <= 10
 constexpr int kBinC = kBinT * kBinS;      // cells
-static_assert(kBinS % 3 == 0, "the shape fold runs three partial sums");
 constexpr int kBinU = 4;                  // 32-sample tiles per load batch
 constexpr size_t kBinWarpSmem = (size_t)kBinC * (sizeof(float4) + sizeof(uint16_t));
 constexpr int64_t kBinMaxSamples = 65535;   // per fit: a cell count fits in 16 bits
@@ -588,15 +587,14 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
     // cell; after the first fold the float4 region holds F as float2 [3][5][51]
     float4* cv = reinterpret_cast<float4*>(smem_raw);
     uint16_t* cn = reinterpret_cast<uint16_t*>(cv + kBinC);
+    unsigned* cnw = reinterpret_cast<unsigned*>(cn);   // the counts of cells 2w, 2w + 1
     float2* Fs = reinterpret_cast<float2*>(cv);
     const float* Y = reinterpret_cast<const float*>(P.y);
     const int ns = P.n_scale_log2, bs = P.b_scale_log2;
     for (int f = blockIdx.x; f < P.n_fits; f += gridDim.x) {
         const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
-        for (int c = lane; c < kBinC; c += 32) {
-            cv[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-            cn[c] = 0;
-        }
+        for (int c = lane; c < kBinC; c += 32) cv[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int w = lane; w < kBinC / 2; w += 32) cnw[w] = 0u;
         __syncwarp();
         bool fallback = s1 - s0 > kBinMaxSamples;
         // ---- stream: two batches of kBinU tiles in flight ----------------------
@@ -648,7 +646,10 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
                     fallback = true;
                     break;
                 }
-                // lanes with the same cell add one after the other
+                // the count by a shared-memory atomic (16-bit halves: at most
+                // kBinMaxSamples per cell); lanes with the same cell add their
+                // values one after the other
+                if (live) atomicAdd(&cnw[cell >> 1], 1u << ((cell & 1) << 4));
                 const unsigned peers = __match_any_sync(full, cell);
                 const unsigned rank = __popc(peers & lt);
                 const unsigned rounds = __reduce_max_sync(full, rank) + 1u;
@@ -666,7 +667,6 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
                         v.z = hs;
                         v.w = __fadd_rn(v.w, __fadd_rn(e, y2l));
                         cv[cell] = v;
-                        cn[cell] = (uint16_t)(cn[cell] + 1);
                     }
                     __syncwarp();
                 }
@@ -729,44 +729,86 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
             }
         }
         __syncwarp();
-        // ---- fold over the block shapes: items (k, moment) ------------------------
-        // the shape fold with two moments per lane as a packed pair (items it
-        // and it + 53 of 105), two interleaved partial sums over the shapes
+        // ---- fold over the block shapes, one exponent at a time ------------------
+        // Shape (2^e0, 2^e1) scales moment (a, i, j) by 2^(i e0' + j e1'), e' =
+        // e - bs.  First H[k][a, j][e0] = sum over e1 of F[k][a][shape] 2^(j e1')
+        // (items as packed pairs), then moment (k; a, i, j) = sum over e0 of
+        // H[k][a, j][e0] 2^(i e0'): 3 x 15 x 51 + 105 x 11 scaled additions
+        // instead of 105 x 51.  (a, j) with j <= 4 - a is numbered
+        // 5a - a(a - 1)/2 + j.
+        constexpr int kAJ = 15, kE0 = 11, kHA = 3 * kAJ * kE0, kHP = (kHA + 1) / 2;
+        float2* Hs = Fs + 3 * 5 * kBinS;              // [3][15][11] after F
+#pragma unroll 1
+        for (int pi = lane; pi < kHP; pi += 32) {
+            int idx[2], n1[2], Tv[2];
+            const float2* Fp[2];
+            float p0[2], qf[2];
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                const int it = g == 0 ? pi : (pi + kHP < kHA ? pi + kHP : pi);
+                const int e0 = it % kE0, r = it / kE0;
+                const int k = r / kAJ;
+                int aj = r - k * kAJ, a = 0;
+                while (aj >= 5 - a) { aj -= 5 - a; ++a; }
+                const int j = aj;
+                const int e1 = e0 < 5 ? 5 - e0 : 0;   // the first shape with this e0
+                n1[g] = 10 - e0 - e1 + 1;
+                Tv[g] = e0 + e1;
+                idx[g] = bin_shape_index(e0, e1);
+                Fp[g] = Fs + (k * 5 + a) * kBinS;
+                p0[g] = pow2f(j * (e1 - bs));
+                qf[g] = pow2f(j);
+            }
+            f2p h = 0ull, l = 0ull;
+            f2p p = f2p_make(p0[0], p0[1]);
+            const f2p q2 = f2p_make(qf[0], qf[1]);
+#pragma unroll
+            for (int mstep = 0; mstep < 6; ++mstep) {
+                float2 v[2];
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    v[g] = mstep < n1[g] ? Fp[g][idx[g]] : make_float2(0.f, 0.f);
+                    idx[g] += Tv[g] + 2;   // index of (e0, e1 + 1): T (T + 1) / 2 grows by T + 1
+                    Tv[g] += 1;
+                }
+                dw_acc_scaled2(h, l, f2p_make(v[0].x, v[1].x), f2p_make(v[0].y, v[1].y), p);
+                p = f2p_mul(p, q2);
+            }
+            const float2 hh = f2p_get(h), ll = f2p_get(l);
+            const dw r0 = dw_2sum(hh.x, ll.x);
+            Hs[pi] = make_float2(r0.h, r0.l);
+            if (pi + kHP < kHA) {
+                const dw r1 = dw_2sum(hh.y, ll.y);
+                Hs[pi + kHP] = make_float2(r1.h, r1.l);
+            }
+        }
+        __syncwarp();
         float2* mom = reinterpret_cast<float2*>(P.mom) + (int64_t)f * 3 * 35;
 #pragma unroll 1
         for (int it = lane; it < 53; it += 32) {
             const int i2 = it + 53;                 // item 105 does not exist
             const bool two = i2 < 3 * 35;
-            int kk[2], aa[2], ii[2], jj[2];
             const int items[2] = {it, two ? i2 : it};
+            const float2* Hp[2];
+            float p0[2], qf[2];
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
-                kk[g] = items[g] / 35;
-                const int mu = items[g] - kk[g] * 35;
-                aa[g] = c_mono34.e[mu][0]; ii[g] = c_mono34.e[mu][1]; jj[g] = c_mono34.e[mu][2];
+                const int kk = items[g] / 35, mu = items[g] - kk * 35;
+                const int a = c_mono34.e[mu][0], i = c_mono34.e[mu][1], j = c_mono34.e[mu][2];
+                Hp[g] = Hs + (kk * kAJ + 5 * a - a * (a - 1) / 2 + j) * kE0;
+                p0[g] = pow2f(-i * bs);
+                qf[g] = pow2f(i);
             }
-            const float2* F0 = Fs + (kk[0] * 5 + aa[0]) * kBinS;
-            const float2* F1 = Fs + (kk[1] * 5 + aa[1]) * kBinS;
-            f2p h[2] = {0ull, 0ull}, l[2] = {0ull, 0ull};
-#pragma unroll 1
-            for (int sh = 0; sh < kBinS - 1; sh += 2) {
+            f2p h = 0ull, l = 0ull;
+            f2p p = f2p_make(p0[0], p0[1]);
+            const f2p q2 = f2p_make(qf[0], qf[1]);
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int e0 = c_bin_shapes.e[sh + q][0] - bs, e1 = c_bin_shapes.e[sh + q][1] - bs;
-                    const float2 v0 = F0[sh + q], v1 = F1[sh + q];
-                    const f2p p = f2p_make(pow2f(ii[0] * e0 + jj[0] * e1), pow2f(ii[1] * e0 + jj[1] * e1));
-                    dw_acc_scaled2(h[q], l[q], f2p_make(v0.x, v1.x), f2p_make(v0.y, v1.y), p);
-                }
+            for (int e0 = 0; e0 < kE0; ++e0) {
+                const float2 v0 = Hp[0][e0], v1 = Hp[1][e0];
+                dw_acc_scaled2(h, l, f2p_make(v0.x, v1.x), f2p_make(v0.y, v1.y), p);
+                p = f2p_mul(p, q2);
             }
-            {   // the last shape (51 is odd)
-                const int sh = kBinS - 1;
-                const int e0 = c_bin_shapes.e[sh][0] - bs, e1 = c_bin_shapes.e[sh][1] - bs;
-                const float2 v0 = F0[sh], v1 = F1[sh];
-                const f2p p = f2p_make(pow2f(ii[0] * e0 + jj[0] * e1), pow2f(ii[1] * e0 + jj[1] * e1));
-                dw_acc_scaled2(h[0], l[0], f2p_make(v0.x, v1.x), f2p_make(v0.y, v1.y), p);
-            }
-            dw_acc_scaled2(h[0], l[0], h[1], l[1], f2p_make(1.f, 1.f));
-            const float2 hh = f2p_get(h[0]), ll = f2p_get(l[0]);
+            const float2 hh = f2p_get(h), ll = f2p_get(l);
             const dw q0 = dw_2sum(hh.x, ll.x);
             mom[it] = make_float2(q0.h, q0.l);
             if (two) {
