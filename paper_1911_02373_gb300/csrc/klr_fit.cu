@@ -598,21 +598,31 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
         __syncwarp();
         bool fallback = s1 - s0 > kBinMaxSamples;
         // ---- stream: two batches of kBinU tiles in flight ----------------------
+        // (32-bit sample indices within the fit: at most kBinMaxSamples)
+        const int ns_f = fallback ? 0 : (int)(s1 - s0);
+        const float* Yf = Y + s0;
+        const unsigned char* xb[3];
+#pragma unroll
+        for (int v = 0; v < 3; ++v)
+            xb[v] = reinterpret_cast<const unsigned char*>(P.x) +
+                    ((int64_t)v * P.x_stride + s0) * (E8 ? 1 : (int64_t)sizeof(float));
         float nb[kBinU][4] = {};
-        auto load = [&](int64_t base, float (&b)[kBinU][4]) {
+        auto load = [&](int base, float (&b)[kBinU][4]) {
 #pragma unroll
             for (int u = 0; u < kBinU; ++u) {
-                const int64_t s = base + u * 32 + lane;
-                if (s < s1) {
-                    b[u][0] = load_coord<float, E8>(P, 0, s);
-                    b[u][1] = load_coord<float, E8>(P, 1, s);
-                    b[u][2] = load_coord<float, E8>(P, 2, s);
-                    b[u][3] = Y[s];
+                const int si = base + u * 32 + lane;
+                if (si < ns_f) {
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) {
+                        if constexpr (E8) b[u][v] = __uint_as_float((unsigned)xb[v][si]);
+                        else b[u][v] = reinterpret_cast<const float*>(xb[v])[si];
+                    }
+                    b[u][3] = Yf[si];
                 }
             }
         };
-        if (!fallback) load(s0, nb);
-        for (int64_t base = s0; base < s1 && !fallback; base += 32 * kBinU) {
+        load(0, nb);
+        for (int base = 0; base < ns_f && !fallback; base += 32 * kBinU) {
             float cb[kBinU][4];
 #pragma unroll
             for (int u = 0; u < kBinU; ++u) {
@@ -620,12 +630,11 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
                 for (int v = 0; v < 3; ++v) cb[u][v] = coord_value<float, E8>(nb[u][v]);
                 cb[u][3] = nb[u][3];
             }
-            if (base + 32 * kBinU < s1) load(base + 32 * kBinU, nb);
+            if (base + 32 * kBinU < ns_f) load(base + 32 * kBinU, nb);
 #pragma unroll
             for (int u = 0; u < kBinU; ++u) {
-                const int64_t s = base + u * 32 + lane;
-                const bool live = s < s1;
-                if (!__any_sync(full, live)) break;
+                if (base + u * 32 >= ns_f) break;   // (uniform)
+                const bool live = base + u * 32 + lane < ns_f;
                 int cell = -1 - lane;   // distinct for idle lanes
                 bool ok = true;
                 if (live) {
