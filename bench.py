@@ -472,6 +472,8 @@ def run_klr(args, cb_kept=None):
     ck = clocks.stop()
     total_ms = start.elapsed_time(stop)
     ms_step, units = whole_job(total_ms / K, n_q, dist, dev)
+    # the device's measured arithmetic peaks (outside the timed region)
+    mpk = ctx.probe_peaks(stream)
     # per-stage breakdown (outside the timed region): each stage's graph
     # replayed with events between stages on the launching stream
     KB = max(3, min(K, 50))
@@ -618,8 +620,10 @@ def run_klr(args, cb_kept=None):
     # above the FP32 ridge of ~12 flop/B): its roofline is the FP32 FMA peak;
     # the HBM fraction of its algorithmic bytes is reported beside it
     mom_flops = FLOP_PER_SAMPLE * n_samples / t_mom / 1e12
+    fp32_meas = max(mpk["fp32_fma_tflops"], mpk["fp32x2_fma_tflops"])
     moments_rf = {"bound": "alu", "achieved": mom_flops, "peak": fp32_peak,
                   "unit": "TFLOP/s", "frac": mom_flops / fp32_peak,
+                  "peak_measured": fp32_meas, "frac_of_measured": mom_flops / fp32_meas,
                   "traffic": (MOMENTS_DRAM_BYTES_PER_SAMPLE * n_samples
                               if MOMENTS_DRAM_BYTES_PER_SAMPLE else None),
                   "kernel": "moments_binned_kernel (+ moments_fast_kernel over left fits)",
@@ -634,10 +638,14 @@ def run_klr(args, cb_kept=None):
                 "frac": FLOP_PER_FIT * n_fits / t_sol / 1e12 / FP64_PEAK_TFLOPS,
                 "traffic": None, "kernel": "solve_group_dw_kernel (double-word FP32)",
                 "frac_of_fp32_peak": FLOP_PER_FIT * n_fits / t_sol / 1e12 / fp32_peak,
+                "peak_measured": mpk["fp64_fma_tflops"],
+                "frac_of_measured": FLOP_PER_FIT * n_fits / t_sol / 1e12 / mpk["fp64_fma_tflops"],
                 "peak_source": "nominal FP64 (the solve's precision class); u^3 per fit"}
     argmin_rf = {"bound": "alu", "achieved": FLOP_PER_EVAL * evals / t_arg / 1e12,
                  "peak": fp32_peak, "unit": "TFLOP/s",
                  "frac": FLOP_PER_EVAL * evals / t_arg / 1e12 / fp32_peak, "traffic": None,
+                 "peak_measured": fp32_meas,
+                 "frac_of_measured": FLOP_PER_EVAL * evals / t_arg / 1e12 / fp32_meas,
                  "kernel": "eval_kernel<float, 2> + tie_kernel (2 passes)",
                  "peak_source": f"FP32 FMA lanes x {n_sm} SMs x max clock"}
     rooflines = {"fit_moments": moments_rf, "fit_solve": solve_rf, "argmin": argmin_rf}
@@ -671,6 +679,7 @@ def run_klr(args, cb_kept=None):
         "kernel_ms": part_ms,
         "roofline": dict(rooflines[dominant], stage=dominant),
         "rooflines": rooflines,
+        "measured_peaks": dict(mpk, method="klr_probe_peaks: independent chains of one instruction, 64 warps per SM, best of 5 (CUDA events)"),
         "table": {"ms": table_ms, "evals_per_s": evals / (table_ms * 1e-3),
                   "bytes": table_bytes, "gbs": table_bytes / (table_ms * 1e-3) / 1e9,
                   "hbm_frac": table_bytes / (table_ms * 1e-3) / 1e9 / hbm_peak,

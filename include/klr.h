@@ -511,6 +511,29 @@ klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw,
                               int32_t* best_idx, float* best_cycles, float* margin,
                               int32_t* q_status, int32_t* launch_out, void* stream);
 
+/* ---- measured peaks ----------------------------------------------------------
+ * The denominators of the rooflines of the ALU-bound kernels, measured on the
+ * context's device: each probe runs independent dependency chains of one
+ * instruction (8 per thread, 64 warps per SM) and takes the best of five
+ * timed launches (CUDA events).  Units: 10^12 flop/s (an FMA is 2 flop) or
+ * 10^12 operations/s.
+ *   fp32_fma_tflops       FFMA (fma.rn.f32)
+ *   fp32x2_fma_tflops     packed FFMA2 (fma.rn.f32x2, 4 flop per instruction)
+ *   fp64_fma_tflops       DFMA (fma.rn.f64)
+ *   mufu_rcp_tops         reciprocal approximations (rcp.approx.ftz.f32)
+ *   tf32_mma_sync_tflops  mma.sync.m16n8k8 TF32 with FP32 accumulation, the
+ *                         instruction of the precision modes' Gram products
+ * Synchronous: waits for `stream` (not capturable: KLR_EINVAL while it
+ * captures a graph); allocates and frees a few KB of device memory. */
+typedef struct klr_peaks {
+    double fp32_fma_tflops;
+    double fp32x2_fma_tflops;
+    double fp64_fma_tflops;
+    double mufu_rcp_tops;
+    double tf32_mma_sync_tflops;
+} klr_peaks;
+klr_status klr_probe_peaks(klr_ctx* ctx, klr_peaks* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

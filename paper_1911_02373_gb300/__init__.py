@@ -37,7 +37,7 @@ ABI_SYMBOLS = ("klr_ctx_create", "klr_ctx_destroy", "klr_ctx_reserve", "klr_last
                "klr_autotune_argmin", "klr_tune_export", "klr_tune_import", "klr_fit_gram",
                "klr_fit_solve", "klr_mlp_query_targets", "klr_history_create",
                "klr_history_clear", "klr_history_destroy", "klr_argmin_history",
-               "klr_argmin_refined", "klr_fit_heldout", "klr_choose_basis")
+               "klr_argmin_refined", "klr_fit_heldout", "klr_choose_basis", "klr_probe_peaks")
 #: largest query count klr_argmin_noalloc accepts
 ARGMIN_NOALLOC_MAX_QUERIES = 65536
 ARGMIN_NOALLOC_TIE_RECORDS = 16384   # FP32 near-ties it lists; more are decided in place
@@ -89,6 +89,12 @@ class MlpNet(ctypes.Structure):
                 ("step", ctypes.c_int64), ("hw_feat", ctypes.c_float * 7)]
 
 
+class Peaks(ctypes.Structure):
+    _fields_ = [("fp32_fma_tflops", ctypes.c_double), ("fp32x2_fma_tflops", ctypes.c_double),
+                ("fp64_fma_tflops", ctypes.c_double), ("mufu_rcp_tops", ctypes.c_double),
+                ("tf32_mma_sync_tflops", ctypes.c_double)]
+
+
 class MlpRows(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("kernel", ctypes.c_void_p), ("N", ctypes.c_void_p),
                 ("cfg_idx", ctypes.c_void_p), ("target", ctypes.c_void_p)]
@@ -120,6 +126,7 @@ for _name, _args in {
     "klr_choose_basis": [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
                          ctypes.c_double, _vp, _vp],
     "klr_history_create": [_vp, ctypes.c_int32, ctypes.POINTER(_vp)],
+    "klr_probe_peaks": [_vp, ctypes.POINTER(Peaks), _vp],
     "klr_history_clear": [_vp, _vp],
     "klr_argmin_refined": [_vp, ctypes.POINTER(Program), ctypes.POINTER(Hw), _vp, ctypes.c_int,
                            ctypes.POINTER(Queries), _vp, ctypes.c_double, _vp, _vp, _vp, _vp],
@@ -300,6 +307,13 @@ class Context:
                                                          n_fits, n_cand, tol, floor, _ptr(out),
                                                          _stream(stream)))
         return out
+
+    def probe_peaks(self, stream=None):
+        """klr_probe_peaks: the device's measured arithmetic peaks (a dict of
+        10^12 flop/s or operations/s; synchronous)."""
+        pk = Peaks()
+        _check("klr_probe_peaks", _lib.klr_probe_peaks(self._h, ctypes.byref(pk), _stream(stream)))
+        return {name: float(getattr(pk, name)) for name, _ in Peaks._fields_}
 
     # -- tuned launch shapes -------------------------------------------------
     def tune_export(self):

@@ -87,3 +87,9 @@ def test_binding_refuses_host_tensors_for_device_arguments():
     with pytest.raises(ValueError):
         klr._ptr(torch.zeros(4, dtype=torch.int32))
     assert klr._ptr(None) is None
+
+
+def test_probe_peaks_refuses_a_null_context():
+    klr = _lib_or_skip()
+    pk = klr.Peaks()
+    assert klr._lib.klr_probe_peaks(None, ctypes.byref(pk), None) == klr.EINVAL
