@@ -2232,6 +2232,8 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
         __syncwarp();
     };
     start_vector();
+    float2 bas[kLanczosSteps][MAXR];   // the Lanczos vectors q_j, this lane's rows
+    float sv[kLanczosSteps];           // the top eigenvector of their projection
     // Phase 1: Lanczos on T = (Ghat - shift I)^-1 from the start vector, by
     // its three-term recurrence (every group runs the same kLanczosSteps
     // solves): alpha_j = q_j . T q_j, r = T q_j - alpha_j q_j - beta_{j-1}
@@ -2249,6 +2251,20 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
         dw bprev{0.f, 0.f};
 #pragma unroll 1
         for (int j = 0; j < kLanczosSteps; ++j) {
+            // keep q_j's rows of this lane for the Ritz vector
+            {
+                float2 cur[MAXR];
+#pragma unroll
+                for (int r = 0; r < MAXR; ++r) {
+                    const int i = q + r * Q;
+                    cur[r] = i < u ? vv[i] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int jj = 0; jj < kLanczosSteps; ++jj)
+#pragma unroll
+                    for (int r = 0; r < MAXR; ++r)
+                        if (jj == j) bas[jj][r] = cur[r];
+            }
             for (int i = q; i < u; i += Q) wv[i] = vv[i];
             __syncwarp();
             solve(ok);
@@ -2275,12 +2291,31 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
             }
             bprev = bj;
         }
-        float sv[kLanczosSteps];
-        const float mu = tridiag_top_eigen<kLanczosSteps, false>(la, lb, sv);
+        const float mu = tridiag_top_eigen<kLanczosSteps, true>(la, lb, sv);
         if (ok) theta = dw_add(shift, dw_div(dw{1.f, 0.f}, dw{mu > 0.f ? mu : FLT_MIN, 0.f}));
     }
-    // the iterations below start again from the start vector
-    start_vector();
+    // the iterations below start from the Ritz vector sum_j s_j q_j (the
+    // start vector where it is not usable)
+    {
+#pragma unroll
+        for (int r = 0; r < MAXR; ++r) {
+            const int i = q + r * Q;
+            dw y{0.f, 0.f};
+#pragma unroll
+            for (int jj = 0; jj < kLanczosSteps; ++jj)
+                y = dw_add(y, dw_mul_f(ld2(bas[jj][r]), sv[jj]));
+            if (i < u) vv[i] = st2(y);
+        }
+        __syncwarp();
+        const dw nn = gdot(vv, vv);
+        if (!(nn.h > 0.f && isfinite(nn.h)))
+            for (int i = q; i < u; i += Q)
+                vv[i] = make_float2(1.0f + 0.0625f * (float)((i * 7) % 11), 0.f);
+        __syncwarp();
+        const dw inv = dw_rsqrt(gdot(vv, vv));
+        for (int i = q; i < u; i += Q) vv[i] = st2(dw_mul(ld2(vv[i]), inv));
+        __syncwarp();
+    }
     bool active = ok;
     float dv2 = 1.f, prev = 1.f;
     // noisy fits: rounds of re-factoring on a ladder of shifts below theta
