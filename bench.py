@@ -34,10 +34,10 @@ WORKLOAD = dict(name="batched_fit_eval_fp32", kernels=10000, metrics=8, counts=(
 METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
 # DRAM bytes (read + write) per sample of the binned moments kernel on this
 # workload's KLR_EXP8 samples, from one ncu capture of the kernel on its
-# 1,000-kernel copy (dram__bytes_read.sum + dram__bytes_write.sum = 57.78 +
-# 0.34 MB over 8,240,324 samples); the traffic of a full launch scales with
+# 1,000-kernel copy (dram__bytes_read.sum + dram__bytes_write.sum = 57.79 +
+# 0.38 MB over 8,240,324 samples); the traffic of a full launch scales with
 # the sample count.
-MOMENTS_DRAM_BYTES_PER_SAMPLE = 7.054
+MOMENTS_DRAM_BYTES_PER_SAMPLE = 7.059
 
 
 def parse():
