@@ -1909,7 +1909,7 @@ solve_lane_dw_kernel(const __grid_constant__ FitParams P) {
 // group's success (false also when not writing).
 template <int Q>
 __device__ __noinline__ bool group_cholesky(float2* Lf, float2* rinv, const float2* M,
-                                            const uint8_t (*pair)[kMaxBasis], const float2* Dv,
+                                            const uint8_t (*pair)[kMaxBasis], const float* Dv,
                                             int m, int u, int n_mom, dw shift, bool write) {
     const unsigned full = 0xffffffffu;
     const int q = (threadIdx.x & 31) % Q;
@@ -1918,7 +1918,7 @@ __device__ __noinline__ bool group_cholesky(float2* Lf, float2* rinv, const floa
     auto gh = [&](int i, int j) -> dw {
         const int bi = i >= m, bj = j >= m;
         const float2 gg = M[(bi + bj) * n_mom + pair[i - bi * m][j - bj * m]];
-        const float sc = ((bi != bj) ? -1.f : 1.f) * Dv[i].x * Dv[j].x;
+        const float sc = ((bi != bj) ? -1.f : 1.f) * Dv[i] * Dv[j];
         return dw{gg.x * sc, gg.y * sc};
     };
     bool good = write;
@@ -2119,7 +2119,7 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
     float2* rinv = Lf + nL;
     float2* vv = rinv + u;
     float2* wv = vv + u;
-    float2* Dv = wv + u;
+    float* Dv = reinterpret_cast<float*>(wv + u);   // the powers of two D, u floats
     auto ld2 = [](const float2 v) -> dw { return dw{v.x, v.y}; };
     auto st2 = [](dw x) -> float2 { return make_float2(x.h, x.l); };
     const unsigned full = 0xffffffffu;
@@ -2153,14 +2153,14 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
             if (mant == 0.5f && g2.y < 0.f) e -= 1;
             dj = ldexpf(1.0f, -(e >> 1));
         }
-        if (q == 0) Dv[j] = make_float2(dj, 0.f);
+        if (q == 0) Dv[j] = dj;
         trace = dw_add(trace, dw{g2.x * dj * dj, g2.y * dj * dj});
     }
     __syncwarp();
     auto gh = [&](int i, int j) -> dw {
         const int bi = i >= m, bj = j >= m;
         const float2 gg = M[(bi + bj) * n_mom + P.pair[i - bi * m][j - bj * m]];
-        const float sc = ((bi != bj) ? -1.f : 1.f) * Dv[i].x * Dv[j].x;
+        const float sc = ((bi != bj) ? -1.f : 1.f) * Dv[i] * Dv[j];
         return dw{gg.x * sc, gg.y * sc};
     };
     // Cholesky of (Ghat - shift I) for groups with `write`; returns the
@@ -2246,7 +2246,7 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
     // about 1e-5, far from the square root of the rounding where Lanczos
     // loses it), so no basis is stored and no reorthogonalisation is needed.
     {
-        float2* pv = Dv + u;        // the previous Lanczos vector
+        float2* pv = wv + u + (u + 1) / 2;   // the previous Lanczos vector (after D)
         float la[kLanczosSteps], lb[kLanczosSteps];
         dw bprev{0.f, 0.f};
 #pragma unroll 1
@@ -2424,7 +2424,7 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
         }
     }
     // c = D v, unit norm, sign rule; lane q writes coefficients i = q mod Q
-    for (int i = q; i < u; i += Q) wv[i] = st2(dw_mul_f(ld2(vv[i]), Dv[i].x));
+    for (int i = q; i < u; i += Q) wv[i] = st2(dw_mul_f(ld2(vv[i]), Dv[i]));
     __syncwarp();
     const dw nrm = dw_sqrt(gdot(wv, wv));
     float sgn = 1.f;
@@ -2769,9 +2769,12 @@ klr_status launch_solve_group_dw_q(const FitParams& P, cudaStream_t stream) {
         return KLR_ENOTSUP;
     }
     FitParams Q_ = P;
-    // L, 1/L_jj, v, w, D and the previous Lanczos vector
-    int stride = P.u * (P.u + 1) / 2 + 5 * P.u;
-    if (stride % 2 == 0) ++stride;          // spread the groups over the banks
+    // L, 1/L_jj, v, w, D (floats) and the previous Lanczos vector
+    int stride = P.u * (P.u + 1) / 2 + 4 * P.u + (P.u + 1) / 2;
+    // stride = Q mod 2Q float2: the eight groups of a half-warp then meet
+    // fewest shared-memory bank conflicts in the solves and the factor (the
+    // lanes of a group read rows i, i + 1, ... of one column)
+    while (stride % (2 * Q) != Q) ++stride;
     Q_.ld = stride;
     const size_t smem = sizeof(float2) * (size_t)stride * GPW;
     KLR_CHECK_CUDA(cudaFuncSetAttribute(solve_group_dw_kernel<Q, MAXR>,
