@@ -1454,13 +1454,10 @@ klr_status klr_argmin(klr_ctx* ctx, const klr_program* prog, const klr_hw* hw,
         P.tie_cap = tie_capacity(P.n_q);
         KLR_CHECK_CUDA(cudaMemsetAsync(P.tie_count, 0, sizeof(int), stream));
     }
-    if (f64 && P.n_q <= kLatencyMaxQueries) {
-        // a few FP64 queries: one block each, spread over the SMs
+    if (f64 && P.n_q <= kLatencyMaxQueries && latency_smem_bytes(P) <= c->smem_optin) {
+        // a few FP64 queries: one block each, spread over the SMs (its tables
+        // add the block-shape monomials; without room for them, the sweep)
         const size_t smem = latency_smem_bytes(P);
-        if (smem > c->smem_optin) {
-            set_error("evaluator needs %zu bytes of shared memory", smem);
-            return KLR_ENOTSUP;
-        }
         auto kern = P.degree == 1 ? eval_query_block_kernel<1>
                   : P.degree == 2 ? eval_query_block_kernel<2> : eval_query_block_kernel<3>;
         KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
