@@ -131,7 +131,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 // reciprocal square root per column, the column scaled by it, and the
 // trailing update spread over the lanes pair by pair (about n^2 / 64
 // instructions for an n x n trailing block, not n).
-__device__ bool warp_cholesky(double* G, const double* gdiag, double* rinv, int u, int ld,
+__device__ __noinline__ bool warp_cholesky(double* G, const double* gdiag, double* rinv, int u, int ld,
                               double shift) {
     const int lane = lane_id();
     for (int idx = lane; idx < u * u; idx += 32) {
@@ -227,7 +227,7 @@ __device__ void warp_chol_solve_r(const double* G, const double* rinv, int u, in
     __syncwarp();
 }
 
-__device__ void warp_chol_solve(const double* G, const double* rinv, int u, int ld, double* w) {
+__device__ __noinline__ void warp_chol_solve(const double* G, const double* rinv, int u, int ld, double* w) {
     static_assert(2 * kMaxBasis <= 96, "three rows per lane at most");
     if (u <= 32) warp_chol_solve_r<1>(G, rinv, u, ld, w);
     else if (u <= 64) warp_chol_solve_r<2>(G, rinv, u, ld, w);
@@ -235,7 +235,7 @@ __device__ void warp_chol_solve(const double* G, const double* rinv, int u, int 
 }
 
 // y = Ghat v (Ghat in the strict upper triangle + gdiag).
-__device__ void warp_gram_matvec(const double* G, const double* gdiag, int u, int ld,
+__device__ __noinline__ void warp_gram_matvec(const double* G, const double* gdiag, int u, int ld,
                                  const double* v, double* y) {
     const int lane = lane_id();
     for (int i = lane; i < u; i += 32) {
@@ -259,7 +259,7 @@ __device__ void warp_scale(double* a, int u, double s) {
 }
 
 // w <- w - (w.v) v, then normalise.  Returns the norm before normalising.
-__device__ double warp_orth_normalise(double* w, const double* v, int u, bool orth) {
+__device__ __noinline__ double warp_orth_normalise(double* w, const double* v, int u, bool orth) {
     if (orth) {
         double c = warp_dot(w, v, u);
         for (int i = lane_id(); i < u; i += 32) w[i] -= c * v[i];
