@@ -2,8 +2,9 @@
 
 A step is one pass of the whole path over the batched workload: fit all
 10,000 kernels x 8 metrics (80,000 rational fits, 50-2000 noisy samples each,
-about 82 M samples: 574 MB in HBM as uint8 base-2 logarithms of the
-power-of-two coordinates and FP32 values), then evaluate the fitted
+about 82 M samples: 492 MB in HBM as one packed 16-bit code of the
+power-of-two coordinates' base-2 logarithms and an FP32 value each), then
+evaluate the fitted
 rational program for 64 data sizes x 51 block shapes per kernel and choose the
 argmin (640,000 queries, 32.6 M evaluations).  The metric is argmin queries
 per second of whole steps.
@@ -37,7 +38,7 @@ METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
 # 1,000-kernel copy (dram__bytes_read.sum + dram__bytes_write.sum = 57.79 +
 # 0.38 MB over 8,240,324 samples); the traffic of a full launch scales with
 # the sample count.
-MOMENTS_DRAM_BYTES_PER_SAMPLE = 7.059
+MOMENTS_DRAM_BYTES_PER_SAMPLE = {"exp8": 7.059}
 
 
 def parse():
@@ -49,6 +50,10 @@ def parse():
     ap.add_argument("--seed", type=int, default=2024)
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--e2e-copy-streams", type=int, default=1)
+    ap.add_argument("--sample-format", choices=("exp8", "exp16"), default="exp16",
+                    help="coordinates of the batched workload's samples: uint8 base-2 "
+                         "logarithms (KLR_EXP8, 7 B per sample) or one packed 16-bit code "
+                         "(KLR_EXP16, 6 B per sample)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="eager launches instead of a CUDA graph")
     ap.add_argument("--kernels", type=int, default=0,
@@ -374,10 +379,16 @@ def run_klr(args, cb_kept=None):
     ctx.reserve(n_fits, n_q)
     off_h = torch.from_numpy(fb.offsets).pin_memory()
     # the coordinates are powers of two: uint8 base-2 logarithms (KLR_EXP8),
-    # 7 bytes per sample with the FP32 values instead of 16
+    # 7 bytes per sample with the FP32 values instead of 16, or one packed
+    # 16-bit code (KLR_EXP16), 6 bytes
     x8 = np.round(np.log2(fb.x)).astype(np.uint8)
     assert np.array_equal(np.ldexp(np.float32(1), x8.astype(np.int32)), fb.x)
-    x_h = torch.from_numpy(x8).pin_memory()
+    if args.sample_format == "exp16":
+        e_ = x8.astype(np.uint16)
+        x_h = torch.from_numpy((e_[0] | (e_[1] << 6) | (e_[2] << 11)).view(np.int16)).pin_memory()
+    else:
+        x_h = torch.from_numpy(x8).pin_memory()
+    sample_bytes = 6 if args.sample_format == "exp16" else 7
     x32_h = torch.from_numpy(np.ascontiguousarray(fb.x)).pin_memory()
     y_h = torch.from_numpy(fb.y).pin_memory()
     qo_h = torch.from_numpy(q.offsets).pin_memory()
@@ -613,7 +624,7 @@ def run_klr(args, cb_kept=None):
     sm_mhz = (ck or {}).get("sm_max_mhz") or 2070.0
     fp32_peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s (FMA = 2 flop)
     # stage rooflines from the per-unit work above
-    mom_bytes = n_samples * 7 + (n_fits + 1) * 8 + n_fits * (3 * 35 * 8 + 4)
+    mom_bytes = n_samples * sample_bytes + (n_fits + 1) * 8 + n_fits * (3 * 35 * 8 + 4)
     t_mom, t_sol, t_arg = (part_ms[k] * 1e-3 for k in names)
     evals = n_q * wl["n_cfg"]
     # the fit's contraction is u^2 = 420 flop per 7-byte sample (60 flop/B,
@@ -624,8 +635,8 @@ def run_klr(args, cb_kept=None):
     moments_rf = {"bound": "alu", "achieved": mom_flops, "peak": fp32_peak,
                   "unit": "TFLOP/s", "frac": mom_flops / fp32_peak,
                   "peak_measured": fp32_meas, "frac_of_measured": mom_flops / fp32_meas,
-                  "traffic": (MOMENTS_DRAM_BYTES_PER_SAMPLE * n_samples
-                              if MOMENTS_DRAM_BYTES_PER_SAMPLE else None),
+                  "traffic": (MOMENTS_DRAM_BYTES_PER_SAMPLE[args.sample_format] * n_samples
+                              if MOMENTS_DRAM_BYTES_PER_SAMPLE.get(args.sample_format) else None),
                   "kernel": "moments_binned_kernel (+ moments_fast_kernel over left fits)",
                   "algorithmic_bytes": mom_bytes,
                   "hbm_gbs": mom_bytes / t_mom / 1e9, "hbm_peak_gbs": hbm_peak,
@@ -668,8 +679,10 @@ def run_klr(args, cb_kept=None):
                    "samples": n_samples, "queries": n_q, "configs": wl["n_cfg"],
                    "evals": evals, "fit_precision": "df32", "refine_iters": 0,
                    "sample_format": ("uint8 base-2 logarithms of (N, b0, b1) + FP32 values "
-                                     "(KLR_EXP8, 7 B per sample)"),
-                   "l2": "inputs larger than L2 (574 MB of samples per step)",
+                                     "(KLR_EXP8, 7 B per sample)" if args.sample_format == "exp8"
+                                     else "one 16-bit code log2 N | log2 b0 << 6 | log2 b1 << 11 "
+                                          "+ FP32 values (KLR_EXP16, 6 B per sample)"),
+                   "l2": f"inputs larger than L2 ({n_samples * (sample_bytes - 4 + 4) / 1e6:.0f} MB of samples per step)",
                    "launch": ("one CUDA graph per step (fit moments, fit solve, argmin)"
                               if graph is not None else "eager"),
                    "autotuned": {k: {"choice": v[0], "ms": v[1]} for k, v in tuned.items()},
@@ -1206,9 +1219,9 @@ def run_single(args):
 
 def run_fit_formats(args):
     """The fit's first stage (klr_fit_gram: the moment sums) on the batched
-    workload with FP32 coordinates and with KLR_EXP8 coordinates (uint8
-    base-2 logarithms, the default line's format): the same samples, 16 and
-    7 bytes per sample."""
+    workload with FP32 coordinates, KLR_EXP8 coordinates (uint8 base-2
+    logarithms) and KLR_EXP16 codes (one packed 16-bit code per sample): the
+    same samples in 16, 7 and 6 bytes per sample."""
     import torch
     import paper_1911_02373_gb300 as klr
     fb, _ = make_inputs(args.seed)
@@ -1216,6 +1229,8 @@ def run_fit_formats(args):
     off, y = torch.from_numpy(fb.offsets).to(dev), torch.from_numpy(fb.y).to(dev)
     xs = {"f32": torch.from_numpy(np.ascontiguousarray(fb.x)).to(dev),
           "exp8": torch.from_numpy(np.round(np.log2(fb.x)).astype(np.uint8)).to(dev)}
+    e_ = np.round(np.log2(fb.x)).astype(np.uint16)
+    xs["exp16"] = torch.from_numpy((e_[0] | (e_[1] << 6) | (e_[2] << 11)).view(np.int16)).to(dev)
     ctx = klr.Context(0)
     ctx.reserve(fb.n_fits, 0)
     kw = dict(n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10, precision=klr.FIT_DF32,
@@ -1235,7 +1250,7 @@ def run_fit_formats(args):
         ms = a.elapsed_time(b) / K
         n_s = int(fb.offsets[-1])
         out[name] = {"ms": ms, "samples_per_s": n_s / (ms * 1e-3),
-                     "bytes_per_sample": 16 if name == "f32" else 7}
+                     "bytes_per_sample": {"f32": 16, "exp8": 7, "exp16": 6}[name]}
     ctx.close()
     return {"metric": "fit moments stage (klr_fit_gram) by sample format",
             "config": {"workload": WORKLOAD["name"], "fits": fb.n_fits,

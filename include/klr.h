@@ -59,6 +59,14 @@ typedef int32_t klr_status;
  * y is FP32.  7 bytes per sample at n_vars = 3 instead of 16 for FP32: the
  * paper's data sizes and block dimensions are powers of two. */
 #define KLR_EXP8 2
+/* Sample coordinates packed in one 16-bit code per sample
+ * (klr_fit_batch.sample_dtype, n_vars = 3): x holds, for sample s, the uint16
+ * e_N | e_b0 << 6 | e_b1 << 11 (x_stride unused), the coordinates being
+ * (2^e_N, 2^e_b0, 2^e_b1) exactly (N up to 2^63, block dimensions up to
+ * 2^31), and y is FP32: 6 bytes per sample.  Accepted where KLR_EXP8 is; a fit
+ * of KLR_EXP16 samples equals the fit of the same samples in FP32 bit for
+ * bit. */
+#define KLR_EXP16 3
 
 /* ---- fit precision modes (how the Gram matrix is accumulated) ------------
  * The Gram matrix G = A^T A of the design matrix A = [Phi | -y Phi] is built
@@ -148,7 +156,8 @@ typedef struct klr_fit_batch {
     int32_t n_scale_log2;  /* N is scaled by 2^-n_scale_log2                  */
     int32_t b_scale_log2;  /* block dimensions are scaled by 2^-b_scale_log2  */
     int32_t sample_dtype;  /* KLR_F32 or KLR_F64: element type of x and y;
-                            * KLR_EXP8: x uint8 log2, y FP32 (supported with
+                            * KLR_EXP8: x uint8 log2, y FP32; KLR_EXP16: x
+                            * one packed uint16 per sample, y FP32 (both with
                             * KLR_FIT_DF32, the degree-2 basis in (N, b0, b1)
                             * and no refinement; else KLR_ENOTSUP)          */
     const int64_t* offsets;/* device, n_fits + 1, non-decreasing, >= 0        */

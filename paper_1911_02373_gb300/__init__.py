@@ -25,6 +25,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ECUDA, ENOMEM, ENOTSUP = 0, 1, 2, 3, 4
 F32, F64 = 0, 1
 EXP8 = 2      # sample coordinates as uint8 base-2 logarithms (klr_fit)
+EXP16 = 3     # one packed code per sample: log2 N | log2 b0 << 6 | log2 b1 << 11 (klr_fit)
 FIT_FP64, FIT_DF32, FIT_FP32, FIT_TF32, FIT_BF16 = 0, 1, 2, 3, 4
 FIT_OK, FIT_EMPTY, FIT_NONFINITE, FIT_RANK_DEFICIENT, FIT_INEXACT, FIT_SOLVE_FAILED = 0, 1, 2, 4, 8, 16
 Q_OK, Q_BAD_METRIC, Q_NONE_FEASIBLE, Q_TIE_RESOLVED, Q_HISTORY, Q_REFINED = 0, 1, 2, 4, 8, 16
@@ -234,7 +235,8 @@ class Context:
             autotune=False, stage=None, var_degree=None):
         """Fit every CSR fit.  offsets: int64 (F+1,); x: (n_vars, S) float32/64
         rows (N, b0, b1[, b2]), or uint8 base-2 logarithms of them (KLR_EXP8,
-        y float32); y: (S,) same dtype.  Returns (coef, status, diag)
+        y float32), or an int16 (S,) of packed codes log2 N | log2 b0 << 6 |
+        log2 b1 << 11 (KLR_EXP16, y float32); y: (S,) same dtype.  Returns (coef, status, diag)
         device tensors; ``out`` may pass preallocated (coef, status, diag).
         autotune=True times the candidate launch shapes first (klr_autotune_fit)
         and records (choice, ms) in ``self.last_tune``.  stage='gram' or
@@ -242,7 +244,8 @@ class Context:
         var_degree: per-variable degree bounds of the basis (else the
         total-degree basis of ``degree``)."""
         import torch
-        sdt = F64 if x.dtype == torch.float64 else EXP8 if x.dtype == torch.uint8 else F32
+        sdt = (F64 if x.dtype == torch.float64 else EXP8 if x.dtype == torch.uint8
+               else EXP16 if x.dtype == torch.int16 else F32)
         cdt = (F64 if sdt == F64 else F32) if coef_dtype is None else coef_dtype
         n_fits = offsets.numel() - 1
         m = _n_monomials(n_vars, degree, var_degree)

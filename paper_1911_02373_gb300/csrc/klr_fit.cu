@@ -76,7 +76,8 @@ struct FitParams {
     int32_t* flags;// scratch: n_fits, bit 0 non-finite sample, bit 1 inexact DF32,
                    // bit 2 left to the per-sample moments kernel by the binned one
     int fallback_only;  // moments_fast_kernel: only the fits with flag bit 2
-    int x_exp8;    // x holds uint8 base-2 logarithms (KLR_EXP8)
+    int x_fmt;     // coordinates: kXFloat (TS), kXExp8 (uint8 base-2 logarithms,
+                   // KLR_EXP8) or kXExp16 (one packed uint16 per sample, KLR_EXP16)
     int fit_warps; // solve_warp_kernel: warps per fit (> 1: one fit per block, the
                    // others join the refinement passes)
     int mom_warps; // moments_fast_kernel with FP64 sums: warps per fit (> 1: one fit
@@ -85,26 +86,41 @@ struct FitParams {
     uint8_t pair[kMaxBasis][kMaxBasis];
 };
 
-// coordinate of a KLR_EXP8 sample: 2^e exactly, +inf above 127
+// sample coordinate formats
+constexpr int kXFloat = 0;   // TS, n_vars rows
+constexpr int kXExp8 = 1;    // KLR_EXP8: uint8 e per coordinate, n_vars rows
+constexpr int kXExp16 = 2;   // KLR_EXP16: one uint16 per sample, log2 N in bits
+                             // 0-5, log2 b0 in 6-10, log2 b1 in 11-15
+
+// coordinate of a KLR_EXP8 (or KLR_EXP16) sample: 2^e exactly, +inf above 127
 __device__ __forceinline__ float exp8_value(uint8_t e) {
     return e <= 127 ? __int_as_float((int)(e + 127u) << 23) : __int_as_float(0x7f800000);
 }
 
+// exponent field v (0: N, 1: b0, 2: b1) of a KLR_EXP16 code
+__device__ __forceinline__ unsigned exp16_field(unsigned code, int v) {
+    return v == 0 ? (code & 63u) : v == 1 ? ((code >> 6) & 31u) : (code >> 11);
+}
+
 // Coordinate v of sample s in two steps, so that a prefetched load is not
 // waited for until its value is used: load_coord gives the raw element (a
-// KLR_EXP8 byte carried in the bits of a float), coord_value the coordinate.
-template <typename TS, bool E8>
+// KLR_EXP8 byte or a KLR_EXP16 exponent field carried in the bits of a
+// float), coord_value the coordinate.
+template <typename TS, int XF>
 __device__ __forceinline__ TS load_coord(const FitParams& P, int v, int64_t s) {
-    if constexpr (E8) {
+    if constexpr (XF == kXExp8) {
         static_assert(sizeof(TS) == 4, "KLR_EXP8 samples come with FP32 values");
         return __uint_as_float((unsigned)reinterpret_cast<const uint8_t*>(P.x)[(int64_t)v * P.x_stride + s]);
+    } else if constexpr (XF == kXExp16) {
+        static_assert(sizeof(TS) == 4, "KLR_EXP16 samples come with FP32 values");
+        return __uint_as_float(exp16_field(reinterpret_cast<const uint16_t*>(P.x)[s], v));
     } else {
         return reinterpret_cast<const TS*>(P.x)[(int64_t)v * P.x_stride + s];
     }
 }
-template <typename TS, bool E8>
+template <typename TS, int XF>
 __device__ __forceinline__ TS coord_value(TS raw) {
-    if constexpr (E8) return exp8_value((uint8_t)__float_as_uint(raw));
+    if constexpr (XF != kXFloat) return exp8_value((uint8_t)__float_as_uint(raw));
     else return raw;
 }
 
@@ -313,7 +329,7 @@ struct MonoTable {
 // moments_kernel specialised on the basis: the staging lane computes all
 // n_mom monomials of its sample once (compile-time exponents, registers
 // only), and each accumulating lane reads its monomial with one load.
-template <typename TS, int ACC, int NV, int D2, int MG, int MAXT, bool E8 = false>
+template <typename TS, int ACC, int NV, int D2, int MG, int MAXT, int XF = kXFloat>
 __global__ void __launch_bounds__(128, 4)
 moments_fast_kernel(const __grid_constant__ FitParams P) {
     constexpr MonoTable<NV, D2> tab{};
@@ -350,7 +366,7 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
     for (int v = 0; v < NV; ++v) cx[v] = nx[v] = TS(1);
     if (s0 + lane < s1) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) cx[v] = load_coord<TS, E8>(P, v, s0 + lane);
+        for (int v = 0; v < NV; ++v) cx[v] = load_coord<TS, XF>(P, v, s0 + lane);
         cy = Y[s0 + lane];
     }
     for (int64_t base = s0; base < s1; base += 32 * W) {
@@ -358,14 +374,14 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
         const int64_t sn = s + 32 * W;
         if (sn < s1) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) nx[v] = load_coord<TS, E8>(P, v, sn);
+            for (int v = 0; v < NV; ++v) nx[v] = load_coord<TS, XF>(P, v, sn);
             ny = Y[sn];
         }
         if (s < s1) {
             TC pw[NV][D2 + 1];
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const TS raw = coord_value<TS, E8>(cx[v]);
+                const TS raw = coord_value<TS, XF>(cx[v]);
                 bad |= !isfinite(raw);
                 if constexpr (ACC == ACC_DF32) inexact |= !is_pow2_positive(raw);
                 const TC xv = (TC)raw * (v == 0 ? sN : sB);
@@ -576,7 +592,7 @@ __device__ __forceinline__ void dw_acc_scaled2(f2p& h, f2p& l, f2p vh, f2p vl, f
     l = f2p_add(l, f2p_add(e, f2p_mul(vl, p)));
 }
 
-template <bool E8>
+template <int XF>
 __global__ void __launch_bounds__(32)
 moments_binned_kernel(const __grid_constant__ FitParams P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -602,20 +618,26 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
         const int ns_f = fallback ? 0 : (int)(s1 - s0);
         const float* Yf = Y + s0;
         const unsigned char* xb[3];
+        constexpr int64_t xes = XF == kXFloat ? 4 : XF == kXExp8 ? 1 : 2;   // bytes per element
 #pragma unroll
         for (int v = 0; v < 3; ++v)
             xb[v] = reinterpret_cast<const unsigned char*>(P.x) +
-                    ((int64_t)v * P.x_stride + s0) * (E8 ? 1 : (int64_t)sizeof(float));
+                    ((XF == kXExp16 ? 0 : (int64_t)v * P.x_stride) + s0) * xes;
         float nb[kBinU][4] = {};
         auto load = [&](int base, float (&b)[kBinU][4]) {
 #pragma unroll
             for (int u = 0; u < kBinU; ++u) {
                 const int si = base + u * 32 + lane;
                 if (si < ns_f) {
+                    if constexpr (XF == kXExp16) {
+                        b[u][0] = __uint_as_float(
+                            (unsigned)reinterpret_cast<const uint16_t*>(xb[0])[si]);
+                    } else {
 #pragma unroll
-                    for (int v = 0; v < 3; ++v) {
-                        if constexpr (E8) b[u][v] = __uint_as_float((unsigned)xb[v][si]);
-                        else b[u][v] = reinterpret_cast<const float*>(xb[v])[si];
+                        for (int v = 0; v < 3; ++v) {
+                            if constexpr (XF == kXExp8) b[u][v] = __uint_as_float((unsigned)xb[v][si]);
+                            else b[u][v] = reinterpret_cast<const float*>(xb[v])[si];
+                        }
                     }
                     b[u][3] = Yf[si];
                 }
@@ -626,8 +648,14 @@ moments_binned_kernel(const __grid_constant__ FitParams P) {
             float cb[kBinU][4];
 #pragma unroll
             for (int u = 0; u < kBinU; ++u) {
+                if constexpr (XF == kXExp16) {
+                    const unsigned code = __float_as_uint(nb[u][0]);
 #pragma unroll
-                for (int v = 0; v < 3; ++v) cb[u][v] = coord_value<float, E8>(nb[u][v]);
+                    for (int v = 0; v < 3; ++v) cb[u][v] = exp8_value((uint8_t)exp16_field(code, v));
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 3; ++v) cb[u][v] = coord_value<float, XF>(nb[u][v]);
+                }
                 cb[u][3] = nb[u][3];
             }
             if (base + 32 * kBinU < ns_f) load(base + 32 * kBinU, nb);
@@ -2682,11 +2710,11 @@ klr_status launch_moments(const FitParams& P, int n_mom, int rec, int wpb, cudaS
 // DF32 degree-2 fits in (N, b0, b1): the binned moments kernel on a
 // persistent grid (one warp per fit at a time), then the per-sample kernel
 // over the fits it left (flag bit 4).
-// moments_fast_kernel for the degree-2 basis in (N, b0, b1), DF32, FP32 or
-// KLR_EXP8 samples (the binned path's per-sample kernel)
-template <bool E8>
-klr_status launch_moments_fast_e8(const FitParams& P, int wpb, cudaStream_t stream) {
-    auto kern = moments_fast_kernel<float, ACC_DF32, 3, 4, 4, 9, E8>;
+// moments_fast_kernel for the degree-2 basis in (N, b0, b1), DF32, FP32,
+// KLR_EXP8 or KLR_EXP16 samples (the binned path's per-sample kernel)
+template <int XF>
+klr_status launch_moments_fast_xf(const FitParams& P, int wpb, cudaStream_t stream) {
+    auto kern = moments_fast_kernel<float, ACC_DF32, 3, 4, 4, 9, XF>;
     FitParams R = P;
     const int rec_ = 35 + 3 + ((35 + 3) % 2 == 0 ? 1 : 0);
     R.warp_smem = (int)((32 * rec_ * 4 + 15) & ~(size_t)15);
@@ -2697,10 +2725,10 @@ klr_status launch_moments_fast_e8(const FitParams& P, int wpb, cudaStream_t stre
     return KLR_OK;
 }
 
-template <bool E8>
+template <int XF>
 klr_status launch_moments_binned_t(const FitParams& P, int n_sm, int wpb, cudaStream_t stream) {
     const size_t smem = kBinWarpSmem;
-    auto kern = moments_binned_kernel<E8>;
+    auto kern = moments_binned_kernel<XF>;
     KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
     int per_sm = 0;
@@ -2712,14 +2740,15 @@ klr_status launch_moments_binned_t(const FitParams& P, int n_sm, int wpb, cudaSt
     // the per-sample kernel over the fits left (flag bit 4)
     FitParams Q = P;
     Q.fallback_only = 1;
-    return launch_moments_fast_e8<E8>(Q, wpb, stream);
+    return launch_moments_fast_xf<XF>(Q, wpb, stream);
 }
 
 klr_status launch_moments_binned(const FitParams& P, int n_sm, int rec, int wpb,
                                  cudaStream_t stream) {
     (void)rec;
-    return P.x_exp8 ? launch_moments_binned_t<true>(P, n_sm, wpb, stream)
-                    : launch_moments_binned_t<false>(P, n_sm, wpb, stream);
+    return P.x_fmt == kXExp8    ? launch_moments_binned_t<kXExp8>(P, n_sm, wpb, stream)
+         : P.x_fmt == kXExp16 ? launch_moments_binned_t<kXExp16>(P, n_sm, wpb, stream)
+                              : launch_moments_binned_t<kXFloat>(P, n_sm, wpb, stream);
 }
 
 template <typename TS>
@@ -2919,7 +2948,8 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     KLR_REQUIRE(box || (b->degree >= 1 && b->degree <= 3), "klr_fit: degree %d not in 1..3",
                 b->degree);
     KLR_REQUIRE(b->sample_dtype == KLR_F32 || b->sample_dtype == KLR_F64 ||
-                b->sample_dtype == KLR_EXP8, "klr_fit: bad sample_dtype");
+                b->sample_dtype == KLR_EXP8 || b->sample_dtype == KLR_EXP16,
+                "klr_fit: bad sample_dtype");
     KLR_REQUIRE(!(stages & STAGE_SOLVE) || coef_dtype == KLR_F32 || coef_dtype == KLR_F64,
                 "klr_fit: bad coef_dtype");
     KLR_REQUIRE(b->precision >= KLR_FIT_FP64 && b->precision <= KLR_FIT_BF16,
@@ -2933,13 +2963,14 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
                 "klr_fit: NULL coef_out or fit_status");
     KLR_REQUIRE(b->x_stride >= 0, "klr_fit: x_stride < 0");
     if (b->precision == KLR_FIT_DF32)
-        KLR_REQUIRE(b->sample_dtype == KLR_F32 || b->sample_dtype == KLR_EXP8,
-                    "klr_fit: DF32 needs KLR_F32 or KLR_EXP8 samples");
-    if (b->sample_dtype == KLR_EXP8 &&
+        KLR_REQUIRE(b->sample_dtype == KLR_F32 || b->sample_dtype == KLR_EXP8 ||
+                    b->sample_dtype == KLR_EXP16,
+                    "klr_fit: DF32 needs KLR_F32, KLR_EXP8 or KLR_EXP16 samples");
+    if ((b->sample_dtype == KLR_EXP8 || b->sample_dtype == KLR_EXP16) &&
         !(b->precision == KLR_FIT_DF32 && b->n_vars == 3 && !box && b->degree == 2 &&
           b->refine_iters == 0)) {
-        set_error("klr_fit: KLR_EXP8 samples need KLR_FIT_DF32, the degree-2 basis in "
-                  "(N, b0, b1) and no refinement");
+        set_error("klr_fit: KLR_EXP8 and KLR_EXP16 samples need KLR_FIT_DF32, the degree-2 "
+                  "basis in (N, b0, b1) and no refinement");
         return KLR_ENOTSUP;
     }
     Basis basis;
@@ -2987,7 +3018,7 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
     P.diag = fit_diag;
     P.refine = b->refine_iters;
     P.fallback_only = 0;
-    P.x_exp8 = b->sample_dtype == KLR_EXP8;
+    P.x_fmt = b->sample_dtype == KLR_EXP8 ? kXExp8 : b->sample_dtype == KLR_EXP16 ? kXExp16 : kXFloat;
     // a few FP64 fits (a latency): each fit's samples over one warp per scheduler
     P.mom_warps = b->precision == KLR_FIT_FP64 && b->n_fits <= (int64_t)c->n_sm ? 4 : 1;
     P.ld = (u % 2) ? u : u + 1;
@@ -3057,8 +3088,10 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
             if (!box && b->n_vars == 3 && b->degree == 2 && b->b_scale_log2 >= 5 &&
                 b->b_scale_log2 <= 15)
                 st = launch_moments_binned(P, c->n_sm, rec, wpb, stream);
-            else if (P.x_exp8)   // (KLR_EXP8 is only accepted with this basis)
-                st = launch_moments_fast_e8<true>(P, wpb, stream);
+            else if (P.x_fmt == kXExp8)   // (the exponent formats come only with this basis)
+                st = launch_moments_fast_xf<kXExp8>(P, wpb, stream);
+            else if (P.x_fmt == kXExp16)
+                st = launch_moments_fast_xf<kXExp16>(P, wpb, stream);
             else
                 st = launch_moments<float, ACC_DF32>(P, basis.n_mom, rec, wpb, stream);
             break;

@@ -209,6 +209,43 @@ def test_exp8_samples_equal_float32_samples(klr, ctx):
         assert e_.value.status == klr.ENOTSUP
 
 
+def test_exp16_samples_equal_float32_samples(klr, ctx):
+    """KLR_EXP16 (one 16-bit code per sample: log2 N | log2 b0 << 6 | log2 b1
+    << 11) carries the same power-of-two samples in 6 bytes: every output
+    equals the FP32-input fit's bit for bit, the per-sample route included (a
+    fit with an N outside the 16 binned octaves, N = 2^63 at the code's top,
+    an empty fit, and a block-size scale outside the binned kernel's range)."""
+    fb = W.fit_batch(30, 3, (50, 900), noise=0.01, dtype=np.float32)
+    e = np.round(np.log2(fb.x.astype(np.float64))).astype(np.int64)
+    assert np.array_equal(np.ldexp(1.0, e), fb.x)
+    e[0, fb.offsets[2]] = 6                       # N = 64: per-sample route
+    e[0, fb.offsets[6] + 3] = 63                  # N = 2^63, the largest code
+    code = (e[0] | (e[1] << 6) | (e[2] << 11)).astype(np.uint16).view(np.int16)
+    x32 = np.ldexp(1.0, e).astype(np.float32)
+    off = fb.offsets.copy()
+    off[9:] = off[9:] - (off[9] - off[8])         # fit 8 empty
+    keep = np.r_[0:fb.offsets[8], fb.offsets[9]:fb.offsets[-1]]
+    code, x32, y = code[keep], x32[:, keep], fb.y[keep]
+    t = lambda a: torch.tensor(np.ascontiguousarray(a)).cuda()
+    kw = dict(n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10, precision=klr.FIT_DF32,
+              refine_iters=0, coef_dtype=klr.F32)
+    c16, s16, d16 = ctx.fit(t(off), t(code), t(y), **kw)
+    c32, s32, d32 = ctx.fit(t(off), t(x32), t(y), **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(c16, c32) and torch.equal(s16, s32) and torch.equal(d16, d32)
+    st = s16.cpu().numpy()
+    assert st[8] == rational.FIT_EMPTY
+    kw16 = dict(kw, b_scale_log2=16)
+    c16b, s16b, _ = ctx.fit(t(off), t(code), t(y), **kw16)
+    c32b, s32b, _ = ctx.fit(t(off), t(x32), t(y), **kw16)
+    torch.cuda.synchronize()
+    assert torch.equal(c16b, c32b) and torch.equal(s16b, s32b)
+    for bad in (dict(kw, precision=klr.FIT_FP64), dict(kw, refine_iters=1), dict(kw, degree=3)):
+        with pytest.raises(klr.KlrError) as e_:
+            ctx.fit(t(off), t(code), t(y), **bad)
+        assert e_.value.status == klr.ENOTSUP
+
+
 def test_degree3_refinement(klr, ctx):
     fb = W.fit_batch(24, 2, 1500, degree=3, n_hi_log2=30, dtype=np.float64)
     ref = rational.fit_batch(fb.offsets, fb.x, fb.y, 3, 3, 30, 10)
