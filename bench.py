@@ -682,7 +682,7 @@ def run_klr(args, cb_kept=None):
                                      "(KLR_EXP8, 7 B per sample)" if args.sample_format == "exp8"
                                      else "one 16-bit code log2 N | log2 b0 << 6 | log2 b1 << 11 "
                                           "+ FP32 values (KLR_EXP16, 6 B per sample)"),
-                   "l2": f"inputs larger than L2 ({n_samples * (sample_bytes - 4 + 4) / 1e6:.0f} MB of samples per step)",
+                   "l2": f"inputs larger than L2 ({n_samples * sample_bytes / 1e6:.0f} MB of samples per step)",
                    "launch": ("one CUDA graph per step (fit moments, fit solve, argmin)"
                               if graph is not None else "eager"),
                    "autotuned": {k: {"choice": v[0], "ms": v[1]} for k, v in tuned.items()},
