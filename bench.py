@@ -34,11 +34,12 @@ WORKLOAD = dict(name="batched_fit_eval_fp32", kernels=10000, metrics=8, counts=(
                 noise=0.01, degree=2, n_vars=3, n_hi_log2=23, sizes_per_kernel=64, n_cfg=51)
 METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
 # DRAM bytes (read + write) per sample of the binned moments kernel on this
-# workload's KLR_EXP8 samples, from one ncu capture of the kernel on its
-# 1,000-kernel copy (dram__bytes_read.sum + dram__bytes_write.sum = 57.79 +
-# 0.38 MB over 8,240,324 samples); the traffic of a full launch scales with
-# the sample count.
-MOMENTS_DRAM_BYTES_PER_SAMPLE = {"exp8": 7.059}
+# workload's samples, from one ncu capture of the kernel's launches on its
+# 1,000-kernel copy (dram__bytes_read.sum + dram__bytes_write.sum over
+# 8,240,324 samples: KLR_EXP16 49.545 + 0.000 MB, KLR_EXP8 57.786 + 0.008 MB;
+# the moment sums written stay in L2); the traffic of a full launch scales
+# with the sample count.
+MOMENTS_DRAM_BYTES_PER_SAMPLE = {"exp16": 6.013, "exp8": 7.013}
 
 
 def parse():
