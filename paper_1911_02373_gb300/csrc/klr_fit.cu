@@ -39,6 +39,7 @@
 #include <cuda_bf16.h>
 
 #include "klr_common.cuh"
+#include "klr_umma.cuh"
 
 namespace klr {
 
@@ -551,22 +552,10 @@ constexpr int kBinU = 4;                  // 32-sample tiles per load batch
 constexpr size_t kBinWarpSmem = (size_t)kBinC * (sizeof(float4) + sizeof(uint16_t));
 constexpr int64_t kBinMaxSamples = 65535;   // per fit: a cell count fits in 16 bits
 
-struct BinShapes {   // exponents (log2 b0, log2 b1), by thread count, then decreasing b0
-    int8_t e[kBinS][2];
-    __host__ __device__ constexpr BinShapes() : e{} {
-        int idx = 0;
-        for (int s = 5; s <= 10; ++s)
-            for (int e0 = s; e0 >= 0; --e0) {
-                e[idx][0] = (int8_t)e0;
-                e[idx][1] = (int8_t)(s - e0);
-                ++idx;
-            }
-    }
-};
-__constant__ BinShapes c_bin_shapes{};
 __constant__ MonoTable<3, 4> c_mono34{};
 
-// index of shape (2^e0, 2^e1) in BinShapes, for 5 <= e0 + e1 <= 10, e0, e1 >= 0
+// index of shape (2^e0, 2^e1) among the 51 cell shapes, ordered by thread
+// count 2^(e0 + e1), then by decreasing b0; for 5 <= e0 + e1 <= 10, e0, e1 >= 0
 __device__ __forceinline__ int bin_shape_index(int e0, int e1) {
     const int T = e0 + e1;
     return T * (T + 1) / 2 - 15 + (T - e0);
@@ -2490,170 +2479,224 @@ solve_group_dw_kernel(const __grid_constant__ FitParams P) {
 #undef LF
 }
 
-// ---------------------------------------------------------------------------
-// Tensor-core Gram matrix (KLR_FIT_TF32 / KLR_FIT_BF16): one warp per fit.
-// Each step the 32 lanes build the rows a_s = [Phi(x_s) | -y_s Phi(x_s)] of 32
-// samples in FP32 into shared memory; G += A^T A then runs as mma.sync with
-// the operands rounded to TF32 (m16n8k8) or BF16 (m16n8k16) and FP32
-// accumulation.  G goes to the scratch for the FP64 solver.
-// ---------------------------------------------------------------------------
+// TF32 operand: FP32 rounded to nearest (ties away) to TF32
 __device__ __forceinline__ uint32_t to_tf32(float x) {
     uint32_t r;
     asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t*>(&v);
-}
 
-template <typename TS, bool BF16, int MT, int NT>
-__global__ void __launch_bounds__(128)
-gram_tc_kernel(const __grid_constant__ FitParams P) {
-    constexpr int UP = MT * 16;                  // padded columns of A
-    constexpr int LDA = UP + 4;                  // shared-memory row stride (floats)
-    extern __shared__ __align__(16) float tcs[];
-    const int lane = lane_id();
-    const int wib = threadIdx.x >> 5;
-    const int f = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (f >= P.n_fits) return;
-    float* As = tcs + (size_t)wib * 32 * LDA;    // [sample][column]
+
+// ---------------------------------------------------------------------------
+// Tensor-core Gram matrix on tcgen05 (KLR_FIT_BF16 and KLR_FIT_TF32): G =
+// A^T A per fit as one product chain D = X X^T, X the fit's design matrix
+// transposed (u rows = unknowns, padded to M = 128; K = the samples).  Both
+// operands are the same shared-memory tile: 64 samples of X in the 128-byte
+// swizzled K-major layout (BF16, or TF32 in two 32-sample blocks), built by
+// the CTA's 128 threads (thread t: sample t mod 64, the numerator rows Phi
+// for t < 64, the denominator rows -y Phi otherwise); one thread issues the
+// M = 128, N = round16(u) products of the tile (four of K = 16 in BF16, eight
+// of K = 8 in TF32) into an FP32 accumulator in tensor memory (row i in lane
+// i) and commits them to the tile's mbarrier, so the threads build the next
+// tile in the other buffer meanwhile.  At the end of a fit the four warps
+// read their 32 lanes back (tcgen05.ld) and write G as FP64 for the solver.
+// Rows of X past u need no zeros (they only reach rows and columns of D that
+// are not read); samples past the fit's end are zero columns.  Every wait is
+// bounded; a CTA whose wait gave up marks its fits as non-finite (status)
+// and waits again, bounded, for its products in flight before freeing its
+// tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int kGramThreads = 128;
+constexpr int kGramK = 64;                               // samples per tile
+template <bool TF32>
+__host__ __device__ constexpr uint32_t gram_tile_bytes() { return 128u * 64u * (TF32 ? 4u : 2u); }   // 128 rows x 64 samples
+
+// NV, D > 0: the total-degree basis of D in NV variables, its monomials from
+// compile-time exponents; D = 0: any basis, from the exponent table
+template <typename TS, int NV, int D, bool TF32>
+__global__ void __launch_bounds__(kGramThreads)
+gram_umma_kernel(const __grid_constant__ FitParams P, int n_cols, int tmem_cols) {
+    constexpr uint32_t kGramTileBytes = gram_tile_bytes<TF32>();
+    extern __shared__ unsigned char gsm_raw[];
+    unsigned char* tiles = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t mb[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mb[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_addr(&mb[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_addr(&tmem_base)), "r"((uint32_t)tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t s_tiles = smem_addr(tiles);
+    const uint32_t idesc = TF32 ? umma_idesc_tf32(128, n_cols) : umma_idesc_bf16(128, n_cols);
     const int nv = P.n_vars, m = P.m, u = P.u;
-    const int gid = lane >> 2, tig = lane & 3;
-    const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
     const TS* X = reinterpret_cast<const TS*>(P.x);
     const TS* Y = reinterpret_cast<const TS*>(P.y);
     const float sN = ldexpf(1.0f, -P.n_scale_log2), sB = ldexpf(1.0f, -P.b_scale_log2);
-    float acc[MT][NT][4];
-#pragma unroll
-    for (int a = 0; a < MT; ++a)
-#pragma unroll
-        for (int b = 0; b < NT; ++b)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-    bool bad = false;
-    for (int64_t base = s0; base < s1; base += 32) {
-        const int64_t s = base + lane;
-        float* row = As + lane * LDA;
-        if (s < s1) {
-            float xs[kMaxVars];
-            for (int v = 0; v < nv; ++v) {
-                const TS raw = X[(int64_t)v * P.x_stride + s];
-                bad |= !isfinite(raw);
-                xs[v] = (float)raw * (v == 0 ? sN : sB);
-            }
-            const TS yr = Y[s];
-            bad |= !isfinite(yr);
-            const float yv = (float)yr;
-            for (int t = 0; t < m; ++t) {
-                float ph = 1.f;
-                for (int v = 0; v < nv; ++v)
-                    for (int e = 0; e < P.exps[t][v]; ++e) ph *= xs[v];
-                row[t] = ph;
-                row[m + t] = -yv * ph;
-            }
-            for (int j = u; j < UP; ++j) row[j] = 0.f;
+    const int k = tid & (kGramK - 1);            // this thread's sample within a tile
+    const int half = tid >> 6;                   // 0: rows Phi, 1: rows -y Phi
+    // one element of the design matrix into the tile, in the operand type
+    auto put = [&](unsigned char* tile, int r, float v) {
+        if constexpr (TF32) *reinterpret_cast<uint32_t*>(tile + swz_off4(r, k, 128)) = to_tf32(v);
+        else *reinterpret_cast<__nv_bfloat16*>(tile + swz_off(r, k, 128)) = __float2bfloat16_rn(v);
+    };
+    uint32_t phase[2] = {0u, 0u};
+    bool pending[2] = {false, false};
+    // wait for buffer b's products (bounded; a wait that gives up stops the
+    // CTA's products, and its buffer stays pending for the final wait)
+    auto drain = [&](int b) {
+        if (!pending[b] || abort_flag) return;
+        if (mbar_wait(&mb[b], phase[b])) {
+            phase[b] ^= 1u;
+            pending[b] = false;
         } else {
-            for (int j = 0; j < UP; ++j) row[j] = 0.f;
+            abort_flag = 1;
         }
-        __syncwarp();
-        if constexpr (!BF16) {
-#pragma unroll
-            for (int k0 = 0; k0 < 32; k0 += 8) {
-                uint32_t a[MT][4], b[NT][2];
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    const int i0 = mt * 16;
-                    a[mt][0] = to_tf32(As[(k0 + tig) * LDA + i0 + gid]);
-                    a[mt][1] = to_tf32(As[(k0 + tig) * LDA + i0 + gid + 8]);
-                    a[mt][2] = to_tf32(As[(k0 + tig + 4) * LDA + i0 + gid]);
-                    a[mt][3] = to_tf32(As[(k0 + tig + 4) * LDA + i0 + gid + 8]);
+    };
+    for (int f = blockIdx.x; f < P.n_fits; f += gridDim.x) {
+        const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
+        const int64_t n_tiles = (s1 - s0 + kGramK - 1) / kGramK;
+        bool bad = false;
+        for (int64_t c = 0; c < n_tiles; ++c) {
+            const int b = (int)(c & 1);
+            drain(b);                            // the products that read this buffer are done
+            unsigned char* tile = tiles + b * kGramTileBytes;
+            const int64_t s = s0 + c * kGramK + k;
+            const bool live = s < s1;
+            float xs[kMaxVars] = {0.f, 0.f, 0.f, 0.f};
+            float sc = 0.f;                      // 0 past the fit's end: zero columns
+            if (live) {
+                for (int v = 0; v < nv; ++v) {
+                    const TS raw = X[(int64_t)v * P.x_stride + s];
+                    bad |= !isfinite(raw);
+                    xs[v] = (float)raw * (v == 0 ? sN : sB);
                 }
-#pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    b[nt][0] = to_tf32(As[(k0 + tig) * LDA + nt * 8 + gid]);
-                    b[nt][1] = to_tf32(As[(k0 + tig + 4) * LDA + nt * 8 + gid]);
-                }
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt)
-                        asm volatile(
-                            "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 "
-                            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                            : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]),
-                              "+f"(acc[mt][nt][3])
-                            : "r"(a[mt][0]), "r"(a[mt][1]), "r"(a[mt][2]), "r"(a[mt][3]),
-                              "r"(b[nt][0]), "r"(b[nt][1]));
+                const TS yr = Y[s];
+                bad |= !isfinite(yr);
+                sc = half ? -(float)yr : 1.0f;
             }
-        } else {
+            if constexpr (D > 0) {
+                constexpr MonoTable<NV, D> tab{};
+                constexpr int NM = MonoTable<NV, D>::count();
+                float pw[NV][D + 1];
 #pragma unroll
-            for (int k0 = 0; k0 < 32; k0 += 16) {
-                uint32_t a[MT][4], b[NT][2];
-                const int ka = k0 + 2 * tig;
+                for (int v = 0; v < NV; ++v) {
+                    pw[v][0] = 1.f;
 #pragma unroll
-                for (int mt = 0; mt < MT; ++mt) {
-                    const int i0 = mt * 16;
-                    a[mt][0] = pack_bf16(As[ka * LDA + i0 + gid], As[(ka + 1) * LDA + i0 + gid]);
-                    a[mt][1] = pack_bf16(As[ka * LDA + i0 + gid + 8], As[(ka + 1) * LDA + i0 + gid + 8]);
-                    a[mt][2] = pack_bf16(As[(ka + 8) * LDA + i0 + gid], As[(ka + 9) * LDA + i0 + gid]);
-                    a[mt][3] = pack_bf16(As[(ka + 8) * LDA + i0 + gid + 8],
-                                         As[(ka + 9) * LDA + i0 + gid + 8]);
+                    for (int e = 1; e <= D; ++e) pw[v][e] = pw[v][e - 1] * xs[v];
                 }
 #pragma unroll
-                for (int nt = 0; nt < NT; ++nt) {
-                    b[nt][0] = pack_bf16(As[ka * LDA + nt * 8 + gid], As[(ka + 1) * LDA + nt * 8 + gid]);
-                    b[nt][1] = pack_bf16(As[(ka + 8) * LDA + nt * 8 + gid],
-                                         As[(ka + 9) * LDA + nt * 8 + gid]);
+                for (int t = 0; t < NM; ++t) {
+                    float ph = pw[0][tab.e[t][0]] * pw[1][tab.e[t][1]];
+                    if constexpr (NV > 2) ph *= pw[2][tab.e[t][2]];
+                    if constexpr (NV > 3) ph *= pw[3][tab.e[t][3]];
+                    put(tile, half * NM + t, sc * ph);
                 }
-#pragma unroll
-                for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                    for (int nt = 0; nt < NT; ++nt)
-                        asm volatile(
-                            "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-                            "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-                            : "+f"(acc[mt][nt][0]), "+f"(acc[mt][nt][1]), "+f"(acc[mt][nt][2]),
-                              "+f"(acc[mt][nt][3])
-                            : "r"(a[mt][0]), "r"(a[mt][1]), "r"(a[mt][2]), "r"(a[mt][3]),
-                              "r"(b[nt][0]), "r"(b[nt][1]));
+            } else {
+                for (int t = 0; t < m; ++t) {
+                    float ph = 1.f;
+                    for (int v = 0; v < nv; ++v)
+                        for (int e = 0; e < P.exps[t][v]; ++e) ph *= xs[v];
+                    put(tile, half * m + t, sc * ph);
+                }
             }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncthreads();
+            if (tid == 0 && !abort_flag) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if constexpr (TF32) {
+#pragma unroll
+                    for (int kk = 0; kk < kGramK / 8; ++kk) {   // 32-byte steps, two blocks
+                        const uint64_t d = umma_desc(s_tiles + b * kGramTileBytes +
+                                                     (kk >> 2) * 128 * 128 + (kk & 3) * 32);
+                        umma_tf32(tmem, d, d, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < kGramK / 16; ++kk) {
+                        const uint64_t d = umma_desc(s_tiles + b * kGramTileBytes + kk * 32);
+                        umma_bf16(tmem, d, d, idesc, (c > 0 || kk > 0) ? 1u : 0u);
+                    }
+                }
+                umma_commit(&mb[b]);
+            }
+            if (!abort_flag) pending[b] = true;
         }
-        __syncwarp();
+        drain(0);
+        drain(1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // the accumulator of rows 32 warp .. 32 warp + 31, read 32 columns at a time
+        double* G = P.mom + (int64_t)f * u * u;
+        const int i = 32 * warp + lane;
+        for (int c0 = 0; c0 < n_cols; c0 += 32) {
+            float v[32];
+            const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            tmem_ld16x2(ta, ta + 16, v);
+            if (i < u && n_tiles > 0 && !abort_flag)
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < u) G[(int64_t)i * u + c0 + j] = (double)v[j];
+        }
+        const int any_bad = __syncthreads_or(bad ? 1 : 0);
+        if (tid == 0) P.flags[f] = (any_bad || abort_flag) ? 1 : 0;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    double* G = P.mom + (int64_t)f * u * u;
-#pragma unroll
-    for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int r = mt * 16 + gid + h * 8, c = nt * 8 + 2 * tig + j;
-                    if (r < u && c < u) G[r * u + c] = (double)acc[mt][nt][h * 2 + j];
-                }
-    bad = __any_sync(0xffffffffu, bad);
-    if (lane == 0) P.flags[f] = bad ? 1 : 0;
+    // the last products of a CTA that gave up a wait: wait again (bounded)
+    if (abort_flag) {
+        if (pending[0]) mbar_wait(&mb[0], phase[0]);
+        if (pending[1]) mbar_wait(&mb[1], phase[1]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tmem), "r"((uint32_t)tmem_cols));
+    }
 }
 
-template <typename TS, bool BF16>
-klr_status launch_gram_tc(const FitParams& P, cudaStream_t stream) {
-    const int wpb = 4;
-    const int blocks = (P.n_fits + wpb - 1) / wpb;
-    auto go = [&](auto kern, int mt) -> klr_status {
-        const size_t smem = sizeof(float) * 32 * (mt * 16 + 4) * wpb;
-        KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)smem));
-        kern<<<blocks, wpb * 32, smem, stream>>>(P);
-        KLR_CHECK_CUDA(cudaGetLastError());
-        return KLR_OK;
-    };
-    // M tiles of 16 rows and N tiles of 8 columns covering u
-    if (P.u <= 16) return go(gram_tc_kernel<TS, BF16, 1, 2>, 1);
-    if (P.u <= 32) return go(gram_tc_kernel<TS, BF16, 2, 4>, 2);
-    if (P.u <= 48) return go(gram_tc_kernel<TS, BF16, 3, 6>, 3);
-    return go(gram_tc_kernel<TS, BF16, 5, 10>, 5);
+template <typename TS, bool TF32>
+klr_status launch_gram_umma(const FitParams& P, int n_sm, size_t smem_optin, cudaStream_t stream) {
+    const size_t kGramSmemMin = 1024 + 2 * (size_t)gram_tile_bytes<TF32>();
+    const int n_cols = (P.u + 15) / 16 * 16;             // N: a multiple of 16 for M = 128
+    const int read_cols = (n_cols + 31) / 32 * 32;
+    const int tmem_cols = read_cols <= 32 ? 32 : read_cols <= 64 ? 64 : read_cols <= 128 ? 128 : 256;
+    if (P.u > 128 || n_cols > 256) {
+        set_error("klr_fit: %d unknowns exceed the tensor-core Gram's 128 rows", P.u);
+        return KLR_ENOTSUP;
+    }
+    // CTAs per SM: as many as tensor memory holds (512 columns), at most 6;
+    // the shared memory asked for keeps more from sharing an SM
+    const int per_sm = std::min(6, 512 / tmem_cols);
+    const size_t smem = std::max(kGramSmemMin, std::min((size_t)smem_optin, (size_t)(228 * 1024) / per_sm - 1024));
+    auto kern = P.box ? gram_umma_kernel<TS, 0, 0, TF32>
+              : P.n_vars == 3 ? (P.degree == 1 ? gram_umma_kernel<TS, 3, 1, TF32>
+                                 : P.degree == 2 ? gram_umma_kernel<TS, 3, 2, TF32>
+                                                 : gram_umma_kernel<TS, 3, 3, TF32>)
+                              : (P.degree == 1 ? gram_umma_kernel<TS, 4, 1, TF32>
+                                 : P.degree == 2 ? gram_umma_kernel<TS, 4, 2, TF32>
+                                                 : gram_umma_kernel<TS, 4, 3, TF32>);
+    KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    const int grid = (int)std::min<int64_t>(P.n_fits, (int64_t)per_sm * n_sm);
+    kern<<<grid, kGramThreads, smem, stream>>>(P, n_cols, tmem_cols);
+    KLR_CHECK_CUDA(cudaGetLastError());
+    return KLR_OK;
 }
 
 // wpb: warps (fits) per block, 1, 2 or 4 (an autotuned choice)
@@ -3059,10 +3102,10 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
         const bool s64 = b->sample_dtype == KLR_F64;
         const bool bf = b->precision == KLR_FIT_BF16;
         if (stages & STAGE_GRAM) {
-            st = s64 ? (bf ? launch_gram_tc<double, true>(P, stream)
-                           : launch_gram_tc<double, false>(P, stream))
-                     : (bf ? launch_gram_tc<float, true>(P, stream)
-                           : launch_gram_tc<float, false>(P, stream));
+            st = s64 ? (bf ? launch_gram_umma<double, false>(P, c->n_sm, c->smem_optin, stream)
+                           : launch_gram_umma<double, true>(P, c->n_sm, c->smem_optin, stream))
+                     : (bf ? launch_gram_umma<float, false>(P, c->n_sm, c->smem_optin, stream)
+                           : launch_gram_umma<float, true>(P, c->n_sm, c->smem_optin, stream));
             if (st != KLR_OK) return st;
         }
         if (!(stages & STAGE_SOLVE)) return KLR_OK;
