@@ -2569,24 +2569,42 @@ gram_umma_kernel(const __grid_constant__ FitParams P, int n_cols, int tmem_cols)
         const int64_t s0 = P.offsets[f], s1 = P.offsets[f + 1];
         const int64_t n_tiles = (s1 - s0 + kGramK - 1) / kGramK;
         bool bad = false;
+        // this thread's sample of the next tile is loaded while the current
+        // one is built, so that its loads are in flight meanwhile
+        TS cx[kMaxVars] = {}, cy = TS(0);
+        auto fetch = [&](int64_t c, TS (&xv)[kMaxVars], TS& yv) {
+            const int64_t s = s0 + c * kGramK + k;
+            if (s < s1) {
+#pragma unroll
+                for (int v = 0; v < kMaxVars; ++v)
+                    if (v < nv) xv[v] = X[(int64_t)v * P.x_stride + s];
+                yv = Y[s];
+            }
+        };
+        if (n_tiles > 0) fetch(0, cx, cy);
         for (int64_t c = 0; c < n_tiles; ++c) {
             const int b = (int)(c & 1);
+            TS nx[kMaxVars] = {}, ny = TS(0);
+            if (c + 1 < n_tiles) fetch(c + 1, nx, ny);
             drain(b);                            // the products that read this buffer are done
             unsigned char* tile = tiles + b * kGramTileBytes;
-            const int64_t s = s0 + c * kGramK + k;
-            const bool live = s < s1;
+            const bool live = s0 + c * kGramK + k < s1;
             float xs[kMaxVars] = {0.f, 0.f, 0.f, 0.f};
             float sc = 0.f;                      // 0 past the fit's end: zero columns
             if (live) {
-                for (int v = 0; v < nv; ++v) {
-                    const TS raw = X[(int64_t)v * P.x_stride + s];
-                    bad |= !isfinite(raw);
-                    xs[v] = (float)raw * (v == 0 ? sN : sB);
+#pragma unroll
+                for (int v = 0; v < kMaxVars; ++v) {
+                    if (v < nv) {
+                        bad |= !isfinite(cx[v]);
+                        xs[v] = (float)cx[v] * (v == 0 ? sN : sB);
+                    }
                 }
-                const TS yr = Y[s];
-                bad |= !isfinite(yr);
-                sc = half ? -(float)yr : 1.0f;
+                bad |= !isfinite(cy);
+                sc = half ? -(float)cy : 1.0f;
             }
+#pragma unroll
+            for (int v = 0; v < kMaxVars; ++v) cx[v] = nx[v];
+            cy = ny;
             if constexpr (D > 0) {
                 constexpr MonoTable<NV, D> tab{};
                 constexpr int NM = MonoTable<NV, D>::count();
