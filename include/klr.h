@@ -530,8 +530,9 @@ klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw,
  *   fp32x2_fma_tflops     packed FFMA2 (fma.rn.f32x2, 4 flop per instruction)
  *   fp64_fma_tflops       DFMA (fma.rn.f64)
  *   mufu_rcp_tops         reciprocal approximations (rcp.approx.ftz.f32)
- *   tf32_mma_sync_tflops  mma.sync.m16n8k8 TF32 with FP32 accumulation, the
- *                         instruction of the precision modes' Gram products
+ *   tf32_mma_sync_tflops  mma.sync.m16n8k8 TF32 with FP32 accumulation (the
+ *                         warp-level tensor path; the library's own tensor
+ *                         kernels issue tcgen05 products)
  * Synchronous: waits for `stream` (not capturable: KLR_EINVAL while it
  * captures a graph); allocates and frees a few KB of device memory. */
 typedef struct klr_peaks {
