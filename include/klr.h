@@ -531,8 +531,8 @@ klr_status klr_argmin_noalloc(const klr_program* prog, const klr_hw* hw,
  *   fp64_fma_tflops       DFMA (fma.rn.f64)
  *   mufu_rcp_tops         reciprocal approximations (rcp.approx.ftz.f32)
  *   tf32_mma_sync_tflops  mma.sync.m16n8k8 TF32 with FP32 accumulation (the
- *                         warp-level tensor path; the library's own tensor
- *                         kernels issue tcgen05 products)
+ *                         warp-level tensor path; the precision modes' Gram
+ *                         and the surrogate's inference issue tcgen05)
  * Synchronous: waits for `stream` (not capturable: KLR_EINVAL while it
  * captures a graph); allocates and frees a few KB of device memory. */
 typedef struct klr_peaks {
