@@ -17,7 +17,12 @@
  * Conventions for every entry point:
  *   - Pointers documented as "device" must point to memory of the context's
  *     device (cudaMalloc'd or a PyTorch CUDA tensor); "host" pointers to host
- *     memory.  The caller owns every array; the library never frees them.
+ *     memory.  The inputs klr_fit and klr_argmin only read (a batch's
+ *     offsets, x and y; a query set's q_offsets and q_N) may also be
+ *     page-locked host memory (cudaHostAlloc / cudaMallocHost) on a device
+ *     with unified addressing: the kernels then read them in place over the
+ *     interconnect.  The caller owns every array; the library never frees
+ *     them.
  *   - Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  *     stream) and the call returns without synchronising, except where noted.
  *   - Argument errors are detected on the host before anything is enqueued

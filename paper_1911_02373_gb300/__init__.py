@@ -190,6 +190,19 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(_dptr(t))
 
 
+def _iptr(t):
+    """Address of an input the kernels only read (klr_fit's samples and
+    offsets, klr_argmin's queries): a CUDA tensor, or a page-locked host
+    tensor (pin_memory), which the device reads in place through unified
+    addressing.  Any other host tensor is refused."""
+    if t.is_cuda:
+        return t.data_ptr()
+    if t.is_pinned() and t.is_contiguous():
+        return t.data_ptr()
+    raise ValueError("expected a CUDA tensor or a contiguous page-locked host tensor, "
+                     f"got one on {t.device}")
+
+
 def _stream(stream):
     import torch
     s = torch.cuda.current_stream() if stream is None else stream
@@ -240,7 +253,9 @@ class Context:
         device tensors; ``out`` may pass preallocated (coef, status, diag).
         autotune=True times the candidate launch shapes first (klr_autotune_fit)
         and records (choice, ms) in ``self.last_tune``.  stage='gram' or
-        'solve' runs one stage only (klr_fit_gram / klr_fit_solve).
+        'solve' runs one stage only (klr_fit_gram / klr_fit_solve).  offsets,
+        x and y may be page-locked host tensors (read in place by the
+        kernels); the outputs are on the context's device.
         var_degree: per-variable degree bounds of the basis (else the
         total-degree basis of ``degree``)."""
         import torch
@@ -250,14 +265,15 @@ class Context:
         n_fits = offsets.numel() - 1
         m = _n_monomials(n_vars, degree, var_degree)
         if out is None:
-            coef = torch.empty((n_fits, 2 * m), device=x.device,
+            dev = torch.device("cuda", self.device)
+            coef = torch.empty((n_fits, 2 * m), device=dev,
                                dtype=torch.float64 if cdt == F64 else torch.float32)
-            status = torch.empty(n_fits, device=x.device, dtype=torch.int32)
-            diag = torch.empty((n_fits, 4), device=x.device, dtype=torch.float64)
+            status = torch.empty(n_fits, device=dev, dtype=torch.int32)
+            diag = torch.empty((n_fits, 4), device=dev, dtype=torch.float64)
         else:
             coef, status, diag = out
         b = FitBatch(n_fits, n_vars, degree, n_scale_log2, b_scale_log2, sdt,
-                     _dptr(offsets), _dptr(x), x.stride(0), _dptr(y),
+                     _iptr(offsets), _iptr(x), x.stride(0), _iptr(y),
                      precision, refine_iters)
         _set_var_degree(b, var_degree)
         if stage == "gram":
@@ -373,10 +389,12 @@ class Context:
                launch=True, stream=None, autotune=False):
         """Per query: (best index, best cycles, margin, status, launch params).
         autotune=True times the candidate launch shapes first
-        (klr_autotune_argmin) and records (choice, ms) in ``self.last_tune``."""
+        (klr_autotune_argmin) and records (choice, ms) in ``self.last_tune``.
+        q_offsets and q_N may be page-locked host tensors (read in place by the
+        kernels); the outputs are on the context's device."""
         import torch
         n_q = q_N.numel()
-        dev = q_N.device
+        dev = torch.device("cuda", self.device)
         if out is None:
             best = torch.empty(n_q, device=dev, dtype=torch.int32)
             cyc = torch.empty(n_q, device=dev,
@@ -386,7 +404,7 @@ class Context:
             lp = torch.empty((n_q, 6), device=dev, dtype=torch.int32) if launch else None
         else:
             best, cyc, margin, status, lp = out
-        q = Queries(_dptr(q_offsets), _dptr(q_N), n_q)
+        q = Queries(_iptr(q_offsets), _iptr(q_N), n_q)
         if autotune:
             ch, ms = ctypes.c_int32(-1), ctypes.c_float(0.0)
             _check("klr_autotune_argmin",

@@ -343,3 +343,21 @@ def test_fp64_latency_mode_equals_the_kernel_sweep(klr, ctx, seed, nv, degree):
     best, cyc, status = full[0], full[1], full[3]
     assert np.all(best[:q_off[1]] == -1) and np.all(status[:q_off[1]] & klr.Q_NONE_FEASIBLE)
     assert np.any(best >= 0) and np.all(np.isfinite(cyc[best >= 0]))
+
+
+def test_page_locked_host_queries_give_the_same_choices(klr, ctx):
+    """klr_argmin's queries may be page-locked host memory, read in place:
+    the outputs equal those of the same queries in device memory."""
+    gt = G.make_program(35, 16)
+    ct = torch.tensor(gt.coef.astype(np.float32)).cuda()
+    prog = G.gpu_program(klr, ct, gt, torch)
+    hw = klr.make_hw(W.HARDWARE)
+    cfg = torch.tensor(klr.enumerate_configs(2)).cuda()
+    q = W.queries_per_kernel(16, W.log_spaced_sizes(64))
+    qo_h = torch.from_numpy(q.offsets).pin_memory()
+    qn_h = torch.from_numpy(q.sizes).pin_memory()
+    a = ctx.argmin(prog, hw, cfg, qo_h, qn_h)
+    b = ctx.argmin(prog, hw, cfg, qo_h.cuda(), qn_h.cuda())
+    torch.cuda.synchronize()
+    for x, y in zip(a, b):
+        assert x.is_cuda and torch.equal(x, y)

@@ -371,3 +371,20 @@ def test_fp64_refinement_in_small_and_large_batches(klr, ctx):
     check(small, coef_s, st_s, "fp64", 0, (oc[:n], ost[:n], od[:n]))
     assert np.array_equal(st_s, st_l[:n])
     assert np.all(np.max(np.abs(coef_s - coef_l[:n]), axis=1) <= 2.0 * b0[:n])
+
+
+def test_page_locked_host_inputs_give_the_same_fit(klr, ctx):
+    """klr_fit's samples and offsets may be page-locked host memory, read in
+    place by the kernels: the outputs equal those of the same inputs in
+    device memory bit for bit; an ordinary host tensor is refused."""
+    fb = W.fit_batch(31, 4, (50, 600), noise=0.01, dtype=np.float32)
+    kw = dict(n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10, precision=klr.FIT_DF32,
+              refine_iters=0, coef_dtype=klr.F32)
+    h = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    off_h, x_h, y_h = h(fb.offsets), h(fb.x), h(fb.y)
+    c_h, s_h, d_h = ctx.fit(off_h, x_h, y_h, **kw)
+    c_d, s_d, d_d = ctx.fit(off_h.cuda(), x_h.cuda(), y_h.cuda(), **kw)
+    torch.cuda.synchronize()
+    assert c_h.is_cuda and torch.equal(c_h, c_d) and torch.equal(s_h, s_d) and torch.equal(d_h, d_d)
+    with pytest.raises(ValueError):
+        ctx.fit(torch.from_numpy(fb.offsets), x_h, y_h, **kw)
