@@ -1,7 +1,7 @@
 // Measured arithmetic peaks of the device, the denominators of the
 // rooflines of the ALU-bound kernels (the moments' double-word folds and
-// streaming, the solver, the FP32 sweep) and of the TF32 Gram of the
-// precision modes.  Each probe is a kernel of independent dependency chains
+// streaming, the solver, the FP32 sweep), and the rate of the warp-level
+// TF32 tensor instruction.  Each probe is a kernel of independent dependency chains
 // of one instruction (enough chains per thread and warps per SM to keep the
 // pipe full), timed with CUDA events, best of five; the chains' results
 // feed a store the compiler cannot drop.  Every loop has a fixed trip count.
@@ -97,9 +97,9 @@ __global__ void __launch_bounds__(kProbeThreads) probe_rcp_kernel(float* out, in
     if (sum == -1.f) out[blockIdx.x] = sum;
 }
 
-// TF32 mma.sync.m16n8k8 (the instruction of the precision modes' Gram):
-// four independent accumulator tiles per warp, the operands fixed small
-// values, 2 * 16 * 8 * 8 flop per instruction
+// TF32 mma.sync.m16n8k8 (the warp-level tensor path): four independent
+// accumulator tiles per warp, the operands fixed small values, 2 * 16 * 8 * 8
+// flop per instruction
 __global__ void __launch_bounds__(kProbeThreads) probe_mma_tf32_kernel(float* out, int iters) {
     constexpr int NT = 4;
     float d[NT][4];

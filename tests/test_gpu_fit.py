@@ -302,6 +302,39 @@ def test_edge_cases(klr, ctx):
     assert c0.shape == (0, 20)
 
 
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+def test_tensor_core_gram_edge_cases(klr, ctx, mode):
+    """The tcgen05 Gram's per-fit cases: an empty fit between others (its
+    tensor memory is not read), a NaN sample, a fit of 1 sample, ragged counts
+    (not multiples of the 64-sample tile) and one of 130 samples (three tiles
+    over two buffers); the statuses equal the oracle's, and a degree-1 fit
+    whose gap leaves room for the operand rounding meets the bound after
+    refinement."""
+    base = W.fit_batch(44, 1, 400, degree=1, dtype=np.float64)
+    xs, ys = [], []
+    xs.append(base.x[:, :130]); ys.append(base.y[:130])
+    xs.append(np.zeros((3, 0))); ys.append(np.zeros(0))
+    x2 = base.x[:, 130:190].copy(); y2 = base.y[130:190].copy(); y2[11] = np.nan
+    xs.append(x2); ys.append(y2)
+    xs.append(base.x[:, 190:191]); ys.append(base.y[190:191])
+    xs.append(base.x[:, 191:400]); ys.append(base.y[191:400])
+    offs = np.concatenate([[0], np.cumsum([len(a) for a in ys])]).astype(np.int64)
+    fb = W.FitBatch(3, 1, 23, 10, offs, np.hstack(xs), np.hstack(ys), base.truth)
+    prec = klr.FIT_TF32 if mode == "tf32" else klr.FIT_BF16
+    coef, st, _ = gpu_fit(klr, ctx, fb, prec, 6)
+    oc, ost, od = rational.fit_batch(fb.offsets, fb.x, fb.y, 3, 1, 23, 10)
+    assert st[1] == klr.FIT_EMPTY and np.all(coef[1] == 0)
+    assert st[2] == klr.FIT_NONFINITE and np.all(coef[2] == 0)
+    assert st[3] & klr.FIT_RANK_DEFICIENT
+    assert ost[1] == rational.FIT_EMPTY and ost[2] == rational.FIT_NONFINITE
+    eps = 2.0 ** -11 if mode == "tf32" else 2.0 ** -8
+    for f in (0, 4):
+        assert (st[f] & ~klr.FIT_RANK_DEFICIENT) == 0
+        gap = od[f][1] ** 2 - od[f][0] ** 2
+        if eps / gap < 0.02:
+            assert np.max(np.abs(coef[f] - oc[f])) <= 1e-9
+
+
 def test_bad_arguments(klr, ctx):
     fb = W.fit_batch(28, 1, 50, dtype=np.float64)
     with pytest.raises(klr.KlrError) as e:
