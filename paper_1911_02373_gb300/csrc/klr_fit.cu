@@ -330,7 +330,11 @@ struct MonoTable {
 // moments_kernel specialised on the basis: the staging lane computes all
 // n_mom monomials of its sample once (compile-time exponents, registers
 // only), and each accumulating lane reads its monomial with one load.
-template <typename TS, int ACC, int NV, int D2, int MG, int MAXT, int XF = kXFloat>
+//
+// FB (the fallback launch after the binned kernel; W = 1): a small grid whose
+// warps step over the fits and take only those with flag bit 2.
+template <typename TS, int ACC, int NV, int D2, int MG, int MAXT, int XF = kXFloat,
+          bool FB = false>
 __global__ void __launch_bounds__(128, 4)
 moments_fast_kernel(const __grid_constant__ FitParams P) {
     constexpr MonoTable<NV, D2> tab{};
@@ -346,180 +350,197 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
     // W > 1 (FP64 sums only): one fit per block, warp hw takes every W-th tile
     const int W = ACC == ACC_FP64 ? P.mom_warps : 1;
     const int hw = W > 1 ? wib : 0;
-    const int f = W > 1 ? (int)blockIdx.x : blockIdx.x * (blockDim.x >> 5) + wib;
+    // one fit per warp (W = 1) or per block (W > 1); with FB, every fit left by
+    // the binned kernel (flag bit 2) from this warp's index on in steps of the
+    // grid, the lanes testing 32 of those fits per load
+    const int fstep = (int)gridDim.x * (int)(blockDim.x >> 5);
+    auto next_left = [&](int g) -> int {
+        for (; g < P.n_fits; g += 32 * fstep) {
+            const int cand = g + lane * fstep;
+            const unsigned hit =
+                __ballot_sync(0xffffffffu, cand < P.n_fits && (P.flags[cand] & 4) != 0);
+            if (hit) return g + (__ffs(hit) - 1) * fstep;
+        }
+        return P.n_fits;
+    };
+    int f = W > 1 ? (int)blockIdx.x : blockIdx.x * (blockDim.x >> 5) + wib;
+    if constexpr (FB) f = next_left(f);
     if (f >= P.n_fits) return;
-    if (P.fallback_only && (P.flags[f] & 4) == 0) return;   // done by the binned kernel
-    TC* stage = reinterpret_cast<TC*>(smem_raw + (size_t)wib * P.warp_smem);
-    const int64_t s0 = P.offsets[f] + 32 * hw, s1 = P.offsets[f + 1];
-    const TS* Y = reinterpret_cast<const TS*>(P.y);
-    const TC sN = (TC)ldexpf(1.0f, -P.n_scale_log2), sB = (TC)ldexpf(1.0f, -P.b_scale_log2);
-    const int mg = lane % MG, sg = lane / MG;
-    TC a0[MAXT], a1[MAXT], a2[MAXT];
-    float c0[MAXT], c1[MAXT], c2[MAXT];
-#pragma unroll
-    for (int i = 0; i < MAXT; ++i) {
-        a0[i] = a1[i] = a2[i] = TC(0);
-        c0[i] = c1[i] = c2[i] = 0.f;
-    }
-    bool bad = false, inexact = false;
-    TS cx[NV], cy = TS(0), nx[NV], ny = TS(0);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) cx[v] = nx[v] = TS(1);
-    if (s0 + lane < s1) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) cx[v] = load_coord<TS, XF>(P, v, s0 + lane);
-        cy = Y[s0 + lane];
-    }
-    for (int64_t base = s0; base < s1; base += 32 * W) {
-        const int64_t s = base + lane;
-        const int64_t sn = s + 32 * W;
-        if (sn < s1) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v) nx[v] = load_coord<TS, XF>(P, v, sn);
-            ny = Y[sn];
+    do {
+        TC* stage = reinterpret_cast<TC*>(smem_raw + (size_t)wib * P.warp_smem);
+        const int64_t s0 = P.offsets[f] + 32 * hw, s1 = P.offsets[f + 1];
+        const TS* Y = reinterpret_cast<const TS*>(P.y);
+        const TC sN = (TC)ldexpf(1.0f, -P.n_scale_log2), sB = (TC)ldexpf(1.0f, -P.b_scale_log2);
+        const int mg = lane % MG, sg = lane / MG;
+        TC a0[MAXT], a1[MAXT], a2[MAXT];
+        float c0[MAXT], c1[MAXT], c2[MAXT];
+    #pragma unroll
+        for (int i = 0; i < MAXT; ++i) {
+            a0[i] = a1[i] = a2[i] = TC(0);
+            c0[i] = c1[i] = c2[i] = 0.f;
         }
-        if (s < s1) {
-            TC pw[NV][D2 + 1];
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                const TS raw = coord_value<TS, XF>(cx[v]);
-                bad |= !isfinite(raw);
-                if constexpr (ACC == ACC_DF32) inexact |= !is_pow2_positive(raw);
-                const TC xv = (TC)raw * (v == 0 ? sN : sB);
-                pw[v][0] = TC(1);
-#pragma unroll
-                for (int k = 1; k <= D2; ++k) pw[v][k] = pw[v][k - 1] * xv;
-            }
-            TC* r = stage + lane * REC;
-#pragma unroll
-            for (int t = 0; t < NM; ++t) {
-                TC x = pw[0][tab.e[t][0]] * pw[1][tab.e[t][1]];
-                if constexpr (NV > 2) x *= pw[2][tab.e[t][2]];
-                if constexpr (NV > 3) x *= pw[3][tab.e[t][3]];
-                r[t] = x;
-            }
-            bad |= !isfinite(cy);
-            const TC yv = (TC)cy;
-            const TC y2h = yv * yv;
-            TC y2l = TC(0);
-            if constexpr (ACC != ACC_FP64) y2l = fmaf(yv, yv, -y2h);
-            r[NM + 0] = yv;
-            r[NM + 1] = y2h;
-            r[NM + 2] = y2l;
+        bool bad = false, inexact = false;
+        TS cx[NV], cy = TS(0), nx[NV], ny = TS(0);
+    #pragma unroll
+        for (int v = 0; v < NV; ++v) cx[v] = nx[v] = TS(1);
+        if (s0 + lane < s1) {
+    #pragma unroll
+            for (int v = 0; v < NV; ++v) cx[v] = load_coord<TS, XF>(P, v, s0 + lane);
+            cy = Y[s0 + lane];
         }
-#pragma unroll
-        for (int v = 0; v < NV; ++v) cx[v] = nx[v];
-        cy = ny;
-        __syncwarp();
-        const int nvalid = (int)min((int64_t)32, s1 - base);
-        for (int ts = sg; ts < nvalid; ts += SG) {
-            const TC* r = stage + ts * REC;
-            const TC yv = r[NM + 0], y2h = r[NM + 1], y2l = r[NM + 2];
-#pragma unroll
-            for (int i = 0; i < MAXT; ++i) {
-                const int mu = mg + MG * i;
-                if (mu < NM) {
-                    const TC xm = r[mu];
-                    if constexpr (ACC == ACC_FP64) {
-                        a0[i] += xm;
-                        a1[i] = fma(yv, xm, a1[i]);
-                        a2[i] = fma(y2h, xm, a2[i]);
-                    } else if constexpr (ACC == ACC_DF32) {
-                        df_add(a0[i], c0[i], xm);
-                        df_add(a1[i], c1[i], __fmul_rn(yv, xm));
-                        df_add(a2[i], c2[i], __fmul_rn(y2h, xm));
-                        c2[i] = fmaf(y2l, xm, c2[i]);
-                    } else {
-                        a0[i] += xm;
-                        a1[i] = fmaf(yv, xm, a1[i]);
-                        a2[i] = fmaf(y2h, xm, a2[i]);
-                    }
+        for (int64_t base = s0; base < s1; base += 32 * W) {
+            const int64_t s = base + lane;
+            const int64_t sn = s + 32 * W;
+            if (sn < s1) {
+    #pragma unroll
+                for (int v = 0; v < NV; ++v) nx[v] = load_coord<TS, XF>(P, v, sn);
+                ny = Y[sn];
+            }
+            if (s < s1) {
+                TC pw[NV][D2 + 1];
+    #pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const TS raw = coord_value<TS, XF>(cx[v]);
+                    bad |= !isfinite(raw);
+                    if constexpr (ACC == ACC_DF32) inexact |= !is_pow2_positive(raw);
+                    const TC xv = (TC)raw * (v == 0 ? sN : sB);
+                    pw[v][0] = TC(1);
+    #pragma unroll
+                    for (int k = 1; k <= D2; ++k) pw[v][k] = pw[v][k - 1] * xv;
                 }
+                TC* r = stage + lane * REC;
+    #pragma unroll
+                for (int t = 0; t < NM; ++t) {
+                    TC x = pw[0][tab.e[t][0]] * pw[1][tab.e[t][1]];
+                    if constexpr (NV > 2) x *= pw[2][tab.e[t][2]];
+                    if constexpr (NV > 3) x *= pw[3][tab.e[t][3]];
+                    r[t] = x;
+                }
+                bad |= !isfinite(cy);
+                const TC yv = (TC)cy;
+                const TC y2h = yv * yv;
+                TC y2l = TC(0);
+                if constexpr (ACC != ACC_FP64) y2l = fmaf(yv, yv, -y2h);
+                r[NM + 0] = yv;
+                r[NM + 1] = y2h;
+                r[NM + 2] = y2l;
             }
-        }
-        __syncwarp();
-    }
-#pragma unroll
-    for (int i = 0; i < MAXT; ++i) {
-#pragma unroll
-        for (int o = MG; o < 32; o <<= 1) {
-            if constexpr (ACC == ACC_DF32) {
-                float h, e;
-                float oh0 = __shfl_xor_sync(0xffffffffu, a0[i], o);
-                float ol0 = __shfl_xor_sync(0xffffffffu, c0[i], o);
-                two_sum(a0[i], oh0, h, e);
-                a0[i] = h; c0[i] = c0[i] + ol0 + e;
-                float oh1 = __shfl_xor_sync(0xffffffffu, a1[i], o);
-                float ol1 = __shfl_xor_sync(0xffffffffu, c1[i], o);
-                two_sum(a1[i], oh1, h, e);
-                a1[i] = h; c1[i] = c1[i] + ol1 + e;
-                float oh2 = __shfl_xor_sync(0xffffffffu, a2[i], o);
-                float ol2 = __shfl_xor_sync(0xffffffffu, c2[i], o);
-                two_sum(a2[i], oh2, h, e);
-                a2[i] = h; c2[i] = c2[i] + ol2 + e;
-            } else {
-                a0[i] += __shfl_xor_sync(0xffffffffu, a0[i], o);
-                a1[i] += __shfl_xor_sync(0xffffffffu, a1[i], o);
-                a2[i] += __shfl_xor_sync(0xffffffffu, a2[i], o);
-            }
-        }
-    }
-    bad = __any_sync(0xffffffffu, bad);
-    inexact = __any_sync(0xffffffffu, inexact);
-    if constexpr (ACC == ACC_FP64) {
-        if (W > 1) {
-            // the warps' sums, added by warp 0 in warp order
-            double* part = reinterpret_cast<double*>(smem_raw + (size_t)W * P.warp_smem);
-            if (sg == 0) {
-#pragma unroll
+    #pragma unroll
+            for (int v = 0; v < NV; ++v) cx[v] = nx[v];
+            cy = ny;
+            __syncwarp();
+            const int nvalid = (int)min((int64_t)32, s1 - base);
+            for (int ts = sg; ts < nvalid; ts += SG) {
+                const TC* r = stage + ts * REC;
+                const TC yv = r[NM + 0], y2h = r[NM + 1], y2l = r[NM + 2];
+    #pragma unroll
                 for (int i = 0; i < MAXT; ++i) {
                     const int mu = mg + MG * i;
                     if (mu < NM) {
-                        part[hw * 3 * NM + mu] = a0[i];
-                        part[hw * 3 * NM + NM + mu] = a1[i];
-                        part[hw * 3 * NM + 2 * NM + mu] = a2[i];
+                        const TC xm = r[mu];
+                        if constexpr (ACC == ACC_FP64) {
+                            a0[i] += xm;
+                            a1[i] = fma(yv, xm, a1[i]);
+                            a2[i] = fma(y2h, xm, a2[i]);
+                        } else if constexpr (ACC == ACC_DF32) {
+                            df_add(a0[i], c0[i], xm);
+                            df_add(a1[i], c1[i], __fmul_rn(yv, xm));
+                            df_add(a2[i], c2[i], __fmul_rn(y2h, xm));
+                            c2[i] = fmaf(y2l, xm, c2[i]);
+                        } else {
+                            a0[i] += xm;
+                            a1[i] = fmaf(yv, xm, a1[i]);
+                            a2[i] = fmaf(y2h, xm, a2[i]);
+                        }
                     }
                 }
             }
-            if (lane == 0) flag_w[hw] = (bad ? 1 : 0) | (inexact ? 2 : 0);
-            __syncthreads();
-            if (hw != 0) return;
-            double* mom = P.mom + (int64_t)f * 3 * NM;
-            for (int idx = lane; idx < 3 * NM; idx += 32) {
-                double acc = part[idx];
-                for (int g = 1; g < W; ++g) acc += part[g * 3 * NM + idx];
-                mom[idx] = acc;
-            }
-            if (lane == 0) {
-                int fl = 0;
-                for (int g = 0; g < W; ++g) fl |= flag_w[g];
-                P.flags[f] = fl;
-            }
-            return;
+            __syncwarp();
         }
-    }
-    if (sg == 0) {
-        double* mom = P.mom + (int64_t)f * 3 * NM;
-#pragma unroll
+    #pragma unroll
         for (int i = 0; i < MAXT; ++i) {
-            const int mu = mg + MG * i;
-            if (mu < NM) {
-                if constexpr (ACC == ACC_FP64) {
-                    mom[mu] = a0[i];
-                    mom[NM + mu] = a1[i];
-                    mom[2 * NM + mu] = a2[i];
+    #pragma unroll
+            for (int o = MG; o < 32; o <<= 1) {
+                if constexpr (ACC == ACC_DF32) {
+                    float h, e;
+                    float oh0 = __shfl_xor_sync(0xffffffffu, a0[i], o);
+                    float ol0 = __shfl_xor_sync(0xffffffffu, c0[i], o);
+                    two_sum(a0[i], oh0, h, e);
+                    a0[i] = h; c0[i] = c0[i] + ol0 + e;
+                    float oh1 = __shfl_xor_sync(0xffffffffu, a1[i], o);
+                    float ol1 = __shfl_xor_sync(0xffffffffu, c1[i], o);
+                    two_sum(a1[i], oh1, h, e);
+                    a1[i] = h; c1[i] = c1[i] + ol1 + e;
+                    float oh2 = __shfl_xor_sync(0xffffffffu, a2[i], o);
+                    float ol2 = __shfl_xor_sync(0xffffffffu, c2[i], o);
+                    two_sum(a2[i], oh2, h, e);
+                    a2[i] = h; c2[i] = c2[i] + ol2 + e;
                 } else {
-                    float2* m2 = reinterpret_cast<float2*>(mom);
-                    const dw q0 = dw_2sum(a0[i], c0[i]), q1 = dw_2sum(a1[i], c1[i]),
-                             q2 = dw_2sum(a2[i], c2[i]);
-                    m2[mu] = make_float2(q0.h, q0.l);
-                    m2[NM + mu] = make_float2(q1.h, q1.l);
-                    m2[2 * NM + mu] = make_float2(q2.h, q2.l);
+                    a0[i] += __shfl_xor_sync(0xffffffffu, a0[i], o);
+                    a1[i] += __shfl_xor_sync(0xffffffffu, a1[i], o);
+                    a2[i] += __shfl_xor_sync(0xffffffffu, a2[i], o);
                 }
             }
         }
-    }
-    if (lane == 0) P.flags[f] = (bad ? 1 : 0) | (inexact ? 2 : 0);
+        bad = __any_sync(0xffffffffu, bad);
+        inexact = __any_sync(0xffffffffu, inexact);
+        if constexpr (ACC == ACC_FP64) {
+            if (W > 1) {
+                // the warps' sums, added by warp 0 in warp order
+                double* part = reinterpret_cast<double*>(smem_raw + (size_t)W * P.warp_smem);
+                if (sg == 0) {
+    #pragma unroll
+                    for (int i = 0; i < MAXT; ++i) {
+                        const int mu = mg + MG * i;
+                        if (mu < NM) {
+                            part[hw * 3 * NM + mu] = a0[i];
+                            part[hw * 3 * NM + NM + mu] = a1[i];
+                            part[hw * 3 * NM + 2 * NM + mu] = a2[i];
+                        }
+                    }
+                }
+                if (lane == 0) flag_w[hw] = (bad ? 1 : 0) | (inexact ? 2 : 0);
+                __syncthreads();
+                if (hw != 0) return;
+                double* mom = P.mom + (int64_t)f * 3 * NM;
+                for (int idx = lane; idx < 3 * NM; idx += 32) {
+                    double acc = part[idx];
+                    for (int g = 1; g < W; ++g) acc += part[g * 3 * NM + idx];
+                    mom[idx] = acc;
+                }
+                if (lane == 0) {
+                    int fl = 0;
+                    for (int g = 0; g < W; ++g) fl |= flag_w[g];
+                    P.flags[f] = fl;
+                }
+                return;
+            }
+        }
+        if (sg == 0) {
+            double* mom = P.mom + (int64_t)f * 3 * NM;
+    #pragma unroll
+            for (int i = 0; i < MAXT; ++i) {
+                const int mu = mg + MG * i;
+                if (mu < NM) {
+                    if constexpr (ACC == ACC_FP64) {
+                        mom[mu] = a0[i];
+                        mom[NM + mu] = a1[i];
+                        mom[2 * NM + mu] = a2[i];
+                    } else {
+                        float2* m2 = reinterpret_cast<float2*>(mom);
+                        const dw q0 = dw_2sum(a0[i], c0[i]), q1 = dw_2sum(a1[i], c1[i]),
+                                 q2 = dw_2sum(a2[i], c2[i]);
+                        m2[mu] = make_float2(q0.h, q0.l);
+                        m2[NM + mu] = make_float2(q1.h, q1.l);
+                        m2[2 * NM + mu] = make_float2(q2.h, q2.l);
+                    }
+                }
+            }
+        }
+        if (lane == 0) P.flags[f] = (bad ? 1 : 0) | (inexact ? 2 : 0);
+        if constexpr (!FB) break;
+        f = next_left(f + fstep);
+    } while (f < P.n_fits);
 }
 
 // ---------------------------------------------------------------------------
@@ -542,7 +563,7 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
 // 51 block shapes of 32..1024 threads.  A fit with any sample outside that
 // set (another N or shape, a coordinate that is not a power of two, a
 // non-finite value) or with more than 65,535 samples (the cell counts are 16
-// bits) is marked with flag bit 4 and left to moments_fast_kernel, which then
+// bits) is marked with flag bit 2 and left to moments_fast_kernel, which then
 // runs over the marked fits only.
 // ---------------------------------------------------------------------------
 constexpr int kBinT = 16;                 // octaves of N per fit
@@ -2770,24 +2791,36 @@ klr_status launch_moments(const FitParams& P, int n_mom, int rec, int wpb, cudaS
     return KLR_OK;
 }
 
-// DF32 degree-2 fits in (N, b0, b1): the binned moments kernel on a
-// persistent grid (one warp per fit at a time), then the per-sample kernel
-// over the fits it left (flag bit 4).
 // moments_fast_kernel for the degree-2 basis in (N, b0, b1), DF32, FP32,
-// KLR_EXP8 or KLR_EXP16 samples (the binned path's per-sample kernel)
+// KLR_EXP8 or KLR_EXP16 samples (the binned path's per-sample kernel).  The
+// fallback launch (P.fallback_only) takes one resident wave of blocks whose
+// warps step over the fits, so that a batch the binned kernel covered whole
+// costs a scan of the flags (one load per 32 fits a warp) instead of a block
+// per wpb fits.
 template <int XF>
-klr_status launch_moments_fast_xf(const FitParams& P, int wpb, cudaStream_t stream) {
-    auto kern = moments_fast_kernel<float, ACC_DF32, 3, 4, 4, 9, XF>;
+klr_status launch_moments_fast_xf(const FitParams& P, int n_sm, int wpb, cudaStream_t stream) {
+    auto kern = P.fallback_only ? moments_fast_kernel<float, ACC_DF32, 3, 4, 4, 9, XF, true>
+                                : moments_fast_kernel<float, ACC_DF32, 3, 4, 4, 9, XF, false>;
     FitParams R = P;
     const int rec_ = 35 + 3 + ((35 + 3) % 2 == 0 ? 1 : 0);
     R.warp_smem = (int)((32 * rec_ * 4 + 15) & ~(size_t)15);
     KLR_CHECK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         R.warp_smem * wpb));
-    kern<<<(P.n_fits + wpb - 1) / wpb, wpb * 32, (size_t)R.warp_smem * wpb, stream>>>(R);
+    int64_t grid = (P.n_fits + wpb - 1) / wpb;
+    if (P.fallback_only) {
+        int per_sm = 0;
+        KLR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, kern, wpb * 32, (size_t)R.warp_smem * wpb));
+        grid = std::min<int64_t>(grid, (int64_t)std::max(1, per_sm) * std::max(1, n_sm));
+    }
+    kern<<<(int)grid, wpb * 32, (size_t)R.warp_smem * wpb, stream>>>(R);
     KLR_CHECK_CUDA(cudaGetLastError());
     return KLR_OK;
 }
 
+// DF32 degree-2 fits in (N, b0, b1): the binned moments kernel on a
+// persistent grid (one warp per fit at a time), then the per-sample kernel
+// over the fits it left (flag bit 2).
 template <int XF>
 klr_status launch_moments_binned_t(const FitParams& P, int n_sm, int wpb, cudaStream_t stream) {
     const size_t smem = kBinWarpSmem;
@@ -2800,10 +2833,10 @@ klr_status launch_moments_binned_t(const FitParams& P, int n_sm, int wpb, cudaSt
     const int grid = (int)std::min<int64_t>(P.n_fits, slots);
     kern<<<grid, 32, smem, stream>>>(P);
     KLR_CHECK_CUDA(cudaGetLastError());
-    // the per-sample kernel over the fits left (flag bit 4)
+    // the per-sample kernel over the fits left (flag bit 2)
     FitParams Q = P;
     Q.fallback_only = 1;
-    return launch_moments_fast_xf<XF>(Q, wpb, stream);
+    return launch_moments_fast_xf<XF>(Q, n_sm, wpb, stream);
 }
 
 klr_status launch_moments_binned(const FitParams& P, int n_sm, int rec, int wpb,
@@ -3152,9 +3185,9 @@ klr_status fit_impl(klr_ctx* ctx, const klr_fit_batch* b, void* coef_out, int32_
                 b->b_scale_log2 <= 15)
                 st = launch_moments_binned(P, c->n_sm, rec, wpb, stream);
             else if (P.x_fmt == kXExp8)   // (the exponent formats come only with this basis)
-                st = launch_moments_fast_xf<kXExp8>(P, wpb, stream);
+                st = launch_moments_fast_xf<kXExp8>(P, c->n_sm, wpb, stream);
             else if (P.x_fmt == kXExp16)
-                st = launch_moments_fast_xf<kXExp16>(P, wpb, stream);
+                st = launch_moments_fast_xf<kXExp16>(P, c->n_sm, wpb, stream);
             else
                 st = launch_moments<float, ACC_DF32>(P, basis.n_mom, rec, wpb, stream);
             break;

@@ -143,6 +143,34 @@ def test_df32_binned_and_per_sample_fits_in_one_batch(klr, ctx):
     assert np.array_equal(coef, coef2) and np.array_equal(st, st2)
 
 
+def test_df32_per_sample_fits_scattered_over_a_large_batch(klr, ctx):
+    """After the binned kernel the per-sample moments kernel runs on one
+    resident wave of blocks (4 per SM of 4 warps) whose warps step over the
+    fits, testing 32 of their fits per flag load; in a batch of 96,000 fits
+    (more than 32 times that wave's warps) every 7th fit has an N below the
+    binned window.  Those fits equal, bit for bit, the same fits fitted as a
+    batch of their own, which the oracle checks."""
+    from types import SimpleNamespace
+    fb = W.fit_batch(28, 12000, (48, 64), noise=0.01, dtype=np.float32)
+    x = np.ascontiguousarray(fb.x).copy()
+    pick = np.arange(3, fb.n_fits, 7)
+    x[0, fb.offsets[pick]] = 2.0 ** 7      # one octave below the window
+    big = SimpleNamespace(offsets=fb.offsets, x=x, y=fb.y, n_vars=3, degree=2,
+                          n_scale_log2=23, b_scale_log2=10)
+    coef, st, _ = gpu_fit(klr, ctx, big, klr.FIT_DF32, 0)
+    idx = np.concatenate([np.arange(fb.offsets[f], fb.offsets[f + 1]) for f in pick])
+    off = np.concatenate([[0], np.cumsum(np.diff(fb.offsets)[pick])]).astype(np.int64)
+    sub = SimpleNamespace(offsets=off, x=np.ascontiguousarray(x[:, idx]), y=fb.y[idx],
+                          n_vars=3, degree=2, n_scale_log2=23, b_scale_log2=10)
+    coef_s, st_s, _ = gpu_fit(klr, ctx, sub, klr.FIT_DF32, 0)
+    assert np.array_equal(coef[pick], coef_s) and np.array_equal(st[pick], st_s)
+    check(sub, coef_s, st_s, "df32", 0)
+    # the fits the binned kernel took are untouched by the fallback launch
+    coef_b, st_b, _ = gpu_fit(klr, ctx, fb, klr.FIT_DF32, 0)
+    keep = np.setdiff1d(np.arange(fb.n_fits), pick)
+    assert np.array_equal(coef[keep], coef_b[keep]) and np.array_equal(st[keep], st_b[keep])
+
+
 def test_df32_fits_beyond_the_binned_sample_limit(klr, ctx):
     """Fits with more samples than a 16-bit cell count holds (65,535) take
     the per-sample moments kernel; a batch mixing them with binned fits."""
