@@ -40,6 +40,12 @@ METRIC = "argmin queries/s (fit + evaluate + argmin per step)"
 # the moment sums written stay in L2); the traffic of a full launch scales
 # with the sample count.
 MOMENTS_DRAM_BYTES_PER_SAMPLE = {"exp16": 6.013, "exp8": 7.013}
+# DRAM bytes (read + write) per fit of the group solver on this workload's
+# noisy degree-2 fits, from one ncu capture of a launch over 8,000 of them
+# (the 1,000-kernel copy): 7,466,752 B read (the moment sums) + 0 B written
+# (the coefficients, statuses and diagnostics stay in L2); the traffic of a
+# full launch scales with the fit count.
+SOLVE_DRAM_BYTES_PER_FIT = 7466752 / 8000
 
 
 def parse():
@@ -664,7 +670,8 @@ def run_klr(args, cb_kept=None):
     solve_rf = {"bound": "alu", "achieved": FLOP_PER_FIT * n_fits / t_sol / 1e12,
                 "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": FLOP_PER_FIT * n_fits / t_sol / 1e12 / FP64_PEAK_TFLOPS,
-                "traffic": None, "kernel": "solve_group_dw_kernel (double-word FP32)",
+                "traffic": SOLVE_DRAM_BYTES_PER_FIT * n_fits,
+                "kernel": "solve_group_dw_kernel (double-word FP32)",
                 "frac_of_fp32_peak": FLOP_PER_FIT * n_fits / t_sol / 1e12 / fp32_peak,
                 "peak_measured": mpk["fp64_fma_tflops"],
                 "frac_of_measured": FLOP_PER_FIT * n_fits / t_sol / 1e12 / mpk["fp64_fma_tflops"],
