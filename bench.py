@@ -345,8 +345,8 @@ def oracle_baseline(seed, per_worker, keep=32):
 # Launches per step of the batched path (fit: binned moments, the per-sample
 # moments kernel over the fits the binned one left, the group solver;
 # argmin: the sweep and the two FP64 tie passes) and the per-unit work of
-# each stage used by the rooflines: the moments stage reads 7 B per sample
-# (KLR_EXP8; 16 B with FP32 coordinates) and writes 3 x 35 double-word
+# each stage used by the rooflines: the moments stage reads 6 B per sample
+# (KLR_EXP16; 7 B with KLR_EXP8, 16 B with FP32 coordinates) and writes 3 x 35 double-word
 # moment sums and a flag per fit; its contraction is u^2 = 420
 # flop per sample; the null-vector solve is u^3 = 8000 FP64-class flop per
 # fit; an evaluation is about 70 flop plus the 8 divides of the metric map.
@@ -650,7 +650,7 @@ def run_klr(args, cb_kept=None):
     mom_bytes = n_samples * sample_bytes + (n_fits + 1) * 8 + n_fits * (3 * 35 * 8 + 4)
     t_mom, t_sol, t_arg = (part_ms[k] * 1e-3 for k in names)
     evals = n_q * wl["n_cfg"]
-    # the fit's contraction is u^2 = 420 flop per 7-byte sample (60 flop/B,
+    # the fit's contraction is u^2 = 420 flop per 6-byte sample (70 flop/B,
     # above the FP32 ridge of ~12 flop/B): its roofline is the FP32 FMA peak;
     # the HBM fraction of its algorithmic bytes is reported beside it
     mom_flops = FLOP_PER_SAMPLE * n_samples / t_mom / 1e12
