@@ -353,13 +353,14 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
     // one fit per warp (W = 1) or per block (W > 1); with FB, every fit left by
     // the binned kernel (flag bit 2) from this warp's index on in steps of the
     // grid, the lanes testing 32 of those fits per load
-    const int fstep = (int)gridDim.x * (int)(blockDim.x >> 5);
-    auto next_left = [&](int g) -> int {
+    static_assert(!FB || ACC != ACC_FP64, "the fallback launch has one warp per fit");
+    const int64_t fstep = (int64_t)gridDim.x * (blockDim.x >> 5);
+    auto next_left = [&](int64_t g) -> int {
         for (; g < P.n_fits; g += 32 * fstep) {
-            const int cand = g + lane * fstep;
+            const int64_t cand = g + lane * fstep;
             const unsigned hit =
                 __ballot_sync(0xffffffffu, cand < P.n_fits && (P.flags[cand] & 4) != 0);
-            if (hit) return g + (__ffs(hit) - 1) * fstep;
+            if (hit) return (int)(g + (__ffs(hit) - 1) * fstep);
         }
         return P.n_fits;
     };
@@ -539,7 +540,7 @@ moments_fast_kernel(const __grid_constant__ FitParams P) {
         }
         if (lane == 0) P.flags[f] = (bad ? 1 : 0) | (inexact ? 2 : 0);
         if constexpr (!FB) break;
-        f = next_left(f + fstep);
+        f = next_left((int64_t)f + fstep);
     } while (f < P.n_fits);
 }
 
