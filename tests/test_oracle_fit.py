@@ -4,7 +4,11 @@
   samples (the closed form the paper states: exact values determine g);
 * optimality invariants of the least-squares null vector on noisy data;
 * equilibration, sign and rank-deficiency rules;
-* degree 0 against its closed form.
+* degree 0 against its closed form;
+* a mutation test: eleven plausible mistakes (a dropped sign, a wrong scale
+  or exponent, transposed variables, the wrong singular vector, p and q
+  swapped, ...) planted one at a time in a private copy of
+  ``oracle.rational``, each of which must break at least one of these pins.
 """
 import itertools
 import math
@@ -221,3 +225,112 @@ def test_choose_basis_rule():
     assert list(rational.choose_basis(E, sizes)) == [1, 0, 2, 2, -1]
     # equal sizes: the earlier candidate
     assert list(rational.choose_basis([[1e-6, 1e-6]], [8, 8])) == [0]
+
+
+# ---------------------------------------------------------------------------
+# The pins above, run against a private copy of ``oracle.rational`` in which
+# one plausible mistake is planted at a time (on the CPU; the oracle itself is
+# untouched): each mistake must break at least one pin.
+
+def _pin_failures(mod):
+    """Names of the pins that ``mod`` (a copy of oracle.rational) fails."""
+    failed = []
+
+    def pin(name, fn):
+        try:
+            if not fn():
+                failed.append(name)
+        except Exception:  # a crash is a failure of the pin
+            failed.append(name)
+
+    def basis_order():
+        return mod.monomial_exponents(3, 2) == [
+            (0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (2, 0, 0), (1, 1, 0),
+            (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2)]
+
+    def exact_recovery():
+        fb = W.fit_batch(7, 1, 200, degree=2, dtype=np.float64)
+        coef, status, _ = mod.fit_batch(fb.offsets, fb.x, fb.y, 3, 2, fb.n_scale_log2,
+                                        fb.b_scale_log2)
+        for f in range(fb.n_fits):
+            truth = _truth_normalised(fb.truth.coef[0, f], 10)
+            if status[f] != mod.FIT_OK or np.max(np.abs(coef[f] - truth)) > 1e-9:
+                return False
+        return True
+
+    def equilibration():
+        rng = np.random.default_rng(4)
+        A = rng.standard_normal((50, 6)) * np.ldexp(1.0, rng.integers(-40, 40, 6))
+        A[:, 2] = 0.5
+        d = mod.equilibration(A)
+        sq = np.sum((A * d) ** 2, axis=0)
+        return d[2] == 0.25 and bool(np.all((sq >= 0.5) & (sq < 2.0)))
+
+    def noisy_sign_norm_and_scaling():
+        fb = W.fit_batch(11, 1, 150, noise=0.02, dtype=np.float64)
+        a, b = fb.offsets[0], fb.offsets[1]
+        c1, _, _ = mod.fit_one(fb.x[:, a:b], fb.y[a:b], 3, 2, 23, 10)
+        c3, _, _ = mod.fit_one(fb.x[:, a:b], 2 * fb.y[a:b], 3, 2, 23, 10)
+        exps = mod.monomial_exponents(3, 2)
+        xs = mod.scale_variables(fb.x[:, a:b].T, 23, 10)
+        return (abs(np.linalg.norm(c1) - 1) < 1e-14 and c1[10] > 0
+                and np.allclose(mod.predict(c3, xs, exps), 2 * mod.predict(c1, xs, exps),
+                                rtol=1e-9))
+
+    def degree_zero():
+        c, st, _ = mod.fit_one(np.ones((3, 10)), np.full(10, 0.375), 3, 0, 0, 0)
+        return st == mod.FIT_OK and abs(c[0] / c[1] - 0.375) <= 1e-15
+
+    def status_flags():
+        x = np.tile(np.array([[1024.0], [32.0], [2.0]]), (1, 40))
+        return (mod.fit_one(np.ones((3, 0)), np.zeros(0), 3, 2, 23, 10)[1] == mod.FIT_EMPTY
+                and bool(mod.fit_one(x, np.full(40, 3.0), 3, 2, 23, 10)[1]
+                         & mod.FIT_RANK_DEFICIENT))
+
+    for name, fn in [("basis order", basis_order), ("exact recovery", exact_recovery),
+                     ("equilibration", equilibration),
+                     ("sign, norm and scaling", noisy_sign_norm_and_scaling),
+                     ("degree zero", degree_zero), ("status flags", status_flags)]:
+        pin(name, fn)
+    return failed
+
+
+# (original text in oracle/rational.py, planted mistake)
+FIT_MUTATIONS = [
+    ("for e in itertools.product(range(d, -1, -1), repeat=n_vars):",
+     "for e in itertools.product(range(d + 1), repeat=n_vars):"),
+    ("xs[..., 0] = x[..., 0] * math.ldexp(1.0, -n_scale_log2)",
+     "xs[..., 0] = x[..., 0] * math.ldexp(1.0, -b_scale_log2)"),
+    ("for var, p in enumerate(e):", "for var, p in enumerate(reversed(e)):"),
+    ("return np.hstack([phi, -np.asarray(y, dtype=np.float64)[:, None] * phi])",
+     "return np.hstack([phi, np.asarray(y, dtype=np.float64)[:, None] * phi])"),
+    ("d[j] = math.ldexp(1.0, -(e // 2))", "d[j] = math.ldexp(1.0, -e)"),
+    ("c = c / np.linalg.norm(c)", "c = c / np.abs(c).max()"),
+    ("s = 1.0 if q[0] > 0 else -1.0", "s = 1.0 if q[0] < 0 else -1.0"),
+    ("c = normalise(d * vt[-1], m)", "c = normalise(vt[-1], m)"),
+    ("c = normalise(d * vt[-1], m)", "c = normalise(d * vt[-2], m)"),
+    ("if sfull[u - 2] <= RANK_TOL * sfull[0]:", "if sfull[u - 1] <= RANK_TOL * sfull[0]:"),
+    ("return np.sum(phi * coef[..., :m], axis=-1) / np.sum(phi * coef[..., m:], axis=-1)",
+     "return np.sum(phi * coef[..., m:], axis=-1) / np.sum(phi * coef[..., :m], axis=-1)"),
+]
+
+
+def _planted(orig, planted):
+    import os
+    import types
+    path = os.path.join(os.path.dirname(rational.__file__), "rational.py")
+    src = open(path).read()
+    assert src.count(orig) == 1, f"oracle/rational.py no longer holds {orig!r} once"
+    mod = types.ModuleType("oracle._planted_rational")
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(orig, planted), path + " (planted)", "exec"), mod.__dict__)
+    return mod
+
+
+def test_fit_pins_pass_on_the_oracle():
+    assert _pin_failures(rational) == []
+
+
+@pytest.mark.parametrize("orig,planted", FIT_MUTATIONS)
+def test_fit_pins_catch_planted_mistakes(orig, planted):
+    assert _pin_failures(_planted(orig, planted)), f"no pin notices {planted!r}"
