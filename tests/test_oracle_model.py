@@ -3,6 +3,8 @@
 Each test checks the oracle against something other than itself: closed-form
 counts, hand-worked cases (tests/golden), brute force over a plain definition,
 or invariants that a dropped term, swapped operand or wrong index would break.
+A mutation test plants such mistakes one at a time in private copies of the
+occupancy and MWP-CWP modules and checks that each breaks at least one pin.
 """
 import itertools
 import json
@@ -217,3 +219,144 @@ def test_refine_reduces_to_argmin_and_prefers_occupancy():
         b1, b2 = P.refine(cyc, W, e1), P.refine(cyc, W, e2)
         ok = b1 >= 0
         assert np.all(W[b2[ok]] >= W[b1[ok]])
+
+
+# --- planted mistakes ------------------------------------------------------------
+# The occupancy and MWP-CWP pins above, run against private copies of the
+# oracle modules with one plausible mistake planted at a time (on the CPU; the
+# oracle itself is untouched): each mistake must break at least one pin.
+
+def _planted_module(module, orig, planted):
+    import types
+    path = module.__file__
+    src = open(path).read()
+    assert src.count(orig) == 1, f"{os.path.basename(path)} no longer holds {orig!r} once"
+    mod = types.ModuleType("oracle._planted_" + module.__name__.rsplit(".", 1)[-1])
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(orig, planted), path + " (planted)", "exec"), mod.__dict__)
+    return mod
+
+
+def _fails(fn):
+    try:
+        fn()
+    except Exception:  # an assertion or a crash: the pin noticed
+        return True
+    return False
+
+
+def _occupancy_pin_failures(occ):
+    def hand():
+        g = _golden("occupancy_cases.json")
+        for c in g["cases"]:
+            B = occ.active_blocks(c["T"], c["R"], c["Z"], g["hw"])
+            assert B == c["B_active"] and occ.active_warps(B, c["T"], g["hw"]) == c["W_active"]
+
+    def brute():
+        for T in range(32, 1025, 32):
+            for R in range(0, 256, 9):
+                for Z in list(range(0, 233473, 16384)) + [233472, 233473]:
+                    assert occ.active_blocks(T, R, Z, HW) == _floor_of_min(T, R, Z, HW)
+
+    def bounds():
+        rng = np.random.default_rng(0)
+        for _ in range(500):
+            T = int(rng.choice([32, 64, 128, 256, 512, 1024, 96, 160]))
+            R, Z = int(rng.integers(1, 256)), int(rng.integers(0, 233473))
+            B = occ.active_blocks(T, R, Z, HW)
+            W = occ.active_warps(B, T, HW)
+            assert B * R * T <= HW["regs_per_sm"] and B * Z <= HW["smem_per_sm"]
+            assert B * T <= 32 * HW["max_warps_per_sm"] and 0 <= W <= HW["max_warps_per_sm"]
+            assert W == min(B * T // 32, HW["max_warps_per_sm"])
+
+    return [n for n, fn in (("hand", hand), ("brute", brute), ("bounds", bounds)) if _fails(fn)]
+
+
+def _mwpcwp_pin_failures(mc):
+    hw = dict(mem_latency=600.0, departure_delay_coal=4.0, departure_delay_uncoal=10.0,
+              mem_bandwidth=8.0e12, clock_hz=1.9e9)
+
+    def hand():
+        g = _golden("mwpcwp_cases.json")
+        for c in g["cases"]:
+            e, br, _ = mc.cycles([np.float64(v) for v in c["L"]], g["hw"], c["W_active"],
+                                 c["B_active"], c["active_sms"], c["rep"])
+            assert int(br) == c["branch"] and float(e) == pytest.approx(c["cycles"], rel=1e-12)
+
+    def synch():
+        L = [np.float64(v) for v in (100, 10, 0, 0, 1, 1, 128, 4)]
+        Ls = list(L)
+        Ls[3] = np.float64(50)
+        assert float(mc.cycles(L, hw, 1, 1, 148, 1)[0]) == float(mc.cycles(Ls, hw, 1, 1, 148, 1)[0])
+        c0 = float(mc.cycles(L, hw, 8, 2, 148, 1)[0])
+        c1 = float(mc.cycles(Ls, hw, 8, 2, 148, 1)[0])
+        Ls[3] = np.float64(100)
+        c2 = float(mc.cycles(Ls, hw, 8, 2, 148, 1)[0])
+        assert c2 - c0 == pytest.approx(2 * (c1 - c0), rel=1e-12)
+
+    def rep():
+        rng = np.random.default_rng(3)
+        for _ in range(200):
+            L = [np.float64(v) for v in (
+                rng.uniform(1, 500), rng.uniform(1, 30), rng.uniform(0, 8), rng.uniform(0, 4),
+                rng.uniform(1, 5), rng.uniform(1, 32), rng.uniform(32, 512), rng.uniform(1, 9))]
+            W = int(rng.integers(1, 65))
+            e1, b1, _ = mc.cycles(L, hw, W, 2, 148, 1)
+            e5, b5, _ = mc.cycles(L, hw, W, 2, 148, 5)
+            assert b1 == b5 and float(e5) == pytest.approx(5 * float(e1), rel=1e-12)
+            assert float(e1) > 0
+
+    return [n for n, fn in (("hand", hand), ("synch", synch), ("rep", rep)) if _fails(fn)]
+
+
+# (original text, planted mistake)
+OCCUPANCY_MUTATIONS = [
+    ("if T * Bm <= 32 * Wm and R * T * Bm <= Rm and Z * Bm <= Zm:",
+     "if T * Bm <= 32 * Wm and R * Bm <= Rm and Z * Bm <= Zm:"),
+    ("return (32 * Wm) // T", "return Wm // T"),
+    ("return Rm // (R * T)", "return Rm // R"),
+    ("return Zm // Z", "return Zm // (Z * T)"),
+    ('return min((B_active * T) // 32, hw["max_warps_per_sm"])',
+     'return max((B_active * T) // 32, hw["max_warps_per_sm"])'),
+    ('if T > hw["max_threads_per_block"] or T <= 0:',
+     'if T >= hw["max_threads_per_block"] or T <= 0:'),
+]
+MWPCWP_MUTATIONS = [
+    ("mem_l_uncoal = mem_ld + (uncoal_mw - 1.0) * dep_u",
+     "mem_l_uncoal = mem_ld + uncoal_mw * dep_u"),
+    ("mem_l = mem_l_uncoal * w_u + mem_l_coal * w_c",
+     "mem_l = mem_l_uncoal * w_c + mem_l_coal * w_u"),
+    ("departure = dep_u * uncoal_mw * w_u + dep_c * coal_mw * w_c",
+     "departure = dep_u * w_u + dep_c * w_c"),
+    ("mwp = np.minimum(np.minimum(mwp_nobw, mwp_peakbw), Nw)",
+     "mwp = np.minimum(mwp_nobw, Nw)"),
+    ('mwp_peakbw = hw["mem_bandwidth"] / (bw_per_warp * active_sms)',
+     'mwp_peakbw = hw["mem_bandwidth"] / bw_per_warp'),
+    ("comp_cycles = issue * (comp + coal + uncoal)", "comp_cycles = issue * comp"),
+    ("cwp = np.minimum(cwp_full, Nw)", "cwp = cwp_full"),
+    ("c4 = comp_cycles > mem_cycles", "c4 = comp_cycles < mem_cycles"),
+    ("branch = np.where(c1 & c2, 1, np.where(c3 | c4, 2, 3))",
+     "branch = np.where(c1 | c2, 1, np.where(c3 | c4, 2, 3))"),
+    ("e1 = (mem_cycles + comp_cycles + comp_cycles / mem_insts * (mwp - 1.0)) * rep",
+     "e1 = (mem_cycles + comp_cycles + comp_cycles / mem_insts * (mwp + 1.0)) * rep"),
+    ("e2 = (mem_cycles * Nw / mwp + comp_cycles / mem_insts * (mwp - 1.0)) * rep",
+     "e2 = (mem_cycles * mwp / Nw + comp_cycles / mem_insts * (mwp - 1.0)) * rep"),
+    ("e3 = (mem_l + comp_cycles * Nw) * rep", "e3 = (mem_l + comp_cycles) * rep"),
+    ("e = e + departure * (mwp - 1.0) * synch * Bact * rep",
+     "e = e + departure * (mwp - 1.0) * synch * Bact"),
+]
+
+
+def test_model_pins_pass_on_the_oracle():
+    assert _occupancy_pin_failures(occupancy) == []
+    assert _mwpcwp_pin_failures(mwpcwp) == []
+
+
+@pytest.mark.parametrize("orig,planted", OCCUPANCY_MUTATIONS)
+def test_occupancy_pins_catch_planted_mistakes(orig, planted):
+    assert _occupancy_pin_failures(_planted_module(occupancy, orig, planted)), planted
+
+
+@pytest.mark.parametrize("orig,planted", MWPCWP_MUTATIONS)
+def test_mwpcwp_pins_catch_planted_mistakes(orig, planted):
+    assert _mwpcwp_pin_failures(_planted_module(mwpcwp, orig, planted)), planted
