@@ -1,9 +1,15 @@
 """Pins of the surrogate network's oracle: analytic gradients against central
 finite differences (FP64), GELU against its defining formula's limits and
-derivative, AdamW's first step against its closed form."""
+derivative and against the exact form z Phi(z) it approximates, AdamW's first
+step against its closed form.  A mutation test reruns these pins on private
+copies of ``oracle.mlp`` with one plausible mistake planted at a time."""
 import math
+import os
+import sys
+import types
 
 import numpy as np
+import pytest
 
 from oracle import mlp
 
@@ -46,6 +52,15 @@ def test_gelu_limits_and_derivative():
     fd = (mlp.gelu(z + h) - mlp.gelu(z - h)) / (2 * h)
     assert np.allclose(fd, mlp.gelu_grad(z), atol=1e-8)
     assert mlp.gelu_grad(np.array([0.0]))[0] == 0.5
+
+
+def test_gelu_is_near_the_exact_form():
+    # the tanh form approximates z Phi(z) (Phi the standard normal CDF, here
+    # from math.erf): within 4.8e-4 everywhere on [-8, 8]; a wrong constant
+    # (sqrt(1/pi) or 2/pi for sqrt(2/pi), no cubic term) misses by 0.03-0.1
+    z = np.linspace(-8.0, 8.0, 3201)
+    exact = np.array([v * 0.5 * (1.0 + math.erf(v / math.sqrt(2.0))) for v in z])
+    assert np.max(np.abs(mlp.gelu(z) - exact)) <= 5e-4
 
 
 def test_adamw_first_step_closed_form():
@@ -135,3 +150,60 @@ def test_per_query_head_masked_loss():
     lr_, gr = mlp.loss_and_grads(p1, feat, coef, t1[:, 0])
     assert np.isclose(lq, lr_, rtol=1e-14)
     assert np.allclose(mlp.pack(gq, n_coef, 1), mlp.pack(gr, n_coef, 0), rtol=1e-12, atol=1e-15)
+
+
+# --- planted mistakes ------------------------------------------------------------
+
+# (original text in oracle/mlp.py, planted mistake)
+MLP_MUTATIONS = [
+    ("C_GELU = math.sqrt(2.0 / math.pi)", "C_GELU = math.sqrt(1.0 / math.pi)"),
+    ("    return 0.5 * z * (1.0 + np.tanh(C_GELU * (z + 0.044715 * z ** 3)))",
+     "    return 0.5 * z * (1.0 + np.tanh(C_GELU * (z + 0.04715 * z ** 3)))"),
+    ("    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * C_GELU * (1.0 + 3 * 0.044715 * z * z)",
+     "    return 0.5 * (1.0 + t) + 0.5 * z * (1.0 - t * t) * C_GELU"),
+    ("    a2 = gelu(z2)", "    a2 = z2"),
+    ("    dz2 = (dz3 @ p[\"W3\"]) * gelu_grad(z2)", "    dz2 = (dz3 @ p[\"W3\"].T) * gelu_grad(z2)"),
+    ("    demb = (dz1 @ p[\"W1\"])[:, FEAT:]", "    demb = (dz1 @ p[\"W1\"])[:, :EMB]"),
+    ("        dpred = 2.0 * r / n", "        dpred = r / n"),
+    ("        loss = float(np.sum(r * r) / count)", "        loss = float(np.sum(r * r) / r.size)"),
+    ("        r = np.where(mask, pred - np.where(mask, target, 0.0), 0.0)",
+     "        r = np.where(mask, pred - np.where(mask, target, 0.0), pred)"),
+    ("    mh = m / (1 - beta1 ** step)", "    mh = m"),
+    ("    param = param - lr * (mh / (np.sqrt(vh) + eps) + wd * param)",
+     "    param = param - lr * (mh / (np.sqrt(vh) + eps) - wd * param)"),
+    ("    f[:, 0] = np.log2(N) / 23.0", "    f[:, 0] = np.log2(N) / 24.0"),
+]
+
+PINS = [test_gradients_match_finite_differences, test_gelu_limits_and_derivative,
+        test_gelu_is_near_the_exact_form, test_adamw_first_step_closed_form,
+        test_parameter_layout, test_features,
+        test_per_query_head_gradients_match_finite_differences,
+        test_per_query_head_masked_loss]
+
+
+def _pins_failing_on(module, monkeypatch):
+    """Names of the pins above that fail with ``module`` in place of oracle.mlp."""
+    monkeypatch.setattr(sys.modules[__name__], "mlp", module)
+    failed = []
+    for pin in PINS:
+        try:
+            with np.errstate(all="ignore"):
+                pin()
+        except Exception:  # an assertion or a crash: the pin noticed
+            failed.append(pin.__name__)
+    return failed
+
+
+def test_mlp_pins_pass_on_the_oracle(monkeypatch):
+    assert _pins_failing_on(mlp, monkeypatch) == []
+
+
+@pytest.mark.parametrize("orig,planted", MLP_MUTATIONS)
+def test_mlp_pins_catch_planted_mistakes(orig, planted, monkeypatch):
+    path = mlp.__file__
+    src = open(path).read()
+    assert src.count(orig) == 1, f"{os.path.basename(path)} no longer holds {orig!r} once"
+    mod = types.ModuleType("oracle._planted_mlp")
+    mod.__package__ = "oracle"
+    exec(compile(src.replace(orig, planted), path + " (planted)", "exec"), mod.__dict__)
+    assert _pins_failing_on(mod, monkeypatch), f"no pin notices {planted!r}"
